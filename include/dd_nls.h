@@ -1,0 +1,159 @@
+/*
+ * dd_nls -- optimized Schwarz time stepping for the 2D nonlinear Schroedinger and
+ * Gross-Pitaevskii equations on one GPU (sm_103a).
+ *
+ * Method: C. Besse, F. Xing, "Domain decomposition algorithms for the two dimensional
+ * nonlinear Schroedinger equation and simulation of Bose-Einstein condensates",
+ * arXiv:1603.05110.  Section / equation labels below are the paper's.
+ *
+ * Problem (eq. Sch, BC): on Omega = (xl,xr) x (yb,yu),
+ *     i u_t + lap * Lap u + V(x,y) u + kappa |u|^2 u = 0,
+ * homogeneous Neumann on y = yb, yu and the transmission operator S-bar (Robin -ip,
+ * eq. TCSRobin, or S_pade^m, eq. TCS) on x = xl, xr (or Neumann there, see `bc`).
+ * The GPE of eq. (GPE_Trans) is this form with lap = 1/2, V = -V_trap, kappa = -beta.
+ * Time: the midpoint scheme of eq. (CNS); one step solves L_x v = (2i/dt) u_{n-1} for
+ * v = (u_n + u_{n-1})/2 and commits u_n = 2v - u_{n-1}.
+ * Space: Q1 finite elements on a uniform mesh of nx x ny cells (Sec. 2.2).
+ * Domain decomposition: n_strips equal x-strips without overlap (Sec. 2.1); the interface
+ * vector g = (r_1, l_2, r_2, ..., l_N) (Sec. 2.3) is iterated by the classical algorithm
+ * (eq. algo_d) or the preconditioned algorithm (eq. algo_pd, P = I - L_h of eq. Lmpi).
+ *
+ * Conventions (all entry points):
+ *  - Complex arrays are interleaved (re, im) doubles.
+ *  - A nodal field is (ny+1) rows of (nx+1) nodes, x fastest: element (iy, ix) at
+ *    index iy*(nx+1) + ix.
+ *  - An interface vector g is 2*(n_strips-1) traces of ny+1 nodes in the order
+ *    (r_1, l_2, r_2, l_3, ..., r_{N-1}, l_N) of Sec. 2.3, i.e. trace 2i is the right
+ *    datum of strip i and trace 2i+1 the left datum of strip i+1 (0-based strips).
+ *  - ptr_kind says whether caller pointers are host (DD_NLS_PTR_HOST, any pageable or
+ *    pinned memory) or device (DD_NLS_PTR_DEVICE) memory.  Pointers are only used during
+ *    the call; the library keeps no reference to caller memory.
+ *  - The handle owns all device memory it uses (allocated in dd_nls_create, released in
+ *    dd_nls_destroy).  All GPU work is issued on the stream given to dd_nls_create
+ *    (NULL: the legacy default stream); calls return after that work has finished.
+ *  - Errors are returned as dd_nls_status codes; the GPU is never trapped.  After an
+ *    error, dd_nls_last_error() describes it.  A handle is not thread safe.
+ */
+#ifndef DD_NLS_H
+#define DD_NLS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dd_nls dd_nls;   /* opaque, library-owned */
+
+typedef enum {
+    DD_NLS_OK = 0,
+    DD_NLS_EINVAL = 1,       /* invalid argument or parameter combination */
+    DD_NLS_ENOMEM = 2,       /* device or host allocation failed */
+    DD_NLS_ECUDA = 3,        /* a CUDA runtime call failed */
+    DD_NLS_ENOCONV = 4,      /* an iteration hit its cap; the step is not committed */
+    DD_NLS_ENONFINITE = 5,   /* NaN/Inf in an input or an iterate; the step is not committed */
+    DD_NLS_ETIMEOUT = 6,     /* a bounded device-side wait gave up; the step is not committed */
+    DD_NLS_EBREAKDOWN = 7    /* Krylov breakdown (p^T A p = 0); the step is not committed */
+} dd_nls_status;
+
+enum { DD_NLS_TC_ROBIN = 0, DD_NLS_TC_PADE = 1 };          /* eq. TCSRobin / eq. TCS */
+enum { DD_NLS_BC_SAME = 0, DD_NLS_BC_NEUMANN = 1 };        /* physical x-edges */
+enum { DD_NLS_CLASSICAL = 0, DD_NLS_PRECONDITIONED = 1 };  /* eq. algo_d / eq. algo_pd */
+enum { DD_NLS_FP64 = 0, DD_NLS_FP32_INNER = 1 };           /* inner Krylov precision */
+enum { DD_NLS_GUESS_ZERO = 0, DD_NLS_GUESS_PREVIOUS = 1 }; /* g_n^0 (Sec. 5) */
+enum { DD_NLS_PTR_HOST = 0, DD_NLS_PTR_DEVICE = 1 };
+
+typedef struct {
+    /* Omega, mesh and strips (Sec. 2.1-2.2); nx must be a multiple of n_strips */
+    double xl, xr, yb, yu;
+    int nx, ny, n_strips;
+    /* equation (Sch) and time step (CNS) */
+    double dt, lap, kappa;
+    /* transmission operator S-bar: Robin parameter p, or Pade order m and rotation theta */
+    int tc;
+    double p;
+    int pade_m;
+    double pade_theta;
+    int bc;           /* DD_NLS_BC_SAME: S-bar with zero data on x = xl, xr; or Neumann */
+    int algorithm;    /* DD_NLS_CLASSICAL or DD_NLS_PRECONDITIONED */
+    int precision;    /* DD_NLS_FP64, or DD_NLS_FP32_INNER: FP32 Krylov + FP64 residual */
+    int guess;        /* interface guess for each step when dd_nls_step is called */
+    /* stopping tests */
+    double tol;          /* ||R(g)-g|| <= tol*||R(g)|| (or <= tol if tol_absolute) */
+    int tol_absolute;
+    int max_schwarz;
+    double nl_tol;       /* strip solves: ||b - A(zeta) zeta|| <= nl_tol * ||b|| */
+    int max_nl;
+    double inner_tol;    /* Krylov: residual reduction per correction */
+    int max_inner;
+    double gmres_tol;    /* P x = y (eq. algo_pd): relative residual */
+    int gmres_restart;
+    int gmres_max;
+} dd_nls_params;
+
+typedef struct {
+    int steps;                    /* steps committed by this call */
+    int schwarz_iterations;       /* Schwarz iterations, summed over the call's steps */
+    int last_schwarz_iterations;  /* of the last step */
+    long long nl_iterations;      /* strip nonlinear iterations, summed over strips */
+    long long krylov_iterations;  /* inner Krylov iterations, summed over strips */
+    long long gmres_iterations;   /* GMRES iterations on P x = y */
+    double residual;              /* last relative interface residual ||R(g)-g||/||R(g)|| */
+    double residual_abs;          /* last absolute interface residual ||R(g)-g|| */
+    double mass;                  /* u_n^H M u_n of the last committed step */
+    double energy;                /* u^H S u - u^H M_W u - (kappa/2lap) sum w|u|^4, scaled by 1/lap */
+    double setup_ms;              /* L_h construction (preconditioned), at create */
+} dd_nls_stats;
+
+/* Device time of the library's kernels, accumulated while profiling is on. */
+typedef struct {
+    double strip_solve_ms;        /* the batched strip solver (Krylov + stencil) */
+    long long strip_solve_launches;
+    double strip_solve_bytes;     /* algorithmic bytes moved by those launches */
+    double strip_solve_flops;
+    double interface_ms;          /* traces, residuals, GMRES, L_h products */
+    double other_ms;              /* right sides, commit, diagnostics */
+} dd_nls_profile;
+
+/* Fill *p with defaults: NLS (lap=1, kappa=1), Robin p=1, classical, FP64, previous-step
+ * guess, tol 1e-10, nl_tol 1e-13, inner_tol 1e-6, GMRES restart 30 / tol 1e-10. */
+void dd_nls_default_params(dd_nls_params* p);
+
+/* Create a solver.  V: real nodal potential (ny+1)*(nx+1) in the sign of eq. (Sch), or
+ * NULL for V = 0.  u0: complex nodal initial datum.  stream: a cudaStream_t or NULL.
+ * Builds L_h (eq. Lmpi) when algorithm is PRECONDITIONED (2(ny+1) strip solves, Sec. 4.2).
+ * Errors: EINVAL (bad sizes / parameters / NULL out or u0), ENOMEM, ECUDA. */
+int dd_nls_create(const dd_nls_params* p, const double* V, const double* u0, int ptr_kind,
+                  void* stream, dd_nls** out);
+
+/* Advance nsteps time steps (eq. CNS), each by the Schwarz iteration to `tol`.
+ * u_out (nullable): receives u_n after the last step.  stats (nullable).
+ * A step whose iteration fails is not committed and the error is returned. */
+int dd_nls_step(dd_nls* h, int nsteps, double* u_out, int ptr_kind, dd_nls_stats* stats);
+
+/* Run the Schwarz iteration of the current step (u_{n-1} = current state) from the
+ * interface guess g0 (nullable: the `guess` policy) without committing; g_out (nullable)
+ * receives the converged R(g); v_out (nullable) the nodal v = (u_n + u_{n-1})/2. */
+int dd_nls_solve_interface(dd_nls* h, const double* g0, double* g_out, double* v_out,
+                           int ptr_kind, dd_nls_stats* stats);
+
+/* Checkpoint: u (complex nodal, nullable) and g (interface vector used as the previous-
+ * step guess, nullable).  set_state also sets the step counter to `step`. */
+int dd_nls_get_state(dd_nls* h, double* u, double* g, int* step, int ptr_kind);
+int dd_nls_set_state(dd_nls* h, const double* u, const double* g, int step, int ptr_kind);
+
+/* Copy the L_h blocks X^{j,1..4} (Props 3.1/3.2) of strip j into x (4 row-major
+ * (ny+1)x(ny+1) complex matrices, X1 X2 X3 X4).  EINVAL if not PRECONDITIONED. */
+int dd_nls_get_blocks(dd_nls* h, int strip, double* x, int ptr_kind);
+
+int dd_nls_set_profiling(dd_nls* h, int on);
+int dd_nls_get_profile(dd_nls* h, dd_nls_profile* prof);
+
+/* Release everything the handle owns.  NULL is ignored. */
+void dd_nls_destroy(dd_nls* h);
+
+/* Text of the last error on this handle (or of the last failed create when h is NULL). */
+const char* dd_nls_last_error(const dd_nls* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DD_NLS_H */

@@ -1,0 +1,233 @@
+"""Thin ctypes binding of the dd_nls C-ABI (include/dd_nls.h): argument marshalling only.
+
+Every step of the method runs in the CUDA library; this module only converts arguments.
+Arrays may be numpy arrays (host memory) or CUDA torch tensors (device memory); the
+pointer kind is passed to the library accordingly.  If the compiled library is missing the
+import of a Solver fails loudly: there is no CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libddnls.so")
+
+TC_ROBIN, TC_PADE = 0, 1
+BC_SAME, BC_NEUMANN = 0, 1
+CLASSICAL, PRECONDITIONED = 0, 1
+FP64, FP32_INNER = 0, 1
+GUESS_ZERO, GUESS_PREVIOUS = 0, 1
+PTR_HOST, PTR_DEVICE = 0, 1
+
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "ENONFINITE",
+          6: "ETIMEOUT", 7: "EBREAKDOWN"}
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("xl", ctypes.c_double), ("xr", ctypes.c_double), ("yb", ctypes.c_double), ("yu", ctypes.c_double),
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("n_strips", ctypes.c_int),
+        ("dt", ctypes.c_double), ("lap", ctypes.c_double), ("kappa", ctypes.c_double),
+        ("tc", ctypes.c_int), ("p", ctypes.c_double), ("pade_m", ctypes.c_int), ("pade_theta", ctypes.c_double),
+        ("bc", ctypes.c_int), ("algorithm", ctypes.c_int), ("precision", ctypes.c_int), ("guess", ctypes.c_int),
+        ("tol", ctypes.c_double), ("tol_absolute", ctypes.c_int), ("max_schwarz", ctypes.c_int),
+        ("nl_tol", ctypes.c_double), ("max_nl", ctypes.c_int),
+        ("inner_tol", ctypes.c_double), ("max_inner", ctypes.c_int),
+        ("gmres_tol", ctypes.c_double), ("gmres_restart", ctypes.c_int), ("gmres_max", ctypes.c_int),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("steps", ctypes.c_int), ("schwarz_iterations", ctypes.c_int), ("last_schwarz_iterations", ctypes.c_int),
+        ("nl_iterations", ctypes.c_longlong), ("krylov_iterations", ctypes.c_longlong),
+        ("gmres_iterations", ctypes.c_longlong),
+        ("residual", ctypes.c_double), ("residual_abs", ctypes.c_double),
+        ("mass", ctypes.c_double), ("energy", ctypes.c_double), ("setup_ms", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [
+        ("strip_solve_ms", ctypes.c_double), ("strip_solve_launches", ctypes.c_longlong),
+        ("strip_solve_bytes", ctypes.c_double), ("strip_solve_flops", ctypes.c_double),
+        ("interface_ms", ctypes.c_double), ("other_ms", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+SYMBOLS = ["dd_nls_default_params", "dd_nls_create", "dd_nls_step", "dd_nls_solve_interface",
+           "dd_nls_get_state", "dd_nls_set_state", "dd_nls_get_blocks", "dd_nls_set_profiling",
+           "dd_nls_get_profile", "dd_nls_destroy", "dd_nls_last_error"]
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load the compiled library (build it with paper_1603_05110_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"dd_nls CUDA library not built: {path} is missing "
+                           "(run `python -c 'import __graft_entry__ as g; g.build()'`)")
+    lib = ctypes.CDLL(path)
+    vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int
+    lib.dd_nls_default_params.argtypes = [ctypes.POINTER(Params)]
+    lib.dd_nls_default_params.restype = None
+    lib.dd_nls_create.argtypes = [ctypes.POINTER(Params), vp, vp, ip, vp, ctypes.POINTER(vp)]
+    lib.dd_nls_create.restype = ip
+    lib.dd_nls_step.argtypes = [vp, ip, vp, ip, ctypes.POINTER(Stats)]
+    lib.dd_nls_step.restype = ip
+    lib.dd_nls_solve_interface.argtypes = [vp, vp, vp, vp, ip, ctypes.POINTER(Stats)]
+    lib.dd_nls_solve_interface.restype = ip
+    lib.dd_nls_get_state.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_int), ip]
+    lib.dd_nls_get_state.restype = ip
+    lib.dd_nls_set_state.argtypes = [vp, vp, vp, ip, ip]
+    lib.dd_nls_set_state.restype = ip
+    lib.dd_nls_get_blocks.argtypes = [vp, ip, vp, ip]
+    lib.dd_nls_get_blocks.restype = ip
+    lib.dd_nls_set_profiling.argtypes = [vp, ip]
+    lib.dd_nls_set_profiling.restype = ip
+    lib.dd_nls_get_profile.argtypes = [vp, ctypes.POINTER(Profile)]
+    lib.dd_nls_get_profile.restype = ip
+    lib.dd_nls_destroy.argtypes = [vp]
+    lib.dd_nls_destroy.restype = None
+    lib.dd_nls_last_error.argtypes = [vp]
+    lib.dd_nls_last_error.restype = ctypes.c_char_p
+    _ = dp
+    _lib = lib
+    return lib
+
+
+class DDNLSError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def default_params(**kw):
+    lib = load()
+    p = Params()
+    lib.dd_nls_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _ptr(a, writable=False):
+    """(pointer, kind) of a numpy array or torch tensor, or (None, None)."""
+    if a is None:
+        return None, None
+    if hasattr(a, "data_ptr"):                      # torch tensor
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), (PTR_DEVICE if a.is_cuda else PTR_HOST)
+    if not isinstance(a, np.ndarray) or not a.flags.c_contiguous:
+        raise ValueError("expected a C-contiguous numpy array or a torch tensor")
+    if writable and not a.flags.writeable:
+        raise ValueError("output array is read-only")
+    return a.ctypes.data, PTR_HOST
+
+
+def _kind(*kinds):
+    ks = {k for k in kinds if k is not None}
+    if len(ks) > 1:
+        raise ValueError("mix of host and device arrays in one call")
+    return ks.pop() if ks else PTR_HOST
+
+
+class Solver:
+    """A dd_nls handle.  ``params``: a Params or a dict of its fields."""
+
+    def __init__(self, params, u0, V=None, stream=None):
+        self.lib = load()
+        if isinstance(params, dict):
+            params = default_params(**params)
+        self.params = params
+        if isinstance(u0, np.ndarray):
+            u0 = np.ascontiguousarray(u0, dtype=np.complex128)
+        if isinstance(V, np.ndarray):
+            V = np.ascontiguousarray(V, dtype=np.float64)
+        pu, ku = _ptr(u0)
+        pv, kv = _ptr(V)
+        kind = _kind(ku, kv)
+        self.shape = (params.ny + 1, params.nx + 1)
+        self.n_traces = 2 * (params.n_strips - 1)
+        s = None
+        if stream is not None:
+            s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        h = ctypes.c_void_p()
+        rc = self.lib.dd_nls_create(ctypes.byref(params), pv, pu, kind, s, ctypes.byref(h))
+        if rc != 0:
+            raise DDNLSError(rc, self.lib.dd_nls_last_error(None).decode())
+        self.h = h
+
+    def _check(self, rc):
+        if rc != 0:
+            raise DDNLSError(rc, self.lib.dd_nls_last_error(self.h).decode())
+
+    def step(self, nsteps=1, u_out=None):
+        st = Stats()
+        pu, ku = _ptr(u_out, writable=True)
+        self._check(self.lib.dd_nls_step(self.h, nsteps, pu, _kind(ku), ctypes.byref(st)))
+        return st.as_dict()
+
+    def solve_interface(self, g0=None, g_out=None, v_out=None):
+        st = Stats()
+        p0, k0 = _ptr(g0)
+        pg, kg = _ptr(g_out, writable=True)
+        pv, kv = _ptr(v_out, writable=True)
+        self._check(self.lib.dd_nls_solve_interface(self.h, p0, pg, pv, _kind(k0, kg, kv), ctypes.byref(st)))
+        return st.as_dict()
+
+    def get_state(self, u=None, g=None):
+        pu, ku = _ptr(u, writable=True)
+        pg, kg = _ptr(g, writable=True)
+        n = ctypes.c_int()
+        self._check(self.lib.dd_nls_get_state(self.h, pu, pg, ctypes.byref(n), _kind(ku, kg)))
+        return n.value
+
+    def set_state(self, u=None, g=None, step=0):
+        pu, ku = _ptr(u)
+        pg, kg = _ptr(g)
+        self._check(self.lib.dd_nls_set_state(self.h, pu, pg, step, _kind(ku, kg)))
+
+    def blocks(self, strip):
+        ne = self.params.ny + 1
+        x = np.zeros((4, ne, ne), np.complex128)
+        self._check(self.lib.dd_nls_get_blocks(self.h, strip, x.ctypes.data, PTR_HOST))
+        return x
+
+    def set_profiling(self, on=True):
+        self._check(self.lib.dd_nls_set_profiling(self.h, 1 if on else 0))
+
+    def profile(self):
+        p = Profile()
+        self._check(self.lib.dd_nls_get_profile(self.h, ctypes.byref(p)))
+        return p.as_dict()
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dd_nls_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

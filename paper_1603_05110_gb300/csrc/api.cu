@@ -1,0 +1,697 @@
+// Host runtime and C-ABI of dd_nls (see include/dd_nls.h).
+//
+// One handle owns the device state of one problem: u_{n-1} and the strip fields in the
+// strip layout of common.cuh, the interface vectors, the inner Krylov vectors of the batched
+// strip solver, and (preconditioned algorithm) the L_h blocks and the GMRES basis.  A time
+// step (eq. CNS) is: right side (2i/dt) M u_{n-1}; Schwarz iterations, each one persistent
+// launch of the strip solver followed by the flux update of eq. (fluxlr) and the interface
+// residual; for eq. (algo_pd) a GMRES solve of (I - L_h) x = g - R(g); then the commit
+// u_n = 2v - u_{n-1} and the diagnostics.  The host reads a few scalars per Schwarz
+// iteration to decide convergence.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/dd_nls.h"
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace ddnls;
+using cplx = std::complex<double>;
+
+static std::string g_create_error;
+
+struct dd_nls {
+    dd_nls_params P{};
+    Geom G{};
+    cudaStream_t s = nullptr;
+    bool fp32 = false;
+    long long nfield = 0;   // elements of one strip field (all strips)
+    long long nI = 0;       // elements of one interface vector (padded)
+    int bps = 1;
+    int NB = 1;             // blocks of one strip-solver launch
+    // device state
+    double2 *u = nullptr, *zeta = nullptr, *rhs0 = nullptr, *gA = nullptr, *gB = nullptr, *gconv = nullptr;
+    double* Wn = nullptr;
+    void *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *cT = nullptr;
+    double* part = nullptr;
+    unsigned* bar = nullptr;
+    int* status = nullptr;
+    int* nl_its = nullptr;
+    long long* kry = nullptr;
+    double* nl_res = nullptr;
+    int* err = nullptr;
+    double* red = nullptr;           // small device results
+    double2* stage = nullptr;        // nodal IO staging (global layout)
+    // preconditioner
+    int ntypes = 0;
+    double2* X64 = nullptr;
+    float2* X32 = nullptr;
+    int* btype = nullptr;
+    std::vector<int> btype_h;
+    double2 *V = nullptr, *w = nullptr, *tmp = nullptr, *hdev = nullptr, *xs = nullptr;
+    double* scratch = nullptr;
+    // host mirrors
+    double* hred = nullptr;          // pinned
+    std::vector<int> h_status, h_nl;
+    std::vector<long long> h_kry;
+    int step = 0;
+    bool have_prev = false;
+    std::string error;
+    bool prof = false;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    dd_nls_profile profile{};
+    double setup_ms = 0.0;
+};
+
+#define CK(call)                                                                           \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) return fail(h, DD_NLS_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+static int fail(dd_nls* h, int code, const std::string& msg) {
+    if (h) h->error = msg; else g_create_error = msg;
+    return code;
+}
+
+extern "C" void dd_nls_default_params(dd_nls_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->xl = -1; p->xr = 1; p->yb = -1; p->yu = 1;
+    p->nx = 32; p->ny = 32; p->n_strips = 2;
+    p->dt = 0.01; p->lap = 1.0; p->kappa = 1.0;
+    p->tc = DD_NLS_TC_ROBIN; p->p = 1.0; p->pade_m = 4; p->pade_theta = M_PI / 4;
+    p->bc = DD_NLS_BC_SAME;
+    p->algorithm = DD_NLS_CLASSICAL;
+    p->precision = DD_NLS_FP64;
+    p->guess = DD_NLS_GUESS_PREVIOUS;
+    p->tol = 1e-10; p->tol_absolute = 0; p->max_schwarz = 500;
+    p->nl_tol = 1e-13; p->max_nl = 60;
+    p->inner_tol = 1e-6; p->max_inner = 2000;
+    p->gmres_tol = 1e-10; p->gmres_restart = 30; p->gmres_max = 300;
+}
+
+template <typename T> static cudaError_t dalloc(T** ptr, size_t n) {
+    cudaError_t e = cudaMalloc((void**)ptr, std::max<size_t>(n, 1) * sizeof(T));
+    if (e == cudaSuccess) e = cudaMemset(*ptr, 0, std::max<size_t>(n, 1) * sizeof(T));
+    return e;
+}
+
+static void release(dd_nls* h) {
+    void* ptrs[] = {h->u, h->zeta, h->rhs0, h->gA, h->gB, h->gconv, h->Wn, h->x, h->r, h->z, h->p, h->q, h->cT,
+                    h->part, h->bar, h->status, h->nl_its, h->kry, h->nl_res, h->err, h->red, h->stage,
+                    h->X64, h->X32, h->btype, h->V, h->w, h->tmp, h->hdev, h->xs, h->scratch};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (h->hred) cudaFreeHost(h->hred);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+}
+
+// ------------------------------------------------------------------------ IO
+static int upload_nodal(dd_nls* h, const double* src, int ptr_kind, double2* strips) {
+    const size_t bytes = (size_t)(h->G.nx + 1) * h->G.nyn * sizeof(double2);
+    CK(cudaMemcpyAsync(h->stage, src, bytes, ptr_kind == DD_NLS_PTR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->s));
+    CK(launch_scatter_u(h->G, h->stage, strips, h->s));
+    return DD_NLS_OK;
+}
+static int download_nodal(dd_nls* h, const double2* strips, double* dst, int ptr_kind) {
+    const size_t bytes = (size_t)(h->G.nx + 1) * h->G.nyn * sizeof(double2);
+    CK(launch_gather_u(h->G, strips, h->stage, h->s));
+    CK(cudaMemcpyAsync(dst, h->stage, bytes, ptr_kind == DD_NLS_PTR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->s));
+    return DD_NLS_OK;
+}
+// interface vectors cross the ABI unpadded: 2(N-1) traces of nyn nodes
+static int upload_g(dd_nls* h, const double* src, int ptr_kind, double2* dst) {
+    const int ntr = 2 * (h->G.N - 1);
+    if (ntr == 0) return DD_NLS_OK;
+    CK(cudaMemcpy2DAsync(dst, h->G.P * sizeof(double2), src, h->G.nyn * sizeof(double2), h->G.nyn * sizeof(double2), ntr,
+                         ptr_kind == DD_NLS_PTR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->s));
+    return DD_NLS_OK;
+}
+static int download_g(dd_nls* h, const double2* src, double* dst, int ptr_kind) {
+    const int ntr = 2 * (h->G.N - 1);
+    if (ntr == 0) return DD_NLS_OK;
+    CK(cudaMemcpy2DAsync(dst, h->G.nyn * sizeof(double2), src, h->G.P * sizeof(double2), h->G.nyn * sizeof(double2), ntr,
+                         ptr_kind == DD_NLS_PTR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->s));
+    return DD_NLS_OK;
+}
+
+// --------------------------------------------------------------- strip solves
+static int strip_solve(dd_nls* h, StripSolveArgs& a, int nstrips, dd_nls_stats* st, bool count) {
+    CK(cudaMemsetAsync(h->bar, 0, sizeof(unsigned) * nstrips, h->s));
+    CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->s));
+    if (h->prof) CK(cudaEventRecord(h->ev0, h->s));
+    CK(launch_strip_solve(a, nstrips, h->fp32, h->s));
+    if (h->prof) CK(cudaEventRecord(h->ev1, h->s));
+    CK(cudaMemcpyAsync(h->h_status.data(), h->status, sizeof(int) * nstrips, cudaMemcpyDeviceToHost, h->s));
+    CK(cudaMemcpyAsync(h->h_nl.data(), h->nl_its, sizeof(int) * nstrips, cudaMemcpyDeviceToHost, h->s));
+    CK(cudaMemcpyAsync(h->h_kry.data(), h->kry, sizeof(long long) * nstrips, cudaMemcpyDeviceToHost, h->s));
+    CK(cudaMemcpyAsync(h->hred + 8, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    long long nl = 0, kr = 0;
+    double bytes = 0.0, flops = 0.0;
+    const double nodes = (double)h->G.nxs * h->G.nyn;
+    const double s2 = h->fp32 ? 8.0 : 16.0, s1 = h->fp32 ? 4.0 : 8.0;
+    const double bR = 40 + s1 + 5 * s2, bA = 5 * s2 + s1, bB = 7 * s2 + s1, bE = 32 + s2;
+    for (int j = 0; j < nstrips; ++j) {
+        nl += h->h_nl[j];
+        kr += h->h_kry[j];
+        bytes += nodes * ((h->h_nl[j] + 1) * bR + h->h_kry[j] * (bA + bB) + h->h_nl[j] * bE);
+        flops += nodes * ((h->h_nl[j] + 1) * 110.0 + h->h_kry[j] * 150.0);
+    }
+    if (h->prof) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+        h->profile.strip_solve_ms += ms;
+        h->profile.strip_solve_launches += 1;
+        h->profile.strip_solve_bytes += bytes;
+        h->profile.strip_solve_flops += flops;
+    }
+    if (st && count) {
+        st->nl_iterations += nl;
+        st->krylov_iterations += kr;
+    }
+    int errw = 0;
+    std::memcpy(&errw, h->hred + 8, sizeof(int));
+    if (errw) return fail(h, errw, "strip solver: device barrier timed out");
+    for (int j = 0; j < nstrips; ++j)
+        if (h->h_status[j]) {
+            char buf[160];
+            std::snprintf(buf, sizeof buf, "strip solver: strip %d status %d after %d nonlinear / %lld Krylov iterations",
+                          j, h->h_status[j], h->h_nl[j], h->h_kry[j]);
+            return fail(h, h->h_status[j], buf);
+        }
+    return DD_NLS_OK;
+}
+
+static StripSolveArgs base_args(dd_nls* h) {
+    StripSolveArgs a{};
+    a.g = h->G;
+    a.bps = h->bps;
+    a.mode = 0;
+    a.zeta = h->zeta;
+    a.rhs0 = h->rhs0;
+    a.Wn = h->Wn;
+    a.x = h->x; a.r = h->r; a.z = h->z; a.p = h->p; a.q = h->q; a.cT = h->cT;
+    a.nl_tol = h->P.nl_tol;
+    a.inner_tol = h->P.inner_tol;
+    a.inner_floor = 0.1 * h->P.nl_tol;
+    a.max_nl = h->P.max_nl;
+    a.max_inner = h->P.max_inner;
+    a.part = h->part;
+    a.bar = h->bar;
+    a.status = h->status;
+    a.nl_its = h->nl_its;
+    a.kry_its = h->kry;
+    a.nl_res = h->nl_res;
+    a.err = h->err;
+    return a;
+}
+
+// ----------------------------------------------------------------- L_h setup
+// Columns of L_h from free strip solves with unit data (Sec. 4.2): for every strip type
+// (edge kinds), 2(ny+1) independent solves batched as virtual strips of one launch.
+static int build_Lh(dd_nls* h) {
+    const Geom& G = h->G;
+    const int nyn = G.nyn;
+    const long long bs = (long long)nyn * nyn;
+    // strip types
+    std::vector<std::pair<int, int>> types;   // (ltc, rtc)
+    h->btype_h.assign(G.N, 0);
+    for (int j = 0; j < G.N; ++j) {
+        const int l = (j > 0 || G.bc_same) ? 1 : 0, r = (j < G.N - 1 || G.bc_same) ? 1 : 0;
+        auto key = std::make_pair(l, r);
+        auto it = std::find(types.begin(), types.end(), key);
+        if (it == types.end()) { types.push_back(key); h->btype_h[j] = (int)types.size() - 1; }
+        else h->btype_h[j] = (int)(it - types.begin());
+    }
+    h->ntypes = (int)types.size();
+    CK(dalloc(&h->X64, (size_t)h->ntypes * 4 * bs));
+    CK(dalloc(&h->btype, G.N));
+    CK(cudaMemcpy(h->btype, h->btype_h.data(), sizeof(int) * G.N, cudaMemcpyHostToDevice));
+
+    // virtual-strip buffers
+    const int maxb = strip_solve_max_blocks(h->fp32);
+    const long long per_strip = (long long)G.nxs * G.P;
+    const double bytes_per_strip = (double)per_strip * (16 + 5 * (h->fp32 ? 8 : 16) + (h->fp32 ? 4 : 8));
+    int chunk = std::max(1, std::min(maxb, (int)std::min(2.0 * nyn, 6e9 / bytes_per_strip)));
+    StripSolveArgs a = base_args(h);
+    double2* vz = nullptr;
+    void *vx = nullptr, *vr = nullptr, *vzz = nullptr, *vp = nullptr, *vq = nullptr, *vc = nullptr;
+    unsigned* vbar = nullptr;
+    int *vstat = nullptr, *vnl = nullptr;
+    long long* vkry = nullptr;
+    double *vres = nullptr, *vpart = nullptr;
+    const size_t s2 = h->fp32 ? sizeof(float2) : sizeof(double2), s1 = h->fp32 ? sizeof(float) : sizeof(double);
+    int rc = DD_NLS_OK;
+    auto cleanup = [&]() {
+        void* ptrs[] = {vz, vx, vr, vzz, vp, vq, vc, vbar, vstat, vnl, vkry, vres, vpart};
+        for (void* p : ptrs)
+            if (p) cudaFree(p);
+    };
+    cudaError_t e = cudaSuccess;
+    e = e ? e : cudaMalloc(&vz, chunk * per_strip * sizeof(double2));
+    e = e ? e : cudaMalloc(&vx, chunk * per_strip * s2);
+    e = e ? e : cudaMalloc(&vr, chunk * per_strip * s2);
+    e = e ? e : cudaMalloc(&vzz, chunk * per_strip * s2);
+    e = e ? e : cudaMalloc(&vp, chunk * per_strip * s2);
+    e = e ? e : cudaMalloc(&vq, chunk * per_strip * s2);
+    e = e ? e : cudaMalloc(&vc, chunk * per_strip * s1);
+    e = e ? e : cudaMalloc(&vbar, chunk * sizeof(unsigned));
+    e = e ? e : cudaMalloc(&vstat, chunk * sizeof(int));
+    e = e ? e : cudaMalloc(&vnl, chunk * sizeof(int));
+    e = e ? e : cudaMalloc(&vkry, chunk * sizeof(long long));
+    e = e ? e : cudaMalloc(&vres, chunk * sizeof(double));
+    e = e ? e : cudaMalloc(&vpart, (size_t)4 * maxb * 4 * sizeof(double));
+    if (e != cudaSuccess) { cleanup(); return fail(h, DD_NLS_ENOMEM, std::string("L_h setup buffers: ") + cudaGetErrorString(e)); }
+    std::vector<int> hs(chunk), hn(chunk);
+    std::vector<long long> hk(chunk);
+
+    cudaEvent_t t0, t1;
+    cudaEventCreate(&t0);
+    cudaEventCreate(&t1);
+    cudaEventRecord(t0, h->s);
+    for (int t = 0; t < h->ntypes && rc == DD_NLS_OK; ++t) {
+        const int u0 = types[t].first ? 0 : nyn, u1 = types[t].second ? 2 * nyn : nyn;
+        for (int ub = u0; ub < u1 && rc == DD_NLS_OK; ub += chunk) {
+            const int nv = std::min(chunk, u1 - ub);
+            a.bps = std::max(1, maxb / nv);
+            a.mode = 1;
+            a.unit_base = ub;
+            a.unit_ltc = types[t].first;
+            a.unit_rtc = types[t].second;
+            a.zeta = vz; a.rhs0 = nullptr; a.Wn = nullptr; a.gtr = nullptr;
+            a.x = vx; a.r = vr; a.z = vzz; a.p = vp; a.q = vq; a.cT = vc;
+            a.bar = vbar; a.status = vstat; a.nl_its = vnl; a.kry_its = vkry; a.nl_res = vres; a.part = vpart;
+            e = cudaMemsetAsync(vz, 0, nv * per_strip * sizeof(double2), h->s);
+            if (!e) e = cudaMemsetAsync(vbar, 0, nv * sizeof(unsigned), h->s);
+            if (!e) e = cudaMemsetAsync(h->err, 0, sizeof(int), h->s);
+            if (!e) e = launch_strip_solve(a, nv, h->fp32, h->s);
+            if (!e) e = launch_extract_blocks(G, vz, nv, ub, h->X64 + (long long)t * 4 * bs, h->s);
+            if (!e) e = cudaMemcpyAsync(hs.data(), vstat, nv * sizeof(int), cudaMemcpyDeviceToHost, h->s);
+            if (!e) e = cudaStreamSynchronize(h->s);
+            if (e) { rc = fail(h, DD_NLS_ECUDA, std::string("L_h setup: ") + cudaGetErrorString(e)); break; }
+            for (int v = 0; v < nv; ++v)
+                if (hs[v]) { rc = fail(h, hs[v], "L_h setup: free strip solve failed"); break; }
+        }
+    }
+    cudaEventRecord(t1, h->s);
+    cudaEventSynchronize(t1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, t0, t1);
+    h->setup_ms = ms;
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    cleanup();
+    if (rc) return rc;
+    if (h->fp32) {
+        CK(dalloc(&h->X32, (size_t)h->ntypes * 4 * bs));
+        CK(launch_convert_blocks(h->X64, h->X32, (long long)h->ntypes * 4 * bs, h->s));
+        CK(cudaStreamSynchronize(h->s));
+    }
+    // GMRES workspace
+    const int m = std::max(1, h->P.gmres_restart);
+    CK(dalloc(&h->V, (size_t)(m + 1) * h->nI));
+    CK(dalloc(&h->w, (size_t)h->nI));
+    CK(dalloc(&h->tmp, (size_t)h->nI));
+    CK(dalloc(&h->xs, (size_t)h->nI));
+    CK(dalloc(&h->hdev, (size_t)(m + 1)));
+    CK(dalloc(&h->scratch, (size_t)(m + 2) * 256 * 2));
+    return DD_NLS_OK;
+}
+
+// y = (I - L_h) x
+static int apply_P(dd_nls* h, const double2* x, double2* y) {
+    CK(launch_apply_P(h->G, h->fp32 ? (const void*)h->X32 : (const void*)h->X64, h->fp32, h->btype, x, y, nullptr, h->s));
+    return DD_NLS_OK;
+}
+
+// Solve (I - L_h) x = b by restarted GMRES(m) (Sec. 4.2).  Krylov vectors and products live
+// on the device; the (m+1) x m Hessenberg least-squares problem is updated on the host with
+// Givens rotations from the few scalars read back per iteration.
+static int gmres(dd_nls* h, const double2* b, double2* x, long long* its_out) {
+    const long long n = h->nI;
+    const int m = std::max(1, h->P.gmres_restart);
+    double* hn = h->hred;                                   // pinned scratch
+    CK(cudaMemsetAsync(x, 0, n * sizeof(double2), h->s));
+    CK(launch_nrm2(b, n, h->red, h->scratch, h->s));
+    CK(cudaMemcpyAsync(hn, h->red, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    const double bnorm = hn[0];
+    long long its = 0;
+    if (!(bnorm > 0.0)) { *its_out = 0; return std::isfinite(bnorm) ? DD_NLS_OK : fail(h, DD_NLS_ENONFINITE, "GMRES: non-finite right side"); }
+    std::vector<cplx> H((m + 1) * m), cs(m), sn(m), gv(m + 1), hcol(m + 1);
+    bool first = true;
+    while (its < h->P.gmres_max) {
+        // r = b - P x
+        if (first) { CK(launch_copy(h->w, b, n, h->s)); }
+        else { int rc = apply_P(h, x, h->tmp); if (rc) return rc; CK(launch_sub(h->w, b, h->tmp, n, h->s)); }
+        CK(launch_nrm2(h->w, n, h->red, h->scratch, h->s));
+        CK(cudaMemcpyAsync(hn, h->red, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+        CK(cudaStreamSynchronize(h->s));
+        const double beta = hn[0];
+        if (beta <= h->P.gmres_tol * bnorm) break;
+        CK(launch_scale(h->V, h->w, h->red, n, h->s));
+        std::fill(gv.begin(), gv.end(), cplx(0));
+        gv[0] = beta;
+        int k = 0;
+        bool done = false;
+        for (; k < m && its < h->P.gmres_max; ++k) {
+            double2* vk = h->V + (long long)k * n;
+            { int rc = apply_P(h, vk, h->w); if (rc) return rc; }
+            // classical Gram-Schmidt, twice
+            CK(launch_dots(h->V, n, k + 1, h->w, n, h->hdev, h->scratch, h->s));
+            CK(launch_axpy_multi(h->V, n, k + 1, h->hdev, h->w, n, h->s));
+            CK(cudaMemcpyAsync(hn, h->hdev, sizeof(double2) * (k + 1), cudaMemcpyDeviceToHost, h->s));
+            CK(cudaStreamSynchronize(h->s));
+            for (int i = 0; i <= k; ++i) hcol[i] = cplx(hn[2 * i], hn[2 * i + 1]);
+            CK(launch_dots(h->V, n, k + 1, h->w, n, h->hdev, h->scratch, h->s));
+            CK(launch_axpy_multi(h->V, n, k + 1, h->hdev, h->w, n, h->s));
+            CK(launch_nrm2(h->w, n, h->red, h->scratch, h->s));
+            CK(cudaMemcpyAsync(hn, h->hdev, sizeof(double2) * (k + 1), cudaMemcpyDeviceToHost, h->s));
+            CK(cudaMemcpyAsync(hn + 2 * (m + 1), h->red, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+            CK(cudaStreamSynchronize(h->s));
+            for (int i = 0; i <= k; ++i) hcol[i] += cplx(hn[2 * i], hn[2 * i + 1]);
+            const double hk1 = hn[2 * (m + 1)];
+            if (hk1 > 0.0) CK(launch_scale(h->V + (long long)(k + 1) * n, h->w, h->red, n, h->s));
+            ++its;
+            // Givens rotations on the new column
+            for (int i = 0; i < k; ++i) {
+                const cplx t = std::conj(cs[i]) * hcol[i] + std::conj(sn[i]) * hcol[i + 1];
+                hcol[i + 1] = -sn[i] * hcol[i] + cs[i] * hcol[i + 1];
+                hcol[i] = t;
+            }
+            const double a = std::abs(hcol[k]);
+            const double rr = std::hypot(a, hk1);
+            if (rr == 0.0) { cs[k] = 1; sn[k] = 0; }
+            else {
+                cs[k] = hcol[k] / rr;
+                sn[k] = cplx(hk1 / rr, 0.0);
+            }
+            hcol[k] = rr;
+            for (int i = 0; i <= k; ++i) H[i * m + k] = hcol[i];
+            gv[k + 1] = -sn[k] * gv[k];
+            gv[k] = std::conj(cs[k]) * gv[k];
+            if (!std::isfinite(std::abs(gv[k + 1]))) return fail(h, DD_NLS_ENONFINITE, "GMRES: non-finite iterate");
+            if (std::abs(gv[k + 1]) <= h->P.gmres_tol * bnorm || hk1 == 0.0) { ++k; done = true; break; }
+        }
+        // y = H^{-1} g, x += V y
+        std::vector<cplx> y(k);
+        for (int i = k - 1; i >= 0; --i) {
+            cplx s = gv[i];
+            for (int l = i + 1; l < k; ++l) s -= H[i * m + l] * y[l];
+            y[i] = s / H[i * m + i];
+        }
+        std::vector<double> ny(2 * k);
+        for (int i = 0; i < k; ++i) { ny[2 * i] = -y[i].real(); ny[2 * i + 1] = -y[i].imag(); }
+        CK(cudaMemcpyAsync(h->hdev, ny.data(), sizeof(double2) * k, cudaMemcpyHostToDevice, h->s));
+        CK(launch_axpy_multi(h->V, n, k, h->hdev, x, n, h->s));
+        CK(cudaStreamSynchronize(h->s));
+        first = false;
+        if (done) break;
+    }
+    *its_out = its;
+    return DD_NLS_OK;
+}
+
+// ------------------------------------------------------------- Schwarz step
+// Runs the iteration of the current step from the interface vector in h->gA.
+// On success h->zeta holds v and h->gconv the converged R(g).
+static int schwarz(dd_nls* h, dd_nls_stats* st) {
+    const Geom& G = h->G;
+    CK(launch_rhs0(G, h->u, h->rhs0, h->s));
+    CK(cudaMemcpyAsync(h->zeta, h->u, h->nfield * sizeof(double2), cudaMemcpyDeviceToDevice, h->s));   // zeta^0 = h
+    StripSolveArgs a = base_args(h);
+    double2* g = h->gA;
+    double2* gn = h->gB;
+    for (int k = 0; k < h->P.max_schwarz; ++k) {
+        a.gtr = g;
+        int rc = strip_solve(h, a, G.N, st, true);
+        if (rc) return rc;
+        int nb = 1;
+        if (G.N > 1) {
+            CK(launch_traces(G, h->zeta, g, gn, h->part, &nb, h->s));
+            CK(launch_finalize(h->part, nb, 2, h->red, h->s));
+            CK(cudaMemcpyAsync(h->hred, h->red, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+            CK(cudaStreamSynchronize(h->s));
+        } else {
+            h->hred[0] = h->hred[1] = 0.0;
+        }
+        const double diff = std::sqrt(h->hred[0]), nrm = std::sqrt(h->hred[1]);
+        const double rel = nrm > 0.0 ? diff / nrm : diff;
+        if (st) {
+            st->schwarz_iterations += 1;
+            st->last_schwarz_iterations = k + 1;
+            st->residual = rel;
+            st->residual_abs = diff;
+        }
+        if (!std::isfinite(diff) || !std::isfinite(nrm)) return fail(h, DD_NLS_ENONFINITE, "interface residual is not finite");
+        if ((h->P.tol_absolute ? diff : rel) <= h->P.tol) {
+            if (G.N > 1) CK(cudaMemcpyAsync(h->gconv, gn, h->nI * sizeof(double2), cudaMemcpyDeviceToDevice, h->s));
+            h->gA = g;
+            h->gB = gn;
+            return DD_NLS_OK;
+        }
+        if (h->P.algorithm == DD_NLS_CLASSICAL) {
+            std::swap(g, gn);                     // g^{k+1} = R(g^k)
+        } else {
+            // g^{k+1} = g^k - P^{-1} (g^k - R(g^k))  (eq. algo_pd, reading D10)
+            CK(launch_sub(h->tmp, g, gn, h->nI, h->s));
+            CK(launch_copy(gn, h->tmp, h->nI, h->s));          // gn := y
+            long long its = 0;
+            rc = gmres(h, gn, h->xs, &its);
+            if (rc) return rc;
+            if (st) st->gmres_iterations += its;
+            CK(launch_sub(gn, g, h->xs, h->nI, h->s));
+            std::swap(g, gn);
+        }
+    }
+    h->gA = g;
+    h->gB = gn;
+    return fail(h, DD_NLS_ENOCONV, "Schwarz iteration reached max_schwarz");
+}
+
+static int load_guess(dd_nls* h, const double* g0, int ptr_kind) {
+    if (h->G.N < 2) return DD_NLS_OK;
+    if (g0) return upload_g(h, g0, ptr_kind, h->gA);
+    if (h->P.guess == DD_NLS_GUESS_PREVIOUS && h->have_prev)
+        CK(cudaMemcpyAsync(h->gA, h->gconv, h->nI * sizeof(double2), cudaMemcpyDeviceToDevice, h->s));
+    else
+        CK(cudaMemsetAsync(h->gA, 0, h->nI * sizeof(double2), h->s));
+    return DD_NLS_OK;
+}
+
+static int diagnostics(dd_nls* h, dd_nls_stats* st) {
+    int nb = 1;
+    CK(launch_diagnostics(h->G, h->u, h->Wn, h->part, &nb, h->s));
+    CK(launch_finalize(h->part, nb, 2, h->red, h->s));
+    CK(cudaMemcpyAsync(h->hred, h->red, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    if (st) { st->mass = h->hred[0]; st->energy = h->hred[1]; }
+    return DD_NLS_OK;
+}
+
+// ------------------------------------------------------------------- C-ABI
+extern "C" int dd_nls_create(const dd_nls_params* p, const double* V, const double* u0, int ptr_kind, void* stream,
+                             dd_nls** out) {
+    g_create_error.clear();
+    if (!p || !u0 || !out) return fail(nullptr, DD_NLS_EINVAL, "dd_nls_create: NULL params, u0 or out");
+    *out = nullptr;
+    if (p->nx < 1 || p->ny < 1 || p->n_strips < 1 || p->nx % p->n_strips != 0)
+        return fail(nullptr, DD_NLS_EINVAL, "dd_nls_create: need nx, ny >= 1 and nx a multiple of n_strips");
+    if (!(p->xr > p->xl) || !(p->yu > p->yb) || !(p->dt > 0) || !(p->lap > 0))
+        return fail(nullptr, DD_NLS_EINVAL, "dd_nls_create: need xr > xl, yu > yb, dt > 0, lap > 0");
+    if (p->tc != DD_NLS_TC_ROBIN)
+        return fail(nullptr, DD_NLS_EINVAL, "dd_nls_create: only the Robin transmission condition is built in this version");
+    if (!(p->p > 0.0)) return fail(nullptr, DD_NLS_EINVAL, "dd_nls_create: Robin p must be > 0");
+    if (p->precision != DD_NLS_FP64 && p->precision != DD_NLS_FP32_INNER)
+        return fail(nullptr, DD_NLS_EINVAL, "dd_nls_create: unknown precision");
+    if (ptr_kind != DD_NLS_PTR_HOST && ptr_kind != DD_NLS_PTR_DEVICE)
+        return fail(nullptr, DD_NLS_EINVAL, "dd_nls_create: unknown ptr_kind");
+    const long long c = p->nx / p->n_strips;
+    const long long nyn = (long long)p->ny + 1;
+    if (nyn > (1 << 20) || c + 1 > (1 << 20) || (c + 1) * nyn > (1LL << 30))
+        return fail(nullptr, DD_NLS_EINVAL, "dd_nls_create: strip too large");
+
+    dd_nls* h = new dd_nls();
+    h->P = *p;
+    if (h->P.max_schwarz < 1) h->P.max_schwarz = 1;
+    if (h->P.gmres_restart < 1) h->P.gmres_restart = 30;
+    h->s = (cudaStream_t)stream;
+    h->fp32 = p->precision == DD_NLS_FP32_INNER;
+    Geom& G = h->G;
+    G.N = p->n_strips;
+    G.nxs = (int)c + 1;
+    G.nyn = (int)nyn;
+    G.P = (int)((nyn + 31) / 32 * 32);
+    G.hx = (p->xr - p->xl) / p->nx;
+    G.hy = (p->yu - p->yb) / p->ny;
+    G.alpha = 2.0 / (p->lap * p->dt);
+    G.kap = p->kappa / p->lap;
+    G.p = p->p;
+    G.bc_same = p->bc == DD_NLS_BC_SAME;
+    G.nx = p->nx;
+    h->nfield = (long long)G.N * G.nxs * G.P;
+    h->nI = std::max<long long>(1, (long long)2 * (G.N - 1) * G.P);
+
+    auto bad = [&](int code) { std::string m = h->error; release(h); delete h; g_create_error = m; return code; };
+#define CKC(call)                                                                                   \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess) {                                                                    \
+            h->error = std::string(#call) + ": " + cudaGetErrorString(e_);                         \
+            return bad(e_ == cudaErrorMemoryAllocation ? DD_NLS_ENOMEM : DD_NLS_ECUDA);             \
+        }                                                                                           \
+    } while (0)
+    const size_t s2 = h->fp32 ? sizeof(float2) : sizeof(double2), s1 = h->fp32 ? sizeof(float) : sizeof(double);
+    CKC(dalloc(&h->u, h->nfield));
+    CKC(dalloc(&h->zeta, h->nfield));
+    CKC(dalloc(&h->rhs0, h->nfield));
+    CKC(dalloc(&h->Wn, h->nfield));
+    CKC(dalloc(&h->gA, h->nI));
+    CKC(dalloc(&h->gB, h->nI));
+    CKC(dalloc(&h->gconv, h->nI));
+    CKC(dalloc((char**)&h->x, h->nfield * s2));
+    CKC(dalloc((char**)&h->r, h->nfield * s2));
+    CKC(dalloc((char**)&h->z, h->nfield * s2));
+    CKC(dalloc((char**)&h->p, h->nfield * s2));
+    CKC(dalloc((char**)&h->q, h->nfield * s2));
+    CKC(dalloc((char**)&h->cT, h->nfield * s1));
+    CKC(dalloc(&h->stage, (size_t)(p->nx + 1) * nyn));
+    CKC(dalloc(&h->bar, G.N));
+    CKC(dalloc(&h->status, G.N));
+    CKC(dalloc(&h->nl_its, G.N));
+    CKC(dalloc(&h->kry, G.N));
+    CKC(dalloc(&h->nl_res, G.N));
+    CKC(dalloc(&h->err, 1));
+    CKC(dalloc(&h->red, 64));
+    CKC(cudaMallocHost((void**)&h->hred, 256 * sizeof(double)));
+    CKC(cudaEventCreate(&h->ev0));
+    CKC(cudaEventCreate(&h->ev1));
+    h->h_status.resize(G.N);
+    h->h_nl.resize(G.N);
+    h->h_kry.resize(G.N);
+
+    // launch shape of the strip solver: all blocks co-resident, bps blocks per strip
+    const int maxb = strip_solve_max_blocks(h->fp32);
+    if (maxb < G.N) { h->error = "dd_nls_create: more strips than co-resident blocks of the strip solver"; return bad(DD_NLS_EINVAL); }
+    const int chunks = (int)((G.nxs * (long long)G.nyn + 255) / 256);
+    h->bps = std::max(1, std::min(maxb / G.N, chunks));
+    h->NB = h->bps * G.N;
+    CKC(dalloc(&h->part, (size_t)4 * std::max(h->NB, maxb) * 4));
+
+    if (upload_nodal(h, u0, ptr_kind, h->u)) return bad(DD_NLS_ECUDA);
+    if (V) {
+        const size_t bytes = (size_t)(p->nx + 1) * nyn * sizeof(double);
+        CKC(cudaMemcpyAsync(h->stage, V, bytes, ptr_kind == DD_NLS_PTR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->s));
+        CKC(launch_scatter_real(G, (const double*)h->stage, 1.0 / p->lap, h->Wn, h->s));
+    }
+    CKC(cudaStreamSynchronize(h->s));
+    if (p->algorithm == DD_NLS_PRECONDITIONED && G.N > 1) {
+        int rc = build_Lh(h);
+        if (rc) return bad(rc);
+    }
+    *out = h;
+    return DD_NLS_OK;
+#undef CKC
+}
+
+extern "C" int dd_nls_step(dd_nls* h, int nsteps, double* u_out, int ptr_kind, dd_nls_stats* st) {
+    if (!h) return fail(nullptr, DD_NLS_EINVAL, "dd_nls_step: NULL handle");
+    if (nsteps < 0) return fail(h, DD_NLS_EINVAL, "dd_nls_step: nsteps < 0");
+    if (st) { std::memset(st, 0, sizeof(*st)); st->setup_ms = h->setup_ms; }
+    for (int n = 0; n < nsteps; ++n) {
+        int rc = load_guess(h, nullptr, ptr_kind);
+        if (rc) return rc;
+        rc = schwarz(h, st);
+        if (rc) return rc;
+        CK(launch_commit(h->G, h->zeta, h->u, h->s));
+        h->have_prev = true;
+        h->step += 1;
+        if (st) st->steps += 1;
+    }
+    if (st) {
+        int rc = diagnostics(h, st);
+        if (rc) return rc;
+    }
+    if (u_out) {
+        int rc = download_nodal(h, h->u, u_out, ptr_kind);
+        if (rc) return rc;
+    }
+    CK(cudaStreamSynchronize(h->s));
+    return DD_NLS_OK;
+}
+
+extern "C" int dd_nls_solve_interface(dd_nls* h, const double* g0, double* g_out, double* v_out, int ptr_kind,
+                                      dd_nls_stats* st) {
+    if (!h) return fail(nullptr, DD_NLS_EINVAL, "dd_nls_solve_interface: NULL handle");
+    if (st) { std::memset(st, 0, sizeof(*st)); st->setup_ms = h->setup_ms; }
+    int rc = load_guess(h, g0, ptr_kind);
+    if (rc) return rc;
+    rc = schwarz(h, st);
+    if (rc) return rc;
+    if (g_out) { rc = download_g(h, h->gconv, g_out, ptr_kind); if (rc) return rc; }
+    if (v_out) { rc = download_nodal(h, h->zeta, v_out, ptr_kind); if (rc) return rc; }
+    CK(cudaStreamSynchronize(h->s));
+    return DD_NLS_OK;
+}
+
+extern "C" int dd_nls_get_state(dd_nls* h, double* u, double* g, int* step, int ptr_kind) {
+    if (!h) return fail(nullptr, DD_NLS_EINVAL, "dd_nls_get_state: NULL handle");
+    if (u) { int rc = download_nodal(h, h->u, u, ptr_kind); if (rc) return rc; }
+    if (g) { int rc = download_g(h, h->gconv, g, ptr_kind); if (rc) return rc; }
+    if (step) *step = h->step;
+    CK(cudaStreamSynchronize(h->s));
+    return DD_NLS_OK;
+}
+
+extern "C" int dd_nls_set_state(dd_nls* h, const double* u, const double* g, int step, int ptr_kind) {
+    if (!h) return fail(nullptr, DD_NLS_EINVAL, "dd_nls_set_state: NULL handle");
+    if (u) { int rc = upload_nodal(h, u, ptr_kind, h->u); if (rc) return rc; }
+    if (g) { int rc = upload_g(h, g, ptr_kind, h->gconv); if (rc) return rc; h->have_prev = true; }
+    h->step = step;
+    CK(cudaStreamSynchronize(h->s));
+    return DD_NLS_OK;
+}
+
+extern "C" int dd_nls_get_blocks(dd_nls* h, int strip, double* x, int ptr_kind) {
+    if (!h) return fail(nullptr, DD_NLS_EINVAL, "dd_nls_get_blocks: NULL handle");
+    if (!h->X64 || strip < 0 || strip >= h->G.N || !x) return fail(h, DD_NLS_EINVAL, "dd_nls_get_blocks: no L_h or bad strip");
+    const long long bs = (long long)h->G.nyn * h->G.nyn;
+    CK(cudaMemcpyAsync(x, h->X64 + (long long)h->btype_h[strip] * 4 * bs, 4 * bs * sizeof(double2),
+                       ptr_kind == DD_NLS_PTR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    return DD_NLS_OK;
+}
+
+extern "C" int dd_nls_set_profiling(dd_nls* h, int on) {
+    if (!h) return fail(nullptr, DD_NLS_EINVAL, "dd_nls_set_profiling: NULL handle");
+    h->prof = on != 0;
+    std::memset(&h->profile, 0, sizeof(h->profile));
+    return DD_NLS_OK;
+}
+
+extern "C" int dd_nls_get_profile(dd_nls* h, dd_nls_profile* prof) {
+    if (!h || !prof) return fail(h, DD_NLS_EINVAL, "dd_nls_get_profile: NULL argument");
+    *prof = h->profile;
+    return DD_NLS_OK;
+}
+
+extern "C" void dd_nls_destroy(dd_nls* h) {
+    if (!h) return;
+    if (h->s) cudaStreamSynchronize(h->s);
+    release(h);
+    delete h;
+}
+
+extern "C" const char* dd_nls_last_error(const dd_nls* h) {
+    return h ? h->error.c_str() : g_create_error.c_str();
+}

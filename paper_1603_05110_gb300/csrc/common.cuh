@@ -1,0 +1,185 @@
+// Internal device helpers shared by the dd_nls kernels: complex arithmetic on float2 /
+// double2, the strip geometry, 1D Q1 coefficients, a bounded inter-block barrier and
+// deterministic block reductions.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/dd_nls.h"
+
+namespace ddnls {
+
+// ------------------------------------------------------------------ complex helpers
+template <typename T> struct C2;
+template <> struct C2<float> { using t = float2; };
+template <> struct C2<double> { using t = double2; };
+
+template <typename T2> __host__ __device__ __forceinline__ T2 mk(double re, double im) {
+    T2 r; r.x = re; r.y = im; return r;
+}
+template <typename T2> __device__ __forceinline__ T2 cadd(T2 a, T2 b) { a.x += b.x; a.y += b.y; return a; }
+template <typename T2> __device__ __forceinline__ T2 csub(T2 a, T2 b) { a.x -= b.x; a.y -= b.y; return a; }
+template <typename T2, typename T> __device__ __forceinline__ T2 cscale(T2 a, T s) { a.x *= s; a.y *= s; return a; }
+template <typename T2> __device__ __forceinline__ T2 cmul(T2 a, T2 b) {
+    T2 r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+}
+// a + s*b for complex s
+template <typename T2> __device__ __forceinline__ T2 cfma(T2 s, T2 b, T2 a) {
+    a.x = fma(s.x, b.x, fma(-s.y, b.y, a.x));
+    a.y = fma(s.x, b.y, fma(s.y, b.x, a.y));
+    return a;
+}
+template <typename T2> __device__ __forceinline__ T2 cinv(T2 a) {
+    auto d = a.x * a.x + a.y * a.y;
+    T2 r; r.x = a.x / d; r.y = -a.y / d; return r;
+}
+__device__ __forceinline__ double2 cd(float2 a) { return make_double2(a.x, a.y); }
+__device__ __forceinline__ double2 cd(double2 a) { return a; }
+template <typename T2> __device__ __forceinline__ T2 cfrom(double2 a);
+template <> __device__ __forceinline__ float2 cfrom<float2>(double2 a) { return make_float2((float)a.x, (float)a.y); }
+template <> __device__ __forceinline__ double2 cfrom<double2>(double2 a) { return a; }
+
+// -------------------------------------------------------------------- geometry
+// Strip field layout: strip j, column ix in [0, nxs), row iy in [0, nyn) at
+// (j*nxs + ix)*P + iy: y is the fastest index, so an interface trace is contiguous.
+struct Geom {
+    int N;        // strips
+    int nxs;      // nodes per strip in x (cells per strip + 1)
+    int nyn;      // nodes in y
+    int P;        // row pitch in elements (>= nyn, multiple of 32)
+    double hx, hy;
+    double alpha; // 2/(lap*dt), eq. (CNS) after division by lap
+    double kap;   // kappa/lap
+    double p;     // Robin parameter
+    int bc_same;  // physical x-edges carry S-bar (1) or Neumann (0)
+    int nx;       // cells in x over all strips
+    __host__ __device__ long long sstride() const { return (long long)nxs * P; }
+    __host__ __device__ int c() const { return nxs - 1; }
+};
+
+// 1D P1 coefficients of a uniform mesh with nodes 0..n: mass (h/6)[1 4 1] with h/3 at the
+// ends, stiffness (1/h)[-1 2 -1] with 1/h at the ends (Sec. 2.2, Q1 = P1 x P1).
+template <typename T> struct Coef1 {
+    T m[3];   // M(i, i-1), M(i, i), M(i, i+1) (zero outside the mesh)
+    T k[3];
+};
+template <typename T> __device__ __forceinline__ Coef1<T> coef1(int i, int n, double h) {
+    Coef1<T> c;
+    const bool lo = (i > 0), hi = (i < n);
+    c.m[0] = lo ? (T)(h / 6.0) : (T)0;
+    c.m[2] = hi ? (T)(h / 6.0) : (T)0;
+    c.m[1] = (lo && hi) ? (T)(4.0 * h / 6.0) : (T)(2.0 * h / 6.0);
+    c.k[0] = lo ? (T)(-1.0 / h) : (T)0;
+    c.k[2] = hi ? (T)(-1.0 / h) : (T)0;
+    c.k[1] = (lo && hi) ? (T)(2.0 / h) : (T)(1.0 / h);
+    return c;
+}
+// trapezoidal (nodal quadrature) weight of node i of a 1D mesh 0..n
+__device__ __forceinline__ double wq(int i, int n, double h) { return (i == 0 || i == n) ? 0.5 * h : h; }
+
+// Strip j's vertical edges: transmission operator (interfaces, and the physical edges when
+// bc_same) and whether a datum (l or r) enters the right side (interfaces only).
+__device__ __forceinline__ bool left_tc(const Geom& g, int j) { return j > 0 || g.bc_same; }
+__device__ __forceinline__ bool right_tc(const Geom& g, int j) { return j < g.N - 1 || g.bc_same; }
+
+// flat node index n -> (ix, iy) with a float reciprocal and an exact fix-up
+__device__ __forceinline__ void split_node(int n, int nyn, float inv_nyn, int& ix, int& iy) {
+    ix = __float2int_rz((float)n * inv_nyn);
+    iy = n - ix * nyn;
+    if (iy < 0) { ix -= 1; iy += nyn; }
+    else if (iy >= nyn) { ix += 1; iy -= nyn; }
+}
+
+// ------------------------------------------------------------------- reductions
+// Sum NV doubles over the block in a fixed order; the result is valid in thread 0.
+template <int NV> __device__ __forceinline__ void block_sum(double (&v)[NV], double* smem) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) smem[wid * NV + k] = v[k];
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double s = lane < nw ? smem[lane * NV + k] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+            v[k] = s;
+        }
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Barrier among the nblk co-resident blocks that share *ctr.  The counter only grows:
+// the k-th barrier of a launch waits for k*nblk arrivals.  The wait is bounded (about
+// two seconds of wall time); on time-out it records DD_NLS_ETIMEOUT in *err and returns
+// false, and every caller leaves its loop.
+__device__ __forceinline__ bool group_barrier(unsigned* ctr, unsigned target, int* err, int* s_flag) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(ctr, 1u);
+        int ok = 1;
+        if (ld_acquire(ctr) < target) {
+            const unsigned long long t0 = globaltimer();
+            unsigned spins = 0;
+            while (ld_acquire(ctr) < target) {
+                __nanosleep(64);
+                if ((++spins & 255u) == 0 && globaltimer() - t0 > 2000000000ull) {
+                    atomicExch(err, DD_NLS_ETIMEOUT);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        if (ok && *(volatile int*)err == DD_NLS_ETIMEOUT) ok = 0;
+        __threadfence();
+        *s_flag = ok;
+    }
+    __syncthreads();
+    return *s_flag != 0;
+}
+
+// Sum slot values written by the nblk blocks of a group (fixed order); result broadcast.
+template <int NV> __device__ __forceinline__ void group_sum(const double* part, int nblk, double (&out)[NV], double* smem) {
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        double acc[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+        for (int b0 = 0; b0 < nblk; b0 += 32) {
+            const int b = b0 + lane;
+#pragma unroll
+            for (int k = 0; k < NV; ++k) {
+                double s = b < nblk ? __ldcg(part + (size_t)b * 4 + k) : 0.0;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                acc[k] += s;
+            }
+        }
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) smem[k] = acc[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) out[k] = smem[k];
+    __syncthreads();
+}
+
+}  // namespace ddnls

@@ -1,0 +1,72 @@
+// Internal launch interface between the host runtime (api.cu) and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace ddnls {
+
+struct StripSolveArgs {
+    Geom g;
+    int bps;                 // blocks per strip
+    int mode;                // 0: Schwarz strips; 1: unit data on free strips (L_h setup)
+    int unit_base;           // mode 1: first unit column (side*nyn + pos) of this launch
+    int unit_ltc, unit_rtc;  // mode 1: edge kinds of the strip type
+    double2* zeta;           // FP64 strip fields, in/out
+    const double2* rhs0;     // (2i/dt) M h per strip, or NULL (zero)
+    const double* Wn;        // V/lap per strip node, or NULL (zero)
+    const double2* gtr;      // interface traces [2(N-1)][P]
+    void *x, *r, *z, *p, *q; // inner Krylov vectors (float2 or double2)
+    void* cT;                // c = w (W + kappa|zeta|^2) in inner precision
+    double nl_tol, inner_tol, inner_floor;
+    int max_nl, max_inner;
+    double* part;            // [4][gridDim][4] partial sums
+    unsigned* bar;           // [strips] barrier counters, zeroed before the launch
+    int* status;             // [strips]
+    int* nl_its;             // [strips]
+    long long* kry_its;      // [strips]
+    double* nl_res;          // [strips]
+    int* err;                // launch-wide error word
+};
+
+cudaError_t launch_strip_solve(const StripSolveArgs& a, int nstrips, bool fp32, cudaStream_t s);
+int strip_solve_max_blocks(bool fp32);
+
+// ---- auxiliary kernels (aux_kernels.cu)
+using AuxGeom = Geom;
+
+// nodal (ny+1)x(nx+1) x-fastest  <->  strip layout
+cudaError_t launch_scatter_u(const AuxGeom& g, const double2* glob, double2* strips, cudaStream_t s);
+cudaError_t launch_gather_u(const AuxGeom& g, const double2* strips, double2* glob, cudaStream_t s);
+cudaError_t launch_scatter_real(const AuxGeom& g, const double* glob, double scale, double* strips, cudaStream_t s);
+// rhs0 = i alpha M h (per strip)
+cudaError_t launch_rhs0(const AuxGeom& g, const double2* h, double2* rhs0, cudaStream_t s);
+// interface flux update, eq. (fluxlr), Robin: writes gnew, partial norms into part[nblk][2]
+cudaError_t launch_traces(const AuxGeom& g, const double2* zeta, const double2* gtr, double2* gnew,
+                          double* part, int* nblk_out, cudaStream_t s);
+// sum part[nblk][k] (k < nv) in fixed order into out[k]
+cudaError_t launch_finalize(const double* part, int nblk, int nv, double* out, cudaStream_t s);
+// u_n = 2 zeta - u_{n-1}, interface columns from the left strip
+cudaError_t launch_commit(const AuxGeom& g, const double2* zeta, double2* u, cudaStream_t s);
+// mass u^H M u and energy parts; partial sums part[nblk][4]
+cudaError_t launch_diagnostics(const AuxGeom& g, const double2* u, const double* Wn, double* part,
+                               int* nblk_out, cudaStream_t s);
+// L_h block extraction from unit-datum solutions (mode 1 of the strip solver)
+cudaError_t launch_extract_blocks(const AuxGeom& g, const double2* zeta, int nvirt, int unit_base,
+                                  double2* X, cudaStream_t s);
+// y = x - L x  (P of eq. algo_pd) with per-strip block sets X[btype[j]] (4 blocks each)
+cudaError_t launch_apply_P(const AuxGeom& g, const void* X, bool fp32, const int* btype_dev,
+                           const double2* x, double2* y, double2* work, cudaStream_t s);
+cudaError_t launch_convert_blocks(const double2* X, float2* Xf, long long n, cudaStream_t s);
+
+// GMRES helpers on vectors of length n (complex, FP64)
+cudaError_t launch_dots(const double2* V, long long ld, int k, const double2* w, long long n, double2* out,
+                        double* scratch, cudaStream_t s);
+cudaError_t launch_axpy_multi(const double2* V, long long ld, int k, const double2* h, double2* w, long long n,
+                              cudaStream_t s);
+cudaError_t launch_nrm2(const double2* w, long long n, double* out, double* scratch, cudaStream_t s);
+cudaError_t launch_scale(double2* y, const double2* x, const double* inv_from, long long n, cudaStream_t s);
+cudaError_t launch_sub(double2* y, const double2* a, const double2* b, long long n, cudaStream_t s);
+cudaError_t launch_copy(double2* y, const double2* x, long long n, cudaStream_t s);
+
+}  // namespace ddnls

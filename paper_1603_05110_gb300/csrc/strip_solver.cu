@@ -1,0 +1,316 @@
+// Batched strip solver: every strip problem of one Schwarz iteration in one persistent
+// (cooperative) launch.
+//
+// Each strip j solves the nonlinear local problem of eq. (localpbrobin) in the matrix form
+// of eq. (NproblemRobinNL):
+//     (A + i p M^Gamma + M_f(zeta)) zeta = (2i/dt) M h - M^Gamma Q^T (l; r),
+//     A = (2i/dt) M - S + M_W,   M_f(zeta) = diag(w kappa |zeta|^2)   (nodal quadrature),
+// by the fixed point of eq. (localpbrobin) written in defect-correction form: with
+// c = w (W + kappa |zeta|^2) frozen at the current iterate,
+//     res = b - A(c) zeta   (FP64, matrix-free 9-point Q1 stencil),
+//     A(c) delta = res      (Jacobi-preconditioned COCG in precision T),
+//     zeta += delta,
+// until ||res|| <= nl_tol ||b||.  With an exact inner solve one correction is exactly one
+// step zeta^q = A(c(zeta^{q-1}))^{-1} b of eq. (localpbrobin); the limit is the same fixed
+// point.  A(c) is complex symmetric, so COCG (CG with the unconjugated bilinear form)
+// applies.
+//
+// Work split: blocks [j*bps, (j+1)*bps) own strip j; they meet only at per-strip barriers
+// (bounded spin, status word on time-out), so strips converge independently.  Every block
+// derives the same scalars from the same fixed-order reductions, so all blocks of a strip
+// take the same branches.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace ddnls {
+
+// y = A(c) v at one node: the 9-point Q1 stencil of Bx (x) My - Mx (x) Ky + diag(c), with
+// Bx = -Kx + i (alpha Mx + p E_x) and E_x the Robin edges of the strip (eq. NproblemRobinNL).
+template <typename T, typename T2>
+__device__ __forceinline__ T2 apply_op(const T2* v, long long idx, int ix, int iy,
+                                       int c, int ny, int P, const Coef1<T>& cx, const Coef1<T>& cy,
+                                       T alpha, T robin, T cdiag) {
+    T2 acc = mk<T2>(0.0, 0.0);
+#pragma unroll
+    for (int dx = -1; dx <= 1; ++dx) {
+        if (ix + dx < 0 || ix + dx > c) continue;
+        const T2* col = v + idx + (long long)dx * P;
+        const T2 a0 = col[0];
+        const T2 am = iy > 0 ? col[-1] : mk<T2>(0.0, 0.0);
+        const T2 ap = iy < ny ? col[1] : mk<T2>(0.0, 0.0);
+        T2 tM, tK;
+        tM.x = cy.m[0] * am.x + cy.m[1] * a0.x + cy.m[2] * ap.x;
+        tM.y = cy.m[0] * am.y + cy.m[1] * a0.y + cy.m[2] * ap.y;
+        tK.x = cy.k[0] * am.x + cy.k[1] * a0.x + cy.k[2] * ap.x;
+        tK.y = cy.k[0] * am.y + cy.k[1] * a0.y + cy.k[2] * ap.y;
+        const T mx = cx.m[dx + 1];
+        const T bre = -cx.k[dx + 1];
+        const T bim = alpha * mx + (dx == 0 ? robin : (T)0);
+        acc.x += bre * tM.x - bim * tM.y - mx * tK.x;
+        acc.y += bre * tM.y + bim * tM.x - mx * tK.y;
+    }
+    const T2 vc = v[idx];
+    acc.x += cdiag * vc.x;
+    acc.y += cdiag * vc.y;
+    return acc;
+}
+
+template <typename T>
+__device__ __forceinline__ typename C2<T>::t diag_inv(const Coef1<T>& cx, const Coef1<T>& cy, T alpha, T robin, T cdiag) {
+    using T2 = typename C2<T>::t;
+    T2 d;
+    d.x = -cx.k[1] * cy.m[1] - cx.m[1] * cy.k[1] + cdiag;
+    d.y = (alpha * cx.m[1] + robin) * cy.m[1];
+    return cinv(d);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+strip_solve_kernel(StripSolveArgs a) {
+    using T2 = typename C2<T>::t;
+    __shared__ double s_red[64];
+    __shared__ int s_flag;
+
+    const Geom& g = a.g;
+    const int bps = a.bps;
+    const int j = blockIdx.x / bps;          // strip (virtual strip in setup mode)
+    const int rank = blockIdx.x - j * bps;
+    const int nyn = g.nyn, ny = nyn - 1, c = g.nxs - 1, P = g.P;
+    const int Ns = g.nxs * nyn;
+    const int nchunks = (Ns + blockDim.x - 1) / blockDim.x;
+    const float inv_nyn = 1.0f / (float)nyn;
+    const long long sbase = (long long)j * g.sstride();
+
+    // edges of this strip
+    bool ltc, rtc, ldata, rdata;
+    int unit_side = -1, unit_pos = -1;
+    if (a.mode == 0) {
+        ltc = left_tc(g, j);
+        rtc = right_tc(g, j);
+        ldata = j > 0;
+        rdata = j < g.N - 1;
+    } else {      // L_h construction: unit datum on one edge of a free strip
+        ltc = a.unit_ltc;
+        rtc = a.unit_rtc;
+        ldata = rdata = false;
+        const int u = a.unit_base + j;
+        unit_side = u / nyn;
+        unit_pos = u - unit_side * nyn;
+    }
+    const double2* gl = ldata ? a.gtr + (size_t)(2 * (j - 1) + 1) * P : nullptr;
+    const double2* gr = rdata ? a.gtr + (size_t)(2 * j) * P : nullptr;
+
+    double2* zeta = a.zeta + sbase;
+    const double2* __restrict__ rhs0 = a.rhs0 ? a.rhs0 + sbase : nullptr;
+    const double* __restrict__ Wn = a.Wn ? a.Wn + sbase : nullptr;
+    T2* x = (T2*)a.x + sbase;
+    T2* r = (T2*)a.r + sbase;
+    T2* z = (T2*)a.z + sbase;
+    T2* p = (T2*)a.p + sbase;
+    T2* q = (T2*)a.q + sbase;
+    T* cT = (T*)a.cT + sbase;
+
+    unsigned* bar = a.bar + j;
+    unsigned epoch = 0;
+    const int NB = gridDim.x;
+    double* part_base = a.part;
+    auto slot_ptr = [&](unsigned e) { return part_base + ((size_t)(e & 3u) * NB + blockIdx.x) * 4; };
+    auto group_ptr = [&](unsigned e) { return part_base + ((size_t)(e & 3u) * NB + (size_t)j * bps) * 4; };
+
+    const double robin_l = ltc ? g.p : 0.0, robin_r = rtc ? g.p : 0.0;
+    const T alphaT = (T)g.alpha;
+    const double kap = a.mode == 0 ? g.kap : 0.0;
+
+    int status = 0, nl_it = 0;
+    long long kry = 0;
+    double nres = 0.0;
+
+    auto robin_at = [&](int ix) -> double {
+        double rb = 0.0;
+        if (ix == 0) rb += robin_l;
+        if (ix == c) rb += robin_r;
+        return rb;
+    };
+    // datum of the Robin data term on an edge node (l on ix=0, r on ix=c)
+    auto edge_term = [&](int ix, int iy, const Coef1<double>& cy) -> double2 {
+        double2 t = make_double2(0.0, 0.0);
+        if (ix == 0 && ldata) {
+            const double2 lm = iy > 0 ? gl[iy - 1] : make_double2(0, 0), l0 = gl[iy], lp = iy < ny ? gl[iy + 1] : make_double2(0, 0);
+            t.x += cy.m[0] * lm.x + cy.m[1] * l0.x + cy.m[2] * lp.x;
+            t.y += cy.m[0] * lm.y + cy.m[1] * l0.y + cy.m[2] * lp.y;
+        }
+        if (ix == c && rdata) {
+            const double2 rm = iy > 0 ? gr[iy - 1] : make_double2(0, 0), r0 = gr[iy], rp = iy < ny ? gr[iy + 1] : make_double2(0, 0);
+            t.x += cy.m[0] * rm.x + cy.m[1] * r0.x + cy.m[2] * rp.x;
+            t.y += cy.m[0] * rm.y + cy.m[1] * r0.y + cy.m[2] * rp.y;
+        }
+        if (unit_side >= 0 && ((unit_side == 0 && ix == 0) || (unit_side == 1 && ix == c))) {
+            const int d = unit_pos - iy;
+            if (d >= -1 && d <= 1) t.x += cy.m[d + 1];
+        }
+        return t;
+    };
+
+    for (;; ++nl_it) {
+        // ---------------- phase R: coefficients c = w (W + kappa|zeta|^2) and FP64 residual
+        double loc[4] = {0.0, 0.0, 0.0, 0.0};   // ||res||^2, ||b||^2, rho = r^T z (re, im)
+        for (int ch = rank; ch < nchunks; ch += bps) {
+            const int n = ch * blockDim.x + threadIdx.x;
+            if (n >= Ns) continue;
+            int ix, iy;
+            split_node(n, nyn, inv_nyn, ix, iy);
+            const long long idx = (long long)ix * P + iy;
+            const Coef1<double> cx = coef1<double>(ix, c, g.hx), cy = coef1<double>(iy, ny, g.hy);
+            const double2 zc = zeta[idx];
+            const double W = Wn ? Wn[idx] : 0.0;
+            const double cdiag = wq(ix, c, g.hx) * wq(iy, ny, g.hy) * (W + kap * (zc.x * zc.x + zc.y * zc.y));
+            const double rb = robin_at(ix);
+            const double2 Az = apply_op<double, double2>(zeta, idx, ix, iy, c, ny, P, cx, cy, g.alpha, rb, cdiag);
+            double2 b = rhs0 ? rhs0[idx] : make_double2(0.0, 0.0);
+            b = csub(b, edge_term(ix, iy, cy));
+            const double2 res = csub(b, Az);
+            loc[0] += res.x * res.x + res.y * res.y;
+            loc[1] += b.x * b.x + b.y * b.y;
+            const Coef1<T> cxT = coef1<T>(ix, c, g.hx), cyT = coef1<T>(iy, ny, g.hy);
+            const T2 rT = cfrom<T2>(res);
+            const T2 di = diag_inv<T>(cxT, cyT, alphaT, (T)rb, (T)cdiag);
+            const T2 zT = cmul(di, rT);
+            cT[idx] = (T)cdiag;
+            r[idx] = rT;
+            z[idx] = zT;
+            x[idx] = mk<T2>(0.0, 0.0);
+            p[idx] = mk<T2>(0.0, 0.0);
+            q[idx] = mk<T2>(0.0, 0.0);
+            loc[2] += (double)(rT.x * zT.x - rT.y * zT.y);
+            loc[3] += (double)(rT.x * zT.y + rT.y * zT.x);
+        }
+        block_sum<4>(loc, s_red);
+        if (threadIdx.x == 0) { double* sp = slot_ptr(epoch + 1); sp[0] = loc[0]; sp[1] = loc[1]; sp[2] = loc[2]; sp[3] = loc[3]; }
+        ++epoch;
+        if (!group_barrier(bar, epoch * bps, a.err, &s_flag)) { status = DD_NLS_ETIMEOUT; break; }
+        double tot[4];
+        group_sum<4>(group_ptr(epoch), bps, tot, s_red);
+        const double bnorm = sqrt(tot[1]);
+        const double rnorm = sqrt(tot[0]);
+        nres = bnorm > 0.0 ? rnorm / bnorm : rnorm;
+        if (!isfinite(tot[0]) || !isfinite(tot[1])) { status = DD_NLS_ENONFINITE; break; }
+        if (nres <= a.nl_tol || rnorm == 0.0) break;
+        if (nl_it >= a.max_nl) { status = DD_NLS_ENOCONV; break; }
+
+        // ---------------- inner COCG on A(c) delta = res, Jacobi preconditioner
+        double rho_re = tot[2], rho_im = tot[3];
+        double beta_re = 0.0, beta_im = 0.0;
+        const double target = fmax(a.inner_tol * rnorm, a.inner_floor * bnorm);
+        for (int it = 0; it < a.max_inner; ++it) {
+            // phase A: q = A z + beta q, p = z + beta p, partial mu = p^T q
+            double lm[4] = {0.0, 0.0, 0.0, 0.0};
+            const T2 bT = mk<T2>(beta_re, beta_im);
+            for (int ch = rank; ch < nchunks; ch += bps) {
+                const int n = ch * blockDim.x + threadIdx.x;
+                if (n >= Ns) continue;
+                int ix, iy;
+                split_node(n, nyn, inv_nyn, ix, iy);
+                const long long idx = (long long)ix * P + iy;
+                const Coef1<T> cxT = coef1<T>(ix, c, g.hx), cyT = coef1<T>(iy, ny, g.hy);
+                const T2 Az = apply_op<T, T2>(z, idx, ix, iy, c, ny, P, cxT, cyT, alphaT, (T)robin_at(ix), cT[idx]);
+                const T2 qn = cfma(bT, q[idx], Az);
+                const T2 pn = cfma(bT, p[idx], z[idx]);
+                q[idx] = qn;
+                p[idx] = pn;
+                lm[0] += (double)(pn.x * qn.x - pn.y * qn.y);
+                lm[1] += (double)(pn.x * qn.y + pn.y * qn.x);
+            }
+            block_sum<4>(lm, s_red);
+            if (threadIdx.x == 0) { double* sp = slot_ptr(epoch + 1); sp[0] = lm[0]; sp[1] = lm[1]; sp[2] = 0; sp[3] = 0; }
+            ++epoch;
+            if (!group_barrier(bar, epoch * bps, a.err, &s_flag)) { status = DD_NLS_ETIMEOUT; break; }
+            double mu[4];
+            group_sum<4>(group_ptr(epoch), bps, mu, s_red);
+            const double mu2 = mu[0] * mu[0] + mu[1] * mu[1];
+            if (!(mu2 > 0.0) || !isfinite(mu2)) { status = isfinite(mu2) ? DD_NLS_EBREAKDOWN : DD_NLS_ENONFINITE; break; }
+            // a = rho / mu
+            const double al_re = (rho_re * mu[0] + rho_im * mu[1]) / mu2;
+            const double al_im = (rho_im * mu[0] - rho_re * mu[1]) / mu2;
+            const T2 alT = mk<T2>(al_re, al_im);
+            const T2 malT = mk<T2>(-al_re, -al_im);
+            // phase B: x += a p, r -= a q, z = D^-1 r, partials rho' = r^T z, ||r||^2
+            double lb[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int ch = rank; ch < nchunks; ch += bps) {
+                const int n = ch * blockDim.x + threadIdx.x;
+                if (n >= Ns) continue;
+                int ix, iy;
+                split_node(n, nyn, inv_nyn, ix, iy);
+                const long long idx = (long long)ix * P + iy;
+                const Coef1<T> cxT = coef1<T>(ix, c, g.hx), cyT = coef1<T>(iy, ny, g.hy);
+                const T2 pc = p[idx];
+                x[idx] = cfma(alT, pc, x[idx]);
+                const T2 rn = cfma(malT, q[idx], r[idx]);
+                r[idx] = rn;
+                const T2 di = diag_inv<T>(cxT, cyT, alphaT, (T)robin_at(ix), cT[idx]);
+                const T2 zn = cmul(di, rn);
+                z[idx] = zn;
+                lb[0] += (double)(rn.x * zn.x - rn.y * zn.y);
+                lb[1] += (double)(rn.x * zn.y + rn.y * zn.x);
+                lb[2] += (double)(rn.x * rn.x + rn.y * rn.y);
+            }
+            block_sum<4>(lb, s_red);
+            if (threadIdx.x == 0) { double* sp = slot_ptr(epoch + 1); sp[0] = lb[0]; sp[1] = lb[1]; sp[2] = lb[2]; sp[3] = 0; }
+            ++epoch;
+            if (!group_barrier(bar, epoch * bps, a.err, &s_flag)) { status = DD_NLS_ETIMEOUT; break; }
+            double rb[4];
+            group_sum<4>(group_ptr(epoch), bps, rb, s_red);
+            ++kry;
+            if (!isfinite(rb[2])) { status = DD_NLS_ENONFINITE; break; }
+            if (sqrt(rb[2]) <= target) break;
+            const double rr2 = rho_re * rho_re + rho_im * rho_im;
+            if (!(rr2 > 0.0)) { status = DD_NLS_EBREAKDOWN; break; }
+            beta_re = (rb[0] * rho_re + rb[1] * rho_im) / rr2;
+            beta_im = (rb[1] * rho_re - rb[0] * rho_im) / rr2;
+            rho_re = rb[0];
+            rho_im = rb[1];
+        }
+        if (status) break;
+        // ---------------- zeta += delta (FP64), then every block must see the new zeta
+        for (int ch = rank; ch < nchunks; ch += bps) {
+            const int n = ch * blockDim.x + threadIdx.x;
+            if (n >= Ns) continue;
+            int ix, iy;
+            split_node(n, nyn, inv_nyn, ix, iy);
+            const long long idx = (long long)ix * P + iy;
+            zeta[idx] = cadd(zeta[idx], cd(x[idx]));
+        }
+        ++epoch;
+        if (!group_barrier(bar, epoch * bps, a.err, &s_flag)) { status = DD_NLS_ETIMEOUT; break; }
+    }
+    if (rank == 0 && threadIdx.x == 0) {
+        a.status[j] = status;
+        a.nl_its[j] = nl_it;
+        a.kry_its[j] = kry;
+        a.nl_res[j] = nres;
+    }
+}
+
+template <typename T>
+static cudaError_t launch_strip_solve_t(const StripSolveArgs& args, int nstrips, cudaStream_t s) {
+    StripSolveArgs a = args;
+    void* params[] = {&a};
+    dim3 grid(nstrips * a.bps), block(256);
+    return cudaLaunchCooperativeKernel((const void*)strip_solve_kernel<T>, grid, block, params, 0, s);
+}
+
+cudaError_t launch_strip_solve(const StripSolveArgs& a, int nstrips, bool fp32, cudaStream_t s) {
+    return fp32 ? launch_strip_solve_t<float>(a, nstrips, s) : launch_strip_solve_t<double>(a, nstrips, s);
+}
+
+int strip_solve_max_blocks(bool fp32) {
+    int dev = 0, nsm = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (fp32)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, strip_solve_kernel<float>, 256, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, strip_solve_kernel<double>, 256, 0);
+    return per * nsm;
+}
+
+}  // namespace ddnls

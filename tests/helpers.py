@@ -1,0 +1,20 @@
+"""Shared test helpers: the same seeded inputs go to the CUDA library and to the oracle."""
+import numpy as np
+
+from oracle import nls
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def oracle_problem(w, V=None, tc="robin", bc="same", m=4):
+    return nls.Problem(xl=w.xl, xr=w.xr, yb=w.yb, yu=w.yu, nx=w.nx, ny=w.ny, dt=w.dt,
+                       V=w.V() if V is None else V, kappa=w.kappa, lap=w.lap, tc=tc, p=w.p, m=m, bc=bc)
+
+
+def gpu_params(w, **kw):
+    d = dict(xl=w.xl, xr=w.xr, yb=w.yb, yu=w.yu, nx=w.nx, ny=w.ny, n_strips=w.n_strips, dt=w.dt,
+             lap=w.lap, kappa=w.kappa, p=w.p)
+    d.update(kw)
+    return d

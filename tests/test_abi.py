@@ -1,0 +1,74 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point that
+include/dd_nls.h declares (no GPU needed: no compute call is made)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "dd_nls.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(dd_nls_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1603_05110_gb300 import binding, build
+    build.build()
+    return binding.load()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    syms = declared_symbols()
+    assert len(syms) >= 11
+    for s in syms:
+        assert hasattr(lib, s), s
+    from paper_1603_05110_gb300 import binding
+    assert set(syms) == set(binding.SYMBOLS)
+
+
+def test_default_params_and_struct_layout(lib):
+    from paper_1603_05110_gb300 import binding
+    p = binding.default_params(nx=64, ny=40, n_strips=4)
+    assert p.nx == 64 and p.n_strips == 4 and p.lap == 1.0 and p.tol == 1e-10
+    assert p.gmres_restart == 30 and p.max_schwarz > 0
+
+
+def test_ctypes_mirrors_match_the_c_layout(tmp_path):
+    """Every field offset and struct size of the ctypes mirrors equals the C compiler's."""
+    import shutil
+    import subprocess
+    from paper_1603_05110_gb300 import binding
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "dd_nls.h"', "int main(void){"]
+    expect = []
+    for cname, cls in (("dd_nls_params", binding.Params), ("dd_nls_stats", binding.Stats),
+                       ("dd_nls_profile", binding.Profile)):
+        lines.append(f'printf("%zu\\n", sizeof({cname}));')
+        expect.append(ctypes.sizeof(cls))
+        for f, _ in cls._fields_:
+            lines.append(f'printf("%zu\\n", offsetof({cname}, {f}));')
+            expect.append(getattr(cls, f).offset)
+    lines.append("return 0;}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert got == expect
+
+
+def test_create_rejects_bad_sizes_without_touching_the_gpu(lib):
+    import numpy as np
+    from paper_1603_05110_gb300 import binding
+    p = binding.default_params(nx=30, ny=8, n_strips=4)       # 30 % 4 != 0
+    u0 = np.zeros((9, 31), np.complex128)
+    with pytest.raises(binding.DDNLSError) as e:
+        binding.Solver(p, u0)
+    assert e.value.code == 1

@@ -1,0 +1,180 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 CPU oracle.
+
+Tolerances: the plain FP64 path must agree with the oracle to 1e-11 relative L2 per step;
+both sides iterate to interface residuals <= 1e-12 (so neither stops one iteration away from
+the other) and strip nonlinear residuals <= 1e-13.  The FP32-inner path keeps its residuals
+in FP64, so it reaches the same discrete solution; it is held to 1e-10 here and to the 1e-6
+contract bound in the workload-size tests.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import nls  # noqa: E402
+from paper_1603_05110_gb300 import binding, workloads as wl  # noqa: E402
+from tests.helpers import gpu_params, oracle_problem, rel  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1603_05110_gb300 import build
+    build.build()
+    binding.load()
+
+
+def run_gpu(w, steps, **kw):
+    u0 = w.u0()
+    out = np.zeros_like(u0)
+    hist = []
+    with binding.Solver(gpu_params(w, **kw), u0, w.V()) as s:
+        for _ in range(steps):
+            st = s.step(1, out)
+            hist.append((out.copy(), st))
+    return hist
+
+
+def run_oracle(w, steps, algorithm="classical", bc="same", tol=TOL):
+    prob = oracle_problem(w, bc=bc)
+    st = nls.Strips(prob, w.n_strips)
+    Lh = st.build_Lh() if algorithm == "preconditioned" else None
+    u = w.u0()
+    g = None
+    out = []
+    for _ in range(steps):
+        u, _, info = nls.schwarz_step(prob, w.n_strips, u, g0=g, algorithm=algorithm, tol=tol, strips=st, Lh=Lh)
+        g = info.g
+        out.append((u.copy(), info))
+    return out
+
+
+SMALL = wl.scaled(wl.NLS_SMALL, 48, 37, n_strips=3, xl=-6.0, xr=6.0, yb=-5.0, yu=5.0, dt=0.02)
+WELL = wl.scaled(wl.NLS_WELL, 40, 45, n_strips=4, xl=-8.0, xr=8.0, yb=-8.0, yu=8.0, dt=0.02, p=3.0)
+
+
+@pytest.mark.parametrize("precision", [binding.FP64, binding.FP32_INNER])
+def test_classical_robin_matches_oracle(precision):
+    ref = run_oracle(SMALL, 3)
+    got = run_gpu(SMALL, 3, tol=TOL, precision=precision)
+    bound = 1e-11 if precision == binding.FP64 else 1e-10
+    for (ug, st), (uo, info) in zip(got, ref):
+        assert rel(ug, uo) < bound
+        assert abs(st["last_schwarz_iterations"] - info.iterations) <= 2
+
+
+@pytest.mark.parametrize("precision", [binding.FP64, binding.FP32_INNER])
+def test_preconditioned_robin_matches_oracle(precision):
+    ref = run_oracle(WELL, 2, algorithm="preconditioned")
+    got = run_gpu(WELL, 2, tol=TOL, precision=precision, algorithm=binding.PRECONDITIONED, gmres_tol=1e-12)
+    bound = 1e-11 if precision == binding.FP64 else 1e-10
+    for (ug, st), (uo, info) in zip(got, ref):
+        assert rel(ug, uo) < bound
+        assert st["last_schwarz_iterations"] <= info.iterations + 3
+
+
+def test_lh_blocks_match_oracle():
+    w = WELL
+    prob = oracle_problem(w)
+    st = nls.Strips(prob, w.n_strips)
+    X = st.strip_blocks(1)
+    with binding.Solver(gpu_params(w, algorithm=binding.PRECONDITIONED, nl_tol=1e-14), w.u0(), w.V()) as s:
+        B = s.blocks(1)
+    for k in range(4):
+        assert np.max(np.abs(B[k] - X[k])) < 1e-11 * max(1.0, np.max(np.abs(X[k])))
+
+
+def test_single_strip_is_the_monodomain_solve():
+    w = wl.scaled(SMALL, 20, 33, n_strips=1)
+    prob = oracle_problem(w)
+    u1, _, _ = nls.mono_step(prob, w.u0())
+    got = run_gpu(w, 1, tol=TOL)
+    assert rel(got[0][0], u1) < 1e-11
+
+
+def test_one_cell_strips_and_ragged_rows():
+    w = wl.scaled(SMALL, 6, 1, n_strips=6, yb=0.0, yu=0.5)       # c = 1, ny = 1
+    ref = run_oracle(w, 2)
+    got = run_gpu(w, 2, tol=TOL)
+    for (ug, _), (uo, _) in zip(got, ref):
+        assert rel(ug, uo) < 1e-11
+
+
+def test_neumann_mass_is_conserved_and_matches_oracle():
+    w = wl.scaled(SMALL, 36, 29, n_strips=3)
+    ref = run_oracle(w, 3, bc="neumann")
+    got = run_gpu(w, 3, tol=TOL, bc=binding.BC_NEUMANN)
+    prob = oracle_problem(w, bc="neumann")
+    m0 = nls.mass(prob, w.u0())
+    for (ug, st), (uo, _) in zip(got, ref):
+        assert rel(ug, uo) < 1e-11
+        assert abs(st["mass"] / m0 - 1.0) < 1e-12
+
+
+def test_random_interface_guess_reaches_the_same_step():
+    w = SMALL
+    rng = np.random.default_rng(5)
+    u0 = w.u0()
+    n = 2 * (w.n_strips - 1)
+    g_rand = rng.standard_normal((n, w.ny + 1)) + 1j * rng.standard_normal((n, w.ny + 1))
+    va = np.zeros_like(u0)
+    vb = np.zeros_like(u0)
+    with binding.Solver(gpu_params(w, tol=TOL), u0, w.V()) as s:
+        s.solve_interface(None, None, va)
+        s.solve_interface(np.ascontiguousarray(g_rand), None, vb)
+    assert rel(vb, va) < 1e-10
+
+
+def test_checkpoint_resume_is_bitwise():
+    w = SMALL
+    u0 = w.u0()
+    full = np.zeros_like(u0)
+    with binding.Solver(gpu_params(w, tol=TOL), u0, w.V()) as s:
+        s.step(4, full)
+    part = np.zeros_like(u0)
+    g = np.zeros((2 * (w.n_strips - 1), w.ny + 1), np.complex128)
+    with binding.Solver(gpu_params(w, tol=TOL), u0, w.V()) as s:
+        s.step(2)
+        n = s.get_state(part, g)
+    with binding.Solver(gpu_params(w, tol=TOL), u0, w.V()) as s2:
+        s2.set_state(part, g, n)
+        out = np.zeros_like(u0)
+        s2.step(2, out)
+    assert np.array_equal(out, full)
+
+
+def test_device_pointers_and_stream():
+    w = SMALL
+    dev = torch.device("cuda:0")
+    u0 = torch.from_numpy(w.u0()).to(dev)
+    V = torch.from_numpy(w.V()).to(dev)
+    out = torch.empty_like(u0)
+    stream = torch.cuda.Stream()
+    with binding.Solver(gpu_params(w, tol=TOL), u0, V, stream=stream) as s:
+        s.step(2, out)
+    host = run_gpu(w, 2, tol=TOL)[-1][0]
+    assert np.array_equal(out.cpu().numpy(), host)
+
+
+def test_nonfinite_input_is_reported_not_committed():
+    w = SMALL
+    u0 = w.u0()
+    u0[5, 7] = np.nan
+    with binding.Solver(gpu_params(w), u0, w.V()) as s:
+        with pytest.raises(binding.DDNLSError) as e:
+            s.step(1)
+        assert e.value.code == 5
+        assert s.get_state() == 0
+
+
+def test_iteration_cap_reports_enoconv():
+    w = SMALL
+    with binding.Solver(gpu_params(w, max_schwarz=2, tol=1e-14), w.u0(), w.V()) as s:
+        with pytest.raises(binding.DDNLSError) as e:
+            s.step(1)
+        assert e.value.code == 4
