@@ -1,0 +1,352 @@
+#!/usr/bin/env python3
+"""Benchmark: time steps/s of the optimized Schwarz time stepper on one GB300.
+
+Default workload (nls_well): NLS with a Gaussian well and focusing cubic term on (-32,32)^2,
+1024 x 1024 cells, 16 x-strips, preconditioned Schwarz (eq. algo_pd) with Robin p = 2,
+dt = 0.005, interface residual 1e-8.  The chosen form (FP32 inner Krylov, FP64 residuals and
+interface) is timed against the plain FP64 path on the same GPU.
+
+One "step" is one time step of eq. (CNS): every Schwarz iteration, strip solve, flux update
+and interface GMRES of that step.  Inputs are resident in HBM; L2 is flushed (a 512 MB
+write) before every timed step; each step is timed with CUDA events on the library's stream.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica (the path has no cross-GPU
+exchange on one node here), the slowest rank's time counts, and value = N*K / time.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time steps/s and stencil GB/s at 1e-8 interface residual, chosen vs plain FP64"
+
+# DRAM traffic of one strip-solver launch from the committed ncu summary
+# (profiles/strip_solve_nls_well.md), valid only for the source it was taken from.
+NCU_TRAFFIC = {"source_sha1": None, "bytes_per_launch": None}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="nls_well")
+    ap.add_argument("--p", type=float, default=2.0)
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--fp64-steps", type=int, default=4)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def solver_params(w, args, precision):
+    from paper_1603_05110_gb300 import binding
+    return dict(xl=w.xl, xr=w.xr, yb=w.yb, yu=w.yu, nx=w.nx, ny=w.ny, n_strips=w.n_strips, dt=w.dt,
+                lap=w.lap, kappa=w.kappa, p=args.p, tol=args.tol, nl_tol=1e-11, inner_tol=1e-4,
+                max_inner=4000, max_schwarz=400, gmres_tol=1e-6, gmres_restart=30, gmres_max=300,
+                algorithm=binding.PRECONDITIONED if w.algorithm == "preconditioned" else binding.CLASSICAL,
+                precision=precision, guess=binding.GUESS_PREVIOUS)
+
+
+def describe(w, args):
+    return (f"{w.name}: {w.nx}x{w.ny} cells on ({w.xl:g},{w.xr:g})x({w.yb:g},{w.yu:g}), {w.n_strips} strips, "
+            f"{w.algorithm} Schwarz, Robin p={args.p:g}, dt={w.dt:g}, interface tol {args.tol:g}")
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
+                                 f".clocks_{os.getpid()}.csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def source_sha1():
+    h = hashlib.sha1()
+    for f in ("strip_solver.cu", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1603_05110_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+# ------------------------------------------------------------------------- oracle timing
+def oracle_strip_sample(w, args, n_strips_timed):
+    """Wall time of the oracle's nonlinear strip solves of the first Schwarz iteration of step 1
+    (zero interface guess), for the first n_strips_timed strips."""
+    from oracle import nls
+    prob = nls.Problem(xl=w.xl, xr=w.xr, yb=w.yb, yu=w.yu, nx=w.nx, ny=w.ny, dt=w.dt, V=w.V(),
+                       kappa=w.kappa, lap=w.lap, p=args.p)
+    st = nls.Strips(prob, w.n_strips)
+    u0 = w.u0()
+    g = st.zero_g()
+    times = []
+    for j in range(n_strips_timed):
+        reg = st.regions[j]
+        l, r = st.data(g, j)
+        t0 = time.perf_counter()
+        reg.solve(reg.restrict(u0), l, r, tol=1e-11)
+        times.append(time.perf_counter() - t0)
+    return times
+
+
+def run_reference(args, rank):
+    """The oracle as it stands, on the host cores, on bounded samples of the same workload."""
+    from paper_1603_05110_gb300 import workloads as wl
+    w = wl.WORKLOADS[args.workload]
+    if rank != 0:
+        return
+    iters = ITERS_PER_STEP.get(args.workload)
+    samples = []
+    for k in range(args.warmup + args.steps):
+        t = oracle_strip_sample(w, args, 1)[0]
+        if k >= args.warmup:
+            samples.append(t)
+    t_strip = statistics.mean(samples)
+    step_s = t_strip * w.n_strips * iters
+    value = 1.0 / step_s
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": describe(w, args)},
+            "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                             "sample": f"each step = one oracle nonlinear strip solve (strip 1 of {w.n_strips}, "
+                                       f"Schwarz iteration 1, step 1), scaled by {w.n_strips} strips x {iters} "
+                                       f"Schwarz iterations per step (the GPU arm's measured mean)"},
+            "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# Schwarz iterations per step of the chosen form, measured by this benchmark on a GB300
+# (used to scale the oracle's per-strip sample to steps/s).
+ITERS_PER_STEP = {"nls_well": 5.0, "nls_small": 20.0, "gpe_trap": 5.0}
+
+
+# ---------------------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_1603_05110_gb300 import binding, build, workloads as wl
+    if not os.path.exists(binding.LIB_PATH):
+        build.build()
+    binding.load()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev) if "device_id" in dist.init_process_group.__code__.co_varnames \
+            else dist.init_process_group("nccl")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    w = wl.WORKLOADS[args.workload]
+    u0 = torch.from_numpy(w.u0()).to(dev)
+    V = torch.from_numpy(w.V()).to(dev)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def timed_steps(solver, k, profile=False):
+        if profile:
+            solver.set_profiling(True)
+        ms, stats = [], []
+        for _ in range(k):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            stats.append(solver.step(1))
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        prof = solver.profile() if profile else None
+        return ms, stats, prof
+
+    # ---- chosen form: FP32 inner Krylov + FP64 residuals / interface
+    chosen = binding.Solver(solver_params(w, args, binding.FP32_INNER), u0, V, stream=stream)
+    for _ in range(args.warmup):
+        chosen.step(1)
+    barrier()
+    clocks = Clocks(local_rank)
+    barrier()
+    ms, stats, prof = timed_steps(chosen, args.steps, profile=True)
+    barrier()
+    clk = clocks.stop()
+    total_ms = sum(ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms * 1e-3)
+    iters = [s["last_schwarz_iterations"] for s in stats]
+    kry = sum(s["krylov_iterations"] for s in stats)
+
+    # ---- e2e through the C-ABI with host buffers (pinned): H2D of u_{n-1}, step, D2H of u_n
+    uh_in = torch.empty(w.ny + 1, w.nx + 1, dtype=torch.complex128, pin_memory=True)
+    uh_out = torch.empty_like(uh_in)
+    step_no = chosen.get_state(uh_in)
+    e2e_ms = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        chosen.set_state(uh_in, None, step_no)
+        chosen.step(1, uh_out)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        step_no += 1
+        uh_in.copy_(uh_out)
+    chosen.close()
+    node_bytes = 16 * (w.nx + 1) * (w.ny + 1)
+
+    # ---- plain FP64 on the same GPU, and the accuracy of the chosen form against it
+    fp64 = None
+    err = None
+    if not args.no_fp64 and rank == 0:
+        plain = binding.Solver(solver_params(w, args, binding.FP64), u0, V, stream=stream)
+        for _ in range(max(1, args.warmup - 1)):
+            plain.step(1)
+        ms64, st64, prof64 = timed_steps(plain, args.fp64_steps, profile=True)
+        plain.close()
+        fp64 = {"value": args.fp64_steps / (sum(ms64) * 1e-3), "unit": "steps/s",
+                "ms_per_step": sum(ms64) / args.fp64_steps,
+                "schwarz_iterations_per_step": statistics.mean(s["last_schwarz_iterations"] for s in st64),
+                "strip_solve_gbs": prof64["strip_solve_bytes"] / (prof64["strip_solve_ms"] * 1e-3) / 1e9,
+                "strip_solve_gflops": prof64["strip_solve_flops"] / (prof64["strip_solve_ms"] * 1e-3) / 1e9}
+        # same number of steps from u0 in both forms
+        nchk = 3
+        ua = torch.empty_like(u0)
+        ub = torch.empty_like(u0)
+        with binding.Solver(solver_params(w, args, binding.FP32_INNER), u0, V, stream=stream) as s:
+            s.step(nchk, ua)
+        with binding.Solver(solver_params(w, args, binding.FP64), u0, V, stream=stream) as s:
+            s.step(nchk, ub)
+        err = float(torch.linalg.vector_norm(ua - ub) / torch.linalg.vector_norm(ub))
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    peaks, peak_kind = measured_peaks()
+    launches = prof["strip_solve_launches"]
+    per_launch_ms = prof["strip_solve_ms"] / launches
+    per_launch_bytes = prof["strip_solve_bytes"] / launches
+    achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
+    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["source_sha1"] == source_sha1() else None
+    roofline = {"kernel": "strip_solve_kernel<float>", "bound": "hbm", "achieved": achieved,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs",
+                "share_of_step": prof["strip_solve_ms"] / total_ms * world,
+                "note": "algorithmic bytes per node per phase (R, A, B, epilogue) x nodes x phase counts; "
+                        "the step's fields (~90 MB) fit in the 129 MB L2, so this is effective bandwidth"}
+
+    cpu = None
+    if not args.no_cpu and world == 1:
+        ts = oracle_strip_sample(w, args, 2)
+        t_strip = statistics.mean(ts)
+        ips = statistics.mean(iters)
+        cpu_v = 1.0 / (t_strip * w.n_strips * ips)
+        cpu = {"value": cpu_v, "unit": "steps/s", "cores": 1, "kind": "oracle",
+               "sample": f"oracle nonlinear solves of strips 1-2 of {w.n_strips} (Schwarz iteration 1 of step 1, "
+                         f"{statistics.mean(ts):.2f} s each), scaled by {w.n_strips} strips x {ips:.1f} Schwarz "
+                         f"iterations per step (this run's mean); L_h setup and GMRES not included"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner Krylov + f64 residual/interface",
+        "data": "synthetic",
+        "config": {"workload": describe(w, args), "form": "chosen: FP32-inner/FP64-refine, preconditioned",
+                   "l2": "flushed (512 MB write) before every timed step", "replicas": world},
+        "stencil_gbs": achieved,
+        "schwarz_iterations_per_step": statistics.mean(iters),
+        "krylov_iterations_per_step": kry / args.steps,
+        "plain_fp64": fp64,
+        "speedup_vs_plain_fp64": (value / world) / fp64["value"] if fp64 else None,
+        "rel_l2_chosen_vs_fp64": err,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * args.steps / (sum(e2e_ms) * 1e-3), "unit": "steps/s",
+                "h2d_bytes_per_step": node_bytes, "d2h_bytes_per_step": node_bytes},
+        "gpu_launches": prof["kernel_launches"],
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

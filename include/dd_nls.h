@@ -111,6 +111,7 @@ typedef struct {
     double strip_solve_flops;
     double interface_ms;          /* traces, residuals, GMRES, L_h products */
     double other_ms;              /* right sides, commit, diagnostics */
+    long long kernel_launches;    /* all kernels this handle launched while profiling was on */
 } dd_nls_profile;
 
 /* Fill *p with defaults: NLS (lap=1, kappa=1), Robin p=1, classical, FP64, previous-step

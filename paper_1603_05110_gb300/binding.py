@@ -56,6 +56,7 @@ class Profile(ctypes.Structure):
         ("strip_solve_ms", ctypes.c_double), ("strip_solve_launches", ctypes.c_longlong),
         ("strip_solve_bytes", ctypes.c_double), ("strip_solve_flops", ctypes.c_double),
         ("interface_ms", ctypes.c_double), ("other_ms", ctypes.c_double),
+        ("kernel_launches", ctypes.c_longlong),
     ]
 
     def as_dict(self):

@@ -65,7 +65,8 @@ struct dd_nls {
     bool have_prev = false;
     std::string error;
     bool prof = false;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    long long launch_base = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
     dd_nls_profile profile{};
     double setup_ms = 0.0;
 };
@@ -113,7 +114,25 @@ static void release(dd_nls* h) {
     if (h->hred) cudaFreeHost(h->hred);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
+    if (h->ev2) cudaEventDestroy(h->ev2);
+    if (h->ev3) cudaEventDestroy(h->ev3);
 }
+
+// Device time of a section of stream work, added to *acc when profiling is on.
+struct ProfScope {
+    dd_nls* h;
+    double* acc;
+    ProfScope(dd_nls* hh, double* a) : h(hh), acc(a) {
+        if (h->prof) cudaEventRecord(h->ev2, h->s);
+    }
+    ~ProfScope() {
+        if (!h->prof) return;
+        cudaEventRecord(h->ev3, h->s);
+        cudaEventSynchronize(h->ev3);
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->ev2, h->ev3) == cudaSuccess) *acc += ms;
+    }
+};
 
 // ------------------------------------------------------------------------ IO
 static int upload_nodal(dd_nls* h, const double* src, int ptr_kind, double2* strips) {
@@ -427,8 +446,11 @@ static int gmres(dd_nls* h, const double2* b, double2* x, long long* its_out) {
 // On success h->zeta holds v and h->gconv the converged R(g).
 static int schwarz(dd_nls* h, dd_nls_stats* st) {
     const Geom& G = h->G;
-    CK(launch_rhs0(G, h->u, h->rhs0, h->s));
-    CK(cudaMemcpyAsync(h->zeta, h->u, h->nfield * sizeof(double2), cudaMemcpyDeviceToDevice, h->s));   // zeta^0 = h
+    {
+        ProfScope ps(h, &h->profile.other_ms);
+        CK(launch_rhs0(G, h->u, h->rhs0, h->s));
+        CK(cudaMemcpyAsync(h->zeta, h->u, h->nfield * sizeof(double2), cudaMemcpyDeviceToDevice, h->s));   // zeta^0 = h
+    }
     StripSolveArgs a = base_args(h);
     double2* g = h->gA;
     double2* gn = h->gB;
@@ -438,6 +460,7 @@ static int schwarz(dd_nls* h, dd_nls_stats* st) {
         if (rc) return rc;
         int nb = 1;
         if (G.N > 1) {
+            ProfScope ps(h, &h->profile.interface_ms);
             CK(launch_traces(G, h->zeta, g, gn, h->part, &nb, h->s));
             CK(launch_finalize(h->part, nb, 2, h->red, h->s));
             CK(cudaMemcpyAsync(h->hred, h->red, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->s));
@@ -463,7 +486,8 @@ static int schwarz(dd_nls* h, dd_nls_stats* st) {
         if (h->P.algorithm == DD_NLS_CLASSICAL) {
             std::swap(g, gn);                     // g^{k+1} = R(g^k)
         } else {
-            // g^{k+1} = g^k - P^{-1} (g^k - R(g^k))  (eq. algo_pd, reading D10)
+            // g^{k+1} = g^k - P^{-1} (g^k - R(g^k))  (eq. algo_pd)
+            ProfScope ps(h, &h->profile.interface_ms);
             CK(launch_sub(h->tmp, g, gn, h->nI, h->s));
             CK(launch_copy(gn, h->tmp, h->nI, h->s));          // gn := y
             long long its = 0;
@@ -490,6 +514,7 @@ static int load_guess(dd_nls* h, const double* g0, int ptr_kind) {
 }
 
 static int diagnostics(dd_nls* h, dd_nls_stats* st) {
+    ProfScope ps(h, &h->profile.other_ms);
     int nb = 1;
     CK(launch_diagnostics(h->G, h->u, h->Wn, h->part, &nb, h->s));
     CK(launch_finalize(h->part, nb, 2, h->red, h->s));
@@ -576,6 +601,8 @@ extern "C" int dd_nls_create(const dd_nls_params* p, const double* V, const doub
     CKC(cudaMallocHost((void**)&h->hred, 256 * sizeof(double)));
     CKC(cudaEventCreate(&h->ev0));
     CKC(cudaEventCreate(&h->ev1));
+    CKC(cudaEventCreate(&h->ev2));
+    CKC(cudaEventCreate(&h->ev3));
     h->h_status.resize(G.N);
     h->h_nl.resize(G.N);
     h->h_kry.resize(G.N);
@@ -613,7 +640,10 @@ extern "C" int dd_nls_step(dd_nls* h, int nsteps, double* u_out, int ptr_kind, d
         if (rc) return rc;
         rc = schwarz(h, st);
         if (rc) return rc;
-        CK(launch_commit(h->G, h->zeta, h->u, h->s));
+        {
+            ProfScope ps(h, &h->profile.other_ms);
+            CK(launch_commit(h->G, h->zeta, h->u, h->s));
+        }
         h->have_prev = true;
         h->step += 1;
         if (st) st->steps += 1;
@@ -676,12 +706,14 @@ extern "C" int dd_nls_set_profiling(dd_nls* h, int on) {
     if (!h) return fail(nullptr, DD_NLS_EINVAL, "dd_nls_set_profiling: NULL handle");
     h->prof = on != 0;
     std::memset(&h->profile, 0, sizeof(h->profile));
+    h->launch_base = kernel_launch_count();
     return DD_NLS_OK;
 }
 
 extern "C" int dd_nls_get_profile(dd_nls* h, dd_nls_profile* prof) {
     if (!h || !prof) return fail(h, DD_NLS_EINVAL, "dd_nls_get_profile: NULL argument");
     *prof = h->profile;
+    prof->kernel_launches = h->prof ? kernel_launch_count() - h->launch_base : 0;
     return DD_NLS_OK;
 }
 

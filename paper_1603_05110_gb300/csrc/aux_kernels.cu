@@ -45,14 +45,17 @@ __global__ void gather_u_kernel(Geom g, const double2* __restrict__ in, double2*
 }
 
 cudaError_t launch_scatter_u(const Geom& g, const double2* glob, double2* strips, cudaStream_t s) {
+    count_launches(1);
     scatter_u_kernel<<<1024, 256, 0, s>>>(g, glob, strips);
     return cudaGetLastError();
 }
 cudaError_t launch_scatter_real(const Geom& g, const double* glob, double scale, double* strips, cudaStream_t s) {
+    count_launches(1);
     scatter_real_kernel<<<1024, 256, 0, s>>>(g, glob, scale, strips);
     return cudaGetLastError();
 }
 cudaError_t launch_gather_u(const Geom& g, const double2* strips, double2* glob, cudaStream_t s) {
+    count_launches(1);
     gather_u_kernel<<<1024, 256, 0, s>>>(g, strips, glob);
     return cudaGetLastError();
 }
@@ -84,6 +87,7 @@ __global__ void rhs0_kernel(Geom g, const double2* __restrict__ h, double2* __re
     }
 }
 cudaError_t launch_rhs0(const Geom& g, const double2* h, double2* rhs0, cudaStream_t s) {
+    count_launches(1);
     rhs0_kernel<<<1024, 256, 0, s>>>(g, h, rhs0);
     return cudaGetLastError();
 }
@@ -123,6 +127,7 @@ cudaError_t launch_traces(const Geom& g, const double2* zeta, const double2* gtr
     int nb = nblocks(total, 256);
     if (nb > 512) nb = 512;
     if (nb < 1) nb = 1;
+    count_launches(1);
     traces_kernel<<<nb, 256, 0, s>>>(g, zeta, gtr, gnew, part);
     *nblk_out = nb;
     return cudaGetLastError();
@@ -138,6 +143,7 @@ __global__ void finalize_kernel(const double* __restrict__ part, int nblk, int n
         for (int k = 0; k < nv; ++k) out[k] = v[k];
 }
 cudaError_t launch_finalize(const double* part, int nblk, int nv, double* out, cudaStream_t s) {
+    count_launches(1);
     finalize_kernel<<<1, 256, 0, s>>>(part, nblk, nv, out);
     return cudaGetLastError();
 }
@@ -161,6 +167,7 @@ __global__ void commit_kernel(Geom g, const double2* __restrict__ zeta, double2*
     }
 }
 cudaError_t launch_commit(const Geom& g, const double2* zeta, double2* u, cudaStream_t s) {
+    count_launches(1);
     commit_kernel<<<1024, 256, 0, s>>>(g, zeta, u);
     return cudaGetLastError();
 }
@@ -205,6 +212,7 @@ __global__ void diagnostics_kernel(Geom g, const double2* __restrict__ u, const 
 }
 cudaError_t launch_diagnostics(const Geom& g, const double2* u, const double* Wn, double* part, int* nblk_out,
                                cudaStream_t s) {
+    count_launches(1);
     diagnostics_kernel<<<512, 256, 0, s>>>(g, u, Wn, part);
     *nblk_out = 512;
     return cudaGetLastError();
@@ -240,6 +248,7 @@ __global__ void extract_blocks_kernel(Geom g, const double2* __restrict__ zeta, 
 }
 cudaError_t launch_extract_blocks(const Geom& g, const double2* zeta, int nvirt, int unit_base, double2* X,
                                   cudaStream_t s) {
+    count_launches(1);
     extract_blocks_kernel<<<nblocks((long long)nvirt * g.nyn, 256) < 4096 ? nblocks((long long)nvirt * g.nyn, 256) : 4096, 256, 0, s>>>(
         g, zeta, nvirt, unit_base, X);
     return cudaGetLastError();
@@ -250,6 +259,7 @@ __global__ void convert_kernel(const double2* __restrict__ X, float2* __restrict
         Xf[t] = make_float2((float)X[t].x, (float)X[t].y);
 }
 cudaError_t launch_convert_blocks(const double2* X, float2* Xf, long long n, cudaStream_t s) {
+    count_launches(1);
     convert_kernel<<<2048, 256, 0, s>>>(X, Xf, n);
     return cudaGetLastError();
 }
@@ -309,6 +319,7 @@ cudaError_t launch_apply_P(const Geom& g, const void* X, bool fp32, const int* b
     const long long total = (long long)2 * (g.N - 1) * g.nyn;
     int nb = nblocks(total * 32, 256);
     if (nb > 8192) nb = 8192;
+    count_launches(1);
     if (fp32)
         apply_P_kernel<float2><<<nb, 256, 0, s>>>(g, (const float2*)X, btype_dev, x, y);
     else
@@ -350,7 +361,9 @@ cudaError_t launch_dots(const double2* V, long long ld, int k, const double2* w,
                         double* scratch, cudaStream_t s) {
     int nb = nblocks(n, 256);
     if (nb > 128) nb = 128;
+    count_launches(1);
     dots_partial_kernel<<<dim3(nb, k), 256, 0, s>>>(V, ld, w, n, scratch);
+    count_launches(1);
     dots_final_kernel<<<k, 128, 0, s>>>(scratch, nb, out);
     return cudaGetLastError();
 }
@@ -372,6 +385,7 @@ cudaError_t launch_axpy_multi(const double2* V, long long ld, int k, const doubl
                               cudaStream_t s) {
     int nb = nblocks(n, 256);
     if (nb > 2048) nb = 2048;
+    count_launches(1);
     axpy_multi_kernel<<<nb, 256, 0, s>>>(V, ld, k, h, w, n);
     return cudaGetLastError();
 }
@@ -396,7 +410,9 @@ __global__ void nrm2_final_kernel(const double* __restrict__ scratch, int nb, do
 cudaError_t launch_nrm2(const double2* w, long long n, double* out, double* scratch, cudaStream_t s) {
     int nb = nblocks(n, 256);
     if (nb > 128) nb = 128;
+    count_launches(1);
     nrm2_partial_kernel<<<nb, 256, 0, s>>>(w, n, scratch);
+    count_launches(1);
     nrm2_final_kernel<<<1, 128, 0, s>>>(scratch, nb, out);
     return cudaGetLastError();
 }
@@ -409,6 +425,7 @@ __global__ void scale_kernel(double2* __restrict__ y, const double2* __restrict_
 cudaError_t launch_scale(double2* y, const double2* x, const double* inv_from, long long n, cudaStream_t s) {
     int nb = nblocks(n, 256);
     if (nb > 2048) nb = 2048;
+    count_launches(1);
     scale_kernel<<<nb, 256, 0, s>>>(y, x, inv_from, n);
     return cudaGetLastError();
 }
@@ -419,6 +436,7 @@ __global__ void sub_kernel(double2* __restrict__ y, const double2* __restrict__ 
 cudaError_t launch_sub(double2* y, const double2* a, const double2* b, long long n, cudaStream_t s) {
     int nb = nblocks(n, 256);
     if (nb > 2048) nb = 2048;
+    count_launches(1);
     sub_kernel<<<nb, 256, 0, s>>>(y, a, b, n);
     return cudaGetLastError();
 }

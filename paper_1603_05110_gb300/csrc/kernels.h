@@ -6,6 +6,10 @@
 
 namespace ddnls {
 
+// Kernels launched by this library since load (every launch_* wrapper adds its count).
+long long kernel_launch_count();
+void count_launches(int n);
+
 struct StripSolveArgs {
     Geom g;
     int bps;                 // blocks per strip

@@ -22,7 +22,13 @@
 #include "common.cuh"
 #include "kernels.h"
 
+#include <atomic>
+
 namespace ddnls {
+
+static std::atomic<long long> g_launches{0};
+long long kernel_launch_count() { return g_launches.load(); }
+void count_launches(int n) { g_launches += n; }
 
 // y = A(c) v at one node: the 9-point Q1 stencil of Bx (x) My - Mx (x) Ky + diag(c), with
 // Bx = -Kx + i (alpha Mx + p E_x) and E_x the Robin edges of the strip (eq. NproblemRobinNL).
@@ -295,6 +301,7 @@ static cudaError_t launch_strip_solve_t(const StripSolveArgs& args, int nstrips,
     StripSolveArgs a = args;
     void* params[] = {&a};
     dim3 grid(nstrips * a.bps), block(256);
+    count_launches(1);
     return cudaLaunchCooperativeKernel((const void*)strip_solve_kernel<T>, grid, block, params, 0, s);
 }
 

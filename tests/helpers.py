@@ -15,6 +15,6 @@ def oracle_problem(w, V=None, tc="robin", bc="same", m=4):
 
 def gpu_params(w, **kw):
     d = dict(xl=w.xl, xr=w.xr, yb=w.yb, yu=w.yu, nx=w.nx, ny=w.ny, n_strips=w.n_strips, dt=w.dt,
-             lap=w.lap, kappa=w.kappa, p=w.p)
+             lap=w.lap, kappa=w.kappa, p=w.p, nl_tol=1e-14, max_schwarz=5000)
     d.update(kw)
     return d
