@@ -223,6 +223,8 @@ static StripSolveArgs base_args(dd_nls* h) {
     a.nl_tol = h->P.nl_tol;
     a.inner_tol = h->P.inner_tol;
     a.inner_floor = 0.1 * h->P.nl_tol;
+    a.bscale = h->red + 8;
+    a.nl_floor_frac = h->P.nl_tol / std::sqrt((double)h->G.N);
     a.max_nl = h->P.max_nl;
     a.max_inner = h->P.max_inner;
     a.part = h->part;
@@ -307,7 +309,7 @@ static int build_Lh(dd_nls* h) {
             a.unit_base = ub;
             a.unit_ltc = types[t].first;
             a.unit_rtc = types[t].second;
-            a.zeta = vz; a.rhs0 = nullptr; a.Wn = nullptr; a.gtr = nullptr;
+            a.zeta = vz; a.rhs0 = nullptr; a.Wn = nullptr; a.gtr = nullptr; a.bscale = nullptr;
             a.x = vx; a.r = vr; a.z = vzz; a.p = vp; a.q = vq; a.cT = vc;
             a.bar = vbar; a.status = vstat; a.nl_its = vnl; a.kry_its = vkry; a.nl_res = vres; a.part = vpart;
             e = cudaMemsetAsync(vz, 0, nv * per_strip * sizeof(double2), h->s);
@@ -448,7 +450,10 @@ static int schwarz(dd_nls* h, dd_nls_stats* st) {
     const Geom& G = h->G;
     {
         ProfScope ps(h, &h->profile.other_ms);
-        CK(launch_rhs0(G, h->u, h->rhs0, h->s));
+        int nb = 1;
+        CK(launch_rhs0(G, h->u, h->rhs0, h->part, &nb, h->s));
+        CK(launch_finalize(h->part, nb, 1, h->red + 8, h->s));
+        CK(launch_sqrt(h->red + 8, h->s));
         CK(cudaMemcpyAsync(h->zeta, h->u, h->nfield * sizeof(double2), cudaMemcpyDeviceToDevice, h->s));   // zeta^0 = h
     }
     StripSolveArgs a = base_args(h);

@@ -62,8 +62,10 @@ cudaError_t launch_gather_u(const Geom& g, const double2* strips, double2* glob,
 
 // ------------------------------------------------------------- step right side
 // rhs0 = (2i/dt) M h on every strip (eq. NproblemRobinNL), M = Mx (x) My of the strip.
-__global__ void rhs0_kernel(Geom g, const double2* __restrict__ h, double2* __restrict__ rhs) {
+__global__ void rhs0_kernel(Geom g, const double2* __restrict__ h, double2* __restrict__ rhs, double* __restrict__ part) {
+    __shared__ double sm[64];
     const int c = g.nxs - 1, ny = g.nyn - 1;
+    double nv[1] = {0.0};
     const long long total = (long long)g.N * g.nxs * g.nyn;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
         const int iy = (int)(t % g.nyn);
@@ -84,11 +86,15 @@ __global__ void rhs0_kernel(Geom g, const double2* __restrict__ h, double2* __re
             }
         }
         rhs[idx] = make_double2(-g.alpha * acc.y, g.alpha * acc.x);
+        nv[0] += g.alpha * g.alpha * (acc.x * acc.x + acc.y * acc.y);
     }
+    block_sum<1>(nv, sm);
+    if (threadIdx.x == 0) part[blockIdx.x * 4] = nv[0];
 }
-cudaError_t launch_rhs0(const Geom& g, const double2* h, double2* rhs0, cudaStream_t s) {
+cudaError_t launch_rhs0(const Geom& g, const double2* h, double2* rhs0, double* part, int* nblk_out, cudaStream_t s) {
     count_launches(1);
-    rhs0_kernel<<<1024, 256, 0, s>>>(g, h, rhs0);
+    rhs0_kernel<<<512, 256, 0, s>>>(g, h, rhs0, part);
+    *nblk_out = 512;
     return cudaGetLastError();
 }
 
@@ -145,6 +151,13 @@ __global__ void finalize_kernel(const double* __restrict__ part, int nblk, int n
 cudaError_t launch_finalize(const double* part, int nblk, int nv, double* out, cudaStream_t s) {
     count_launches(1);
     finalize_kernel<<<1, 256, 0, s>>>(part, nblk, nv, out);
+    return cudaGetLastError();
+}
+
+__global__ void sqrt_kernel(double* v) { v[0] = sqrt(v[0]); }
+cudaError_t launch_sqrt(double* v, cudaStream_t s) {
+    count_launches(1);
+    sqrt_kernel<<<1, 1, 0, s>>>(v);
     return cudaGetLastError();
 }
 

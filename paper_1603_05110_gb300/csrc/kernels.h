@@ -23,6 +23,8 @@ struct StripSolveArgs {
     void *x, *r, *z, *p, *q; // inner Krylov vectors (float2 or double2)
     void* cT;                // c = w (W + kappa|zeta|^2) in inner precision
     double nl_tol, inner_tol, inner_floor;
+    const double* bscale;    // ||(2i/dt) M u_{n-1}|| over all strips (device scalar), or NULL
+    double nl_floor_frac;    // strips stop once ||res|| <= nl_floor_frac * (*bscale)
     int max_nl, max_inner;
     double* part;            // [4][gridDim][4] partial sums
     unsigned* bar;           // [strips] barrier counters, zeroed before the launch
@@ -43,11 +45,13 @@ using AuxGeom = Geom;
 cudaError_t launch_scatter_u(const AuxGeom& g, const double2* glob, double2* strips, cudaStream_t s);
 cudaError_t launch_gather_u(const AuxGeom& g, const double2* strips, double2* glob, cudaStream_t s);
 cudaError_t launch_scatter_real(const AuxGeom& g, const double* glob, double scale, double* strips, cudaStream_t s);
-// rhs0 = i alpha M h (per strip)
-cudaError_t launch_rhs0(const AuxGeom& g, const double2* h, double2* rhs0, cudaStream_t s);
+// rhs0 = i alpha M h (per strip); partial sums of ||rhs0||^2 into part[nblk][1]
+cudaError_t launch_rhs0(const AuxGeom& g, const double2* h, double2* rhs0, double* part, int* nblk_out, cudaStream_t s);
 // interface flux update, eq. (fluxlr), Robin: writes gnew, partial norms into part[nblk][2]
 cudaError_t launch_traces(const AuxGeom& g, const double2* zeta, const double2* gtr, double2* gnew,
                           double* part, int* nblk_out, cudaStream_t s);
+// v[0] = sqrt(v[0]) on the device
+cudaError_t launch_sqrt(double* v, cudaStream_t s);
 // sum part[nblk][k] (k < nv) in fixed order into out[k]
 cudaError_t launch_finalize(const double* part, int nblk, int nv, double* out, cudaStream_t s);
 // u_n = 2 zeta - u_{n-1}, interface columns from the left strip

@@ -10,7 +10,11 @@
 //     res = b - A(c) zeta   (FP64, matrix-free 9-point Q1 stencil),
 //     A(c) delta = res      (Jacobi-preconditioned COCG in precision T),
 //     zeta += delta,
-// until ||res|| <= nl_tol ||b||.  With an exact inner solve one correction is exactly one
+// until ||res|| <= max(nl_tol ||b||, floor) (floor: a fraction of the whole step's right side,
+// so strips that hold almost nothing of the solution stop early).  The inner system is solved
+// for res / s with s the previous residual norm, so FP32 never sees values below its range
+// (far-field strips can hold values near 1e-111).  With an exact inner solve one correction is
+// exactly one
 // step zeta^q = A(c(zeta^{q-1}))^{-1} b of eq. (localpbrobin); the limit is the same fixed
 // point.  A(c) is complex symmetric, so COCG (CG with the unconjugated bilinear form)
 // applies.
@@ -157,7 +161,33 @@ strip_solve_kernel(StripSolveArgs a) {
         return t;
     };
 
-    for (;; ++nl_it) {
+    // ---------------- ||b|| of the strip, b = (2i/dt) M h - M^Gamma Q^T (l; r)
+    double bnorm;
+    {
+        double lb[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int ch = rank; ch < nchunks; ch += bps) {
+            const int n = ch * blockDim.x + threadIdx.x;
+            if (n >= Ns) continue;
+            int ix, iy;
+            split_node(n, nyn, inv_nyn, ix, iy);
+            const long long idx = (long long)ix * P + iy;
+            const Coef1<double> cy = coef1<double>(iy, ny, g.hy);
+            double2 b = rhs0 ? rhs0[idx] : make_double2(0.0, 0.0);
+            b = csub(b, edge_term(ix, iy, cy));
+            lb[0] += b.x * b.x + b.y * b.y;
+        }
+        block_sum<4>(lb, s_red);
+        if (threadIdx.x == 0) { double* sp = slot_ptr(epoch + 1); sp[0] = lb[0]; sp[1] = 0; sp[2] = 0; sp[3] = 0; }
+        ++epoch;
+        if (!group_barrier(bar, epoch * bps, a.err, &s_flag)) status = DD_NLS_ETIMEOUT;
+        double tb[4];
+        group_sum<4>(group_ptr(epoch), bps, tb, s_red);
+        bnorm = sqrt(tb[0]);
+    }
+    const double floor_abs = a.bscale ? a.nl_floor_frac * (*(volatile const double*)a.bscale) : 0.0;
+    double inv_s = bnorm > 0.0 ? 1.0 / bnorm : 1.0;      // scale of the inner system
+
+    for (; status == 0; ++nl_it) {
         // ---------------- phase R: coefficients c = w (W + kappa|zeta|^2) and FP64 residual
         double loc[4] = {0.0, 0.0, 0.0, 0.0};   // ||res||^2, ||b||^2, rho = r^T z (re, im)
         for (int ch = rank; ch < nchunks; ch += bps) {
@@ -178,7 +208,7 @@ strip_solve_kernel(StripSolveArgs a) {
             loc[0] += res.x * res.x + res.y * res.y;
             loc[1] += b.x * b.x + b.y * b.y;
             const Coef1<T> cxT = coef1<T>(ix, c, g.hx), cyT = coef1<T>(iy, ny, g.hy);
-            const T2 rT = cfrom<T2>(res);
+            const T2 rT = cfrom<T2>(make_double2(res.x * inv_s, res.y * inv_s));
             const T2 di = diag_inv<T>(cxT, cyT, alphaT, (T)rb, (T)cdiag);
             const T2 zT = cmul(di, rT);
             cT[idx] = (T)cdiag;
@@ -196,17 +226,17 @@ strip_solve_kernel(StripSolveArgs a) {
         if (!group_barrier(bar, epoch * bps, a.err, &s_flag)) { status = DD_NLS_ETIMEOUT; break; }
         double tot[4];
         group_sum<4>(group_ptr(epoch), bps, tot, s_red);
-        const double bnorm = sqrt(tot[1]);
         const double rnorm = sqrt(tot[0]);
         nres = bnorm > 0.0 ? rnorm / bnorm : rnorm;
         if (!isfinite(tot[0]) || !isfinite(tot[1])) { status = DD_NLS_ENONFINITE; break; }
-        if (nres <= a.nl_tol || rnorm == 0.0) break;
+        if (nres <= a.nl_tol || rnorm <= floor_abs || rnorm == 0.0) break;
         if (nl_it >= a.max_nl) { status = DD_NLS_ENOCONV; break; }
 
         // ---------------- inner COCG on A(c) delta = res, Jacobi preconditioner
         double rho_re = tot[2], rho_im = tot[3];
         double beta_re = 0.0, beta_im = 0.0;
-        const double target = fmax(a.inner_tol * rnorm, a.inner_floor * bnorm);
+        // inner stopping test in the scaled units of r
+        const double target = fmax(a.inner_tol * rnorm, fmax(a.inner_floor * bnorm, 0.1 * floor_abs)) * inv_s;
         for (int it = 0; it < a.max_inner; ++it) {
             // phase A: q = A z + beta q, p = z + beta p, partial mu = p^T q
             double lm[4] = {0.0, 0.0, 0.0, 0.0};
@@ -283,8 +313,11 @@ strip_solve_kernel(StripSolveArgs a) {
             int ix, iy;
             split_node(n, nyn, inv_nyn, ix, iy);
             const long long idx = (long long)ix * P + iy;
-            zeta[idx] = cadd(zeta[idx], cd(x[idx]));
+            const double2 dx = cd(x[idx]);
+            const double sc = 1.0 / inv_s;
+            zeta[idx] = make_double2(zeta[idx].x + sc * dx.x, zeta[idx].y + sc * dx.y);
         }
+        inv_s = 1.0 / rnorm;           // scale of the next correction
         ++epoch;
         if (!group_barrier(bar, epoch * bps, a.err, &s_flag)) { status = DD_NLS_ETIMEOUT; break; }
     }
