@@ -108,9 +108,10 @@ def load(path=LIB_PATH):
 
 
 class DDNLSError(RuntimeError):
-    def __init__(self, code, msg):
+    def __init__(self, code, msg, stats=None):
         super().__init__(f"{STATUS.get(code, code)}: {msg}")
         self.code = code
+        self.stats = stats          # the call's statistics up to the failure, when it has any
 
 
 def default_params(**kw):
@@ -172,14 +173,15 @@ class Solver:
             raise DDNLSError(rc, self.lib.dd_nls_last_error(None).decode())
         self.h = h
 
-    def _check(self, rc):
+    def _check(self, rc, stats=None):
         if rc != 0:
-            raise DDNLSError(rc, self.lib.dd_nls_last_error(self.h).decode())
+            raise DDNLSError(rc, self.lib.dd_nls_last_error(self.h).decode(),
+                             stats.as_dict() if stats is not None else None)
 
     def step(self, nsteps=1, u_out=None):
         st = Stats()
         pu, ku = _ptr(u_out, writable=True)
-        self._check(self.lib.dd_nls_step(self.h, nsteps, pu, _kind(ku), ctypes.byref(st)))
+        self._check(self.lib.dd_nls_step(self.h, nsteps, pu, _kind(ku), ctypes.byref(st)), st)
         return st.as_dict()
 
     def solve_interface(self, g0=None, g_out=None, v_out=None):
@@ -187,7 +189,7 @@ class Solver:
         p0, k0 = _ptr(g0)
         pg, kg = _ptr(g_out, writable=True)
         pv, kv = _ptr(v_out, writable=True)
-        self._check(self.lib.dd_nls_solve_interface(self.h, p0, pg, pv, _kind(k0, kg, kv), ctypes.byref(st)))
+        self._check(self.lib.dd_nls_solve_interface(self.h, p0, pg, pv, _kind(k0, kg, kv), ctypes.byref(st)), st)
         return st.as_dict()
 
     def get_state(self, u=None, g=None):

@@ -224,7 +224,7 @@ static StripSolveArgs base_args(dd_nls* h) {
     a.inner_tol = h->P.inner_tol;
     a.inner_floor = 0.1 * h->P.nl_tol;
     a.bscale = h->red + 8;
-    a.nl_floor_frac = h->P.nl_tol / std::sqrt((double)h->G.N);
+    a.nl_floor_frac = 0.01 * h->P.nl_tol / std::sqrt((double)h->G.N);
     a.max_nl = h->P.max_nl;
     a.max_inner = h->P.max_inner;
     a.part = h->part;

@@ -10,8 +10,8 @@
 //     res = b - A(c) zeta   (FP64, matrix-free 9-point Q1 stencil),
 //     A(c) delta = res      (Jacobi-preconditioned COCG in precision T),
 //     zeta += delta,
-// until ||res|| <= max(nl_tol ||b||, floor) (floor: a fraction of the whole step's right side,
-// so strips that hold almost nothing of the solution stop early).  The inner system is solved
+// until ||res|| <= max(nl_tol ||b||, floor) (floor: 1% of nl_tol times the whole step's right
+// side per strip, so strips that hold almost nothing of the solution stop early).  The inner system is solved
 // for res / s with s the previous residual norm, so FP32 never sees values below its range
 // (far-field strips can hold values near 1e-111).  With an exact inner solve one correction is
 // exactly one
