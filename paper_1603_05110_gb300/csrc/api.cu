@@ -569,6 +569,7 @@ extern "C" int dd_nls_create(const dd_nls_params* p, const double* V, const doub
     G.p = p->p;
     G.bc_same = p->bc == DD_NLS_BC_SAME;
     G.nx = p->nx;
+    G.fill_coefficients();
     h->nfield = (long long)G.N * G.nxs * G.P;
     h->nI = std::max<long long>(1, (long long)2 * (G.N - 1) * G.P);
 

@@ -73,7 +73,7 @@ __global__ void rhs0_kernel(Geom g, const double2* __restrict__ h, double2* __re
         const int ix = (int)(rest % g.nxs);
         const int j = (int)(rest / g.nxs);
         const long long idx = (long long)(j * g.nxs + ix) * g.P + iy;
-        const Coef1<double> cx = coef1<double>(ix, c, g.hx), cy = coef1<double>(iy, ny, g.hy);
+        const Coef1<double> cx = coef1<double>(ix, c, consts_x<double>(g)), cy = coef1<double>(iy, ny, consts_y<double>(g));
         double2 acc = make_double2(0, 0);
         for (int dx = -1; dx <= 1; ++dx) {
             if (ix + dx < 0 || ix + dx > c) continue;
@@ -200,7 +200,7 @@ __global__ void diagnostics_kernel(Geom g, const double2* __restrict__ u, const 
         const int ix = (int)(rest % g.nxs);
         const int j = (int)(rest / g.nxs);
         const long long idx = (long long)(j * g.nxs + ix) * g.P + iy;
-        const Coef1<double> cx = coef1<double>(ix, c, g.hx), cy = coef1<double>(iy, ny, g.hy);
+        const Coef1<double> cx = coef1<double>(ix, c, consts_x<double>(g)), cy = coef1<double>(iy, ny, consts_y<double>(g));
         double2 Mu = make_double2(0, 0), Su = make_double2(0, 0);
         for (int dx = -1; dx <= 1; ++dx) {
             if (ix + dx < 0 || ix + dx > c) continue;
@@ -280,9 +280,14 @@ cudaError_t launch_convert_blocks(const double2* X, float2* Xf, long long n, cud
 // y = x - L_h x.  Output trace o is fed by exactly one strip:
 //   o = 2(j-1) (new r_{j-1}):  X1 l_j + X2 r_j,     o = 2j+1 (new l_{j+1}): X3 l_j + X4 r_j,
 // with l_j = x[2(j-1)+1] (j > 0) and r_j = x[2j] (j < N-1).  One warp per output node.
+template <typename TX> struct Acc;
+template <> struct Acc<float2> { using t = float; };
+template <> struct Acc<double2> { using t = double; };
+
 template <typename TX>
 __global__ void apply_P_kernel(Geom g, const TX* __restrict__ X, const int* __restrict__ btype,
                                const double2* __restrict__ x, double2* __restrict__ y) {
+    using A = typename Acc<TX>::t;    // accumulate in the precision of the blocks
     const int nyn = g.nyn, P = g.P;
     const int lane = threadIdx.x & 31;
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
@@ -298,21 +303,23 @@ __global__ void apply_P_kernel(Geom g, const TX* __restrict__ X, const int* __re
         const TX* Xs = X + (long long)btype[j] * 4 * bs;
         const double2* in_l = j > 0 ? x + (long long)(2 * (j - 1) + 1) * P : nullptr;
         const double2* in_r = j < g.N - 1 ? x + (long long)(2 * j) * P : nullptr;
-        double sr = 0.0, si = 0.0;
+        A sr = 0, si = 0;
         const TX* ra = Xs + ka * bs + (long long)row * nyn;
         const TX* rb = Xs + kb * bs + (long long)row * nyn;
         for (int col = lane; col < nyn; col += 32) {
             if (in_l) {
                 const TX a = ra[col];
                 const double2 v = in_l[col];
-                sr += (double)a.x * v.x - (double)a.y * v.y;
-                si += (double)a.x * v.y + (double)a.y * v.x;
+                const A vx = (A)v.x, vy = (A)v.y;
+                sr += a.x * vx - a.y * vy;
+                si += a.x * vy + a.y * vx;
             }
             if (in_r) {
                 const TX b = rb[col];
                 const double2 v = in_r[col];
-                sr += (double)b.x * v.x - (double)b.y * v.y;
-                si += (double)b.x * v.y + (double)b.y * v.x;
+                const A vx = (A)v.x, vy = (A)v.y;
+                sr += b.x * vx - b.y * vy;
+                si += b.x * vy + b.y * vx;
             }
         }
 #pragma unroll
@@ -322,7 +329,7 @@ __global__ void apply_P_kernel(Geom g, const TX* __restrict__ X, const int* __re
         }
         if (lane == 0) {
             const long long e = (long long)o * P + row;
-            y[e] = make_double2(x[e].x - sr, x[e].y - si);
+            y[e] = make_double2(x[e].x - (double)sr, x[e].y - (double)si);
         }
     }
 }

@@ -29,9 +29,11 @@ template <typename T2> __device__ __forceinline__ T2 cfma(T2 s, T2 b, T2 a) {
     a.y = fma(s.x, b.y, fma(s.y, b.x, a.y));
     return a;
 }
+__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp(double x) { return __drcp_rn(x); }
 template <typename T2> __device__ __forceinline__ T2 cinv(T2 a) {
-    auto d = a.x * a.x + a.y * a.y;
-    T2 r; r.x = a.x / d; r.y = -a.y / d; return r;
+    const auto r = rcp(a.x * a.x + a.y * a.y);
+    T2 o; o.x = a.x * r; o.y = -a.y * r; return o;
 }
 __device__ __forceinline__ double2 cd(float2 a) { return make_double2(a.x, a.y); }
 __device__ __forceinline__ double2 cd(double2 a) { return a; }
@@ -53,6 +55,17 @@ struct Geom {
     double p;     // Robin parameter
     int bc_same;  // physical x-edges carry S-bar (1) or Neumann (0)
     int nx;       // cells in x over all strips
+    // 1D P1 coefficients (filled on the host so kernels never divide):
+    // mass off-diagonal h/6, diagonal 4h/6 inside and 2h/6 at the ends; stiffness
+    // off-diagonal -1/h, diagonal 2/h inside and 1/h at the ends; trapezoid weight h.
+    double mxo, mxi, mxe, kxo, kxi, kxe;
+    double myo, myi, mye, kyo, kyi, kye;
+    __host__ void fill_coefficients() {
+        mxo = hx / 6.0; mxi = 4.0 * hx / 6.0; mxe = 2.0 * hx / 6.0;
+        kxo = -1.0 / hx; kxi = 2.0 / hx; kxe = 1.0 / hx;
+        myo = hy / 6.0; myi = 4.0 * hy / 6.0; mye = 2.0 * hy / 6.0;
+        kyo = -1.0 / hy; kyi = 2.0 / hy; kye = 1.0 / hy;
+    }
     __host__ __device__ long long sstride() const { return (long long)nxs * P; }
     __host__ __device__ int c() const { return nxs - 1; }
 };
@@ -63,15 +76,25 @@ template <typename T> struct Coef1 {
     T m[3];   // M(i, i-1), M(i, i), M(i, i+1) (zero outside the mesh)
     T k[3];
 };
-template <typename T> __device__ __forceinline__ Coef1<T> coef1(int i, int n, double h) {
+// The six constants of one direction, converted once to the working precision.
+template <typename T> struct Coef1Consts {
+    T mo, mi, me, ko, ki, ke;
+};
+template <typename T> __device__ __forceinline__ Coef1Consts<T> consts_x(const Geom& g) {
+    return {(T)g.mxo, (T)g.mxi, (T)g.mxe, (T)g.kxo, (T)g.kxi, (T)g.kxe};
+}
+template <typename T> __device__ __forceinline__ Coef1Consts<T> consts_y(const Geom& g) {
+    return {(T)g.myo, (T)g.myi, (T)g.mye, (T)g.kyo, (T)g.kyi, (T)g.kye};
+}
+template <typename T> __device__ __forceinline__ Coef1<T> coef1(int i, int n, const Coef1Consts<T>& k) {
     Coef1<T> c;
     const bool lo = (i > 0), hi = (i < n);
-    c.m[0] = lo ? (T)(h / 6.0) : (T)0;
-    c.m[2] = hi ? (T)(h / 6.0) : (T)0;
-    c.m[1] = (lo && hi) ? (T)(4.0 * h / 6.0) : (T)(2.0 * h / 6.0);
-    c.k[0] = lo ? (T)(-1.0 / h) : (T)0;
-    c.k[2] = hi ? (T)(-1.0 / h) : (T)0;
-    c.k[1] = (lo && hi) ? (T)(2.0 / h) : (T)(1.0 / h);
+    c.m[0] = lo ? k.mo : (T)0;
+    c.m[2] = hi ? k.mo : (T)0;
+    c.m[1] = (lo && hi) ? k.mi : k.me;
+    c.k[0] = lo ? k.ko : (T)0;
+    c.k[2] = hi ? k.ko : (T)0;
+    c.k[1] = (lo && hi) ? k.ki : k.ke;
     return c;
 }
 // trapezoidal (nodal quadrature) weight of node i of a 1D mesh 0..n

@@ -128,6 +128,8 @@ strip_solve_kernel(StripSolveArgs a) {
     auto group_ptr = [&](unsigned e) { return part_base + ((size_t)(e & 3u) * NB + (size_t)j * bps) * 4; };
 
     const double robin_l = ltc ? g.p : 0.0, robin_r = rtc ? g.p : 0.0;
+    const Coef1Consts<double> KXd = consts_x<double>(g), KYd = consts_y<double>(g);
+    const Coef1Consts<T> KXt = consts_x<T>(g), KYt = consts_y<T>(g);
     const T alphaT = (T)g.alpha;
     const double kap = a.mode == 0 ? g.kap : 0.0;
 
@@ -171,7 +173,7 @@ strip_solve_kernel(StripSolveArgs a) {
             int ix, iy;
             split_node(n, nyn, inv_nyn, ix, iy);
             const long long idx = (long long)ix * P + iy;
-            const Coef1<double> cy = coef1<double>(iy, ny, g.hy);
+            const Coef1<double> cy = coef1<double>(iy, ny, KYd);
             double2 b = rhs0 ? rhs0[idx] : make_double2(0.0, 0.0);
             b = csub(b, edge_term(ix, iy, cy));
             lb[0] += b.x * b.x + b.y * b.y;
@@ -196,7 +198,7 @@ strip_solve_kernel(StripSolveArgs a) {
             int ix, iy;
             split_node(n, nyn, inv_nyn, ix, iy);
             const long long idx = (long long)ix * P + iy;
-            const Coef1<double> cx = coef1<double>(ix, c, g.hx), cy = coef1<double>(iy, ny, g.hy);
+            const Coef1<double> cx = coef1<double>(ix, c, KXd), cy = coef1<double>(iy, ny, KYd);
             const double2 zc = zeta[idx];
             const double W = Wn ? Wn[idx] : 0.0;
             const double cdiag = wq(ix, c, g.hx) * wq(iy, ny, g.hy) * (W + kap * (zc.x * zc.x + zc.y * zc.y));
@@ -207,7 +209,7 @@ strip_solve_kernel(StripSolveArgs a) {
             const double2 res = csub(b, Az);
             loc[0] += res.x * res.x + res.y * res.y;
             loc[1] += b.x * b.x + b.y * b.y;
-            const Coef1<T> cxT = coef1<T>(ix, c, g.hx), cyT = coef1<T>(iy, ny, g.hy);
+            const Coef1<T> cxT = coef1<T>(ix, c, KXt), cyT = coef1<T>(iy, ny, KYt);
             const T2 rT = cfrom<T2>(make_double2(res.x * inv_s, res.y * inv_s));
             const T2 di = diag_inv<T>(cxT, cyT, alphaT, (T)rb, (T)cdiag);
             const T2 zT = cmul(di, rT);
@@ -247,7 +249,7 @@ strip_solve_kernel(StripSolveArgs a) {
                 int ix, iy;
                 split_node(n, nyn, inv_nyn, ix, iy);
                 const long long idx = (long long)ix * P + iy;
-                const Coef1<T> cxT = coef1<T>(ix, c, g.hx), cyT = coef1<T>(iy, ny, g.hy);
+                const Coef1<T> cxT = coef1<T>(ix, c, KXt), cyT = coef1<T>(iy, ny, KYt);
                 const T2 Az = apply_op<T, T2>(z, idx, ix, iy, c, ny, P, cxT, cyT, alphaT, (T)robin_at(ix), cT[idx]);
                 const T2 qn = cfma(bT, q[idx], Az);
                 const T2 pn = cfma(bT, p[idx], z[idx]);
@@ -277,7 +279,7 @@ strip_solve_kernel(StripSolveArgs a) {
                 int ix, iy;
                 split_node(n, nyn, inv_nyn, ix, iy);
                 const long long idx = (long long)ix * P + iy;
-                const Coef1<T> cxT = coef1<T>(ix, c, g.hx), cyT = coef1<T>(iy, ny, g.hy);
+                const Coef1<T> cxT = coef1<T>(ix, c, KXt), cyT = coef1<T>(iy, ny, KYt);
                 const T2 pc = p[idx];
                 x[idx] = cfma(alT, pc, x[idx]);
                 const T2 rn = cfma(malT, q[idx], r[idx]);
