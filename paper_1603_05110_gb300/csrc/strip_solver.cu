@@ -241,7 +241,8 @@ strip_solve_kernel(StripSolveArgs a) {
         const double target = fmax(a.inner_tol * rnorm, fmax(a.inner_floor * bnorm, 0.1 * floor_abs)) * inv_s;
         for (int it = 0; it < a.max_inner; ++it) {
             // phase A: q = A z + beta q, p = z + beta p, partial mu = p^T q
-            double lm[4] = {0.0, 0.0, 0.0, 0.0};
+            // (per-thread partials in T: the FP64 pipe is ~1/64 of FP32 on this part)
+            T am_re = 0, am_im = 0;
             const T2 bT = mk<T2>(beta_re, beta_im);
             for (int ch = rank; ch < nchunks; ch += bps) {
                 const int n = ch * blockDim.x + threadIdx.x;
@@ -255,9 +256,10 @@ strip_solve_kernel(StripSolveArgs a) {
                 const T2 pn = cfma(bT, p[idx], z[idx]);
                 q[idx] = qn;
                 p[idx] = pn;
-                lm[0] += (double)(pn.x * qn.x - pn.y * qn.y);
-                lm[1] += (double)(pn.x * qn.y + pn.y * qn.x);
+                am_re += pn.x * qn.x - pn.y * qn.y;
+                am_im += pn.x * qn.y + pn.y * qn.x;
             }
+            double lm[4] = {(double)am_re, (double)am_im, 0.0, 0.0};
             block_sum<4>(lm, s_red);
             if (threadIdx.x == 0) { double* sp = slot_ptr(epoch + 1); sp[0] = lm[0]; sp[1] = lm[1]; sp[2] = 0; sp[3] = 0; }
             ++epoch;
@@ -272,7 +274,7 @@ strip_solve_kernel(StripSolveArgs a) {
             const T2 alT = mk<T2>(al_re, al_im);
             const T2 malT = mk<T2>(-al_re, -al_im);
             // phase B: x += a p, r -= a q, z = D^-1 r, partials rho' = r^T z, ||r||^2
-            double lb[4] = {0.0, 0.0, 0.0, 0.0};
+            T b0 = 0, b1 = 0, b2 = 0;
             for (int ch = rank; ch < nchunks; ch += bps) {
                 const int n = ch * blockDim.x + threadIdx.x;
                 if (n >= Ns) continue;
@@ -287,10 +289,11 @@ strip_solve_kernel(StripSolveArgs a) {
                 const T2 di = diag_inv<T>(cxT, cyT, alphaT, (T)robin_at(ix), cT[idx]);
                 const T2 zn = cmul(di, rn);
                 z[idx] = zn;
-                lb[0] += (double)(rn.x * zn.x - rn.y * zn.y);
-                lb[1] += (double)(rn.x * zn.y + rn.y * zn.x);
-                lb[2] += (double)(rn.x * rn.x + rn.y * rn.y);
+                b0 += rn.x * zn.x - rn.y * zn.y;
+                b1 += rn.x * zn.y + rn.y * zn.x;
+                b2 += rn.x * rn.x + rn.y * rn.y;
             }
+            double lb[4] = {(double)b0, (double)b1, (double)b2, 0.0};
             block_sum<4>(lb, s_red);
             if (threadIdx.x == 0) { double* sp = slot_ptr(epoch + 1); sp[0] = lb[0]; sp[1] = lb[1]; sp[2] = lb[2]; sp[3] = 0; }
             ++epoch;
