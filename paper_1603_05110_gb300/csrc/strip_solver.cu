@@ -143,6 +143,13 @@ strip_solve_kernel(StripSolveArgs a) {
         if (ix == c) rb += robin_r;
         return rb;
     };
+    const T robin_lT = (T)robin_l, robin_rT = (T)robin_r;
+    auto robin_atT = [&](int ix) -> T {
+        T rb = (T)0;
+        if (ix == 0) rb += robin_lT;
+        if (ix == c) rb += robin_rT;
+        return rb;
+    };
     // datum of the Robin data term on an edge node (l on ix=0, r on ix=c)
     auto edge_term = [&](int ix, int iy, const Coef1<double>& cy) -> double2 {
         double2 t = make_double2(0.0, 0.0);
@@ -251,7 +258,7 @@ strip_solve_kernel(StripSolveArgs a) {
                 split_node(n, nyn, inv_nyn, ix, iy);
                 const long long idx = (long long)ix * P + iy;
                 const Coef1<T> cxT = coef1<T>(ix, c, KXt), cyT = coef1<T>(iy, ny, KYt);
-                const T2 Az = apply_op<T, T2>(z, idx, ix, iy, c, ny, P, cxT, cyT, alphaT, (T)robin_at(ix), cT[idx]);
+                const T2 Az = apply_op<T, T2>(z, idx, ix, iy, c, ny, P, cxT, cyT, alphaT, robin_atT(ix), cT[idx]);
                 const T2 qn = cfma(bT, q[idx], Az);
                 const T2 pn = cfma(bT, p[idx], z[idx]);
                 q[idx] = qn;
@@ -259,8 +266,9 @@ strip_solve_kernel(StripSolveArgs a) {
                 am_re += pn.x * qn.x - pn.y * qn.y;
                 am_im += pn.x * qn.y + pn.y * qn.x;
             }
-            double lm[4] = {(double)am_re, (double)am_im, 0.0, 0.0};
-            block_sum<4>(lm, s_red);
+            T lmT[2] = {am_re, am_im};
+            double lm[2];
+            block_sum_t<T, 2>(lmT, lm, s_red);
             if (threadIdx.x == 0) { double* sp = slot_ptr(epoch + 1); sp[0] = lm[0]; sp[1] = lm[1]; sp[2] = 0; sp[3] = 0; }
             ++epoch;
             if (!group_barrier(bar, epoch * bps, a.err, &s_flag)) { status = DD_NLS_ETIMEOUT; break; }
@@ -286,15 +294,16 @@ strip_solve_kernel(StripSolveArgs a) {
                 x[idx] = cfma(alT, pc, x[idx]);
                 const T2 rn = cfma(malT, q[idx], r[idx]);
                 r[idx] = rn;
-                const T2 di = diag_inv<T>(cxT, cyT, alphaT, (T)robin_at(ix), cT[idx]);
+                const T2 di = diag_inv<T>(cxT, cyT, alphaT, robin_atT(ix), cT[idx]);
                 const T2 zn = cmul(di, rn);
                 z[idx] = zn;
                 b0 += rn.x * zn.x - rn.y * zn.y;
                 b1 += rn.x * zn.y + rn.y * zn.x;
                 b2 += rn.x * rn.x + rn.y * rn.y;
             }
-            double lb[4] = {(double)b0, (double)b1, (double)b2, 0.0};
-            block_sum<4>(lb, s_red);
+            T lbT[3] = {b0, b1, b2};
+            double lb[3];
+            block_sum_t<T, 3>(lbT, lb, s_red);
             if (threadIdx.x == 0) { double* sp = slot_ptr(epoch + 1); sp[0] = lb[0]; sp[1] = lb[1]; sp[2] = lb[2]; sp[3] = 0; }
             ++epoch;
             if (!group_barrier(bar, epoch * bps, a.err, &s_flag)) { status = DD_NLS_ETIMEOUT; break; }
