@@ -34,8 +34,12 @@ struct dd_nls {
     bool fp32 = false;
     long long nfield = 0;   // elements of one strip field (all strips)
     long long nI = 0;       // elements of one interface vector (padded)
-    int bps = 1;
-    int NB = 1;             // blocks of one strip-solver launch
+    int maxb = 1;           // co-resident blocks of the strip solver
+    int chunks = 1;         // 256-node chunks of one strip (most blocks a strip can use)
+    int* d_blk = nullptr;   // [maxb] block -> strip, then [maxb+1] strip -> first block
+    int* h_blk = nullptr;   // pinned mirror
+    double* bnorm0 = nullptr;   // [N] per-strip ||(2i/dt) M h||
+    std::vector<double> wts;    // scheduling weights
     // device state
     double2 *u = nullptr, *zeta = nullptr, *rhs0 = nullptr, *gA = nullptr, *gB = nullptr, *gconv = nullptr;
     double* Wn = nullptr;
@@ -112,6 +116,9 @@ static void release(dd_nls* h) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->hred) cudaFreeHost(h->hred);
+    if (h->h_blk) cudaFreeHost(h->h_blk);
+    if (h->d_blk) cudaFree(h->d_blk);
+    if (h->bnorm0) cudaFree(h->bnorm0);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
     if (h->ev2) cudaEventDestroy(h->ev2);
@@ -164,11 +171,35 @@ static int download_g(dd_nls* h, const double2* src, double* dst, int ptr_kind) 
 }
 
 // --------------------------------------------------------------- strip solves
-static int strip_solve(dd_nls* h, StripSolveArgs& a, int nstrips, dd_nls_stats* st, bool count) {
+// Blocks per strip for the next launch: at least one each, the rest of the co-resident
+// blocks in proportion to the weights, at most `cap` per strip.  Fills the pinned table
+// (block -> strip, then strip -> first block), copies it to the device, returns the total.
+static int schedule(dd_nls* h, const std::vector<double>& w, int nstrips, int cap, StripSolveArgs& a) {
+    double W = 0.0;
+    for (int j = 0; j < nstrips; ++j) W += w[j];
+    const int spare = std::max(0, h->maxb - nstrips);
+    int* bs = h->h_blk;                       // block -> strip
+    int* st = h->h_blk + h->maxb;             // strip -> first block
+    int total = 0;
+    for (int j = 0; j < nstrips; ++j) {
+        int n = 1 + (W > 0.0 ? (int)std::floor(spare * (w[j] / W)) : spare / nstrips);
+        n = std::max(1, std::min(n, cap));
+        st[j] = total;
+        for (int k = 0; k < n; ++k) bs[total + k] = j;
+        total += n;
+    }
+    st[nstrips] = total;
+    cudaMemcpyAsync(h->d_blk, h->h_blk, sizeof(int) * (h->maxb + nstrips + 1), cudaMemcpyHostToDevice, h->s);
+    a.blk_strip = h->d_blk;
+    a.blk_start = h->d_blk + h->maxb;
+    return total;
+}
+
+static int strip_solve(dd_nls* h, StripSolveArgs& a, int nstrips, int nblocks, dd_nls_stats* st, bool count) {
     CK(cudaMemsetAsync(h->bar, 0, sizeof(unsigned) * nstrips, h->s));
     CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->s));
     if (h->prof) CK(cudaEventRecord(h->ev0, h->s));
-    CK(launch_strip_solve(a, nstrips, h->fp32, h->s));
+    CK(launch_strip_solve(a, nblocks, h->fp32, h->s));
     if (h->prof) CK(cudaEventRecord(h->ev1, h->s));
     CK(cudaMemcpyAsync(h->h_status.data(), h->status, sizeof(int) * nstrips, cudaMemcpyDeviceToHost, h->s));
     CK(cudaMemcpyAsync(h->h_nl.data(), h->nl_its, sizeof(int) * nstrips, cudaMemcpyDeviceToHost, h->s));
@@ -214,8 +245,8 @@ static int strip_solve(dd_nls* h, StripSolveArgs& a, int nstrips, dd_nls_stats* 
 static StripSolveArgs base_args(dd_nls* h) {
     StripSolveArgs a{};
     a.g = h->G;
-    a.bps = h->bps;
     a.mode = 0;
+    a.bnorm0 = h->bnorm0;
     a.zeta = h->zeta;
     a.rhs0 = h->rhs0;
     a.Wn = h->Wn;
@@ -304,7 +335,9 @@ static int build_Lh(dd_nls* h) {
         const int u0 = types[t].first ? 0 : nyn, u1 = types[t].second ? 2 * nyn : nyn;
         for (int ub = u0; ub < u1 && rc == DD_NLS_OK; ub += chunk) {
             const int nv = std::min(chunk, u1 - ub);
-            a.bps = std::max(1, maxb / nv);
+            std::vector<double> wu(nv, 1.0);
+            const int nblk = schedule(h, wu, nv, h->chunks, a);
+            a.bnorm0 = nullptr;
             a.mode = 1;
             a.unit_base = ub;
             a.unit_ltc = types[t].first;
@@ -315,7 +348,7 @@ static int build_Lh(dd_nls* h) {
             e = cudaMemsetAsync(vz, 0, nv * per_strip * sizeof(double2), h->s);
             if (!e) e = cudaMemsetAsync(vbar, 0, nv * sizeof(unsigned), h->s);
             if (!e) e = cudaMemsetAsync(h->err, 0, sizeof(int), h->s);
-            if (!e) e = launch_strip_solve(a, nv, h->fp32, h->s);
+            if (!e) e = launch_strip_solve(a, nblk, h->fp32, h->s);
             if (!e) e = launch_extract_blocks(G, vz, nv, ub, h->X64 + (long long)t * 4 * bs, h->s);
             if (!e) e = cudaMemcpyAsync(hs.data(), vstat, nv * sizeof(int), cudaMemcpyDeviceToHost, h->s);
             if (!e) e = cudaStreamSynchronize(h->s);
@@ -455,14 +488,27 @@ static int schwarz(dd_nls* h, dd_nls_stats* st) {
         CK(launch_finalize(h->part, nb, 1, h->red + 8, h->s));
         CK(launch_sqrt(h->red + 8, h->s));
         CK(cudaMemcpyAsync(h->zeta, h->u, h->nfield * sizeof(double2), cudaMemcpyDeviceToDevice, h->s));   // zeta^0 = h
+        CK(launch_strip_norms(G, h->rhs0, h->bnorm0, h->s));
+        CK(cudaMemcpyAsync(h->hred + 16, h->bnorm0, sizeof(double) * G.N, cudaMemcpyDeviceToHost, h->s));
+        CK(cudaStreamSynchronize(h->s));
     }
+    // First launch of the step: weight strips by their share of the right side (a strip that
+    // holds nothing of the solution converges at once); later launches: by the work the
+    // previous launch of this step did.  Nothing carries over from earlier steps, so a
+    // restored checkpoint reproduces the same schedule and bitwise the same results.
+    double bmax = 0.0;
+    for (int j = 0; j < G.N; ++j) bmax = std::max(bmax, h->hred[16 + j]);
+    h->wts.assign(G.N, 1.0);
+    for (int j = 0; j < G.N; ++j) h->wts[j] = 1.0 + (bmax > 0.0 ? 15.0 * std::sqrt(h->hred[16 + j] / bmax) : 0.0);
     StripSolveArgs a = base_args(h);
     double2* g = h->gA;
     double2* gn = h->gB;
     for (int k = 0; k < h->P.max_schwarz; ++k) {
         a.gtr = g;
-        int rc = strip_solve(h, a, G.N, st, true);
+        const int nblk = schedule(h, h->wts, G.N, h->chunks, a);
+        int rc = strip_solve(h, a, G.N, nblk, st, true);
         if (rc) return rc;
+        for (int j = 0; j < G.N; ++j) h->wts[j] = 1.0 + (double)h->h_kry[j] + 4.0 * (h->h_nl[j] + 1);
         int nb = 1;
         if (G.N > 1) {
             ProfScope ps(h, &h->profile.interface_ms);
@@ -604,7 +650,7 @@ extern "C" int dd_nls_create(const dd_nls_params* p, const double* V, const doub
     CKC(dalloc(&h->nl_res, G.N));
     CKC(dalloc(&h->err, 1));
     CKC(dalloc(&h->red, 64));
-    CKC(cudaMallocHost((void**)&h->hred, 256 * sizeof(double)));
+    CKC(cudaMallocHost((void**)&h->hred, (size_t)(256 + p->n_strips) * sizeof(double)));
     CKC(cudaEventCreate(&h->ev0));
     CKC(cudaEventCreate(&h->ev1));
     CKC(cudaEventCreate(&h->ev2));
@@ -613,13 +659,15 @@ extern "C" int dd_nls_create(const dd_nls_params* p, const double* V, const doub
     h->h_nl.resize(G.N);
     h->h_kry.resize(G.N);
 
-    // launch shape of the strip solver: all blocks co-resident, bps blocks per strip
+    // launch shape of the strip solver: all blocks co-resident, blocks split among strips per launch
     const int maxb = strip_solve_max_blocks(h->fp32);
     if (maxb < G.N) { h->error = "dd_nls_create: more strips than co-resident blocks of the strip solver"; return bad(DD_NLS_EINVAL); }
-    const int chunks = (int)((G.nxs * (long long)G.nyn + 255) / 256);
-    h->bps = std::max(1, std::min(maxb / G.N, chunks));
-    h->NB = h->bps * G.N;
-    CKC(dalloc(&h->part, (size_t)4 * std::max(h->NB, maxb) * 4));
+    h->maxb = maxb;
+    h->chunks = (int)((G.nxs * (long long)G.nyn + 255) / 256);
+    CKC(dalloc(&h->part, (size_t)4 * maxb * 4));
+    CKC(dalloc(&h->d_blk, (size_t)2 * maxb + 2));
+    CKC(cudaMallocHost((void**)&h->h_blk, sizeof(int) * (2 * maxb + 2)));
+    CKC(dalloc(&h->bnorm0, G.N));
 
     if (upload_nodal(h, u0, ptr_kind, h->u)) return bad(DD_NLS_ECUDA);
     if (V) {

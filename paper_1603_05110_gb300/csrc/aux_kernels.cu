@@ -98,6 +98,26 @@ cudaError_t launch_rhs0(const Geom& g, const double2* h, double2* rhs0, double* 
     return cudaGetLastError();
 }
 
+__global__ void strip_norms_kernel(Geom g, const double2* __restrict__ rhs0, double* __restrict__ out) {
+    __shared__ double sm[64];
+    const int j = blockIdx.x;
+    const double2* b = rhs0 + (long long)j * g.sstride();
+    const int Ns = g.nxs * g.nyn;
+    double v[1] = {0.0};
+    for (int n = threadIdx.x; n < Ns; n += blockDim.x) {
+        const int ix = n / g.nyn, iy = n - ix * g.nyn;
+        const double2 a = b[(long long)ix * g.P + iy];
+        v[0] += a.x * a.x + a.y * a.y;
+    }
+    block_sum<1>(v, sm);
+    if (threadIdx.x == 0) out[j] = sqrt(v[0]);
+}
+cudaError_t launch_strip_norms(const Geom& g, const double2* rhs0, double* out, cudaStream_t s) {
+    count_launches(1);
+    strip_norms_kernel<<<g.N, 256, 0, s>>>(g, rhs0, out);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ flux update
 // eq. (fluxlr) with Robin S v = -i p v (eq. TCSRobin):
 //   new r_i     = -l_{i+1} + 2 S v_{i+1}(a_{i+1}) = -g[2i+1] - 2ip zeta_{i+1}(0, .)

@@ -12,7 +12,10 @@ void count_launches(int n);
 
 struct StripSolveArgs {
     Geom g;
-    int bps;                 // blocks per strip
+    int bps;                 // unused when blk_strip is set
+    const int* blk_strip;    // [gridDim] strip of each block
+    const int* blk_start;    // [strips+1] first block of each strip
+    const double* bnorm0;    // [strips] ||(2i/dt) M h|| per strip (scale of the first correction), or NULL
     int mode;                // 0: Schwarz strips; 1: unit data on free strips (L_h setup)
     int unit_base;           // mode 1: first unit column (side*nyn + pos) of this launch
     int unit_ltc, unit_rtc;  // mode 1: edge kinds of the strip type
@@ -35,7 +38,8 @@ struct StripSolveArgs {
     int* err;                // launch-wide error word
 };
 
-cudaError_t launch_strip_solve(const StripSolveArgs& a, int nstrips, bool fp32, cudaStream_t s);
+// cooperative launch of nblocks blocks (a.blk_strip / a.blk_start map blocks to strips)
+cudaError_t launch_strip_solve(const StripSolveArgs& a, int nblocks, bool fp32, cudaStream_t s);
 int strip_solve_max_blocks(bool fp32);
 
 // ---- auxiliary kernels (aux_kernels.cu)
@@ -45,6 +49,8 @@ using AuxGeom = Geom;
 cudaError_t launch_scatter_u(const AuxGeom& g, const double2* glob, double2* strips, cudaStream_t s);
 cudaError_t launch_gather_u(const AuxGeom& g, const double2* strips, double2* glob, cudaStream_t s);
 cudaError_t launch_scatter_real(const AuxGeom& g, const double* glob, double scale, double* strips, cudaStream_t s);
+// out[j] = ||rhs0|| over strip j (one block per strip)
+cudaError_t launch_strip_norms(const AuxGeom& g, const double2* rhs0, double* out, cudaStream_t s);
 // rhs0 = i alpha M h (per strip); partial sums of ||rhs0||^2 into part[nblk][1]
 cudaError_t launch_rhs0(const AuxGeom& g, const double2* h, double2* rhs0, double* part, int* nblk_out, cudaStream_t s);
 // interface flux update, eq. (fluxlr), Robin: writes gnew, partial norms into part[nblk][2]

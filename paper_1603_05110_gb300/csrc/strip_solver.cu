@@ -82,9 +82,10 @@ strip_solve_kernel(StripSolveArgs a) {
     __shared__ int s_flag;
 
     const Geom& g = a.g;
-    const int bps = a.bps;
-    const int j = blockIdx.x / bps;          // strip (virtual strip in setup mode)
-    const int rank = blockIdx.x - j * bps;
+    const int j = a.blk_strip[blockIdx.x];   // strip (virtual strip in setup mode)
+    const int b0 = a.blk_start[j];
+    const int bps = a.blk_start[j + 1] - b0; // blocks of this strip (weighted by the host)
+    const int rank = blockIdx.x - b0;
     const int nyn = g.nyn, ny = nyn - 1, c = g.nxs - 1, P = g.P;
     const int Ns = g.nxs * nyn;
     const int nchunks = (Ns + blockDim.x - 1) / blockDim.x;
@@ -125,7 +126,7 @@ strip_solve_kernel(StripSolveArgs a) {
     const int NB = gridDim.x;
     double* part_base = a.part;
     auto slot_ptr = [&](unsigned e) { return part_base + ((size_t)(e & 3u) * NB + blockIdx.x) * 4; };
-    auto group_ptr = [&](unsigned e) { return part_base + ((size_t)(e & 3u) * NB + (size_t)j * bps) * 4; };
+    auto group_ptr = [&](unsigned e) { return part_base + ((size_t)(e & 3u) * NB + (size_t)b0) * 4; };
 
     const double robin_l = ltc ? g.p : 0.0, robin_r = rtc ? g.p : 0.0;
     const Coef1Consts<double> KXd = consts_x<double>(g), KYd = consts_y<double>(g);
@@ -170,33 +171,12 @@ strip_solve_kernel(StripSolveArgs a) {
         return t;
     };
 
-    // ---------------- ||b|| of the strip, b = (2i/dt) M h - M^Gamma Q^T (l; r)
-    double bnorm;
-    {
-        double lb[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int ch = rank; ch < nchunks; ch += bps) {
-            const int n = ch * blockDim.x + threadIdx.x;
-            if (n >= Ns) continue;
-            int ix, iy;
-            split_node(n, nyn, inv_nyn, ix, iy);
-            const long long idx = (long long)ix * P + iy;
-            const Coef1<double> cy = coef1<double>(iy, ny, KYd);
-            double2 b = rhs0 ? rhs0[idx] : make_double2(0.0, 0.0);
-            b = csub(b, edge_term(ix, iy, cy));
-            lb[0] += b.x * b.x + b.y * b.y;
-        }
-        block_sum<4>(lb, s_red);
-        if (threadIdx.x == 0) { double* sp = slot_ptr(epoch + 1); sp[0] = lb[0]; sp[1] = 0; sp[2] = 0; sp[3] = 0; }
-        ++epoch;
-        if (!group_barrier(bar, epoch * bps, a.err, &s_flag)) status = DD_NLS_ETIMEOUT;
-        double tb[4];
-        group_sum<4>(group_ptr(epoch), bps, tb, s_red);
-        bnorm = sqrt(tb[0]);
-    }
+    // scale of the first correction: the strip's ||(2i/dt) M h|| (FP32 must not see ~1e-111)
+    double bnorm = 0.0;
+    double inv_s = (a.bnorm0 && a.bnorm0[j] > 0.0) ? 1.0 / a.bnorm0[j] : 1.0;
     const double floor_abs = a.bscale ? a.nl_floor_frac * (*(volatile const double*)a.bscale) : 0.0;
-    double inv_s = bnorm > 0.0 ? 1.0 / bnorm : 1.0;      // scale of the inner system
 
-    for (; status == 0; ++nl_it) {
+    for (;; ++nl_it) {
         // ---------------- phase R: coefficients c = w (W + kappa|zeta|^2) and FP64 residual
         double loc[4] = {0.0, 0.0, 0.0, 0.0};   // ||res||^2, ||b||^2, rho = r^T z (re, im)
         for (int ch = rank; ch < nchunks; ch += bps) {
@@ -236,6 +216,7 @@ strip_solve_kernel(StripSolveArgs a) {
         double tot[4];
         group_sum<4>(group_ptr(epoch), bps, tot, s_red);
         const double rnorm = sqrt(tot[0]);
+        bnorm = sqrt(tot[1]);
         nres = bnorm > 0.0 ? rnorm / bnorm : rnorm;
         if (!isfinite(tot[0]) || !isfinite(tot[1])) { status = DD_NLS_ENONFINITE; break; }
         if (nres <= a.nl_tol || rnorm <= floor_abs || rnorm == 0.0) break;
@@ -344,16 +325,16 @@ strip_solve_kernel(StripSolveArgs a) {
 }
 
 template <typename T>
-static cudaError_t launch_strip_solve_t(const StripSolveArgs& args, int nstrips, cudaStream_t s) {
+static cudaError_t launch_strip_solve_t(const StripSolveArgs& args, int nblocks, cudaStream_t s) {
     StripSolveArgs a = args;
     void* params[] = {&a};
-    dim3 grid(nstrips * a.bps), block(256);
+    dim3 grid(nblocks), block(256);
     count_launches(1);
     return cudaLaunchCooperativeKernel((const void*)strip_solve_kernel<T>, grid, block, params, 0, s);
 }
 
-cudaError_t launch_strip_solve(const StripSolveArgs& a, int nstrips, bool fp32, cudaStream_t s) {
-    return fp32 ? launch_strip_solve_t<float>(a, nstrips, s) : launch_strip_solve_t<double>(a, nstrips, s);
+cudaError_t launch_strip_solve(const StripSolveArgs& a, int nblocks, bool fp32, cudaStream_t s) {
+    return fp32 ? launch_strip_solve_t<float>(a, nblocks, s) : launch_strip_solve_t<double>(a, nblocks, s);
 }
 
 int strip_solve_max_blocks(bool fp32) {
