@@ -60,6 +60,10 @@ enum { DD_NLS_CLASSICAL = 0, DD_NLS_PRECONDITIONED = 1 };  /* eq. algo_d / eq. a
 enum { DD_NLS_FP64 = 0, DD_NLS_FP32_INNER = 1 };           /* inner Krylov precision */
 enum { DD_NLS_GUESS_ZERO = 0, DD_NLS_GUESS_PREVIOUS = 1 }; /* g_n^0 (Sec. 5) */
 enum { DD_NLS_PTR_HOST = 0, DD_NLS_PTR_DEVICE = 1 };
+/* How P x = y of eq. (algo_pd) is solved: GMRES on the assembled L_h blocks (Sec. 4.2), or
+ * exactly in the cosine basis that diagonalises every block of L_h (uniform mesh, Neumann
+ * data on y = yb, yu); both apply the same P. */
+enum { DD_NLS_PSOLVE_GMRES = 0, DD_NLS_PSOLVE_MODAL = 1 };
 
 typedef struct {
     /* Omega, mesh and strips (Sec. 2.1-2.2); nx must be a multiple of n_strips */
@@ -87,6 +91,7 @@ typedef struct {
     double gmres_tol;    /* P x = y (eq. algo_pd): relative residual */
     int gmres_restart;
     int gmres_max;
+    int psolve;          /* DD_NLS_PSOLVE_MODAL (default) or DD_NLS_PSOLVE_GMRES */
 } dd_nls_params;
 
 typedef struct {
@@ -115,7 +120,7 @@ typedef struct {
 } dd_nls_profile;
 
 /* Fill *p with defaults: NLS (lap=1, kappa=1), Robin p=1, classical, FP64, previous-step
- * guess, tol 1e-10, nl_tol 1e-13, inner_tol 1e-6, GMRES restart 30 / tol 1e-10. */
+ * guess, tol 1e-10, nl_tol 1e-13, inner_tol 1e-6, GMRES restart 30 / tol 1e-10, modal P solve. */
 void dd_nls_default_params(dd_nls_params* p);
 
 /* Create a solver.  V: real nodal potential (ny+1)*(nx+1) in the sign of eq. (Sch), or
@@ -142,8 +147,11 @@ int dd_nls_get_state(dd_nls* h, double* u, double* g, int* step, int ptr_kind);
 int dd_nls_set_state(dd_nls* h, const double* u, const double* g, int step, int ptr_kind);
 
 /* Copy the L_h blocks X^{j,1..4} (Props 3.1/3.2) of strip j into x (4 row-major
- * (ny+1)x(ny+1) complex matrices, X1 X2 X3 X4).  EINVAL if not PRECONDITIONED. */
+ * (ny+1)x(ny+1) complex matrices, X1 X2 X3 X4).  EINVAL unless PRECONDITIONED with GMRES.
+ * dd_nls_get_modal copies the diagonal of the blocks in the cosine basis instead: 4 vectors
+ * of ny+1 complex values (x1 x2 x3 x4); EINVAL unless PRECONDITIONED with MODAL. */
 int dd_nls_get_blocks(dd_nls* h, int strip, double* x, int ptr_kind);
+int dd_nls_get_modal(dd_nls* h, int strip, double* x, int ptr_kind);
 
 int dd_nls_set_profiling(dd_nls* h, int on);
 int dd_nls_get_profile(dd_nls* h, dd_nls_profile* prof);

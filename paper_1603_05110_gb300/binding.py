@@ -19,6 +19,7 @@ CLASSICAL, PRECONDITIONED = 0, 1
 FP64, FP32_INNER = 0, 1
 GUESS_ZERO, GUESS_PREVIOUS = 0, 1
 PTR_HOST, PTR_DEVICE = 0, 1
+PSOLVE_GMRES, PSOLVE_MODAL = 0, 1
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "ENONFINITE",
           6: "ETIMEOUT", 7: "EBREAKDOWN"}
@@ -35,6 +36,7 @@ class Params(ctypes.Structure):
         ("nl_tol", ctypes.c_double), ("max_nl", ctypes.c_int),
         ("inner_tol", ctypes.c_double), ("max_inner", ctypes.c_int),
         ("gmres_tol", ctypes.c_double), ("gmres_restart", ctypes.c_int), ("gmres_max", ctypes.c_int),
+        ("psolve", ctypes.c_int),
     ]
 
 
@@ -64,7 +66,7 @@ class Profile(ctypes.Structure):
 
 
 SYMBOLS = ["dd_nls_default_params", "dd_nls_create", "dd_nls_step", "dd_nls_solve_interface",
-           "dd_nls_get_state", "dd_nls_set_state", "dd_nls_get_blocks", "dd_nls_set_profiling",
+           "dd_nls_get_state", "dd_nls_set_state", "dd_nls_get_blocks", "dd_nls_get_modal", "dd_nls_set_profiling",
            "dd_nls_get_profile", "dd_nls_destroy", "dd_nls_last_error"]
 
 _lib = None
@@ -94,6 +96,8 @@ def load(path=LIB_PATH):
     lib.dd_nls_set_state.restype = ip
     lib.dd_nls_get_blocks.argtypes = [vp, ip, vp, ip]
     lib.dd_nls_get_blocks.restype = ip
+    lib.dd_nls_get_modal.argtypes = [vp, ip, vp, ip]
+    lib.dd_nls_get_modal.restype = ip
     lib.dd_nls_set_profiling.argtypes = [vp, ip]
     lib.dd_nls_set_profiling.restype = ip
     lib.dd_nls_get_profile.argtypes = [vp, ctypes.POINTER(Profile)]
@@ -208,6 +212,12 @@ class Solver:
         ne = self.params.ny + 1
         x = np.zeros((4, ne, ne), np.complex128)
         self._check(self.lib.dd_nls_get_blocks(self.h, strip, x.ctypes.data, PTR_HOST))
+        return x
+
+    def modal(self, strip):
+        ne = self.params.ny + 1
+        x = np.zeros((4, ne), np.complex128)
+        self._check(self.lib.dd_nls_get_modal(self.h, strip, x.ctypes.data, PTR_HOST))
         return x
 
     def set_profiling(self, on=True):

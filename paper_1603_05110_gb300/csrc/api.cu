@@ -61,6 +61,11 @@ struct dd_nls {
     std::vector<int> btype_h;
     double2 *V = nullptr, *w = nullptr, *tmp = nullptr, *hdev = nullptr, *xs = nullptr;
     double* scratch = nullptr;
+    // modal P solve
+    double *Cf = nullptr, *Ci = nullptr;
+    float *Cf32 = nullptr, *Ci32 = nullptr;
+    double2 *xm = nullptr, *fac = nullptr;
+    int* tkind = nullptr;
     // host mirrors
     double* hred = nullptr;          // pinned
     std::vector<int> h_status, h_nl;
@@ -101,6 +106,7 @@ extern "C" void dd_nls_default_params(dd_nls_params* p) {
     p->nl_tol = 1e-13; p->max_nl = 60;
     p->inner_tol = 1e-6; p->max_inner = 2000;
     p->gmres_tol = 1e-10; p->gmres_restart = 30; p->gmres_max = 300;
+    p->psolve = DD_NLS_PSOLVE_MODAL;
 }
 
 template <typename T> static cudaError_t dalloc(T** ptr, size_t n) {
@@ -112,7 +118,8 @@ template <typename T> static cudaError_t dalloc(T** ptr, size_t n) {
 static void release(dd_nls* h) {
     void* ptrs[] = {h->u, h->zeta, h->rhs0, h->gA, h->gB, h->gconv, h->Wn, h->x, h->r, h->z, h->p, h->q, h->cT,
                     h->part, h->bar, h->status, h->nl_its, h->kry, h->nl_res, h->err, h->red, h->stage,
-                    h->X64, h->X32, h->btype, h->V, h->w, h->tmp, h->hdev, h->xs, h->scratch};
+                    h->X64, h->X32, h->btype, h->V, h->w, h->tmp, h->hdev, h->xs, h->scratch,
+                    h->Cf, h->Ci, h->Cf32, h->Ci32, h->xm, h->fac, h->tkind};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->hred) cudaFreeHost(h->hred);
@@ -271,12 +278,11 @@ static StripSolveArgs base_args(dd_nls* h) {
 // ----------------------------------------------------------------- L_h setup
 // Columns of L_h from free strip solves with unit data (Sec. 4.2): for every strip type
 // (edge kinds), 2(ny+1) independent solves batched as virtual strips of one launch.
-static int build_Lh(dd_nls* h) {
+// Strip types (edge kinds: transmission or Neumann on each side).  Equal strips of one type
+// share their L_h blocks (Props 3.1/3.2).
+static int strip_types(dd_nls* h, std::vector<std::pair<int, int>>& types) {
     const Geom& G = h->G;
-    const int nyn = G.nyn;
-    const long long bs = (long long)nyn * nyn;
-    // strip types
-    std::vector<std::pair<int, int>> types;   // (ltc, rtc)
+    types.clear();
     h->btype_h.assign(G.N, 0);
     for (int j = 0; j < G.N; ++j) {
         const int l = (j > 0 || G.bc_same) ? 1 : 0, r = (j < G.N - 1 || G.bc_same) ? 1 : 0;
@@ -286,9 +292,57 @@ static int build_Lh(dd_nls* h) {
         else h->btype_h[j] = (int)(it - types.begin());
     }
     h->ntypes = (int)types.size();
-    CK(dalloc(&h->X64, (size_t)h->ntypes * 4 * bs));
     CK(dalloc(&h->btype, G.N));
     CK(cudaMemcpy(h->btype, h->btype_h.data(), sizeof(int) * G.N, cudaMemcpyHostToDevice));
+    return DD_NLS_OK;
+}
+
+// Diagonal of L_h in the cosine basis and the per-mode block-Thomas factors of P (modal.cu).
+static int build_modal(dd_nls* h) {
+    const Geom& G = h->G;
+    std::vector<std::pair<int, int>> types;
+    int rc = strip_types(h, types);
+    if (rc) return rc;
+    const long long nn = (long long)G.nyn * G.nyn;
+    std::vector<int> tk(2 * h->ntypes);
+    for (int t = 0; t < h->ntypes; ++t) { tk[2 * t] = types[t].first; tk[2 * t + 1] = types[t].second; }
+    CK(dalloc(&h->tkind, tk.size()));
+    CK(cudaMemcpy(h->tkind, tk.data(), sizeof(int) * tk.size(), cudaMemcpyHostToDevice));
+    CK(dalloc(&h->Cf, nn));
+    CK(dalloc(&h->Ci, nn));
+    if (h->fp32) { CK(dalloc(&h->Cf32, nn)); CK(dalloc(&h->Ci32, nn)); }
+    CK(dalloc(&h->xm, (size_t)h->ntypes * 4 * G.nyn));
+    CK(dalloc(&h->fac, (size_t)9 * std::max(1, G.N - 1) * G.nyn));
+    CK(dalloc(&h->tmp, (size_t)h->nI));
+    CK(dalloc(&h->xs, (size_t)h->nI));
+    double2* work = nullptr;
+    CK(cudaMalloc(&work, sizeof(double2) * (size_t)h->ntypes * G.nyn * 2 * G.nxs));
+    cudaEvent_t t0, t1;
+    cudaEventCreate(&t0);
+    cudaEventCreate(&t1);
+    cudaEventRecord(t0, h->s);
+    cudaError_t e = launch_modal_setup(G, h->ntypes, h->tkind, h->btype, h->Cf, h->Ci, h->Cf32, h->Ci32, h->xm, h->fac,
+                                       work, h->s);
+    cudaEventRecord(t1, h->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, t0, t1);
+    h->setup_ms = ms;
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    cudaFree(work);
+    if (e != cudaSuccess) return fail(h, DD_NLS_ECUDA, std::string("modal set-up: ") + cudaGetErrorString(e));
+    return DD_NLS_OK;
+}
+
+static int build_Lh(dd_nls* h) {
+    const Geom& G = h->G;
+    const int nyn = G.nyn;
+    const long long bs = (long long)nyn * nyn;
+    std::vector<std::pair<int, int>> types;
+    int rc0 = strip_types(h, types);
+    if (rc0) return rc0;
+    CK(dalloc(&h->X64, (size_t)h->ntypes * 4 * bs));
 
     // virtual-strip buffers
     const int maxb = strip_solve_max_blocks(h->fp32);
@@ -539,13 +593,19 @@ static int schwarz(dd_nls* h, dd_nls_stats* st) {
         } else {
             // g^{k+1} = g^k - P^{-1} (g^k - R(g^k))  (eq. algo_pd)
             ProfScope ps(h, &h->profile.interface_ms);
-            CK(launch_sub(h->tmp, g, gn, h->nI, h->s));
-            CK(launch_copy(gn, h->tmp, h->nI, h->s));          // gn := y
-            long long its = 0;
-            rc = gmres(h, gn, h->xs, &its);
-            if (rc) return rc;
-            if (st) st->gmres_iterations += its;
-            CK(launch_sub(gn, g, h->xs, h->nI, h->s));
+            if (h->P.psolve == DD_NLS_PSOLVE_MODAL) {
+                CK(launch_sub(h->tmp, g, gn, h->nI, h->s));     // y = g - R(g)
+                CK(launch_modal_apply(G, h->fp32, h->Cf, h->Ci, h->Cf32, h->Ci32, h->fac, h->tmp, h->xs, gn, h->s));
+                CK(launch_sub(gn, g, h->xs, h->nI, h->s));
+            } else {
+                CK(launch_sub(h->tmp, g, gn, h->nI, h->s));
+                CK(launch_copy(gn, h->tmp, h->nI, h->s));          // gn := y
+                long long its = 0;
+                rc = gmres(h, gn, h->xs, &its);
+                if (rc) return rc;
+                if (st) st->gmres_iterations += its;
+                CK(launch_sub(gn, g, h->xs, h->nI, h->s));
+            }
             std::swap(g, gn);
         }
     }
@@ -677,7 +737,11 @@ extern "C" int dd_nls_create(const dd_nls_params* p, const double* V, const doub
     }
     CKC(cudaStreamSynchronize(h->s));
     if (p->algorithm == DD_NLS_PRECONDITIONED && G.N > 1) {
-        int rc = build_Lh(h);
+        if (p->psolve != DD_NLS_PSOLVE_GMRES && p->psolve != DD_NLS_PSOLVE_MODAL) {
+            h->error = "dd_nls_create: unknown psolve";
+            return bad(DD_NLS_EINVAL);
+        }
+        int rc = p->psolve == DD_NLS_PSOLVE_MODAL ? build_modal(h) : build_Lh(h);
         if (rc) return bad(rc);
     }
     *out = h;
@@ -751,6 +815,15 @@ extern "C" int dd_nls_get_blocks(dd_nls* h, int strip, double* x, int ptr_kind) 
     if (!h->X64 || strip < 0 || strip >= h->G.N || !x) return fail(h, DD_NLS_EINVAL, "dd_nls_get_blocks: no L_h or bad strip");
     const long long bs = (long long)h->G.nyn * h->G.nyn;
     CK(cudaMemcpyAsync(x, h->X64 + (long long)h->btype_h[strip] * 4 * bs, 4 * bs * sizeof(double2),
+                       ptr_kind == DD_NLS_PTR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    return DD_NLS_OK;
+}
+
+extern "C" int dd_nls_get_modal(dd_nls* h, int strip, double* x, int ptr_kind) {
+    if (!h) return fail(nullptr, DD_NLS_EINVAL, "dd_nls_get_modal: NULL handle");
+    if (!h->xm || strip < 0 || strip >= h->G.N || !x) return fail(h, DD_NLS_EINVAL, "dd_nls_get_modal: no modal P or bad strip");
+    CK(cudaMemcpyAsync(x, h->xm + (long long)h->btype_h[strip] * 4 * h->G.nyn, 4 * h->G.nyn * sizeof(double2),
                        ptr_kind == DD_NLS_PTR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->s));
     CK(cudaStreamSynchronize(h->s));
     return DD_NLS_OK;

@@ -73,6 +73,14 @@ cudaError_t launch_apply_P(const AuxGeom& g, const void* X, bool fp32, const int
                            const double2* x, double2* y, double2* work, cudaStream_t s);
 cudaError_t launch_convert_blocks(const double2* X, float2* Xf, long long n, cudaStream_t s);
 
+// exact P^{-1} in the cosine basis (modal.cu)
+cudaError_t launch_modal_setup(const AuxGeom& g, int ntypes, const int* tkind_dev, const int* btype_dev,
+                               double* Cf, double* Ci, float* Cf32, float* Ci32, double2* xm, double2* fac,
+                               double2* work, cudaStream_t s);
+cudaError_t launch_modal_apply(const AuxGeom& g, bool fp32, const double* Cf, const double* Ci, const float* Cf32,
+                               const float* Ci32, const double2* fac, const double2* y, double2* x, double2* tmp,
+                               cudaStream_t s);
+
 // GMRES helpers on vectors of length n (complex, FP64)
 cudaError_t launch_dots(const double2* V, long long ld, int k, const double2* w, long long n, double2* out,
                         double* scratch, cudaStream_t s);

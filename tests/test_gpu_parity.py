@@ -75,10 +75,12 @@ def test_schwarz_iteration_counts_match_oracle_away_from_roundoff():
         assert abs(st["last_schwarz_iterations"] - info.iterations) <= 1
 
 
+@pytest.mark.parametrize("psolve", [binding.PSOLVE_MODAL, binding.PSOLVE_GMRES])
 @pytest.mark.parametrize("precision", [binding.FP64, binding.FP32_INNER])
-def test_preconditioned_robin_matches_oracle(precision):
+def test_preconditioned_robin_matches_oracle(precision, psolve):
     ref = run_oracle(WELL, 2, algorithm="preconditioned")
-    got = run_gpu(WELL, 2, tol=TOL, precision=precision, algorithm=binding.PRECONDITIONED, gmres_tol=1e-12)
+    got = run_gpu(WELL, 2, tol=TOL, precision=precision, algorithm=binding.PRECONDITIONED, gmres_tol=1e-12,
+                  psolve=psolve)
     bound = 1e-11 if precision == binding.FP64 else 1e-10
     for (ug, st), (uo, info) in zip(got, ref):
         assert rel(ug, uo) < bound
@@ -90,10 +92,48 @@ def test_lh_blocks_match_oracle():
     prob = oracle_problem(w)
     st = nls.Strips(prob, w.n_strips)
     X = st.strip_blocks(1)
-    with binding.Solver(gpu_params(w, algorithm=binding.PRECONDITIONED, nl_tol=1e-14), w.u0(), w.V()) as s:
+    with binding.Solver(gpu_params(w, algorithm=binding.PRECONDITIONED, nl_tol=1e-14, psolve=binding.PSOLVE_GMRES),
+                        w.u0(), w.V()) as s:
         B = s.blocks(1)
     for k in range(4):
         assert np.max(np.abs(B[k] - X[k])) < 1e-11 * max(1.0, np.max(np.abs(X[k])))
+
+
+@pytest.mark.parametrize("bc", ["same", "neumann"])
+def test_modal_diagonal_matches_oracle_blocks(bc):
+    """The GPU's per-mode entries x1..x4 equal the diagonal of the oracle's L_h blocks (built by
+    unit solves) in the cosine basis."""
+    w = WELL
+    prob = oracle_problem(w, bc=bc)
+    st = nls.Strips(prob, w.n_strips)
+    ny = w.ny
+    j = np.arange(ny + 1)
+    Z = np.cos(np.pi * np.outer(j, j) / ny)
+    D = np.ones(ny + 1)
+    D[0] = D[-1] = 0.5
+    Zi = np.diag(1.0 / np.diag((Z.T * D) @ Z)) @ Z.T @ np.diag(D)
+    kw = dict(algorithm=binding.PRECONDITIONED, psolve=binding.PSOLVE_MODAL,
+              bc=binding.BC_NEUMANN if bc == "neumann" else binding.BC_SAME)
+    with binding.Solver(gpu_params(w, **kw), w.u0(), w.V()) as s:
+        for strip in (0, 1, w.n_strips - 1):
+            xm = s.modal(strip)
+            X = st.strip_blocks(strip)
+            reg = st.regions[strip]
+            for a in range(4):
+                if (a in (0, 2) and reg.kind["l"] != "tc") or (a in (1, 3) and reg.kind["r"] != "tc"):
+                    continue
+                np.testing.assert_allclose(xm[a], np.diag(Zi @ X[a] @ Z), atol=1e-11)
+
+
+@pytest.mark.parametrize("precision", [binding.FP64, binding.FP32_INNER])
+def test_free_problem_converges_in_one_exact_preconditioned_update(precision):
+    """V = 0, f = 0: R is affine with linear part L_h, so g^1 = g^0 - P^{-1}(g^0 - R g^0) is the
+    fixed point when P^{-1} is exact (the modal solve): the second residual is at round-off."""
+    w = wl.scaled(WELL, 40, 45, n_strips=5, potential="zero", kappa=0.0)
+    got = run_gpu(w, 1, tol=1e-10, precision=precision, algorithm=binding.PRECONDITIONED,
+                  psolve=binding.PSOLVE_MODAL)
+    # the FP32 form applies the cosine transforms in FP32 (P^{-1} exact to ~1e-6)
+    assert got[0][1]["last_schwarz_iterations"] == (2 if precision == binding.FP64 else 3)
 
 
 def test_single_strip_is_the_monodomain_solve():

@@ -257,3 +257,27 @@ def test_any_initial_guess_reaches_the_same_step():
     ua, _, _ = nls.schwarz_step(prob, 2, u0, tol=1e-12, strips=st)
     ub, _, ib = nls.schwarz_step(prob, 2, u0, g0=g_rand, tol=1e-12, strips=st)
     assert rel(ua, ub) < 1e-10
+
+
+def cosine_basis(ny):
+    j = np.arange(ny + 1)
+    Z = np.cos(np.pi * np.outer(j, j) / ny)
+    D = np.ones(ny + 1)
+    D[0] = D[-1] = 0.5
+    sig = np.diag((Z.T * D) @ Z)
+    return Z, np.diag(1.0 / sig) @ Z.T @ np.diag(D)
+
+
+@pytest.mark.parametrize("bc", ["same", "neumann"])
+def test_lh_blocks_are_diagonal_in_the_cosine_basis(bc):
+    """Uniform Q1 mesh with Neumann data in y: My and Ky share the eigenvectors cos(pi j k/ny)
+    (w.r.t. D = diag(1/2,1,..,1,1/2)), so every block of L_h built by unit solves is diagonal
+    in that basis.  This is what the exact modal P solve relies on."""
+    prob, _ = small_problem(nx=20, ny=10, kappa=0.0, with_V=False, bc=bc)
+    st = nls.Strips(prob, 4)
+    Z, Zi = cosine_basis(prob.ny)
+    np.testing.assert_allclose(Zi @ Z, np.eye(prob.ny + 1), atol=1e-14)
+    for j in (0, 1, 3):
+        for X in st.strip_blocks(j):
+            Xh = Zi @ X @ Z
+            assert np.max(np.abs(Xh - np.diag(np.diag(Xh)))) < 1e-13
