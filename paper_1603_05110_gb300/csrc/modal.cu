@@ -59,7 +59,7 @@ __global__ void modal_eigs_kernel(Geom g, int ntypes, const int* __restrict__ tk
     double2 out[4];
     for (int side = 0; side < 2; ++side) {
         const int active = side == 0 ? ltc : rtc;
-        if (!active) { out[2 * side] = out[2 * side + 1] = make_double2(0, 0); continue; }
+        if (!active) { out[side] = out[side + 2] = make_double2(0, 0); continue; }   // side 0: x1, x3; side 1: x2, x4
         for (int i = 0; i < m; ++i) {
             const bool lo = i > 0, hi = i < c;
             const double mii = (lo && hi) ? g.mxi : g.mxe, kii = (lo && hi) ? g.kxi : g.kxe;
