@@ -333,6 +333,8 @@ def run_ours(args, rank, world, local_rank):
         "krylov_iterations_per_step": kry / args.steps,
         "nl_iterations_per_step": sum(s["nl_iterations"] for s in stats) / args.steps,
         "gmres_iterations_per_step": sum(s["gmres_iterations"] for s in stats) / args.steps,
+        "strip_solve_phase_share": dict(zip(["fp64_residual", "krylov_stencil", "krylov_update", "commit", "waits"],
+                                            [c / max(1.0, sum(prof["phase_cycles"])) for c in prof["phase_cycles"]])),
         "time_split_ms_per_step": {"strip_solve": prof["strip_solve_ms"] / args.steps,
                                    "interface": prof["interface_ms"] / args.steps,
                                    "other": prof["other_ms"] / args.steps},

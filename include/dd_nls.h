@@ -117,6 +117,9 @@ typedef struct {
     double interface_ms;          /* traces, residuals, GMRES, L_h products */
     double other_ms;              /* right sides, commit, diagnostics */
     long long kernel_launches;    /* all kernels this handle launched while profiling was on */
+    double phase_cycles[5];       /* strip solver, SM cycles per block (averaged over blocks, summed
+                                     over launches): FP64 residual, Krylov stencil phase, Krylov
+                                     update phase, correction commit, waits at barriers/reductions */
 } dd_nls_profile;
 
 /* Fill *p with defaults: NLS (lap=1, kappa=1), Robin p=1, classical, FP64, previous-step

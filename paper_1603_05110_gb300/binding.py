@@ -59,10 +59,13 @@ class Profile(ctypes.Structure):
         ("strip_solve_bytes", ctypes.c_double), ("strip_solve_flops", ctypes.c_double),
         ("interface_ms", ctypes.c_double), ("other_ms", ctypes.c_double),
         ("kernel_launches", ctypes.c_longlong),
+        ("phase_cycles", ctypes.c_double * 5),
     ]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["phase_cycles"] = list(self.phase_cycles)
+        return d
 
 
 SYMBOLS = ["dd_nls_default_params", "dd_nls_create", "dd_nls_step", "dd_nls_solve_interface",

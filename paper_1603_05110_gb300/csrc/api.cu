@@ -39,6 +39,8 @@ struct dd_nls {
     int* d_blk = nullptr;   // [maxb] block -> strip, then [maxb+1] strip -> first block
     int* h_blk = nullptr;   // pinned mirror
     double* bnorm0 = nullptr;   // [N] per-strip ||(2i/dt) M h||
+    long long* pcyc = nullptr;  // [maxb][8] phase cycles of the strip solver
+    std::vector<long long> h_pcyc;
     std::vector<double> wts;    // scheduling weights
     // device state
     double2 *u = nullptr, *zeta = nullptr, *rhs0 = nullptr, *gA = nullptr, *gB = nullptr, *gconv = nullptr;
@@ -126,6 +128,7 @@ static void release(dd_nls* h) {
     if (h->h_blk) cudaFreeHost(h->h_blk);
     if (h->d_blk) cudaFree(h->d_blk);
     if (h->bnorm0) cudaFree(h->bnorm0);
+    if (h->pcyc) cudaFree(h->pcyc);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
     if (h->ev2) cudaEventDestroy(h->ev2);
@@ -205,8 +208,10 @@ static int schedule(dd_nls* h, const std::vector<double>& w, int nstrips, int ca
 static int strip_solve(dd_nls* h, StripSolveArgs& a, int nstrips, int nblocks, dd_nls_stats* st, bool count) {
     CK(cudaMemsetAsync(h->bar, 0, sizeof(unsigned) * nstrips, h->s));
     CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->s));
+    a.pcyc = h->prof ? h->pcyc : nullptr;
     if (h->prof) CK(cudaEventRecord(h->ev0, h->s));
     CK(launch_strip_solve(a, nblocks, h->fp32, h->s));
+    if (h->prof) CK(cudaMemcpyAsync(h->h_pcyc.data(), h->pcyc, sizeof(long long) * 8 * nblocks, cudaMemcpyDeviceToHost, h->s));
     if (h->prof) CK(cudaEventRecord(h->ev1, h->s));
     CK(cudaMemcpyAsync(h->h_status.data(), h->status, sizeof(int) * nstrips, cudaMemcpyDeviceToHost, h->s));
     CK(cudaMemcpyAsync(h->h_nl.data(), h->nl_its, sizeof(int) * nstrips, cudaMemcpyDeviceToHost, h->s));
@@ -231,6 +236,11 @@ static int strip_solve(dd_nls* h, StripSolveArgs& a, int nstrips, int nblocks, d
         h->profile.strip_solve_launches += 1;
         h->profile.strip_solve_bytes += bytes;
         h->profile.strip_solve_flops += flops;
+        for (int k = 0; k < 5; ++k) {
+            double sum = 0.0;
+            for (int b = 0; b < nblocks; ++b) sum += (double)h->h_pcyc[(size_t)b * 8 + k];
+            h->profile.phase_cycles[k] += sum / nblocks;
+        }
     }
     if (st && count) {
         st->nl_iterations += nl;
@@ -728,6 +738,8 @@ extern "C" int dd_nls_create(const dd_nls_params* p, const double* V, const doub
     CKC(dalloc(&h->d_blk, (size_t)2 * maxb + 2));
     CKC(cudaMallocHost((void**)&h->h_blk, sizeof(int) * (2 * maxb + 2)));
     CKC(dalloc(&h->bnorm0, G.N));
+    CKC(dalloc(&h->pcyc, (size_t)8 * maxb));
+    h->h_pcyc.assign((size_t)8 * maxb, 0);
 
     if (upload_nodal(h, u0, ptr_kind, h->u)) return bad(DD_NLS_ECUDA);
     if (V) {

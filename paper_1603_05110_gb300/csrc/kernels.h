@@ -36,6 +36,7 @@ struct StripSolveArgs {
     long long* kry_its;      // [strips]
     double* nl_res;          // [strips]
     int* err;                // launch-wide error word
+    long long* pcyc;         // [gridDim][8] phase cycles (R, A, B, epilogue, waits) or NULL
 };
 
 // cooperative launch of nblocks blocks (a.blk_strip / a.blk_start map blocks to strips)

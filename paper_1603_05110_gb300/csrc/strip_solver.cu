@@ -137,6 +137,14 @@ strip_solve_kernel(StripSolveArgs a) {
     int status = 0, nl_it = 0;
     long long kry = 0;
     double nres = 0.0;
+    // optional phase timing (thread 0, SM clock cycles): R, A, B, epilogue compute; waits
+    long long cyc[5] = {0, 0, 0, 0, 0};
+    long long tmark = clock64();
+    auto lap = [&](int slot) {
+        const long long t = clock64();
+        cyc[slot] += t - tmark;
+        tmark = t;
+    };
 
     auto robin_at = [&](int ix) -> double {
         double rb = 0.0;
@@ -212,9 +220,11 @@ strip_solve_kernel(StripSolveArgs a) {
         block_sum<4>(loc, s_red);
         if (threadIdx.x == 0) { double* sp = slot_ptr(epoch + 1); sp[0] = loc[0]; sp[1] = loc[1]; sp[2] = loc[2]; sp[3] = loc[3]; }
         ++epoch;
+        lap(0);
         if (!group_barrier(bar, epoch * bps, a.err, &s_flag)) { status = DD_NLS_ETIMEOUT; break; }
         double tot[4];
         group_sum<4>(group_ptr(epoch), bps, tot, s_red);
+        lap(4);
         const double rnorm = sqrt(tot[0]);
         bnorm = sqrt(tot[1]);
         nres = bnorm > 0.0 ? rnorm / bnorm : rnorm;
@@ -252,9 +262,11 @@ strip_solve_kernel(StripSolveArgs a) {
             block_sum_t<T, 2>(lmT, lm, s_red);
             if (threadIdx.x == 0) { double* sp = slot_ptr(epoch + 1); sp[0] = lm[0]; sp[1] = lm[1]; sp[2] = 0; sp[3] = 0; }
             ++epoch;
+            lap(1);
             if (!group_barrier(bar, epoch * bps, a.err, &s_flag)) { status = DD_NLS_ETIMEOUT; break; }
             double mu[4];
             group_sum<4>(group_ptr(epoch), bps, mu, s_red);
+            lap(4);
             const double mu2 = mu[0] * mu[0] + mu[1] * mu[1];
             if (!(mu2 > 0.0) || !isfinite(mu2)) { status = isfinite(mu2) ? DD_NLS_EBREAKDOWN : DD_NLS_ENONFINITE; break; }
             // a = rho / mu
@@ -287,9 +299,11 @@ strip_solve_kernel(StripSolveArgs a) {
             block_sum_t<T, 3>(lbT, lb, s_red);
             if (threadIdx.x == 0) { double* sp = slot_ptr(epoch + 1); sp[0] = lb[0]; sp[1] = lb[1]; sp[2] = lb[2]; sp[3] = 0; }
             ++epoch;
+            lap(2);
             if (!group_barrier(bar, epoch * bps, a.err, &s_flag)) { status = DD_NLS_ETIMEOUT; break; }
             double rb[4];
             group_sum<4>(group_ptr(epoch), bps, rb, s_red);
+            lap(4);
             ++kry;
             if (!isfinite(rb[2])) { status = DD_NLS_ENONFINITE; break; }
             if (sqrt(rb[2]) <= target) break;
@@ -314,8 +328,12 @@ strip_solve_kernel(StripSolveArgs a) {
         }
         inv_s = 1.0 / rnorm;           // scale of the next correction
         ++epoch;
+        lap(3);
         if (!group_barrier(bar, epoch * bps, a.err, &s_flag)) { status = DD_NLS_ETIMEOUT; break; }
+        lap(4);
     }
+    if (a.pcyc && threadIdx.x == 0)
+        for (int k = 0; k < 5; ++k) a.pcyc[(size_t)blockIdx.x * 8 + k] = cyc[k];
     if (rank == 0 && threadIdx.x == 0) {
         a.status[j] = status;
         a.nl_its[j] = nl_it;
