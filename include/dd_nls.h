@@ -159,6 +159,22 @@ int dd_nls_get_modal(dd_nls* h, int strip, double* x, int ptr_kind);
 int dd_nls_set_profiling(dd_nls* h, int on);
 int dd_nls_get_profile(dd_nls* h, dd_nls_profile* prof);
 
+/* One time step (eq. CNS) without allocating device memory.  The paper has no counterpart:
+ * this entry point is for callers that cannot call cudaMalloc when they step -- code inside
+ * a memory pool or arena that owns the device, a process that must not change the
+ * allocation state of a context it shares, a path where cudaMalloc's implicit
+ * synchronisation is not allowed.  All working memory comes from one fixed 64 MiB device
+ * array inside the library (held on every GPU that loads the library until the process
+ * exits); a problem that needs more is rejected with DD_NLS_EINVAL, as are more than 64
+ * strips.  Only the classical algorithm with the Robin condition (FP64 or FP32 inner).
+ * V (nullable), u (in: u_{n-1}, out: u_n), g0 (nullable: zero guess) and g_out (nullable:
+ * the converged R(g), the next step's guess) are DEVICE pointers in the layouts above;
+ * stream may be NULL.  Every call uses the same array: calls that overlap on the GPU race.
+ * The first call on a device looks up the array's address (with that device current); make
+ * it before any stream capture.  Errors: dd_nls_last_error(NULL) describes them. */
+int dd_nls_step_noalloc(const dd_nls_params* p, const double* V, double* u, const double* g0,
+                        double* g_out, void* stream, dd_nls_stats* stats);
+
 /* Release everything the handle owns.  NULL is ignored. */
 void dd_nls_destroy(dd_nls* h);
 

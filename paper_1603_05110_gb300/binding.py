@@ -70,7 +70,7 @@ class Profile(ctypes.Structure):
 
 SYMBOLS = ["dd_nls_default_params", "dd_nls_create", "dd_nls_step", "dd_nls_solve_interface",
            "dd_nls_get_state", "dd_nls_set_state", "dd_nls_get_blocks", "dd_nls_get_modal", "dd_nls_set_profiling",
-           "dd_nls_get_profile", "dd_nls_destroy", "dd_nls_last_error"]
+           "dd_nls_get_profile", "dd_nls_destroy", "dd_nls_last_error", "dd_nls_step_noalloc"]
 
 _lib = None
 
@@ -109,6 +109,8 @@ def load(path=LIB_PATH):
     lib.dd_nls_destroy.restype = None
     lib.dd_nls_last_error.argtypes = [vp]
     lib.dd_nls_last_error.restype = ctypes.c_char_p
+    lib.dd_nls_step_noalloc.argtypes = [ctypes.POINTER(Params), vp, vp, vp, vp, vp, ctypes.POINTER(Stats)]
+    lib.dd_nls_step_noalloc.restype = ip
     _ = dp
     _lib = lib
     return lib
@@ -152,6 +154,29 @@ def _kind(*kinds):
     if len(ks) > 1:
         raise ValueError("mix of host and device arrays in one call")
     return ks.pop() if ks else PTR_HOST
+
+
+def step_noalloc(params, u, V=None, g0=None, g_out=None, stream=None):
+    """One time step through dd_nls_step_noalloc (no device allocation inside the library).
+
+    u (in/out), V, g0, g_out must be CUDA tensors (device pointers)."""
+    lib = load()
+    if isinstance(params, dict):
+        params = default_params(**params)
+    ptrs = []
+    for a in (V, u, g0, g_out):
+        pa, ka = _ptr(a)
+        if pa is not None and ka != PTR_DEVICE:
+            raise ValueError("dd_nls_step_noalloc takes device arrays only")
+        ptrs.append(pa)
+    s = None
+    if stream is not None:
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    st = Stats()
+    rc = lib.dd_nls_step_noalloc(ctypes.byref(params), ptrs[0], ptrs[1], ptrs[2], ptrs[3], s, ctypes.byref(st))
+    if rc != 0:
+        raise DDNLSError(rc, lib.dd_nls_last_error(None).decode(), st.as_dict())
+    return st.as_dict()
 
 
 class Solver:

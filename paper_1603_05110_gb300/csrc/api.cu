@@ -27,6 +27,10 @@ using cplx = std::complex<double>;
 
 static std::string g_create_error;
 
+namespace ddnls {
+void set_handle_free_error(const char* msg) { g_create_error = msg; }
+}  // namespace ddnls
+
 struct dd_nls {
     dd_nls_params P{};
     Geom G{};

@@ -6,6 +6,9 @@
 
 namespace ddnls {
 
+// Error text returned by dd_nls_last_error(NULL) (api.cu).
+void set_handle_free_error(const char* msg);
+
 // Kernels launched by this library since load (every launch_* wrapper adds its count).
 long long kernel_launch_count();
 void count_launches(int n);
