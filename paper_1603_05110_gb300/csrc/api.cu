@@ -67,6 +67,11 @@ struct dd_nls {
     std::vector<int> btype_h;
     double2 *V = nullptr, *w = nullptr, *tmp = nullptr, *hdev = nullptr, *xs = nullptr;
     double* scratch = nullptr;
+    // S_pade^m (eq. TCS): coefficients and auxiliary unknowns
+    int pade_m = 0;
+    double2 pade_a[kMaxPade], pade_d[kMaxPade];
+    double2 *pa_dev = nullptr, *pd_dev = nullptr, *phi = nullptr;
+    void *xf = nullptr, *rf = nullptr, *zf = nullptr, *pf = nullptr, *qf = nullptr, *cTf = nullptr;
     // modal P solve
     double *Cf = nullptr, *Ci = nullptr;
     float *Cf32 = nullptr, *Ci32 = nullptr;
@@ -125,7 +130,8 @@ static void release(dd_nls* h) {
     void* ptrs[] = {h->u, h->zeta, h->rhs0, h->gA, h->gB, h->gconv, h->Wn, h->x, h->r, h->z, h->p, h->q, h->cT,
                     h->part, h->bar, h->status, h->nl_its, h->kry, h->nl_res, h->err, h->red, h->stage,
                     h->X64, h->X32, h->btype, h->V, h->w, h->tmp, h->hdev, h->xs, h->scratch,
-                    h->Cf, h->Ci, h->Cf32, h->Ci32, h->xm, h->fac, h->tkind};
+                    h->Cf, h->Ci, h->Cf32, h->Ci32, h->xm, h->fac, h->tkind,
+                    h->pa_dev, h->pd_dev, h->phi, h->xf, h->rf, h->zf, h->pf, h->qf, h->cTf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->hred) cudaFreeHost(h->hred);
@@ -286,6 +292,11 @@ static StripSolveArgs base_args(dd_nls* h) {
     a.kry_its = h->kry;
     a.nl_res = h->nl_res;
     a.err = h->err;
+    a.pcyc = nullptr;
+    a.pade_m = h->pade_m;
+    a.phi = h->phi;
+    a.xf = h->xf; a.rf = h->rf; a.zf = h->zf; a.pf = h->pf; a.qf = h->qf; a.cTf = h->cTf;
+    for (int s2 = 0; s2 < h->pade_m; ++s2) { a.pade_a[s2] = h->pade_a[s2]; a.pade_d[s2] = h->pade_d[s2]; }
     return a;
 }
 
@@ -336,7 +347,7 @@ static int build_modal(dd_nls* h) {
     cudaEventCreate(&t1);
     cudaEventRecord(t0, h->s);
     cudaError_t e = launch_modal_setup(G, h->ntypes, h->tkind, h->btype, h->Cf, h->Ci, h->Cf32, h->Ci32, h->xm, h->fac,
-                                       work, h->s);
+                                       work, h->s, h->pade_m, h->pa_dev, h->pd_dev);
     cudaEventRecord(t1, h->s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
     float ms = 0.f;
@@ -556,6 +567,8 @@ static int schwarz(dd_nls* h, dd_nls_stats* st) {
         CK(launch_finalize(h->part, nb, 1, h->red + 8, h->s));
         CK(launch_sqrt(h->red + 8, h->s));
         CK(cudaMemcpyAsync(h->zeta, h->u, h->nfield * sizeof(double2), cudaMemcpyDeviceToDevice, h->s));   // zeta^0 = h
+        if (h->pade_m)        // phi^0 = 0 (eq. localpbS2p)
+            CK(cudaMemsetAsync(h->phi, 0, sizeof(double2) * (size_t)G.N * 2 * h->pade_m * G.P, h->s));
         CK(launch_strip_norms(G, h->rhs0, h->bnorm0, h->s));
         CK(cudaMemcpyAsync(h->hred + 16, h->bnorm0, sizeof(double) * G.N, cudaMemcpyDeviceToHost, h->s));
         CK(cudaStreamSynchronize(h->s));
@@ -580,7 +593,7 @@ static int schwarz(dd_nls* h, dd_nls_stats* st) {
         int nb = 1;
         if (G.N > 1) {
             ProfScope ps(h, &h->profile.interface_ms);
-            CK(launch_traces(G, h->zeta, g, gn, h->part, &nb, h->s));
+            CK(launch_traces(G, h->zeta, g, gn, h->part, &nb, h->s, h->pade_m, h->phi, h->pa_dev, h->pd_dev));
             CK(launch_finalize(h->part, nb, 2, h->red, h->s));
             CK(cudaMemcpyAsync(h->hred, h->red, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->s));
             CK(cudaStreamSynchronize(h->s));
@@ -659,9 +672,13 @@ extern "C" int dd_nls_create(const dd_nls_params* p, const double* V, const doub
         return fail(nullptr, DD_NLS_EINVAL, "dd_nls_create: need nx, ny >= 1 and nx a multiple of n_strips");
     if (!(p->xr > p->xl) || !(p->yu > p->yb) || !(p->dt > 0) || !(p->lap > 0))
         return fail(nullptr, DD_NLS_EINVAL, "dd_nls_create: need xr > xl, yu > yb, dt > 0, lap > 0");
-    if (p->tc != DD_NLS_TC_ROBIN)
-        return fail(nullptr, DD_NLS_EINVAL, "dd_nls_create: only the Robin transmission condition is built in this version");
-    if (!(p->p > 0.0)) return fail(nullptr, DD_NLS_EINVAL, "dd_nls_create: Robin p must be > 0");
+    if (p->tc != DD_NLS_TC_ROBIN && p->tc != DD_NLS_TC_PADE)
+        return fail(nullptr, DD_NLS_EINVAL, "dd_nls_create: unknown transmission condition");
+    if (p->tc == DD_NLS_TC_ROBIN && !(p->p > 0.0)) return fail(nullptr, DD_NLS_EINVAL, "dd_nls_create: Robin p must be > 0");
+    if (p->tc == DD_NLS_TC_PADE && (p->pade_m < 1 || p->pade_m > kMaxPade))
+        return fail(nullptr, DD_NLS_EINVAL, "dd_nls_create: Pade order m must be in 1..96");
+    if (p->tc == DD_NLS_TC_PADE && p->algorithm == DD_NLS_PRECONDITIONED && p->psolve == DD_NLS_PSOLVE_GMRES)
+        return fail(nullptr, DD_NLS_EINVAL, "dd_nls_create: S_pade with the preconditioned algorithm uses the modal P solve");
     if (p->precision != DD_NLS_FP64 && p->precision != DD_NLS_FP32_INNER)
         return fail(nullptr, DD_NLS_EINVAL, "dd_nls_create: unknown precision");
     if (ptr_kind != DD_NLS_PTR_HOST && ptr_kind != DD_NLS_PTR_DEVICE)
@@ -743,6 +760,30 @@ extern "C" int dd_nls_create(const dd_nls_params* p, const double* V, const doub
     CKC(cudaMallocHost((void**)&h->h_blk, sizeof(int) * (2 * maxb + 2)));
     CKC(dalloc(&h->bnorm0, G.N));
     CKC(dalloc(&h->pcyc, (size_t)8 * maxb));
+    if (p->tc == DD_NLS_TC_PADE) {
+        // a_s = e^{i theta/2} / (m cos^2 phi_s), d_s = e^{i theta} tan^2 phi_s, phi_s = (2s-1) pi/(4m),
+        // s = 1..m (eq. TCS; the sums start at s = 1)
+        const int m = p->pade_m;
+        h->pade_m = m;
+        for (int s2 = 1; s2 <= m; ++s2) {
+            const double ph = (2.0 * s2 - 1.0) * M_PI / (4.0 * m);
+            const double ca = 1.0 / (m * std::cos(ph) * std::cos(ph)), tn = std::tan(ph) * std::tan(ph);
+            h->pade_a[s2 - 1] = make_double2(ca * std::cos(0.5 * p->pade_theta), ca * std::sin(0.5 * p->pade_theta));
+            h->pade_d[s2 - 1] = make_double2(tn * std::cos(p->pade_theta), tn * std::sin(p->pade_theta));
+        }
+        CKC(dalloc(&h->pa_dev, m));
+        CKC(dalloc(&h->pd_dev, m));
+        CKC(cudaMemcpy(h->pa_dev, h->pade_a, sizeof(double2) * m, cudaMemcpyHostToDevice));
+        CKC(cudaMemcpy(h->pd_dev, h->pade_d, sizeof(double2) * m, cudaMemcpyHostToDevice));
+        const size_t nf = (size_t)G.N * 2 * m * G.P;
+        CKC(dalloc(&h->phi, nf));
+        CKC(dalloc((char**)&h->xf, nf * s2));
+        CKC(dalloc((char**)&h->rf, nf * s2));
+        CKC(dalloc((char**)&h->zf, nf * s2));
+        CKC(dalloc((char**)&h->pf, nf * s2));
+        CKC(dalloc((char**)&h->qf, nf * s2));
+        CKC(dalloc((char**)&h->cTf, (size_t)G.N * 2 * G.P * s1));
+    }
     h->h_pcyc.assign((size_t)8 * maxb, 0);
 
     if (upload_nodal(h, u0, ptr_kind, h->u)) return bad(DD_NLS_ECUDA);

@@ -119,12 +119,26 @@ cudaError_t launch_strip_norms(const Geom& g, const double2* rhs0, double* out, 
 }
 
 // ------------------------------------------------------------------ flux update
-// eq. (fluxlr) with Robin S v = -i p v (eq. TCSRobin):
-//   new r_i     = -l_{i+1} + 2 S v_{i+1}(a_{i+1}) = -g[2i+1] - 2ip zeta_{i+1}(0, .)
-//   new l_{i+1} = -r_i     + 2 S v_i(b_i)         = -g[2i]   - 2ip zeta_i(c, .)
+// eq. (fluxlr):  new r_i = -l_{i+1} + 2 S v_{i+1}(a_{i+1}),  new l_{i+1} = -r_i + 2 S v_i(b_i),
+// with S of eq. (TCSdist): Robin  S v = -i p v;  S_pade  S v = -i sum_s a_s v + i sum_s a_s d_s phi_s
+// (phi_s of the strip the trace belongs to, on that edge).
 // Partial sums per block: ||gnew - g||^2, ||gnew||^2.
+__device__ __forceinline__ double2 two_S(const Geom& g, double2 v, int pade_m, const double2* phi_e, long long P,
+                                         int iy, const double2* pa, const double2* pd) {
+    if (pade_m == 0) return make_double2(2.0 * g.p * v.y, -2.0 * g.p * v.x);
+    double2 sa = make_double2(0, 0), acc = make_double2(0, 0);
+    for (int s = 0; s < pade_m; ++s) {
+        sa = cadd(sa, pa[s]);
+        acc = cadd(acc, cmul(cmul(pa[s], pd[s]), phi_e[(long long)s * P + iy]));
+    }
+    // -i sa v + i acc
+    const double2 t = csub(acc, cmul(sa, v));
+    return make_double2(-2.0 * t.y, 2.0 * t.x);
+}
 __global__ void traces_kernel(Geom g, const double2* __restrict__ zeta, const double2* __restrict__ gtr,
-                              double2* __restrict__ gnew, double* __restrict__ part) {
+                              double2* __restrict__ gnew, double* __restrict__ part, int pade_m,
+                              const double2* __restrict__ phi, const double2* __restrict__ pa,
+                              const double2* __restrict__ pd) {
     __shared__ double sm[64];
     const int c = g.nxs - 1;
     const long long total = (long long)(g.N - 1) * g.nyn;
@@ -136,8 +150,12 @@ __global__ void traces_kernel(Geom g, const double2* __restrict__ zeta, const do
         const double2 zr = zeta[(long long)(i * g.nxs + c) * g.P + iy];           // strip i,   x = b_i
         const double2 gr = gtr[(long long)(2 * i) * g.P + iy];
         const double2 gl = gtr[(long long)(2 * i + 1) * g.P + iy];
-        const double2 nr = make_double2(-gl.x + 2.0 * g.p * zl.y, -gl.y - 2.0 * g.p * zl.x);
-        const double2 nl = make_double2(-gr.x + 2.0 * g.p * zr.y, -gr.y - 2.0 * g.p * zr.x);
+        const double2* phl = pade_m ? phi + ((long long)(i + 1) * 2 + 0) * pade_m * g.P : nullptr;   // strip i+1, left edge
+        const double2* phr = pade_m ? phi + ((long long)i * 2 + 1) * pade_m * g.P : nullptr;         // strip i, right edge
+        const double2 sl = two_S(g, zl, pade_m, phl, g.P, iy, pa, pd);
+        const double2 sr = two_S(g, zr, pade_m, phr, g.P, iy, pa, pd);
+        const double2 nr = make_double2(-gl.x + sl.x, -gl.y + sl.y);
+        const double2 nl = make_double2(-gr.x + sr.x, -gr.y + sr.y);
         gnew[(long long)(2 * i) * g.P + iy] = nr;
         gnew[(long long)(2 * i + 1) * g.P + iy] = nl;
         v[0] += (nr.x - gr.x) * (nr.x - gr.x) + (nr.y - gr.y) * (nr.y - gr.y)
@@ -148,13 +166,14 @@ __global__ void traces_kernel(Geom g, const double2* __restrict__ zeta, const do
     if (threadIdx.x == 0) { part[blockIdx.x * 4 + 0] = v[0]; part[blockIdx.x * 4 + 1] = v[1]; }
 }
 cudaError_t launch_traces(const Geom& g, const double2* zeta, const double2* gtr, double2* gnew, double* part,
-                          int* nblk_out, cudaStream_t s) {
+                          int* nblk_out, cudaStream_t s, int pade_m, const double2* phi, const double2* pa,
+                          const double2* pd) {
     const long long total = (long long)(g.N - 1) * g.nyn;
     int nb = nblocks(total, 256);
     if (nb > 512) nb = 512;
     if (nb < 1) nb = 1;
     count_launches(1);
-    traces_kernel<<<nb, 256, 0, s>>>(g, zeta, gtr, gnew, part);
+    traces_kernel<<<nb, 256, 0, s>>>(g, zeta, gtr, gnew, part, pade_m, phi, pa, pd);
     *nblk_out = nb;
     return cudaGetLastError();
 }

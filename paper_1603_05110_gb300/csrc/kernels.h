@@ -13,6 +13,8 @@ void set_handle_free_error(const char* msg);
 long long kernel_launch_count();
 void count_launches(int n);
 
+constexpr int kMaxPade = 96;   // largest Pade order m of eq. (TCS) the kernels take
+
 struct StripSolveArgs {
     Geom g;
     int bps;                 // unused when blk_strip is set
@@ -40,6 +42,12 @@ struct StripSolveArgs {
     double* nl_res;          // [strips]
     int* err;                // launch-wide error word
     long long* pcyc;         // [gridDim][8] phase cycles (R, A, B, epilogue, waits) or NULL
+    // S_pade^m transmission (eq. TCS): auxiliary unknowns phi_{e,s} on both vertical edges
+    int pade_m;              // 0: Robin
+    double2* phi;            // [strips][2][m][P] FP64 state
+    void *xf, *rf, *zf, *pf, *qf;   // their inner Krylov vectors
+    void* cTf;               // [strips][2][P] w_y (W + kappa|zeta|^2) on each edge, inner precision
+    double2 pade_a[kMaxPade], pade_d[kMaxPade];
 };
 
 // cooperative launch of nblocks blocks (a.blk_strip / a.blk_start map blocks to strips)
@@ -57,9 +65,11 @@ cudaError_t launch_scatter_real(const AuxGeom& g, const double* glob, double sca
 cudaError_t launch_strip_norms(const AuxGeom& g, const double2* rhs0, double* out, cudaStream_t s);
 // rhs0 = i alpha M h (per strip); partial sums of ||rhs0||^2 into part[nblk][1]
 cudaError_t launch_rhs0(const AuxGeom& g, const double2* h, double2* rhs0, double* part, int* nblk_out, cudaStream_t s);
-// interface flux update, eq. (fluxlr), Robin: writes gnew, partial norms into part[nblk][2]
+// interface flux update, eq. (fluxlr): writes gnew, partial norms into part[nblk][2].
+// Robin when pade_m == 0, else S v = -i sum a_s v + i sum a_s d_s phi_s (eq. TCSdist).
 cudaError_t launch_traces(const AuxGeom& g, const double2* zeta, const double2* gtr, double2* gnew,
-                          double* part, int* nblk_out, cudaStream_t s);
+                          double* part, int* nblk_out, cudaStream_t s, int pade_m = 0,
+                          const double2* phi = nullptr, const double2* pa = nullptr, const double2* pd = nullptr);
 // v[0] = sqrt(v[0]) on the device
 cudaError_t launch_sqrt(double* v, cudaStream_t s);
 // sum part[nblk][k] (k < nv) in fixed order into out[k]
@@ -80,7 +90,8 @@ cudaError_t launch_convert_blocks(const double2* X, float2* Xf, long long n, cud
 // exact P^{-1} in the cosine basis (modal.cu)
 cudaError_t launch_modal_setup(const AuxGeom& g, int ntypes, const int* tkind_dev, const int* btype_dev,
                                double* Cf, double* Ci, float* Cf32, float* Ci32, double2* xm, double2* fac,
-                               double2* work, cudaStream_t s);
+                               double2* work, cudaStream_t s, int pade_m = 0, const double2* pa = nullptr,
+                               const double2* pd = nullptr);
 cudaError_t launch_modal_apply(const AuxGeom& g, bool fp32, const double* Cf, const double* Ci, const float* Cf32,
                                const float* Ci32, const double2* fac, const double2* y, double2* x, double2* tmp,
                                cudaStream_t s);

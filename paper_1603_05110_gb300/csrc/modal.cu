@@ -41,9 +41,13 @@ __global__ void to_float_kernel(const double* __restrict__ a, float* __restrict_
         b[t] = (float)a[t];
 }
 
-// Per strip type (ltc, rtc) and mode k: x1..x4 of the diagonal blocks.
+// Per strip type (ltc, rtc) and mode k: x1..x4 of the diagonal blocks.  S_k is the transmission
+// operator on mode k: -i p (Robin), or -i sum a_s + i sum a_s d_s mu_k / dh_s with
+// dh_s = i alpha mu_k - lambda_k + d_s mu_k, since the auxiliary equation (eq. TCS_phi) of the
+// free problem, D_s phi_s = M^G v, is diagonal on the modes too (S_pade).
 __global__ void modal_eigs_kernel(Geom g, int ntypes, const int* __restrict__ tkind, double2* __restrict__ xm,
-                                  double2* __restrict__ work) {
+                                  double2* __restrict__ work, int pade_m, const double2* __restrict__ pa,
+                                  const double2* __restrict__ pd) {
     const int n = g.nyn, ny = n - 1, c = g.nxs - 1, m = c + 1;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ntypes * n) return;
@@ -53,6 +57,18 @@ __global__ void modal_eigs_kernel(Geom g, int ntypes, const int* __restrict__ tk
     const double ck = cospi(th);
     const double mu = g.hy / 6.0 * (4.0 + 2.0 * ck);
     const double la = (2.0 - 2.0 * ck) / g.hy;
+    double2 Sk = make_double2(0.0, -g.p);
+    if (pade_m > 0) {
+        double2 sa = make_double2(0, 0), acc = make_double2(0, 0);
+        for (int s = 0; s < pade_m; ++s) {
+            sa = cadd(sa, pa[s]);
+            const double2 dh = make_double2(-la + pd[s].x * mu, g.alpha * mu + pd[s].y * mu);
+            acc = cadd(acc, cmul(cmul(pa[s], pd[s]), cmul(make_double2(mu, 0.0), cinv(dh))));
+        }
+        const double2 t = csub(acc, sa);          // -sa + acc, times i
+        Sk = make_double2(-t.y, t.x);
+    }
+    const double2 rk = make_double2(-Sk.x, -Sk.y);   // edge coefficient rho_k = -S_k
     // T = mu Bx - la Mx, tridiagonal; Bx = i alpha Mx - Kx + i p E
     double2* cp = work + (long long)t * 2 * m;   // Thomas scratch (c', d')
     double2* dp = cp + m;
@@ -63,10 +79,10 @@ __global__ void modal_eigs_kernel(Geom g, int ntypes, const int* __restrict__ tk
         for (int i = 0; i < m; ++i) {
             const bool lo = i > 0, hi = i < c;
             const double mii = (lo && hi) ? g.mxi : g.mxe, kii = (lo && hi) ? g.kxi : g.kxe;
-            double pe = 0.0;
-            if (i == 0 && ltc) pe += g.p;
-            if (i == c && rtc) pe += g.p;
-            const double2 diag = make_double2(-mu * kii - la * mii, mu * (g.alpha * mii + pe));
+            double pre = 0.0, pim = 0.0;
+            if (i == 0 && ltc) { pre += rk.x; pim += rk.y; }
+            if (i == c && rtc) { pre += rk.x; pim += rk.y; }
+            const double2 diag = make_double2(-mu * kii - la * mii + mu * pre, mu * (g.alpha * mii + pim));
             const double2 off = make_double2(-mu * g.kxo - la * g.mxo, mu * g.alpha * g.mxo);
             const double2 rhs = make_double2((side == 0 && i == 0) || (side == 1 && i == c) ? mu : 0.0, 0.0);
             if (i == 0) {
@@ -85,9 +101,9 @@ __global__ void modal_eigs_kernel(Geom g, int ntypes, const int* __restrict__ tk
         const double2 wc = wnext;
         for (int i = m - 2; i >= 0; --i) wnext = csub(dp[i], cmul(cp[i], wnext));
         const double2 w0 = wnext;
-        // 2ip w
-        const double2 a0 = make_double2(-2.0 * g.p * w0.y, 2.0 * g.p * w0.x);
-        const double2 ac = make_double2(-2.0 * g.p * wc.y, 2.0 * g.p * wc.x);
+        // -2 S_k w (the datum enters the right side with a minus sign)
+        const double2 a0 = cmul(make_double2(-2.0 * Sk.x, -2.0 * Sk.y), w0);
+        const double2 ac = cmul(make_double2(-2.0 * Sk.x, -2.0 * Sk.y), wc);
         if (side == 0) { out[0] = make_double2(a0.x - 1.0, a0.y); out[2] = ac; }   // x1, x3
         else { out[1] = a0; out[3] = make_double2(ac.x - 1.0, ac.y); }             // x2, x4
     }
@@ -220,7 +236,7 @@ __global__ void __launch_bounds__(256) cosine_apply_kernel(int n, int ntr, int P
 
 cudaError_t launch_modal_setup(const Geom& g, int ntypes, const int* tkind_dev, const int* btype_dev,
                                double* Cf, double* Ci, float* Cf32, float* Ci32, double2* xm, double2* fac,
-                               double2* work, cudaStream_t s) {
+                               double2* work, cudaStream_t s, int pade_m, const double2* pa, const double2* pd) {
     const long long nn = (long long)g.nyn * g.nyn;
     count_launches(1);
     cosine_matrices_kernel<<<2048, 256, 0, s>>>(g.nyn - 1, Cf, Ci);
@@ -231,7 +247,7 @@ cudaError_t launch_modal_setup(const Geom& g, int ntypes, const int* tkind_dev, 
     }
     const int nt = ntypes * g.nyn;
     count_launches(2);
-    modal_eigs_kernel<<<(nt + 127) / 128, 128, 0, s>>>(g, ntypes, tkind_dev, xm, work);
+    modal_eigs_kernel<<<(nt + 127) / 128, 128, 0, s>>>(g, ntypes, tkind_dev, xm, work, pade_m, pa, pd);
     modal_factor_kernel<<<(g.nyn + 127) / 128, 128, 0, s>>>(g, btype_dev, xm, fac);
     return cudaGetLastError();
 }

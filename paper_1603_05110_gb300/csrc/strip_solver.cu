@@ -26,6 +26,7 @@
 #include "common.cuh"
 #include "kernels.h"
 
+#include <algorithm>
 #include <atomic>
 
 namespace ddnls {
@@ -35,11 +36,12 @@ long long kernel_launch_count() { return g_launches.load(); }
 void count_launches(int n) { g_launches += n; }
 
 // y = A(c) v at one node: the 9-point Q1 stencil of Bx (x) My - Mx (x) Ky + diag(c), with
-// Bx = -Kx + i (alpha Mx + p E_x) and E_x the Robin edges of the strip (eq. NproblemRobinNL).
+// Bx = -Kx + i alpha Mx + rho E_x, E_x the transmission edges of the strip and rho the edge
+// coefficient: i p for Robin (eq. NproblemRobinNL), i sum a_s for S_pade (eq. NproblemSPNL).
 template <typename T, typename T2>
 __device__ __forceinline__ T2 apply_op(const T2* v, long long idx, int ix, int iy,
                                        int c, int ny, int P, const Coef1<T>& cx, const Coef1<T>& cy,
-                                       T alpha, T robin, T cdiag) {
+                                       T alpha, T rho_re, T rho_im, T cdiag) {
     T2 acc = mk<T2>(0.0, 0.0);
 #pragma unroll
     for (int dx = -1; dx <= 1; ++dx) {
@@ -54,8 +56,8 @@ __device__ __forceinline__ T2 apply_op(const T2* v, long long idx, int ix, int i
         tK.x = cy.k[0] * am.x + cy.k[1] * a0.x + cy.k[2] * ap.x;
         tK.y = cy.k[0] * am.y + cy.k[1] * a0.y + cy.k[2] * ap.y;
         const T mx = cx.m[dx + 1];
-        const T bre = -cx.k[dx + 1];
-        const T bim = alpha * mx + (dx == 0 ? robin : (T)0);
+        const T bre = -cx.k[dx + 1] + (dx == 0 ? rho_re : (T)0);
+        const T bim = alpha * mx + (dx == 0 ? rho_im : (T)0);
         acc.x += bre * tM.x - bim * tM.y - mx * tK.x;
         acc.y += bre * tM.y + bim * tM.x - mx * tK.y;
     }
@@ -66,15 +68,55 @@ __device__ __forceinline__ T2 apply_op(const T2* v, long long idx, int ix, int i
 }
 
 template <typename T>
-__device__ __forceinline__ typename C2<T>::t diag_inv(const Coef1<T>& cx, const Coef1<T>& cy, T alpha, T robin, T cdiag) {
+__device__ __forceinline__ typename C2<T>::t diag_inv(const Coef1<T>& cx, const Coef1<T>& cy, T alpha, T rho_re,
+                                                      T rho_im, T cdiag) {
     using T2 = typename C2<T>::t;
     T2 d;
-    d.x = -cx.k[1] * cy.m[1] - cx.m[1] * cy.k[1] + cdiag;
-    d.y = (alpha * cx.m[1] + robin) * cy.m[1];
+    d.x = (-cx.k[1] + rho_re) * cy.m[1] - cx.m[1] * cy.k[1] + cdiag;
+    d.y = (alpha * cx.m[1] + rho_im) * cy.m[1];
     return cinv(d);
 }
 
-template <typename T>
+// (M^Gamma v)(iy) along an edge column (consistent 1D mass in y)
+template <typename T, typename T2>
+__device__ __forceinline__ T2 edge_mass(const T2* v, int iy, int ny, const Coef1<T>& cy) {
+    const T2 a0 = v[iy];
+    const T2 am = iy > 0 ? v[iy - 1] : mk<T2>(0.0, 0.0);
+    const T2 ap = iy < ny ? v[iy + 1] : mk<T2>(0.0, 0.0);
+    T2 t;
+    t.x = cy.m[0] * am.x + cy.m[1] * a0.x + cy.m[2] * ap.x;
+    t.y = cy.m[0] * am.y + cy.m[1] * a0.y + cy.m[2] * ap.y;
+    return t;
+}
+
+// The auxiliary row of phi_s on one edge, eq. (NproblemSPNL) rows (C, D_s), scaled by
+// sigma_s = i a_s d_s so that the coupled system is complex symmetric (sigma_s C = B_s^T):
+//   sigma_s [ -(M^G zeta_e) + ((i alpha + d_s) M^G - S^G + diag(c_phi)) phi_s ]
+template <typename T, typename T2>
+__device__ __forceinline__ T2 phi_row(const T2* ze, const T2* ph, int iy, int ny, const Coef1<T>& cy, T2 gam,
+                                      T2 sig, T cphi) {
+    const T2 mz = edge_mass<T, T2>(ze, iy, ny, cy);
+    const T2 a0 = ph[iy];
+    const T2 am = iy > 0 ? ph[iy - 1] : mk<T2>(0.0, 0.0);
+    const T2 ap = iy < ny ? ph[iy + 1] : mk<T2>(0.0, 0.0);
+    T2 tM, tK;
+    tM.x = cy.m[0] * am.x + cy.m[1] * a0.x + cy.m[2] * ap.x;
+    tM.y = cy.m[0] * am.y + cy.m[1] * a0.y + cy.m[2] * ap.y;
+    tK.x = cy.k[0] * am.x + cy.k[1] * a0.x + cy.k[2] * ap.x;
+    tK.y = cy.k[0] * am.y + cy.k[1] * a0.y + cy.k[2] * ap.y;
+    T2 j = cmul(gam, tM);
+    j.x += -tK.x + cphi * a0.x - mz.x;
+    j.y += -tK.y + cphi * a0.y - mz.y;
+    return cmul(sig, j);
+}
+template <typename T, typename T2>
+__device__ __forceinline__ T2 phi_diag_inv(const Coef1<T>& cy, T2 gam, T2 sig, T cphi) {
+    T2 d = cmul(gam, mk<T2>(cy.m[1], 0.0));
+    d.x += -cy.k[1] + cphi;
+    return cinv(cmul(sig, d));
+}
+
+template <typename T, bool PADE>
 __global__ void __launch_bounds__(256)
 strip_solve_kernel(StripSolveArgs a) {
     using T2 = typename C2<T>::t;
@@ -88,7 +130,9 @@ strip_solve_kernel(StripSolveArgs a) {
     const int rank = blockIdx.x - b0;
     const int nyn = g.nyn, ny = nyn - 1, c = g.nxs - 1, P = g.P;
     const int Ns = g.nxs * nyn;
-    const int nchunks = (Ns + blockDim.x - 1) / blockDim.x;
+    const int m = PADE ? a.pade_m : 0;
+    const int Nall = Ns + 2 * m * nyn;       // strip nodes, then phi_{e,s} nodes
+    const int nchunks = (Nall + blockDim.x - 1) / blockDim.x;
     const float inv_nyn = 1.0f / (float)nyn;
     const long long sbase = (long long)j * g.sstride();
 
@@ -120,6 +164,15 @@ strip_solve_kernel(StripSolveArgs a) {
     T2* p = (T2*)a.p + sbase;
     T2* q = (T2*)a.q + sbase;
     T* cT = (T*)a.cT + sbase;
+    // auxiliary unknowns: phi_{e,s}(iy) at ((j*2 + e)*m + s)*P + iy
+    const long long fbase = (long long)j * 2 * m * P;
+    double2* phi = PADE ? a.phi + fbase : nullptr;
+    T2* xf = PADE ? (T2*)a.xf + fbase : nullptr;
+    T2* rf = PADE ? (T2*)a.rf + fbase : nullptr;
+    T2* zf = PADE ? (T2*)a.zf + fbase : nullptr;
+    T2* pf = PADE ? (T2*)a.pf + fbase : nullptr;
+    T2* qf = PADE ? (T2*)a.qf + fbase : nullptr;
+    T* cTf = PADE ? (T*)a.cTf + (long long)j * 2 * P : nullptr;
 
     unsigned* bar = a.bar + j;
     unsigned epoch = 0;
@@ -128,7 +181,14 @@ strip_solve_kernel(StripSolveArgs a) {
     auto slot_ptr = [&](unsigned e) { return part_base + ((size_t)(e & 3u) * NB + blockIdx.x) * 4; };
     auto group_ptr = [&](unsigned e) { return part_base + ((size_t)(e & 3u) * NB + (size_t)b0) * 4; };
 
-    const double robin_l = ltc ? g.p : 0.0, robin_r = rtc ? g.p : 0.0;
+    // edge coefficient rho: i p (Robin) or i sum_s a_s (S_pade)
+    double rho_re = 0.0, rho_im = g.p;
+    if (PADE) {
+        double sre = 0.0, sim = 0.0;
+        for (int s2 = 0; s2 < m; ++s2) { sre += a.pade_a[s2].x; sim += a.pade_a[s2].y; }
+        rho_re = -sim;
+        rho_im = sre;
+    }
     const Coef1Consts<double> KXd = consts_x<double>(g), KYd = consts_y<double>(g);
     const Coef1Consts<T> KXt = consts_x<T>(g), KYt = consts_y<T>(g);
     const T alphaT = (T)g.alpha;
@@ -146,19 +206,18 @@ strip_solve_kernel(StripSolveArgs a) {
         tmark = t;
     };
 
-    auto robin_at = [&](int ix) -> double {
-        double rb = 0.0;
-        if (ix == 0) rb += robin_l;
-        if (ix == c) rb += robin_r;
-        return rb;
+    // edge coefficient at column ix (zero inside the strip and on Neumann edges)
+    auto rho_at = [&](int ix, double& re, double& im) {
+        re = im = 0.0;
+        if ((ix == 0 && ltc) || (ix == c && rtc)) { re = rho_re; im = rho_im; }
     };
-    const T robin_lT = (T)robin_l, robin_rT = (T)robin_r;
-    auto robin_atT = [&](int ix) -> T {
-        T rb = (T)0;
-        if (ix == 0) rb += robin_lT;
-        if (ix == c) rb += robin_rT;
-        return rb;
+    const T rho_reT = (T)rho_re, rho_imT = (T)rho_im;
+    auto rho_atT = [&](int ix, T& re, T& im) {
+        re = im = (T)0;
+        if ((ix == 0 && ltc) || (ix == c && rtc)) { re = rho_reT; im = rho_imT; }
     };
+    // edge index (0 left, 1 right) of a transmission-edge column, else -1
+    auto tc_edge = [&](int ix) -> int { return (ix == 0 && ltc) ? 0 : ((ix == c && rtc) ? 1 : -1); };
     // datum of the Robin data term on an edge node (l on ix=0, r on ix=c)
     auto edge_term = [&](int ix, int iy, const Coef1<double>& cy) -> double2 {
         double2 t = make_double2(0.0, 0.0);
@@ -178,6 +237,16 @@ strip_solve_kernel(StripSolveArgs a) {
         }
         return t;
     };
+    // phi node n >= Ns -> edge e, order s, row iy
+    auto split_phi = [&](int n, int& e, int& s2, int& iy) {
+        const int qq = n - Ns;
+        e = qq / (m * nyn);
+        const int rem = qq - e * m * nyn;
+        s2 = rem / nyn;
+        iy = rem - s2 * nyn;
+    };
+    auto gam_of = [&](int s2) { return make_double2(a.pade_d[s2].x, g.alpha + a.pade_d[s2].y); };   // i alpha + d_s
+    auto sig_of = [&](int s2) { return cmul(make_double2(0.0, 1.0), cmul(a.pade_a[s2], a.pade_d[s2])); };  // i a_s d_s
 
     // scale of the first correction: the strip's ||(2i/dt) M h|| (FP32 must not see ~1e-111)
     double bnorm = 0.0;
@@ -189,33 +258,72 @@ strip_solve_kernel(StripSolveArgs a) {
         double loc[4] = {0.0, 0.0, 0.0, 0.0};   // ||res||^2, ||b||^2, rho = r^T z (re, im)
         for (int ch = rank; ch < nchunks; ch += bps) {
             const int n = ch * blockDim.x + threadIdx.x;
-            if (n >= Ns) continue;
-            int ix, iy;
-            split_node(n, nyn, inv_nyn, ix, iy);
-            const long long idx = (long long)ix * P + iy;
-            const Coef1<double> cx = coef1<double>(ix, c, KXd), cy = coef1<double>(iy, ny, KYd);
-            const double2 zc = zeta[idx];
-            const double W = Wn ? Wn[idx] : 0.0;
-            const double cdiag = wq(ix, c, g.hx) * wq(iy, ny, g.hy) * (W + kap * (zc.x * zc.x + zc.y * zc.y));
-            const double rb = robin_at(ix);
-            const double2 Az = apply_op<double, double2>(zeta, idx, ix, iy, c, ny, P, cx, cy, g.alpha, rb, cdiag);
-            double2 b = rhs0 ? rhs0[idx] : make_double2(0.0, 0.0);
-            b = csub(b, edge_term(ix, iy, cy));
-            const double2 res = csub(b, Az);
-            loc[0] += res.x * res.x + res.y * res.y;
-            loc[1] += b.x * b.x + b.y * b.y;
-            const Coef1<T> cxT = coef1<T>(ix, c, KXt), cyT = coef1<T>(iy, ny, KYt);
-            const T2 rT = cfrom<T2>(make_double2(res.x * inv_s, res.y * inv_s));
-            const T2 di = diag_inv<T>(cxT, cyT, alphaT, (T)rb, (T)cdiag);
-            const T2 zT = cmul(di, rT);
-            cT[idx] = (T)cdiag;
-            r[idx] = rT;
-            z[idx] = zT;
-            x[idx] = mk<T2>(0.0, 0.0);
-            p[idx] = mk<T2>(0.0, 0.0);
-            q[idx] = mk<T2>(0.0, 0.0);
-            loc[2] += (double)(rT.x * zT.x - rT.y * zT.y);
-            loc[3] += (double)(rT.x * zT.y + rT.y * zT.x);
+            if (n >= Nall) continue;
+            if (!PADE || n < Ns) {
+                int ix, iy;
+                split_node(n, nyn, inv_nyn, ix, iy);
+                const long long idx = (long long)ix * P + iy;
+                const Coef1<double> cx = coef1<double>(ix, c, KXd), cy = coef1<double>(iy, ny, KYd);
+                const double2 zc = zeta[idx];
+                const double W = Wn ? Wn[idx] : 0.0;
+                const double cdiag = wq(ix, c, g.hx) * wq(iy, ny, g.hy) * (W + kap * (zc.x * zc.x + zc.y * zc.y));
+                double rre, rim;
+                rho_at(ix, rre, rim);
+                double2 Az = apply_op<double, double2>(zeta, idx, ix, iy, c, ny, P, cx, cy, g.alpha, rre, rim, cdiag);
+                if (PADE) {
+                    const int e = tc_edge(ix);
+                    if (e >= 0)            // B_s phi_s = -i a_s d_s M^G phi_s on the edge rows
+                        for (int s2 = 0; s2 < m; ++s2) {
+                            const double2 mph = edge_mass<double, double2>(phi + ((long long)e * m + s2) * P, iy, ny, cy);
+                            Az = csub(Az, cmul(sig_of(s2), mph));
+                        }
+                }
+                double2 b = rhs0 ? rhs0[idx] : make_double2(0.0, 0.0);
+                b = csub(b, edge_term(ix, iy, cy));
+                const double2 res = csub(b, Az);
+                loc[0] += res.x * res.x + res.y * res.y;
+                loc[1] += b.x * b.x + b.y * b.y;
+                const Coef1<T> cxT = coef1<T>(ix, c, KXt), cyT = coef1<T>(iy, ny, KYt);
+                const T2 rT = cfrom<T2>(make_double2(res.x * inv_s, res.y * inv_s));
+                const T2 di = diag_inv<T>(cxT, cyT, alphaT, (T)rre, (T)rim, (T)cdiag);
+                const T2 zT = cmul(di, rT);
+                cT[idx] = (T)cdiag;
+                r[idx] = rT;
+                z[idx] = zT;
+                x[idx] = mk<T2>(0.0, 0.0);
+                p[idx] = mk<T2>(0.0, 0.0);
+                q[idx] = mk<T2>(0.0, 0.0);
+                loc[2] += (double)(rT.x * zT.x - rT.y * zT.y);
+                loc[3] += (double)(rT.x * zT.y + rT.y * zT.x);
+            } else {
+                int e, s2, iy;
+                split_phi(n, e, s2, iy);
+                if (!(e == 0 ? ltc : rtc)) continue;
+                const int ixe = e == 0 ? 0 : c;
+                const long long fi = ((long long)e * m + s2) * P + iy;
+                const Coef1<double> cy = coef1<double>(iy, ny, KYd);
+                const double2 ze = zeta[(long long)ixe * P + iy];
+                const double W = Wn ? Wn[(long long)ixe * P + iy] : 0.0;
+                const double cphi = wq(iy, ny, g.hy) * (W + kap * (ze.x * ze.x + ze.y * ze.y));
+                const double2 gam = gam_of(s2), sig = sig_of(s2);
+                const double2 res = make_double2(0.0, 0.0);
+                const double2 J = phi_row<double, double2>(zeta + (long long)ixe * P, phi + ((long long)e * m + s2) * P, iy, ny,
+                                                           cy, gam, sig, cphi);
+                const double2 rs = csub(res, J);
+                loc[0] += rs.x * rs.x + rs.y * rs.y;
+                const Coef1<T> cyT = coef1<T>(iy, ny, KYt);
+                const T2 rT = cfrom<T2>(make_double2(rs.x * inv_s, rs.y * inv_s));
+                const T2 di = phi_diag_inv<T, T2>(cyT, cfrom<T2>(gam), cfrom<T2>(sig), (T)cphi);
+                const T2 zT = cmul(di, rT);
+                if (s2 == 0) cTf[(long long)e * P + iy] = (T)cphi;
+                rf[fi] = rT;
+                zf[fi] = zT;
+                xf[fi] = mk<T2>(0.0, 0.0);
+                pf[fi] = mk<T2>(0.0, 0.0);
+                qf[fi] = mk<T2>(0.0, 0.0);
+                loc[2] += (double)(rT.x * zT.x - rT.y * zT.y);
+                loc[3] += (double)(rT.x * zT.y + rT.y * zT.x);
+            }
         }
         block_sum<4>(loc, s_red);
         if (threadIdx.x == 0) { double* sp = slot_ptr(epoch + 1); sp[0] = loc[0]; sp[1] = loc[1]; sp[2] = loc[2]; sp[3] = loc[3]; }
@@ -233,7 +341,7 @@ strip_solve_kernel(StripSolveArgs a) {
         if (nl_it >= a.max_nl) { status = DD_NLS_ENOCONV; break; }
 
         // ---------------- inner COCG on A(c) delta = res, Jacobi preconditioner
-        double rho_re = tot[2], rho_im = tot[3];
+        double rho_r = tot[2], rho_i = tot[3];
         double beta_re = 0.0, beta_im = 0.0;
         // inner stopping test in the scaled units of r
         const double target = fmax(a.inner_tol * rnorm, fmax(a.inner_floor * bnorm, 0.1 * floor_abs)) * inv_s;
@@ -244,18 +352,45 @@ strip_solve_kernel(StripSolveArgs a) {
             const T2 bT = mk<T2>(beta_re, beta_im);
             for (int ch = rank; ch < nchunks; ch += bps) {
                 const int n = ch * blockDim.x + threadIdx.x;
-                if (n >= Ns) continue;
-                int ix, iy;
-                split_node(n, nyn, inv_nyn, ix, iy);
-                const long long idx = (long long)ix * P + iy;
-                const Coef1<T> cxT = coef1<T>(ix, c, KXt), cyT = coef1<T>(iy, ny, KYt);
-                const T2 Az = apply_op<T, T2>(z, idx, ix, iy, c, ny, P, cxT, cyT, alphaT, robin_atT(ix), cT[idx]);
-                const T2 qn = cfma(bT, q[idx], Az);
-                const T2 pn = cfma(bT, p[idx], z[idx]);
-                q[idx] = qn;
-                p[idx] = pn;
-                am_re += pn.x * qn.x - pn.y * qn.y;
-                am_im += pn.x * qn.y + pn.y * qn.x;
+                if (n >= Nall) continue;
+                if (!PADE || n < Ns) {
+                    int ix, iy;
+                    split_node(n, nyn, inv_nyn, ix, iy);
+                    const long long idx = (long long)ix * P + iy;
+                    const Coef1<T> cxT = coef1<T>(ix, c, KXt), cyT = coef1<T>(iy, ny, KYt);
+                    T rre, rim;
+                    rho_atT(ix, rre, rim);
+                    T2 Az = apply_op<T, T2>(z, idx, ix, iy, c, ny, P, cxT, cyT, alphaT, rre, rim, cT[idx]);
+                    if (PADE) {
+                        const int e = tc_edge(ix);
+                        if (e >= 0)
+                            for (int s2 = 0; s2 < m; ++s2) {
+                                const T2 mph = edge_mass<T, T2>(zf + ((long long)e * m + s2) * P, iy, ny, cyT);
+                                Az = csub(Az, cmul(cfrom<T2>(sig_of(s2)), mph));
+                            }
+                    }
+                    const T2 qn = cfma(bT, q[idx], Az);
+                    const T2 pn = cfma(bT, p[idx], z[idx]);
+                    q[idx] = qn;
+                    p[idx] = pn;
+                    am_re += pn.x * qn.x - pn.y * qn.y;
+                    am_im += pn.x * qn.y + pn.y * qn.x;
+                } else {
+                    int e, s2, iy;
+                    split_phi(n, e, s2, iy);
+                    if (!(e == 0 ? ltc : rtc)) continue;
+                    const int ixe = e == 0 ? 0 : c;
+                    const long long fi = ((long long)e * m + s2) * P + iy;
+                    const Coef1<T> cyT = coef1<T>(iy, ny, KYt);
+                    const T2 J = phi_row<T, T2>(z + (long long)ixe * P, zf + ((long long)e * m + s2) * P, iy, ny, cyT,
+                                                cfrom<T2>(gam_of(s2)), cfrom<T2>(sig_of(s2)), cTf[(long long)e * P + iy]);
+                    const T2 qn = cfma(bT, qf[fi], J);
+                    const T2 pn = cfma(bT, pf[fi], zf[fi]);
+                    qf[fi] = qn;
+                    pf[fi] = pn;
+                    am_re += pn.x * qn.x - pn.y * qn.y;
+                    am_im += pn.x * qn.y + pn.y * qn.x;
+                }
             }
             T lmT[2] = {am_re, am_im};
             double lm[2];
@@ -270,31 +405,48 @@ strip_solve_kernel(StripSolveArgs a) {
             const double mu2 = mu[0] * mu[0] + mu[1] * mu[1];
             if (!(mu2 > 0.0) || !isfinite(mu2)) { status = isfinite(mu2) ? DD_NLS_EBREAKDOWN : DD_NLS_ENONFINITE; break; }
             // a = rho / mu
-            const double al_re = (rho_re * mu[0] + rho_im * mu[1]) / mu2;
-            const double al_im = (rho_im * mu[0] - rho_re * mu[1]) / mu2;
+            const double al_re = (rho_r * mu[0] + rho_i * mu[1]) / mu2;
+            const double al_im = (rho_i * mu[0] - rho_r * mu[1]) / mu2;
             const T2 alT = mk<T2>(al_re, al_im);
             const T2 malT = mk<T2>(-al_re, -al_im);
             // phase B: x += a p, r -= a q, z = D^-1 r, partials rho' = r^T z, ||r||^2
-            T b0 = 0, b1 = 0, b2 = 0;
+            T b0s = 0, b1s = 0, b2s = 0;
             for (int ch = rank; ch < nchunks; ch += bps) {
                 const int n = ch * blockDim.x + threadIdx.x;
-                if (n >= Ns) continue;
-                int ix, iy;
-                split_node(n, nyn, inv_nyn, ix, iy);
-                const long long idx = (long long)ix * P + iy;
-                const Coef1<T> cxT = coef1<T>(ix, c, KXt), cyT = coef1<T>(iy, ny, KYt);
-                const T2 pc = p[idx];
-                x[idx] = cfma(alT, pc, x[idx]);
-                const T2 rn = cfma(malT, q[idx], r[idx]);
-                r[idx] = rn;
-                const T2 di = diag_inv<T>(cxT, cyT, alphaT, robin_atT(ix), cT[idx]);
-                const T2 zn = cmul(di, rn);
-                z[idx] = zn;
-                b0 += rn.x * zn.x - rn.y * zn.y;
-                b1 += rn.x * zn.y + rn.y * zn.x;
-                b2 += rn.x * rn.x + rn.y * rn.y;
+                if (n >= Nall) continue;
+                T2 rn, zn;
+                if (!PADE || n < Ns) {
+                    int ix, iy;
+                    split_node(n, nyn, inv_nyn, ix, iy);
+                    const long long idx = (long long)ix * P + iy;
+                    const Coef1<T> cxT = coef1<T>(ix, c, KXt), cyT = coef1<T>(iy, ny, KYt);
+                    const T2 pc = p[idx];
+                    x[idx] = cfma(alT, pc, x[idx]);
+                    rn = cfma(malT, q[idx], r[idx]);
+                    r[idx] = rn;
+                    T rre, rim;
+                    rho_atT(ix, rre, rim);
+                    const T2 di = diag_inv<T>(cxT, cyT, alphaT, rre, rim, cT[idx]);
+                    zn = cmul(di, rn);
+                    z[idx] = zn;
+                } else {
+                    int e, s2, iy;
+                    split_phi(n, e, s2, iy);
+                    if (!(e == 0 ? ltc : rtc)) continue;
+                    const long long fi = ((long long)e * m + s2) * P + iy;
+                    const Coef1<T> cyT = coef1<T>(iy, ny, KYt);
+                    xf[fi] = cfma(alT, pf[fi], xf[fi]);
+                    rn = cfma(malT, qf[fi], rf[fi]);
+                    rf[fi] = rn;
+                    const T2 di = phi_diag_inv<T, T2>(cyT, cfrom<T2>(gam_of(s2)), cfrom<T2>(sig_of(s2)), cTf[(long long)e * P + iy]);
+                    zn = cmul(di, rn);
+                    zf[fi] = zn;
+                }
+                b0s += rn.x * zn.x - rn.y * zn.y;
+                b1s += rn.x * zn.y + rn.y * zn.x;
+                b2s += rn.x * rn.x + rn.y * rn.y;
             }
-            T lbT[3] = {b0, b1, b2};
+            T lbT[3] = {b0s, b1s, b2s};
             double lb[3];
             block_sum_t<T, 3>(lbT, lb, s_red);
             if (threadIdx.x == 0) { double* sp = slot_ptr(epoch + 1); sp[0] = lb[0]; sp[1] = lb[1]; sp[2] = lb[2]; sp[3] = 0; }
@@ -307,24 +459,33 @@ strip_solve_kernel(StripSolveArgs a) {
             ++kry;
             if (!isfinite(rb[2])) { status = DD_NLS_ENONFINITE; break; }
             if (sqrt(rb[2]) <= target) break;
-            const double rr2 = rho_re * rho_re + rho_im * rho_im;
+            const double rr2 = rho_r * rho_r + rho_i * rho_i;
             if (!(rr2 > 0.0)) { status = DD_NLS_EBREAKDOWN; break; }
-            beta_re = (rb[0] * rho_re + rb[1] * rho_im) / rr2;
-            beta_im = (rb[1] * rho_re - rb[0] * rho_im) / rr2;
-            rho_re = rb[0];
-            rho_im = rb[1];
+            beta_re = (rb[0] * rho_r + rb[1] * rho_i) / rr2;
+            beta_im = (rb[1] * rho_r - rb[0] * rho_i) / rr2;
+            rho_r = rb[0];
+            rho_i = rb[1];
         }
         if (status) break;
         // ---------------- zeta += delta (FP64), then every block must see the new zeta
+        const double sc = 1.0 / inv_s;
         for (int ch = rank; ch < nchunks; ch += bps) {
             const int n = ch * blockDim.x + threadIdx.x;
-            if (n >= Ns) continue;
-            int ix, iy;
-            split_node(n, nyn, inv_nyn, ix, iy);
-            const long long idx = (long long)ix * P + iy;
-            const double2 dx = cd(x[idx]);
-            const double sc = 1.0 / inv_s;
-            zeta[idx] = make_double2(zeta[idx].x + sc * dx.x, zeta[idx].y + sc * dx.y);
+            if (n >= Nall) continue;
+            if (!PADE || n < Ns) {
+                int ix, iy;
+                split_node(n, nyn, inv_nyn, ix, iy);
+                const long long idx = (long long)ix * P + iy;
+                const double2 dx = cd(x[idx]);
+                zeta[idx] = make_double2(zeta[idx].x + sc * dx.x, zeta[idx].y + sc * dx.y);
+            } else {
+                int e, s2, iy;
+                split_phi(n, e, s2, iy);
+                if (!(e == 0 ? ltc : rtc)) continue;
+                const long long fi = ((long long)e * m + s2) * P + iy;
+                const double2 dx = cd(xf[fi]);
+                phi[fi] = make_double2(phi[fi].x + sc * dx.x, phi[fi].y + sc * dx.y);
+            }
         }
         inv_s = 1.0 / rnorm;           // scale of the next correction
         ++epoch;
@@ -348,7 +509,9 @@ static cudaError_t launch_strip_solve_t(const StripSolveArgs& args, int nblocks,
     void* params[] = {&a};
     dim3 grid(nblocks), block(256);
     count_launches(1);
-    return cudaLaunchCooperativeKernel((const void*)strip_solve_kernel<T>, grid, block, params, 0, s);
+    if (a.pade_m > 0)
+        return cudaLaunchCooperativeKernel((const void*)strip_solve_kernel<T, true>, grid, block, params, 0, s);
+    return cudaLaunchCooperativeKernel((const void*)strip_solve_kernel<T, false>, grid, block, params, 0, s);
 }
 
 cudaError_t launch_strip_solve(const StripSolveArgs& a, int nblocks, bool fp32, cudaStream_t s) {
@@ -359,11 +522,16 @@ int strip_solve_max_blocks(bool fp32) {
     int dev = 0, nsm = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (fp32)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, strip_solve_kernel<float>, 256, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, strip_solve_kernel<double>, 256, 0);
-    return per * nsm;
+    // the smaller of the Robin and S_pade instances, so one schedule fits both
+    int per2 = 0;
+    if (fp32) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, strip_solve_kernel<float, false>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, strip_solve_kernel<float, true>, 256, 0);
+    } else {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, strip_solve_kernel<double, false>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, strip_solve_kernel<double, true>, 256, 0);
+    }
+    return std::min(per, per2) * nsm;
 }
 
 }  // namespace ddnls

@@ -40,8 +40,8 @@ def run_gpu(w, steps, **kw):
     return hist
 
 
-def run_oracle(w, steps, algorithm="classical", bc="same", tol=TOL):
-    prob = oracle_problem(w, bc=bc)
+def run_oracle(w, steps, algorithm="classical", bc="same", tol=TOL, tc="robin", m=4):
+    prob = oracle_problem(w, bc=bc, tc=tc, m=m)
     st = nls.Strips(prob, w.n_strips)
     Lh = st.build_Lh() if algorithm == "preconditioned" else None
     u = w.u0()
@@ -134,6 +134,37 @@ def test_free_problem_converges_in_one_exact_preconditioned_update(precision):
                   psolve=binding.PSOLVE_MODAL)
     # the FP32 form applies the cosine transforms in FP32 (P^{-1} exact to ~1e-6)
     assert got[0][1]["last_schwarz_iterations"] == (2 if precision == binding.FP64 else 3)
+
+
+@pytest.mark.parametrize("precision", [binding.FP64, binding.FP32_INNER])
+@pytest.mark.parametrize("algorithm", ["classical", "preconditioned"])
+def test_pade_transmission_matches_oracle(precision, algorithm):
+    """S_pade^m (eq. TCS) with its auxiliary unknowns phi_s (eq. TCS_phi), m = 4, theta = pi/4."""
+    w = SMALL
+    ref = run_oracle(w, 2, algorithm=algorithm, tc="pade", m=4)
+    got = run_gpu(w, 2, tol=TOL, precision=precision, tc=binding.TC_PADE, pade_m=4,
+                  algorithm=binding.PRECONDITIONED if algorithm == "preconditioned" else binding.CLASSICAL)
+    bound = 1e-11 if precision == binding.FP64 else 1e-10
+    for (ug, st), (uo, info) in zip(got, ref):
+        assert rel(ug, uo) < bound
+        assert abs(st["last_schwarz_iterations"] - info.iterations) <= 3
+
+
+def test_pade_modal_diagonal_matches_oracle_blocks():
+    w = wl.scaled(WELL, 24, 20, n_strips=4)
+    prob = oracle_problem(w, tc="pade", m=3)
+    st = nls.Strips(prob, w.n_strips)
+    ny = w.ny
+    j = np.arange(ny + 1)
+    Z = np.cos(np.pi * np.outer(j, j) / ny)
+    D = np.ones(ny + 1)
+    D[0] = D[-1] = 0.5
+    Zi = np.diag(1.0 / np.diag((Z.T * D) @ Z)) @ Z.T @ np.diag(D)
+    X = st.strip_blocks(1)
+    with binding.Solver(gpu_params(w, algorithm=binding.PRECONDITIONED, tc=binding.TC_PADE, pade_m=3), w.u0(), w.V()) as s:
+        xm = s.modal(1)
+    for a in range(4):
+        np.testing.assert_allclose(xm[a], np.diag(Zi @ X[a] @ Z), atol=1e-11)
 
 
 def test_single_strip_is_the_monodomain_solve():
