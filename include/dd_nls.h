@@ -175,6 +175,29 @@ int dd_nls_get_profile(dd_nls* h, dd_nls_profile* prof);
 int dd_nls_step_noalloc(const dd_nls_params* p, const double* V, double* u, const double* g0,
                         double* g_out, void* stream, dd_nls_stats* stats);
 
+/* Batched instances (many independent problems stepped together).  Every Schwarz
+ * iteration solves the strips of all instances that have not yet converged in one
+ * persistent launch, then updates every instance's interface vector (eq. fluxlr) in one
+ * launch; each instance stops at its own `tol`.  Instances may differ in every field of
+ * dd_nls_params except `precision`; each must use the classical algorithm with Robin
+ * transmission.  An autotuner picks the strip solver's block size and block count for the
+ * batch shape the first time a shape is stepped (timed on the first Schwarz iteration).
+ * params, V (nullable, or entries NULL) and u0 are arrays of n entries; pointers are host or
+ * device per ptr_kind.  Errors: dd_nls_batch_last_error(). */
+typedef struct dd_nls_batch dd_nls_batch;
+int dd_nls_batch_create(int n, const dd_nls_params* params, const double* const* V,
+                        const double* const* u0, int ptr_kind, void* stream, dd_nls_batch** out);
+/* nsteps steps of every instance; stats (nullable) receives n entries. */
+int dd_nls_batch_step(dd_nls_batch* b, int nsteps, dd_nls_stats* stats);
+/* u_n of instance i, nodal layout above. */
+int dd_nls_batch_get_u(dd_nls_batch* b, int i, double* u, int ptr_kind);
+/* The autotuner's choice: threads per block and blocks per launch (0 before the first step). */
+int dd_nls_batch_tuning(dd_nls_batch* b, int* block_size, int* blocks);
+int dd_nls_batch_set_profiling(dd_nls_batch* b, int on);
+int dd_nls_batch_get_profile(dd_nls_batch* b, dd_nls_profile* prof);
+const char* dd_nls_batch_last_error(const dd_nls_batch* b);
+void dd_nls_batch_destroy(dd_nls_batch* b);
+
 /* Release everything the handle owns.  NULL is ignored. */
 void dd_nls_destroy(dd_nls* h);
 

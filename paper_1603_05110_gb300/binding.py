@@ -70,7 +70,10 @@ class Profile(ctypes.Structure):
 
 SYMBOLS = ["dd_nls_default_params", "dd_nls_create", "dd_nls_step", "dd_nls_solve_interface",
            "dd_nls_get_state", "dd_nls_set_state", "dd_nls_get_blocks", "dd_nls_get_modal", "dd_nls_set_profiling",
-           "dd_nls_get_profile", "dd_nls_destroy", "dd_nls_last_error", "dd_nls_step_noalloc"]
+           "dd_nls_get_profile", "dd_nls_destroy", "dd_nls_last_error", "dd_nls_step_noalloc",
+           "dd_nls_batch_create", "dd_nls_batch_step", "dd_nls_batch_get_u", "dd_nls_batch_tuning",
+           "dd_nls_batch_set_profiling", "dd_nls_batch_get_profile", "dd_nls_batch_last_error",
+           "dd_nls_batch_destroy"]
 
 _lib = None
 
@@ -111,6 +114,23 @@ def load(path=LIB_PATH):
     lib.dd_nls_last_error.restype = ctypes.c_char_p
     lib.dd_nls_step_noalloc.argtypes = [ctypes.POINTER(Params), vp, vp, vp, vp, vp, ctypes.POINTER(Stats)]
     lib.dd_nls_step_noalloc.restype = ip
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    lib.dd_nls_batch_create.argtypes = [ip, ctypes.POINTER(Params), pp, pp, ip, vp, ctypes.POINTER(vp)]
+    lib.dd_nls_batch_create.restype = ip
+    lib.dd_nls_batch_step.argtypes = [vp, ip, ctypes.POINTER(Stats)]
+    lib.dd_nls_batch_step.restype = ip
+    lib.dd_nls_batch_get_u.argtypes = [vp, ip, vp, ip]
+    lib.dd_nls_batch_get_u.restype = ip
+    lib.dd_nls_batch_tuning.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    lib.dd_nls_batch_tuning.restype = ip
+    lib.dd_nls_batch_set_profiling.argtypes = [vp, ip]
+    lib.dd_nls_batch_set_profiling.restype = ip
+    lib.dd_nls_batch_get_profile.argtypes = [vp, ctypes.POINTER(Profile)]
+    lib.dd_nls_batch_get_profile.restype = ip
+    lib.dd_nls_batch_last_error.argtypes = [vp]
+    lib.dd_nls_batch_last_error.restype = ctypes.c_char_p
+    lib.dd_nls_batch_destroy.argtypes = [vp]
+    lib.dd_nls_batch_destroy.restype = None
     _ = dp
     _lib = lib
     return lib
@@ -259,6 +279,99 @@ class Solver:
     def close(self):
         if getattr(self, "h", None):
             self.lib.dd_nls_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Batch:
+    """A dd_nls_batch handle: n independent instances stepped together.
+
+    params: list of Params or dicts; u0, V: lists of arrays (numpy = host, CUDA tensors = device).
+    """
+
+    def __init__(self, params, u0, V=None, stream=None):
+        self.lib = load()
+        n = len(params)
+        arr = (Params * n)()
+        for i, p in enumerate(params):
+            arr[i] = default_params(**p) if isinstance(p, dict) else p
+        self.params = list(arr)
+        keep = []
+        kinds = []
+        up = (ctypes.c_void_p * n)()
+        vp_ = (ctypes.c_void_p * n)()
+        for i in range(n):
+            u = u0[i]
+            if isinstance(u, np.ndarray):
+                u = np.ascontiguousarray(u, dtype=np.complex128)
+            keep.append(u)
+            pu, ku = _ptr(u)
+            up[i] = pu
+            kinds.append(ku)
+            if V is not None and V[i] is not None:
+                v = V[i]
+                if isinstance(v, np.ndarray):
+                    v = np.ascontiguousarray(v, dtype=np.float64)
+                keep.append(v)
+                pv, kv = _ptr(v)
+                vp_[i] = pv
+                kinds.append(kv)
+        kind = _kind(*kinds)
+        s = None
+        if stream is not None:
+            s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        h = ctypes.c_void_p()
+        rc = self.lib.dd_nls_batch_create(n, arr, vp_, up, kind, s, ctypes.byref(h))
+        if rc != 0:
+            raise DDNLSError(rc, self.lib.dd_nls_batch_last_error(None).decode())
+        self.h = h
+        self.n = n
+
+    def _check(self, rc, stats=None):
+        if rc != 0:
+            raise DDNLSError(rc, self.lib.dd_nls_batch_last_error(self.h).decode(), stats)
+
+    def step(self, nsteps=1):
+        st = (Stats * self.n)()
+        rc = self.lib.dd_nls_batch_step(self.h, nsteps, st)
+        self._check(rc, [x.as_dict() for x in st])
+        return [x.as_dict() for x in st]
+
+    def get_u(self, i, out=None):
+        p = self.params[i]
+        if out is None:
+            out = np.zeros((p.ny + 1, p.nx + 1), np.complex128)
+        po, ko = _ptr(out, writable=True)
+        self._check(self.lib.dd_nls_batch_get_u(self.h, i, po, ko))
+        return out
+
+    def tuning(self):
+        a, b = ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.dd_nls_batch_tuning(self.h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def set_profiling(self, on=True):
+        self._check(self.lib.dd_nls_batch_set_profiling(self.h, 1 if on else 0))
+
+    def profile(self):
+        p = Profile()
+        self._check(self.lib.dd_nls_batch_get_profile(self.h, ctypes.byref(p)))
+        return p.as_dict()
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dd_nls_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):

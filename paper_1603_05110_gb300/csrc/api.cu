@@ -765,11 +765,11 @@ extern "C" int dd_nls_create(const dd_nls_params* p, const double* V, const doub
         // s = 1..m (eq. TCS; the sums start at s = 1)
         const int m = p->pade_m;
         h->pade_m = m;
-        for (int s2 = 1; s2 <= m; ++s2) {
-            const double ph = (2.0 * s2 - 1.0) * M_PI / (4.0 * m);
+        for (int k = 1; k <= m; ++k) {
+            const double ph = (2.0 * k - 1.0) * M_PI / (4.0 * m);
             const double ca = 1.0 / (m * std::cos(ph) * std::cos(ph)), tn = std::tan(ph) * std::tan(ph);
-            h->pade_a[s2 - 1] = make_double2(ca * std::cos(0.5 * p->pade_theta), ca * std::sin(0.5 * p->pade_theta));
-            h->pade_d[s2 - 1] = make_double2(tn * std::cos(p->pade_theta), tn * std::sin(p->pade_theta));
+            h->pade_a[k - 1] = make_double2(ca * std::cos(0.5 * p->pade_theta), ca * std::sin(0.5 * p->pade_theta));
+            h->pade_d[k - 1] = make_double2(tn * std::cos(p->pade_theta), tn * std::sin(p->pade_theta));
         }
         CKC(dalloc(&h->pa_dev, m));
         CKC(dalloc(&h->pd_dev, m));

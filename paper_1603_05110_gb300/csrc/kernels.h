@@ -15,8 +15,18 @@ void count_launches(int n);
 
 constexpr int kMaxPade = 96;   // largest Pade order m of eq. (TCS) the kernels take
 
+// Batched instances: strip j of the launch belongs to instance `inst` (its own geometry),
+// is strip `jloc` of that instance, and its fields start at element `off` of the field arrays;
+// the instance's interface vector starts at element `goff` of gtr.
+struct StripInfo {
+    int inst, jloc;
+    long long off, goff;
+};
+
 struct StripSolveArgs {
     Geom g;
+    const Geom* geoms;       // batched: [instances] geometry, else NULL (use g)
+    const StripInfo* sinfo;  // batched: [strips] descriptors, else NULL
     int bps;                 // unused when blk_strip is set
     const int* blk_strip;    // [gridDim] strip of each block
     const int* blk_start;    // [strips+1] first block of each strip
@@ -31,7 +41,7 @@ struct StripSolveArgs {
     void *x, *r, *z, *p, *q; // inner Krylov vectors (float2 or double2)
     void* cT;                // c = w (W + kappa|zeta|^2) in inner precision
     double nl_tol, inner_tol, inner_floor;
-    const double* bscale;    // ||(2i/dt) M u_{n-1}|| over all strips (device scalar), or NULL
+    const double* bscale;    // ||(2i/dt) M u_{n-1}|| over all strips, one per instance (device), or NULL
     double nl_floor_frac;    // strips stop once ||res|| <= nl_floor_frac * (*bscale)
     int max_nl, max_inner;
     double* part;            // [4][gridDim][4] partial sums
@@ -51,8 +61,9 @@ struct StripSolveArgs {
 };
 
 // cooperative launch of nblocks blocks (a.blk_strip / a.blk_start map blocks to strips)
-cudaError_t launch_strip_solve(const StripSolveArgs& a, int nblocks, bool fp32, cudaStream_t s);
+cudaError_t launch_strip_solve(const StripSolveArgs& a, int nblocks, bool fp32, cudaStream_t s, int block_size = 256);
 int strip_solve_max_blocks(bool fp32);
+int strip_solve_max_blocks_bs(bool fp32, int block_size);   // Robin kernel with 128 or 256 threads
 
 // ---- auxiliary kernels (aux_kernels.cu)
 using AuxGeom = Geom;

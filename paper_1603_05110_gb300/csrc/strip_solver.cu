@@ -116,34 +116,37 @@ __device__ __forceinline__ T2 phi_diag_inv(const Coef1<T>& cy, T2 gam, T2 sig, T
     return cinv(cmul(sig, d));
 }
 
-template <typename T, bool PADE>
-__global__ void __launch_bounds__(256)
+template <typename T, bool PADE, int BS>
+__global__ void __launch_bounds__(BS, 512 / BS)
 strip_solve_kernel(StripSolveArgs a) {
     using T2 = typename C2<T>::t;
     __shared__ double s_red[64];
     __shared__ int s_flag;
 
-    const Geom& g = a.g;
-    const int j = a.blk_strip[blockIdx.x];   // strip (virtual strip in setup mode)
+    const int j = a.blk_strip[blockIdx.x];   // strip of the launch (virtual strip in setup mode)
     const int b0 = a.blk_start[j];
     const int bps = a.blk_start[j + 1] - b0; // blocks of this strip (weighted by the host)
     const int rank = blockIdx.x - b0;
+    // geometry: the launch's, or the instance's when instances are batched
+    const StripInfo si = a.sinfo ? a.sinfo[j] : StripInfo{0, j, (long long)j * a.g.sstride(), 0};
+    const Geom g = a.geoms ? a.geoms[si.inst] : a.g;
+    const int jl = si.jloc;                  // strip index inside its instance
     const int nyn = g.nyn, ny = nyn - 1, c = g.nxs - 1, P = g.P;
     const int Ns = g.nxs * nyn;
     const int m = PADE ? a.pade_m : 0;
     const int Nall = Ns + 2 * m * nyn;       // strip nodes, then phi_{e,s} nodes
     const int nchunks = (Nall + blockDim.x - 1) / blockDim.x;
     const float inv_nyn = 1.0f / (float)nyn;
-    const long long sbase = (long long)j * g.sstride();
+    const long long sbase = si.off;
 
     // edges of this strip
     bool ltc, rtc, ldata, rdata;
     int unit_side = -1, unit_pos = -1;
     if (a.mode == 0) {
-        ltc = left_tc(g, j);
-        rtc = right_tc(g, j);
-        ldata = j > 0;
-        rdata = j < g.N - 1;
+        ltc = left_tc(g, jl);
+        rtc = right_tc(g, jl);
+        ldata = jl > 0;
+        rdata = jl < g.N - 1;
     } else {      // L_h construction: unit datum on one edge of a free strip
         ltc = a.unit_ltc;
         rtc = a.unit_rtc;
@@ -152,8 +155,8 @@ strip_solve_kernel(StripSolveArgs a) {
         unit_side = u / nyn;
         unit_pos = u - unit_side * nyn;
     }
-    const double2* gl = ldata ? a.gtr + (size_t)(2 * (j - 1) + 1) * P : nullptr;
-    const double2* gr = rdata ? a.gtr + (size_t)(2 * j) * P : nullptr;
+    const double2* gl = ldata ? a.gtr + si.goff + (size_t)(2 * (jl - 1) + 1) * P : nullptr;
+    const double2* gr = rdata ? a.gtr + si.goff + (size_t)(2 * jl) * P : nullptr;
 
     double2* zeta = a.zeta + sbase;
     const double2* __restrict__ rhs0 = a.rhs0 ? a.rhs0 + sbase : nullptr;
@@ -251,7 +254,7 @@ strip_solve_kernel(StripSolveArgs a) {
     // scale of the first correction: the strip's ||(2i/dt) M h|| (FP32 must not see ~1e-111)
     double bnorm = 0.0;
     double inv_s = (a.bnorm0 && a.bnorm0[j] > 0.0) ? 1.0 / a.bnorm0[j] : 1.0;
-    const double floor_abs = a.bscale ? a.nl_floor_frac * (*(volatile const double*)a.bscale) : 0.0;
+    const double floor_abs = a.bscale ? a.nl_floor_frac * ((volatile const double*)a.bscale)[si.inst] : 0.0;
 
     for (;; ++nl_it) {
         // ---------------- phase R: coefficients c = w (W + kappa|zeta|^2) and FP64 residual
@@ -504,18 +507,33 @@ strip_solve_kernel(StripSolveArgs a) {
 }
 
 template <typename T>
-static cudaError_t launch_strip_solve_t(const StripSolveArgs& args, int nblocks, cudaStream_t s) {
+static cudaError_t launch_strip_solve_t(const StripSolveArgs& args, int nblocks, int bs, cudaStream_t s) {
     StripSolveArgs a = args;
     void* params[] = {&a};
-    dim3 grid(nblocks), block(256);
+    dim3 grid(nblocks), block(bs);
     count_launches(1);
     if (a.pade_m > 0)
-        return cudaLaunchCooperativeKernel((const void*)strip_solve_kernel<T, true>, grid, block, params, 0, s);
-    return cudaLaunchCooperativeKernel((const void*)strip_solve_kernel<T, false>, grid, block, params, 0, s);
+        return cudaLaunchCooperativeKernel((const void*)strip_solve_kernel<T, true, 256>, grid, dim3(256), params, 0, s);
+    if (bs == 128)
+        return cudaLaunchCooperativeKernel((const void*)strip_solve_kernel<T, false, 128>, grid, block, params, 0, s);
+    return cudaLaunchCooperativeKernel((const void*)strip_solve_kernel<T, false, 256>, grid, dim3(256), params, 0, s);
 }
 
-cudaError_t launch_strip_solve(const StripSolveArgs& a, int nblocks, bool fp32, cudaStream_t s) {
-    return fp32 ? launch_strip_solve_t<float>(a, nblocks, s) : launch_strip_solve_t<double>(a, nblocks, s);
+cudaError_t launch_strip_solve(const StripSolveArgs& a, int nblocks, bool fp32, cudaStream_t s, int block_size) {
+    return fp32 ? launch_strip_solve_t<float>(a, nblocks, block_size, s)
+                : launch_strip_solve_t<double>(a, nblocks, block_size, s);
+}
+
+int strip_solve_max_blocks_bs(bool fp32, int bs) {
+    int dev = 0, nsm = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (bs == 128) {
+        if (fp32) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, strip_solve_kernel<float, false, 128>, 128, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, strip_solve_kernel<double, false, 128>, 128, 0);
+        return per * nsm;
+    }
+    return strip_solve_max_blocks(fp32);
 }
 
 int strip_solve_max_blocks(bool fp32) {
@@ -525,11 +543,11 @@ int strip_solve_max_blocks(bool fp32) {
     // the smaller of the Robin and S_pade instances, so one schedule fits both
     int per2 = 0;
     if (fp32) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, strip_solve_kernel<float, false>, 256, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, strip_solve_kernel<float, true>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, strip_solve_kernel<float, false, 256>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, strip_solve_kernel<float, true, 256>, 256, 0);
     } else {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, strip_solve_kernel<double, false>, 256, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, strip_solve_kernel<double, true>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, strip_solve_kernel<double, false, 256>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, strip_solve_kernel<double, true, 256>, 256, 0);
     }
     return std::min(per, per2) * nsm;
 }

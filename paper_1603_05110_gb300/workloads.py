@@ -17,6 +17,12 @@ Workloads (sizes are cells; nodes are cells + 1 per direction):
                 2048 x 2048 cells, 32 strips, dt = 0.001, 500 steps;
                 u0 = pi^{-1/2} exp(-(x^2+y^2)/2) exp(i eps xi), eps = 1e-3, xi ~ U[-1,1]
                 per node from numpy's PCG64 with seed 1603.
+* gpe_batch  -- 64 independent GPE instances on (-16,16)^2, dt = 0.002, 100 steps, Robin
+                p = sqrt(4/dt), classical: instance i draws (numpy PCG64, seed 1603 + i) the
+                strip count N ~ U{4..16}, cells per strip c ~ U{ceil(256/N)..floor(1024/N)}
+                (a square mesh of N*c cells), beta ~ U[100, 1000] and omega ~ U[0, 0.6]
+                (omega leaves the rotating-frame solve unchanged for the isotropic trap and is
+                carried as metadata only); u0 as gpe_trap with the instance's seed.
 """
 from dataclasses import dataclass, field
 
@@ -88,3 +94,19 @@ def scaled(w, nx, ny, n_strips=None, **kw):
     d.update(nx=nx, ny=ny, n_strips=n_strips or w.n_strips, **kw)
     d.pop("extra", None)
     return Workload(**d)
+
+
+def gpe_batch(n_instances=64, seed=1603, dt=0.002, steps=100, max_cells=1024, min_cells=256):
+    """The batched GPE instances (see the module docstring)."""
+    out = []
+    for i in range(n_instances):
+        rng = np.random.default_rng(seed + i)
+        N = int(rng.integers(4, 17))
+        c = int(rng.integers(-(-min_cells // N), max_cells // N + 1))
+        beta = float(rng.uniform(100.0, 1000.0))
+        omega = float(rng.uniform(0.0, 0.6))
+        n = N * c
+        out.append(Workload(f"gpe_batch_{i}", -16.0, 16.0, -16.0, 16.0, n, n, N, dt, steps, lap=0.5,
+                            kappa=-beta, p=float(np.sqrt(4.0 / dt)), potential="trap", datum="ground_noise",
+                            seed=seed + i, extra={"omega": omega, "beta": beta}))
+    return out

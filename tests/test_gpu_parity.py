@@ -256,3 +256,23 @@ def test_iteration_cap_reports_enoconv():
         with pytest.raises(binding.DDNLSError) as e:
             s.step(1)
         assert e.value.code == 4
+
+
+def test_batched_uneven_instances_match_oracle():
+    """Instances of different meshes, strip counts and nonlinearities stepped in one batch."""
+    shapes = [(24, 20, 3, -120.0), (30, 17, 5, -400.0), (16, 33, 2, -900.0), (40, 41, 4, -250.0)]
+    ws = [wl.Workload(f"b{i}", -4.0, 4.0, -4.0, 4.0, nx, ny, N, 0.01, 2, lap=0.5, kappa=k, p=20.0,
+                      potential="trap", datum="ground_noise", seed=1603 + i)
+          for i, (nx, ny, N, k) in enumerate(shapes)]
+    prms = [gpu_params(w, tol=TOL) for w in ws]
+    with binding.Batch(prms, [w.u0() for w in ws], [w.V() for w in ws]) as b:
+        for step in range(2):
+            st = b.step(1)
+            for i, w in enumerate(ws):
+                assert st[i]["steps"] == 1 and st[i]["schwarz_iterations"] > 0
+        got = [b.get_u(i) for i in range(len(ws))]
+        bs, nblk = b.tuning()
+        assert bs in (128, 256) and nblk >= sum(w.n_strips for w in ws)
+    for i, w in enumerate(ws):
+        ref = run_oracle(w, 2)
+        assert rel(got[i], ref[-1][0]) < 1e-11
