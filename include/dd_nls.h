@@ -123,7 +123,8 @@ typedef struct {
 } dd_nls_profile;
 
 /* Fill *p with defaults: NLS (lap=1, kappa=1), Robin p=1, classical, FP64, previous-step
- * guess, tol 1e-10, nl_tol 1e-13, inner_tol 1e-6, GMRES restart 30 / tol 1e-10, modal P solve. */
+ * guess, tol 1e-10, nl_tol 1e-13 (max_nl 300), inner_tol 1e-6, GMRES restart 30 / tol 1e-10,
+ * modal P solve. */
 void dd_nls_default_params(dd_nls_params* p);
 
 /* Create a solver.  V: real nodal potential (ny+1)*(nx+1) in the sign of eq. (Sch), or

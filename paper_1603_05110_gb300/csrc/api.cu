@@ -114,7 +114,7 @@ extern "C" void dd_nls_default_params(dd_nls_params* p) {
     p->precision = DD_NLS_FP64;
     p->guess = DD_NLS_GUESS_PREVIOUS;
     p->tol = 1e-10; p->tol_absolute = 0; p->max_schwarz = 500;
-    p->nl_tol = 1e-13; p->max_nl = 60;
+    p->nl_tol = 1e-13; p->max_nl = 300;
     p->inner_tol = 1e-6; p->max_inner = 2000;
     p->gmres_tol = 1e-10; p->gmres_restart = 30; p->gmres_max = 300;
     p->psolve = DD_NLS_PSOLVE_MODAL;

@@ -261,7 +261,7 @@ def test_iteration_cap_reports_enoconv():
 def test_batched_uneven_instances_match_oracle():
     """Instances of different meshes, strip counts and nonlinearities stepped in one batch."""
     shapes = [(24, 20, 3, -120.0), (30, 17, 5, -400.0), (16, 33, 2, -900.0), (40, 41, 4, -250.0)]
-    ws = [wl.Workload(f"b{i}", -4.0, 4.0, -4.0, 4.0, nx, ny, N, 0.01, 2, lap=0.5, kappa=k, p=20.0,
+    ws = [wl.Workload(f"b{i}", -4.0, 4.0, -4.0, 4.0, nx, ny, N, 0.002, 2, lap=0.5, kappa=k, p=45.0,
                       potential="trap", datum="ground_noise", seed=1603 + i)
           for i, (nx, ny, N, k) in enumerate(shapes)]
     prms = [gpu_params(w, tol=TOL) for w in ws]
