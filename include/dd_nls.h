@@ -92,6 +92,9 @@ typedef struct {
     int gmres_restart;
     int gmres_max;
     int psolve;          /* DD_NLS_PSOLVE_MODAL (default) or DD_NLS_PSOLVE_GMRES */
+    double nl_relax;     /* first relaxation factor of the strip fixed point (1: eq. localpbrobin
+                            as printed); a correction that does not cut the residual by 10%
+                            multiplies it by 0.6 (down to 0.25).  Same limit, safer path. */
 } dd_nls_params;
 
 typedef struct {

@@ -214,11 +214,14 @@ class Region:
         return out
 
     # -- nonlinear solve of the local problem ---------------------------------------------
-    def solve(self, h, l, r, tol=1e-13, maxit=200):
+    def solve(self, h, l, r, tol=1e-13, maxit=400, relax=1.0):
         """Fixed point of eq. (localpbrobin) / (localpbS2p), zeta^0 = h, phi^0 = 0.
 
-        Stops when ||zeta^q - zeta^{q-1}|| <= tol ||zeta^q||.  Returns (v, phi, iterations);
-        phi maps an edge to its list of m traces (empty for Robin).
+        Stops when ||F(zeta^{q-1}) - zeta^{q-1}|| <= tol ||F(zeta^{q-1})||, F one solve of the
+        fixed point.  ``relax`` < 1 takes zeta^q = relax F(zeta^{q-1}) + (1 - relax) zeta^{q-1}
+        (same fixed point; the plain iteration diverges for strong nonlinearity, the paper is
+        silent on safeguards).  Returns (v, phi, iterations); phi maps an edge to its list of m
+        traces (empty for Robin).
         """
         prob = self.prob
         b = self.rhs(h, l, r)
@@ -239,8 +242,13 @@ class Region:
                     off = self.n + ie * prob.m * ne
                     new_phi[e] = [sol[off + s * ne: off + (s + 1) * ne] for s in range(prob.m)]
             step = np.linalg.norm(new - zeta)
-            zeta, phi = new, new_phi
-            if linear or step <= tol * np.linalg.norm(zeta):
+            done = linear or step <= tol * np.linalg.norm(new)
+            if done or relax == 1.0:
+                zeta, phi = new, new_phi
+            else:
+                zeta = relax * new + (1.0 - relax) * zeta
+                phi = {e: [relax * a + (1.0 - relax) * b for a, b in zip(new_phi[e], phi[e])] for e in new_phi}
+            if done:
                 return zeta, phi, q
         raise RuntimeError("fixed point did not converge")
 
@@ -257,12 +265,12 @@ def mono_region(prob):
     return Region(prob, 0, prob.nx, left=k, right=k)
 
 
-def mono_step(prob, u_prev, tol=1e-13, l=None, r=None, region=None):
+def mono_step(prob, u_prev, tol=1e-13, l=None, r=None, region=None, relax=1.0):
     """One step of eq. (CNS) on the whole of Omega.  ``l``/``r`` are optional physical
     Robin data on x = xl / x = xr (eq. eqdist); they default to the homogeneous BC (BC)."""
     reg = region or mono_region(prob)
     h = u_prev.ravel().astype(np.complex128)
-    v, _, q = reg.solve(h, l, r, tol=tol)
+    v, _, q = reg.solve(h, l, r, tol=tol, relax=relax)
     v = v.reshape(reg.shape)
     return 2.0 * v - u_prev, v, q
 
@@ -292,13 +300,13 @@ class Strips:
         r = g[2 * j] if j < self.N - 1 else np.zeros(self.ne, complex)
         return l, r
 
-    def apply_R(self, g, u_prev, tol_fp=1e-13):
+    def apply_R(self, g, u_prev, tol_fp=1e-13, relax=1.0):
         """R(g) of eq. (algo_d): solve every strip, then the flux update of eq. (fluxlr)."""
         Rg = np.zeros_like(g)
         vs, fp_its = [], []
         for j, reg in enumerate(self.regions):
             l, r = self.data(g, j)
-            v, phi, q = reg.solve(reg.restrict(u_prev), l, r, tol=tol_fp)
+            v, phi, q = reg.solve(reg.restrict(u_prev), l, r, tol=tol_fp, relax=relax)
             vs.append(v)
             fp_its.append(q)
             if j > 0:        # new r_{j-1} = -l_j + 2 S v_j(a_j)
@@ -406,7 +414,7 @@ class StepInfo:
 
 
 def schwarz_step(prob, N, u_prev, g0=None, algorithm="classical", tol=1e-10, max_iter=2000,
-                 strips=None, Lh=None, tol_fp=1e-13, gmres_tol=1e-13, absolute=False):
+                 strips=None, Lh=None, tol_fp=1e-13, gmres_tol=1e-13, absolute=False, relax=1.0):
     """One time step by the classical (eq. algo_d) or preconditioned (eq. algo_pd) algorithm.
 
     Stops at the first k with ||R(g^k) - g^k|| <= tol * ||R(g^k)|| (or <= tol if
@@ -418,7 +426,7 @@ def schwarz_step(prob, N, u_prev, g0=None, algorithm="classical", tol=1e-10, max
         Lh = st.build_Lh()
     info = StepInfo()
     for k in range(max_iter):
-        Rg, vs, fp = st.apply_R(g, u_prev, tol_fp=tol_fp)
+        Rg, vs, fp = st.apply_R(g, u_prev, tol_fp=tol_fp, relax=relax)
         diff = np.linalg.norm(Rg - g)
         nrm = np.linalg.norm(Rg)
         rel = diff / nrm if nrm > 0 else diff

@@ -118,6 +118,7 @@ extern "C" void dd_nls_default_params(dd_nls_params* p) {
     p->inner_tol = 1e-6; p->max_inner = 2000;
     p->gmres_tol = 1e-10; p->gmres_restart = 30; p->gmres_max = 300;
     p->psolve = DD_NLS_PSOLVE_MODAL;
+    p->nl_relax = 1.0;
 }
 
 template <typename T> static cudaError_t dalloc(T** ptr, size_t n) {
@@ -285,6 +286,7 @@ static StripSolveArgs base_args(dd_nls* h) {
     a.nl_floor_frac = 0.01 * h->P.nl_tol / std::sqrt((double)h->G.N);
     a.max_nl = h->P.max_nl;
     a.max_inner = h->P.max_inner;
+    a.nl_relax = h->P.nl_relax;
     a.part = h->part;
     a.bar = h->bar;
     a.status = h->status;

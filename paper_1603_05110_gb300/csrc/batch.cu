@@ -215,6 +215,7 @@ static StripSolveArgs batch_args(dd_nls_batch* b) {
     a.nl_floor_frac = 0.01 * b->P[0].nl_tol / 4.0;
     a.max_nl = b->P[0].max_nl;
     a.max_inner = b->P[0].max_inner;
+    a.nl_relax = b->P[0].nl_relax;
     a.part = b->part;
     a.bar = b->bar;
     a.status = b->status;

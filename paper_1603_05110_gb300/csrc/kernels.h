@@ -44,6 +44,7 @@ struct StripSolveArgs {
     const double* bscale;    // ||(2i/dt) M u_{n-1}|| over all strips, one per instance (device), or NULL
     double nl_floor_frac;    // strips stop once ||res|| <= nl_floor_frac * (*bscale)
     int max_nl, max_inner;
+    double nl_relax;         // first relaxation factor of the fixed point (adaptive below it)
     double* part;            // [4][gridDim][4] partial sums
     unsigned* bar;           // [strips] barrier counters, zeroed before the launch
     int* status;             // [strips]

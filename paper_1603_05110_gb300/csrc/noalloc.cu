@@ -203,6 +203,7 @@ extern "C" int dd_nls_step_noalloc(const dd_nls_params* p, const double* V, doub
     a.nl_floor_frac = 0.01 * p->nl_tol / std::sqrt((double)G.N);
     a.max_nl = p->max_nl;
     a.max_inner = p->max_inner;
+    a.nl_relax = p->nl_relax;
     a.part = part;
     a.bar = bar;
     a.status = status;

@@ -255,6 +255,11 @@ strip_solve_kernel(StripSolveArgs a) {
     double bnorm = 0.0;
     double inv_s = (a.bnorm0 && a.bnorm0[j] > 0.0) ? 1.0 / a.bnorm0[j] : 1.0;
     const double floor_abs = a.bscale ? a.nl_floor_frac * ((volatile const double*)a.bscale)[si.inst] : 0.0;
+    // relaxation of the fixed point: zeta += omega delta, i.e. zeta^q = omega F(zeta^{q-1}) +
+    // (1 - omega) zeta^{q-1} (same limit); omega shrinks when a correction does not cut the
+    // residual by 10% (the plain iteration diverges for strong nonlinearity)
+    double omega = (a.nl_relax > 0.0 && a.nl_relax <= 1.0) ? a.nl_relax : 1.0;
+    double rprev = 0.0;
 
     for (;; ++nl_it) {
         // ---------------- phase R: coefficients c = w (W + kappa|zeta|^2) and FP64 residual
@@ -342,6 +347,8 @@ strip_solve_kernel(StripSolveArgs a) {
         if (!isfinite(tot[0]) || !isfinite(tot[1])) { status = DD_NLS_ENONFINITE; break; }
         if (nres <= a.nl_tol || rnorm <= floor_abs || rnorm == 0.0) break;
         if (nl_it >= a.max_nl) { status = DD_NLS_ENOCONV; break; }
+        if (nl_it > 0 && rnorm > 0.9 * rprev) omega = fmax(0.25, 0.6 * omega);
+        rprev = rnorm;
 
         // ---------------- inner COCG on A(c) delta = res, Jacobi preconditioner
         double rho_r = tot[2], rho_i = tot[3];
@@ -471,7 +478,7 @@ strip_solve_kernel(StripSolveArgs a) {
         }
         if (status) break;
         // ---------------- zeta += delta (FP64), then every block must see the new zeta
-        const double sc = 1.0 / inv_s;
+        const double sc = omega / inv_s;
         for (int ch = rank; ch < nchunks; ch += bps) {
             const int n = ch * blockDim.x + threadIdx.x;
             if (n >= Nall) continue;

@@ -40,7 +40,7 @@ def run_gpu(w, steps, **kw):
     return hist
 
 
-def run_oracle(w, steps, algorithm="classical", bc="same", tol=TOL, tc="robin", m=4):
+def run_oracle(w, steps, algorithm="classical", bc="same", tol=TOL, tc="robin", m=4, relax=1.0):
     prob = oracle_problem(w, bc=bc, tc=tc, m=m)
     st = nls.Strips(prob, w.n_strips)
     Lh = st.build_Lh() if algorithm == "preconditioned" else None
@@ -48,7 +48,8 @@ def run_oracle(w, steps, algorithm="classical", bc="same", tol=TOL, tc="robin", 
     g = None
     out = []
     for _ in range(steps):
-        u, _, info = nls.schwarz_step(prob, w.n_strips, u, g0=g, algorithm=algorithm, tol=tol, strips=st, Lh=Lh)
+        u, _, info = nls.schwarz_step(prob, w.n_strips, u, g0=g, algorithm=algorithm, tol=tol, strips=st, Lh=Lh,
+                                      relax=relax)
         g = info.g
         out.append((u.copy(), info))
     return out
@@ -274,5 +275,6 @@ def test_batched_uneven_instances_match_oracle():
         bs, nblk = b.tuning()
         assert bs in (128, 256) and nblk >= sum(w.n_strips for w in ws)
     for i, w in enumerate(ws):
-        ref = run_oracle(w, 2)
+        # beta = 900 at dt = 0.002: the plain fixed point diverges; both sides relax it
+        ref = run_oracle(w, 2, relax=0.6)
         assert rel(got[i], ref[-1][0]) < 1e-11

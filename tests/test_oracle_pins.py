@@ -281,3 +281,25 @@ def test_lh_blocks_are_diagonal_in_the_cosine_basis(bc):
         for X in st.strip_blocks(j):
             Xh = Zi @ X @ Z
             assert np.max(np.abs(Xh - np.diag(np.diag(Xh)))) < 1e-13
+
+
+def test_relaxed_fixed_point_has_the_same_limit_and_converges_where_plain_diverges():
+    """Strong defocusing nonlinearity (GPE, beta = 900, dt = 0.002): the plain fixed point of
+    eq. (localpbrobin) diverges; relaxed by 0.6 it converges, to a v that satisfies the
+    discrete nonlinear system (checked by its residual), and for a mild nonlinearity both
+    reach the same v."""
+    prob = nls.Problem(xl=-4.0, xr=4.0, yb=-4.0, yu=4.0, nx=16, ny=33, dt=0.002, kappa=-900.0, lap=0.5, p=45.0)
+    X, Y = prob.grid()
+    prob.V = -0.5 * (X ** 2 + Y ** 2)
+    u0 = np.pi ** -0.5 * np.exp(-(X ** 2 + Y ** 2) / 2)
+    with pytest.raises(RuntimeError):
+        nls.mono_step(prob, u0, relax=1.0)
+    u1, v, _ = nls.mono_step(prob, u0, relax=0.6)
+    reg = nls.mono_region(prob)
+    vv = v.ravel()
+    res = reg.robin_matrix(vv) @ vv - reg.rhs(u0.ravel(), None, None)
+    assert np.linalg.norm(res) < 1e-11 * np.linalg.norm(reg.rhs(u0.ravel(), None, None))
+    mild = nls.Problem(xl=-4.0, xr=4.0, yb=-4.0, yu=4.0, nx=16, ny=33, dt=0.002, kappa=-100.0, lap=0.5, p=45.0, V=prob.V)
+    a, _, _ = nls.mono_step(mild, u0, relax=1.0)
+    b, _, _ = nls.mono_step(mild, u0, relax=0.6)
+    assert rel(b, a) < 1e-12
