@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--instances", type=int, default=64)
+    ap.add_argument("--max-schwarz", type=int, default=5000)
     return ap.parse_args()
 
 
@@ -369,7 +370,7 @@ def run_batch(args, rank, world, local_rank):
     prms = []
     for w in ws:
         d = solver_params(w, args, binding.FP32_INNER)
-        d.update(p=w.p, algorithm=binding.CLASSICAL, tol=args.tol)
+        d.update(p=w.p, algorithm=binding.CLASSICAL, tol=args.tol, max_schwarz=args.max_schwarz)
         prms.append(d)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -409,6 +410,8 @@ def run_batch(args, rank, world, local_rank):
                        "l2": "flushed (512 MB write) before every timed step"},
             "autotuned": {"block_size": bs, "blocks_per_launch": nblk, "first_call_s": warm_s},
             "schwarz_iterations_per_step_max": max(max(s2["last_schwarz_iterations"] for s2 in st) for st in stats),
+            "schwarz_iterations_per_step_mean": statistics.mean(statistics.mean(s2["last_schwarz_iterations"] for s2 in st)
+                                                                for st in stats),
             "strip_solve_ms_per_step": prof["strip_solve_ms"] / args.steps,
             "strip_solve_launches_per_step": prof["strip_solve_launches"] / args.steps,
             "gpu_launches": prof["kernel_launches"], "clocks": clk}
