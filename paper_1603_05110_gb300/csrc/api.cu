@@ -586,8 +586,15 @@ static int schwarz(dd_nls* h, dd_nls_stats* st) {
     StripSolveArgs a = base_args(h);
     double2* g = h->gA;
     double2* gn = h->gB;
+    double rel_prev = 1.0;
     for (int k = 0; k < h->P.max_schwarz; ++k) {
         a.gtr = g;
+        // inexact strip solves while the interface residual is large: 1% of the last relative
+        // residual (at most 1e-6), down to nl_tol.  Same fixed point, cheaper early iterations.
+        const double tol_k = std::max(h->P.nl_tol, std::min(1e-6, 0.01 * rel_prev));
+        a.nl_tol = tol_k;
+        a.inner_floor = 0.1 * tol_k;
+        a.nl_floor_frac = 0.01 * tol_k / std::sqrt((double)G.N);
         const int nblk = schedule(h, h->wts, G.N, h->chunks, a);
         int rc = strip_solve(h, a, G.N, nblk, st, true);
         if (rc) return rc;
@@ -611,7 +618,9 @@ static int schwarz(dd_nls* h, dd_nls_stats* st) {
             st->residual_abs = diff;
         }
         if (!std::isfinite(diff) || !std::isfinite(nrm)) return fail(h, DD_NLS_ENONFINITE, "interface residual is not finite");
-        if ((h->P.tol_absolute ? diff : rel) <= h->P.tol) {
+        rel_prev = rel;
+        // converged only once the strip solves behind R(g) were at full accuracy
+        if ((h->P.tol_absolute ? diff : rel) <= h->P.tol && tol_k <= std::max(h->P.nl_tol, 0.01 * h->P.tol)) {
             if (G.N > 1) CK(cudaMemcpyAsync(h->gconv, gn, h->nI * sizeof(double2), cudaMemcpyDeviceToDevice, h->s));
             h->gA = g;
             h->gB = gn;

@@ -97,6 +97,9 @@ struct dd_nls_batch {
     double* Wn = nullptr;
     void *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *cT = nullptr;
     double *part = nullptr, *bscale = nullptr, *bnorm0 = nullptr, *res = nullptr, *nl_res = nullptr;
+    double* d_tol = nullptr;        // per-strip nonlinear tolerance of the next launch
+    double* h_tol = nullptr;        // pinned mirror
+    std::vector<double> rel_prev;   // last relative interface residual per instance
     unsigned* bar = nullptr;
     int *status = nullptr, *nl_its = nullptr, *err = nullptr, *d_blk = nullptr;
     long long* kry = nullptr;
@@ -143,10 +146,10 @@ template <typename T> static cudaError_t zalloc(T** ptr, size_t n) {
 static void batch_release(dd_nls_batch* b) {
     void* dev[] = {b->d_geoms, b->d_sinfo, b->d_foff, b->d_goff, b->d_cur, b->d_active, b->u, b->zeta, b->rhs0,
                    b->gbuf, b->Wn, b->x, b->r, b->z, b->p, b->q, b->cT, b->part, b->bscale, b->bnorm0, b->res,
-                   b->nl_res, b->bar, b->status, b->nl_its, b->err, b->d_blk, b->kry};
+                   b->nl_res, b->bar, b->status, b->nl_its, b->err, b->d_blk, b->kry, b->d_tol};
     for (void* p : dev)
         if (p) cudaFree(p);
-    void* host[] = {b->h_blk, b->h_cur, b->h_active, b->h_res, b->h_bn};
+    void* host[] = {b->h_blk, b->h_cur, b->h_active, b->h_res, b->h_bn, b->h_tol};
     for (void* p : host)
         if (p) cudaFreeHost(p);
     if (b->ev0) cudaEventDestroy(b->ev0);
@@ -209,6 +212,7 @@ static StripSolveArgs batch_args(dd_nls_batch* b) {
     a.gtr = b->gbuf;
     a.x = b->x; a.r = b->r; a.z = b->z; a.p = b->p; a.q = b->q; a.cT = b->cT;
     a.nl_tol = b->P[0].nl_tol;
+    a.nl_tol_strip = b->d_tol;
     a.inner_tol = b->P[0].inner_tol;
     a.inner_floor = 0.1 * b->P[0].nl_tol;
     a.bscale = b->bscale;
@@ -238,6 +242,11 @@ static int batch_solve(dd_nls_batch* b, StripSolveArgs& a, int nblk, float* ms_o
     }
     BCK(cudaMemcpyAsync(b->d_sinfo, b->sinfo.data(), sizeof(StripInfo) * b->nstrips, cudaMemcpyHostToDevice, b->s));
     BCK(cudaMemcpyAsync(b->d_blk, b->h_blk, sizeof(int) * (b->maxb + b->nstrips + 1), cudaMemcpyHostToDevice, b->s));
+    for (int j = 0; j < b->nstrips; ++j) {
+        const int i = b->sinfo[j].inst;
+        b->h_tol[j] = std::max(b->P[i].nl_tol, std::min(1e-6, 0.01 * b->rel_prev[i]));
+    }
+    BCK(cudaMemcpyAsync(b->d_tol, b->h_tol, sizeof(double) * b->nstrips, cudaMemcpyHostToDevice, b->s));
     BCK(cudaMemsetAsync(b->bar, 0, sizeof(unsigned) * b->nstrips, b->s));
     BCK(cudaMemsetAsync(b->err, 0, sizeof(int), b->s));
     BCK(cudaEventRecord(b->ev0, b->s));
@@ -395,6 +404,9 @@ extern "C" int dd_nls_batch_create(int n, const dd_nls_params* params, const dou
     BCKC(zalloc(&b->d_goff, n));
     BCKC(zalloc(&b->d_cur, n));
     BCKC(zalloc(&b->d_active, n));
+    BCKC(zalloc(&b->d_tol, b->nstrips));
+    BCKC(cudaMallocHost((void**)&b->h_tol, sizeof(double) * b->nstrips));
+    b->rel_prev.assign(n, 1.0);
     BCKC(cudaMallocHost((void**)&b->h_blk, sizeof(int) * (maxb + b->nstrips + 2)));
     BCKC(cudaMallocHost((void**)&b->h_cur, sizeof(int) * (n + 1)));
     BCKC(cudaMallocHost((void**)&b->h_active, sizeof(int) * n));
@@ -459,6 +471,7 @@ extern "C" int dd_nls_batch_step(dd_nls_batch* b, int nsteps, dd_nls_stats* stat
                 if (gb) BCK(cudaMemsetAsync(b->gbuf + b->goff[i], 0, gb, b->s));
             }
             b->h_active[i] = 1;
+            b->rel_prev[i] = 1.0;
         }
         BCK(cudaMemcpyAsync(b->zeta, b->u, sizeof(double2) * b->nfield, cudaMemcpyDeviceToDevice, b->s));
         BCK(cudaMemcpyAsync(b->h_bn, b->bnorm0, sizeof(double) * b->nstrips, cudaMemcpyDeviceToHost, b->s));
@@ -514,7 +527,10 @@ extern "C" int dd_nls_batch_step(dd_nls_batch* b, int nsteps, dd_nls_stats* stat
                 if (stats) { stats[i].residual = rel; stats[i].residual_abs = diff; stats[i].schwarz_iterations += 1;
                              stats[i].last_schwarz_iterations = k + 1; }
                 b->cur[i] ^= 1;                       // the new R(g) is the next g
-                if ((b->P[i].tol_absolute ? diff : rel) <= b->P[i].tol || b->G[i].N == 1) {
+                const double tol_k = std::max(b->P[i].nl_tol, std::min(1e-6, 0.01 * b->rel_prev[i]));
+                b->rel_prev[i] = rel;
+                if (((b->P[i].tol_absolute ? diff : rel) <= b->P[i].tol && tol_k <= std::max(b->P[i].nl_tol, 0.01 * b->P[i].tol))
+                    || b->G[i].N == 1) {
                     // zeta holds v for g^k; R(g^k) (now current) is the next step's guess
                     b->conv_half[i] = b->cur[i];
                     b->h_active[i] = 0;

@@ -41,6 +41,7 @@ struct StripSolveArgs {
     void *x, *r, *z, *p, *q; // inner Krylov vectors (float2 or double2)
     void* cT;                // c = w (W + kappa|zeta|^2) in inner precision
     double nl_tol, inner_tol, inner_floor;
+    const double* nl_tol_strip;   // batched: per-strip nonlinear tolerance (device), or NULL
     const double* bscale;    // ||(2i/dt) M u_{n-1}|| over all strips, one per instance (device), or NULL
     double nl_floor_frac;    // strips stop once ||res|| <= nl_floor_frac * (*bscale)
     int max_nl, max_inner;

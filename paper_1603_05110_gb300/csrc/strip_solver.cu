@@ -254,7 +254,10 @@ strip_solve_kernel(StripSolveArgs a) {
     // scale of the first correction: the strip's ||(2i/dt) M h|| (FP32 must not see ~1e-111)
     double bnorm = 0.0;
     double inv_s = (a.bnorm0 && a.bnorm0[j] > 0.0) ? 1.0 / a.bnorm0[j] : 1.0;
-    const double floor_abs = a.bscale ? a.nl_floor_frac * ((volatile const double*)a.bscale)[si.inst] : 0.0;
+    const double nl_tol = a.nl_tol_strip ? a.nl_tol_strip[j] : a.nl_tol;
+    const double nl_floor_frac = a.nl_tol_strip ? a.nl_floor_frac * nl_tol / a.nl_tol : a.nl_floor_frac;
+    const double inner_floor = a.nl_tol_strip ? 0.1 * nl_tol : a.inner_floor;
+    const double floor_abs = a.bscale ? nl_floor_frac * ((volatile const double*)a.bscale)[si.inst] : 0.0;
     // relaxation of the fixed point: zeta += omega delta, i.e. zeta^q = omega F(zeta^{q-1}) +
     // (1 - omega) zeta^{q-1} (same limit); omega shrinks when a correction does not cut the
     // residual by 10% (the plain iteration diverges for strong nonlinearity)
@@ -345,7 +348,7 @@ strip_solve_kernel(StripSolveArgs a) {
         bnorm = sqrt(tot[1]);
         nres = bnorm > 0.0 ? rnorm / bnorm : rnorm;
         if (!isfinite(tot[0]) || !isfinite(tot[1])) { status = DD_NLS_ENONFINITE; break; }
-        if (nres <= a.nl_tol || rnorm <= floor_abs || rnorm == 0.0) break;
+        if (nres <= nl_tol || rnorm <= floor_abs || rnorm == 0.0) break;
         if (nl_it >= a.max_nl) { status = DD_NLS_ENOCONV; break; }
         if (nl_it > 0 && rnorm > 0.9 * rprev) omega = fmax(0.25, 0.6 * omega);
         rprev = rnorm;
@@ -354,7 +357,7 @@ strip_solve_kernel(StripSolveArgs a) {
         double rho_r = tot[2], rho_i = tot[3];
         double beta_re = 0.0, beta_im = 0.0;
         // inner stopping test in the scaled units of r
-        const double target = fmax(a.inner_tol * rnorm, fmax(a.inner_floor * bnorm, 0.1 * floor_abs)) * inv_s;
+        const double target = fmax(a.inner_tol * rnorm, fmax(inner_floor * bnorm, 0.1 * floor_abs)) * inv_s;
         for (int it = 0; it < a.max_inner; ++it) {
             // phase A: q = A z + beta q, p = z + beta p, partial mu = p^T q
             // (per-thread partials in T: the FP64 pipe is ~1/64 of FP32 on this part)
