@@ -370,7 +370,7 @@ def run_batch(args, rank, world, local_rank):
     prms = []
     for w in ws:
         d = solver_params(w, args, binding.FP32_INNER)
-        d.update(p=w.p, algorithm=binding.CLASSICAL, tol=args.tol, max_schwarz=args.max_schwarz)
+        d.update(p=w.p, algorithm=binding.CLASSICAL, tol=args.tol, max_schwarz=args.max_schwarz, nl_tol=1e-13)
         prms.append(d)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)

@@ -84,10 +84,10 @@ typedef struct {
     double tol;          /* ||R(g)-g|| <= tol*||R(g)|| (or <= tol if tol_absolute) */
     int tol_absolute;
     int max_schwarz;
-    double nl_tol;       /* strip solves: ||b - A(zeta) zeta|| <= tol_k * ||b||, where tol_k is
-                            1% of the last relative interface residual (at most 1e-6) and never
-                            below nl_tol; a step converges only once tol_k <= max(nl_tol,
-                            tol/100) */
+    double nl_tol;       /* strip solves: ||b - A(zeta) zeta|| <= tol_k * ||b||.  Classical:
+                            tol_k = nl_tol.  Preconditioned: tol_k is 1% of the last relative
+                            interface residual (at most 1e-6), never below nl_tol, and a step
+                            converges only once tol_k <= max(nl_tol, tol/100) */
     int max_nl;
     double inner_tol;    /* Krylov: residual reduction per correction */
     int max_inner;

@@ -242,10 +242,7 @@ static int batch_solve(dd_nls_batch* b, StripSolveArgs& a, int nblk, float* ms_o
     }
     BCK(cudaMemcpyAsync(b->d_sinfo, b->sinfo.data(), sizeof(StripInfo) * b->nstrips, cudaMemcpyHostToDevice, b->s));
     BCK(cudaMemcpyAsync(b->d_blk, b->h_blk, sizeof(int) * (b->maxb + b->nstrips + 1), cudaMemcpyHostToDevice, b->s));
-    for (int j = 0; j < b->nstrips; ++j) {
-        const int i = b->sinfo[j].inst;
-        b->h_tol[j] = std::max(b->P[i].nl_tol, std::min(1e-6, 0.01 * b->rel_prev[i]));
-    }
+    for (int j = 0; j < b->nstrips; ++j) b->h_tol[j] = b->P[b->sinfo[j].inst].nl_tol;   // classical: fixed
     BCK(cudaMemcpyAsync(b->d_tol, b->h_tol, sizeof(double) * b->nstrips, cudaMemcpyHostToDevice, b->s));
     BCK(cudaMemsetAsync(b->bar, 0, sizeof(unsigned) * b->nstrips, b->s));
     BCK(cudaMemsetAsync(b->err, 0, sizeof(int), b->s));
@@ -527,10 +524,8 @@ extern "C" int dd_nls_batch_step(dd_nls_batch* b, int nsteps, dd_nls_stats* stat
                 if (stats) { stats[i].residual = rel; stats[i].residual_abs = diff; stats[i].schwarz_iterations += 1;
                              stats[i].last_schwarz_iterations = k + 1; }
                 b->cur[i] ^= 1;                       // the new R(g) is the next g
-                const double tol_k = std::max(b->P[i].nl_tol, std::min(1e-6, 0.01 * b->rel_prev[i]));
                 b->rel_prev[i] = rel;
-                if (((b->P[i].tol_absolute ? diff : rel) <= b->P[i].tol && tol_k <= std::max(b->P[i].nl_tol, 0.01 * b->P[i].tol))
-                    || b->G[i].N == 1) {
+                if ((b->P[i].tol_absolute ? diff : rel) <= b->P[i].tol || b->G[i].N == 1) {
                     // zeta holds v for g^k; R(g^k) (now current) is the next step's guess
                     b->conv_half[i] = b->cur[i];
                     b->h_active[i] = 0;
