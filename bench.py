@@ -53,9 +53,9 @@ def parse():
     return ap.parse_args()
 
 
-def solver_params(w, args, precision, psolve=None):
+def solver_params(w, args, precision, psolve=None, adapt=0.01):
     from paper_1603_05110_gb300 import binding
-    return dict(psolve=binding.PSOLVE_MODAL if psolve is None else psolve,xl=w.xl, xr=w.xr, yb=w.yb, yu=w.yu, nx=w.nx, ny=w.ny, n_strips=w.n_strips, dt=w.dt,
+    return dict(psolve=binding.PSOLVE_MODAL if psolve is None else psolve, nl_adapt=adapt,xl=w.xl, xr=w.xr, yb=w.yb, yu=w.yu, nx=w.nx, ny=w.ny, n_strips=w.n_strips, dt=w.dt,
                 lap=w.lap, kappa=w.kappa, p=args.p, tol=args.tol, nl_tol=1e-11, inner_tol=1e-4,
                 max_inner=4000, max_schwarz=400, gmres_tol=1e-6, gmres_restart=30, gmres_max=300,
                 algorithm=binding.PRECONDITIONED if w.algorithm == "preconditioned" else binding.CLASSICAL,
@@ -276,7 +276,7 @@ def run_ours(args, rank, world, local_rank):
                 "strip_solve_gbs": prof64["strip_solve_bytes"] / (prof64["strip_solve_ms"] * 1e-3) / 1e9,
                 "strip_solve_gflops": prof64["strip_solve_flops"] / (prof64["strip_solve_ms"] * 1e-3) / 1e9}
         # the paper-literal path: FP64, L_h from unit solves, P x = y by GMRES
-        gm = binding.Solver(solver_params(w, args, binding.FP64, binding.PSOLVE_GMRES), u0, V, stream=stream)
+        gm = binding.Solver(solver_params(w, args, binding.FP64, binding.PSOLVE_GMRES, adapt=0.0), u0, V, stream=stream)
         gm.step(1)
         msg, stg, _ = timed_steps(gm, 2)
         gm.close()

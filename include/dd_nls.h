@@ -84,10 +84,8 @@ typedef struct {
     double tol;          /* ||R(g)-g|| <= tol*||R(g)|| (or <= tol if tol_absolute) */
     int tol_absolute;
     int max_schwarz;
-    double nl_tol;       /* strip solves: ||b - A(zeta) zeta|| <= tol_k * ||b||.  Classical:
-                            tol_k = nl_tol.  Preconditioned: tol_k is 1% of the last relative
-                            interface residual (at most 1e-6), never below nl_tol, and a step
-                            converges only once tol_k <= max(nl_tol, tol/100) */
+    double nl_tol;       /* strip solves: ||b - A(zeta) zeta|| <= tol_k * ||b||; tol_k = nl_tol
+                            unless nl_adapt is set (see below) */
     int max_nl;
     double inner_tol;    /* Krylov: residual reduction per correction */
     int max_inner;
@@ -98,6 +96,11 @@ typedef struct {
     double nl_relax;     /* first relaxation factor of the strip fixed point (1: eq. localpbrobin
                             as printed); a correction that does not cut the residual by 10%
                             multiplies it by 0.6 (down to 0.25).  Same limit, safer path. */
+    double nl_adapt;     /* 0 (default): strip solves always to nl_tol.  > 0, preconditioned
+                            algorithm only: tol_k = nl_adapt x the last relative interface
+                            residual (at most 1e-6, never below nl_tol), and a step converges
+                            only once tol_k <= max(nl_tol, nl_adapt x tol).  Same fixed point,
+                            cheaper early Schwarz iterations. */
 } dd_nls_params;
 
 typedef struct {

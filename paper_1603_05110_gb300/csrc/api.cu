@@ -119,6 +119,7 @@ extern "C" void dd_nls_default_params(dd_nls_params* p) {
     p->gmres_tol = 1e-10; p->gmres_restart = 30; p->gmres_max = 300;
     p->psolve = DD_NLS_PSOLVE_MODAL;
     p->nl_relax = 1.0;
+    p->nl_adapt = 0.0;
 }
 
 template <typename T> static cudaError_t dalloc(T** ptr, size_t n) {
@@ -589,12 +590,12 @@ static int schwarz(dd_nls* h, dd_nls_stats* st) {
     double rel_prev = 1.0;
     for (int k = 0; k < h->P.max_schwarz; ++k) {
         a.gtr = g;
-        // preconditioned algorithm: inexact strip solves while the interface residual is large
-        // (1% of the last relative residual, at most 1e-6, down to nl_tol); same fixed point,
-        // cheaper early iterations.  The classical algorithm contracts too slowly (0.98-0.99 per
-        // iteration) to absorb that perturbation and keeps nl_tol throughout.
-        const double tol_k = h->P.algorithm == DD_NLS_PRECONDITIONED
-                                 ? std::max(h->P.nl_tol, std::min(1e-6, 0.01 * rel_prev)) : h->P.nl_tol;
+        // nl_adapt > 0 with the preconditioned algorithm: inexact strip solves while the interface
+        // residual is large (nl_adapt x the last relative residual, at most 1e-6, down to
+        // nl_tol); same fixed point, cheaper early iterations.  The classical algorithm contracts
+        // too slowly (0.98-0.99 per iteration) to absorb that perturbation.
+        const bool adapt = h->P.algorithm == DD_NLS_PRECONDITIONED && h->P.nl_adapt > 0.0;
+        const double tol_k = adapt ? std::max(h->P.nl_tol, std::min(1e-6, h->P.nl_adapt * rel_prev)) : h->P.nl_tol;
         a.nl_tol = tol_k;
         a.inner_floor = 0.1 * tol_k;
         a.nl_floor_frac = 0.01 * tol_k / std::sqrt((double)G.N);
@@ -623,7 +624,7 @@ static int schwarz(dd_nls* h, dd_nls_stats* st) {
         if (!std::isfinite(diff) || !std::isfinite(nrm)) return fail(h, DD_NLS_ENONFINITE, "interface residual is not finite");
         rel_prev = rel;
         // converged only once the strip solves behind R(g) were at full accuracy
-        if ((h->P.tol_absolute ? diff : rel) <= h->P.tol && tol_k <= std::max(h->P.nl_tol, 0.01 * h->P.tol)) {
+        if ((h->P.tol_absolute ? diff : rel) <= h->P.tol && (!adapt || tol_k <= std::max(h->P.nl_tol, h->P.nl_adapt * h->P.tol))) {
             if (G.N > 1) CK(cudaMemcpyAsync(h->gconv, gn, h->nI * sizeof(double2), cudaMemcpyDeviceToDevice, h->s));
             h->gA = g;
             h->gB = gn;

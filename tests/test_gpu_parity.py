@@ -88,6 +88,15 @@ def test_preconditioned_robin_matches_oracle(precision, psolve):
         assert st["last_schwarz_iterations"] <= info.iterations + 5
 
 
+@pytest.mark.parametrize("precision", [binding.FP64, binding.FP32_INNER])
+def test_adaptive_strip_tolerance_reaches_the_same_step(precision):
+    """nl_adapt: loose strip solves in early preconditioned iterations, same converged step."""
+    ref = run_oracle(WELL, 2, algorithm="preconditioned")
+    got = run_gpu(WELL, 2, tol=TOL, precision=precision, algorithm=binding.PRECONDITIONED, nl_adapt=0.01)
+    for (ug, st), (uo, info) in zip(got, ref):
+        assert rel(ug, uo) < 1e-10
+
+
 def test_lh_blocks_match_oracle():
     w = WELL
     prob = oracle_problem(w)
