@@ -96,6 +96,10 @@ typedef struct {
     double nl_relax;     /* first relaxation factor of the strip fixed point (1: eq. localpbrobin
                             as printed); a correction that does not cut the residual by 10%
                             multiplies it by 0.6 (down to 0.25).  Same limit, safer path. */
+    int nl_picard;       /* operator of each strip correction: 0 (default) the complex-linear part
+                            of the Jacobian, diag(w(W + 2 kappa|zeta|^2)); 1 the frozen operator
+                            of the fixed point of eq. localpbrobin, diag(w(W + kappa|zeta|^2)).
+                            The residual is exact either way, so the limit is the same. */
     double nl_adapt;     /* 0 (default): strip solves always to nl_tol.  > 0, preconditioned
                             algorithm only: tol_k = nl_adapt x the last relative interface
                             residual (at most 1e-6, never below nl_tol), and a step converges

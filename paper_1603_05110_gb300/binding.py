@@ -36,7 +36,8 @@ class Params(ctypes.Structure):
         ("nl_tol", ctypes.c_double), ("max_nl", ctypes.c_int),
         ("inner_tol", ctypes.c_double), ("max_inner", ctypes.c_int),
         ("gmres_tol", ctypes.c_double), ("gmres_restart", ctypes.c_int), ("gmres_max", ctypes.c_int),
-        ("psolve", ctypes.c_int), ("nl_relax", ctypes.c_double), ("nl_adapt", ctypes.c_double),
+        ("psolve", ctypes.c_int), ("nl_relax", ctypes.c_double), ("nl_picard", ctypes.c_int),
+        ("nl_adapt", ctypes.c_double),
     ]
 
 

@@ -288,6 +288,7 @@ static StripSolveArgs base_args(dd_nls* h) {
     a.max_nl = h->P.max_nl;
     a.max_inner = h->P.max_inner;
     a.nl_relax = h->P.nl_relax;
+    a.nl_picard = h->P.nl_picard;
     a.part = h->part;
     a.bar = h->bar;
     a.status = h->status;

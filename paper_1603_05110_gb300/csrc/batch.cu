@@ -220,6 +220,7 @@ static StripSolveArgs batch_args(dd_nls_batch* b) {
     a.max_nl = b->P[0].max_nl;
     a.max_inner = b->P[0].max_inner;
     a.nl_relax = b->P[0].nl_relax;
+    a.nl_picard = b->P[0].nl_picard;
     a.part = b->part;
     a.bar = b->bar;
     a.status = b->status;

@@ -46,6 +46,7 @@ struct StripSolveArgs {
     double nl_floor_frac;    // strips stop once ||res|| <= nl_floor_frac * (*bscale)
     int max_nl, max_inner;
     double nl_relax;         // first relaxation factor of the fixed point (adaptive below it)
+    int nl_picard;           // 1: corrections with the fixed point's operator; 0: Jacobian diagonal
     double* part;            // [4][gridDim][4] partial sums
     unsigned* bar;           // [strips] barrier counters, zeroed before the launch
     int* status;             // [strips]

@@ -204,6 +204,7 @@ extern "C" int dd_nls_step_noalloc(const dd_nls_params* p, const double* V, doub
     a.max_nl = p->max_nl;
     a.max_inner = p->max_inner;
     a.nl_relax = p->nl_relax;
+    a.nl_picard = p->nl_picard;
     a.part = part;
     a.bar = bar;
     a.status = status;

@@ -196,6 +196,9 @@ strip_solve_kernel(StripSolveArgs a) {
     const Coef1Consts<T> KXt = consts_x<T>(g), KYt = consts_y<T>(g);
     const T alphaT = (T)g.alpha;
     const double kap = a.mode == 0 ? g.kap : 0.0;
+    // correction operator: the complex-linear part of the Jacobian of kappa|z|^2 z (2 kappa|z|^2),
+    // or the frozen operator of the fixed point (kappa|z|^2)
+    const double cfac = a.nl_picard ? 1.0 : 2.0;
 
     int status = 0, nl_it = 0;
     long long kry = 0;
@@ -277,7 +280,9 @@ strip_solve_kernel(StripSolveArgs a) {
                 const Coef1<double> cx = coef1<double>(ix, c, KXd), cy = coef1<double>(iy, ny, KYd);
                 const double2 zc = zeta[idx];
                 const double W = Wn ? Wn[idx] : 0.0;
-                const double cdiag = wq(ix, c, g.hx) * wq(iy, ny, g.hy) * (W + kap * (zc.x * zc.x + zc.y * zc.y));
+                const double wxy = wq(ix, c, g.hx) * wq(iy, ny, g.hy), a2 = zc.x * zc.x + zc.y * zc.y;
+                const double cdiag = wxy * (W + kap * a2);                 // the residual's operator
+                const double cop = wxy * (W + cfac * kap * a2);            // the correction's operator
                 double rre, rim;
                 rho_at(ix, rre, rim);
                 double2 Az = apply_op<double, double2>(zeta, idx, ix, iy, c, ny, P, cx, cy, g.alpha, rre, rim, cdiag);
@@ -296,9 +301,9 @@ strip_solve_kernel(StripSolveArgs a) {
                 loc[1] += b.x * b.x + b.y * b.y;
                 const Coef1<T> cxT = coef1<T>(ix, c, KXt), cyT = coef1<T>(iy, ny, KYt);
                 const T2 rT = cfrom<T2>(make_double2(res.x * inv_s, res.y * inv_s));
-                const T2 di = diag_inv<T>(cxT, cyT, alphaT, (T)rre, (T)rim, (T)cdiag);
+                const T2 di = diag_inv<T>(cxT, cyT, alphaT, (T)rre, (T)rim, (T)cop);
                 const T2 zT = cmul(di, rT);
-                cT[idx] = (T)cdiag;
+                cT[idx] = (T)cop;
                 r[idx] = rT;
                 z[idx] = zT;
                 x[idx] = mk<T2>(0.0, 0.0);
@@ -315,7 +320,9 @@ strip_solve_kernel(StripSolveArgs a) {
                 const Coef1<double> cy = coef1<double>(iy, ny, KYd);
                 const double2 ze = zeta[(long long)ixe * P + iy];
                 const double W = Wn ? Wn[(long long)ixe * P + iy] : 0.0;
-                const double cphi = wq(iy, ny, g.hy) * (W + kap * (ze.x * ze.x + ze.y * ze.y));
+                const double ae2 = ze.x * ze.x + ze.y * ze.y;
+                const double cphi = wq(iy, ny, g.hy) * (W + kap * ae2);
+                const double cphi_op = wq(iy, ny, g.hy) * (W + cfac * kap * ae2);
                 const double2 gam = gam_of(s2), sig = sig_of(s2);
                 const double2 res = make_double2(0.0, 0.0);
                 const double2 J = phi_row<double, double2>(zeta + (long long)ixe * P, phi + ((long long)e * m + s2) * P, iy, ny,
@@ -324,9 +331,9 @@ strip_solve_kernel(StripSolveArgs a) {
                 loc[0] += rs.x * rs.x + rs.y * rs.y;
                 const Coef1<T> cyT = coef1<T>(iy, ny, KYt);
                 const T2 rT = cfrom<T2>(make_double2(rs.x * inv_s, rs.y * inv_s));
-                const T2 di = phi_diag_inv<T, T2>(cyT, cfrom<T2>(gam), cfrom<T2>(sig), (T)cphi);
+                const T2 di = phi_diag_inv<T, T2>(cyT, cfrom<T2>(gam), cfrom<T2>(sig), (T)cphi_op);
                 const T2 zT = cmul(di, rT);
-                if (s2 == 0) cTf[(long long)e * P + iy] = (T)cphi;
+                if (s2 == 0) cTf[(long long)e * P + iy] = (T)cphi_op;
                 rf[fi] = rT;
                 zf[fi] = zT;
                 xf[fi] = mk<T2>(0.0, 0.0);
