@@ -68,6 +68,16 @@ def test_classical_robin_matches_oracle(precision):
         assert rel(ug, uo) < bound
 
 
+def test_picard_operator_and_jacobian_diagonal_reach_the_same_step():
+    """The strip correction operator (fixed point of eq. localpbrobin, or the Jacobian
+    diagonal) changes the path only: the converged step is the oracle's either way."""
+    ref = run_oracle(SMALL, 2)
+    for picard in (0, 1):
+        got = run_gpu(SMALL, 2, tol=TOL, nl_picard=picard)
+        for (ug, _), (uo, _) in zip(got, ref):
+            assert rel(ug, uo) < 1e-11
+
+
 def test_schwarz_iteration_counts_match_oracle_away_from_roundoff():
     """At tol 1e-8 the interface residual histories agree, so the iteration counts do."""
     ref = run_oracle(SMALL, 2, tol=1e-8)
