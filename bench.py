@@ -179,7 +179,7 @@ def run_reference(args, rank):
 
 # Schwarz iterations per step of the chosen form, measured by this benchmark on a GB300
 # (used to scale the oracle's per-strip sample to steps/s).
-ITERS_PER_STEP = {"nls_well": 4.0, "nls_small": 20.0, "gpe_trap": 5.0}
+ITERS_PER_STEP = {"nls_well": 6.0, "nls_small": 20.0, "gpe_trap": 5.0}
 
 
 # ---------------------------------------------------------------------------- our arm
