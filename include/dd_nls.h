@@ -158,6 +158,10 @@ int dd_nls_step(dd_nls* h, int nsteps, double* u_out, int ptr_kind, dd_nls_stats
 int dd_nls_solve_interface(dd_nls* h, const double* g0, double* g_out, double* v_out,
                            int ptr_kind, dd_nls_stats* stats);
 
+/* One time step like dd_nls_step(h, 1, ...) but started from the interface guess g0
+ * (instead of the `guess` policy), e.g. a learned guess from dd_cnn_guess. */
+int dd_nls_step_guess(dd_nls* h, const double* g0, double* u_out, int ptr_kind, dd_nls_stats* stats);
+
 /* Checkpoint: u (complex nodal, nullable) and g (interface vector used as the previous-
  * step guess, nullable).  set_state also sets the step counter to `step`. */
 int dd_nls_get_state(dd_nls* h, double* u, double* g, int* step, int ptr_kind);
@@ -211,6 +215,31 @@ int dd_nls_batch_set_profiling(dd_nls_batch* b, int on);
 int dd_nls_batch_get_profile(dd_nls_batch* b, dd_nls_profile* prof);
 const char* dd_nls_batch_last_error(const dd_nls_batch* b);
 void dd_nls_batch_destroy(dd_nls_batch* b);
+
+/* Learned interface guess (no counterpart in the paper, which starts each step from the
+ * previous converged vector, Sec. 5).  A 4-layer CNN (3x3 convolutions 6->32->32->32->2, ReLU,
+ * BF16 operands with FP32 accumulation on the tensor cores) maps the last three converged
+ * interface vectors of a problem with n_traces = 2(N-1) traces of nodes_per_trace = ny+1
+ * nodes to a correction of linear extrapolation:
+ *     g0 = 2 g1 - g2 + s1 * net(g1/s0, (g1-g2)/s1, (g2-g3)/s1),
+ * s0 = rms(g1), s1 = rms(g1-g2) (g1 the most recent).  Interface vectors are DEVICE pointers
+ * in the ABI layout.  Parameters: one FP32 array of dd_cnn_num_params() values, per layer the
+ * weights [Cout][Cin][3][3] then the biases [Cout]; the caller supplies the initial values.
+ * dd_cnn_train_step: one Adam step (lr, betas 0.9/0.999) on the squared error of the
+ * correction for the target vector gt; loss (nullable) receives the mean squared error.
+ * dd_cnn_loss_grad: the same loss and its gradient (host or device per ptr_kind), no update. */
+typedef struct dd_cnn dd_cnn;
+int dd_cnn_create(int n_traces, int nodes_per_trace, void* stream, dd_cnn** out);
+long long dd_cnn_num_params(const dd_cnn* c);
+int dd_cnn_set_params(dd_cnn* c, const float* w, int ptr_kind);
+int dd_cnn_get_params(dd_cnn* c, float* w, int ptr_kind);
+int dd_cnn_guess(dd_cnn* c, const double* g1, const double* g2, const double* g3, double* g0);
+int dd_cnn_train_step(dd_cnn* c, const double* g1, const double* g2, const double* g3, const double* gt,
+                      float lr, double* loss);
+int dd_cnn_loss_grad(dd_cnn* c, const double* g1, const double* g2, const double* g3, const double* gt,
+                     float* grad, double* loss, int ptr_kind);
+const char* dd_cnn_last_error(const dd_cnn* c);
+void dd_cnn_destroy(dd_cnn* c);
 
 /* Release everything the handle owns.  NULL is ignored. */
 void dd_nls_destroy(dd_nls* h);

@@ -9,5 +9,5 @@ The method runs in the CUDA library ``libddnls.so`` behind the C-ABI of
 from . import workloads  # noqa: F401
 from .binding import (BC_NEUMANN, BC_SAME, CLASSICAL, FP32_INNER, FP64, GUESS_PREVIOUS,  # noqa: F401
                       GUESS_ZERO, PRECONDITIONED, PSOLVE_GMRES, PSOLVE_MODAL, TC_PADE, TC_ROBIN,
-                      Batch, DDNLSError, Solver,
+                      CNN, Batch, DDNLSError, Solver,
                       default_params, load)

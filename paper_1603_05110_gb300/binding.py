@@ -74,7 +74,9 @@ SYMBOLS = ["dd_nls_default_params", "dd_nls_create", "dd_nls_step", "dd_nls_solv
            "dd_nls_get_profile", "dd_nls_destroy", "dd_nls_last_error", "dd_nls_step_noalloc",
            "dd_nls_batch_create", "dd_nls_batch_step", "dd_nls_batch_get_u", "dd_nls_batch_tuning",
            "dd_nls_batch_set_profiling", "dd_nls_batch_get_profile", "dd_nls_batch_last_error",
-           "dd_nls_batch_destroy"]
+           "dd_nls_batch_destroy", "dd_nls_step_guess", "dd_cnn_create", "dd_cnn_num_params",
+           "dd_cnn_set_params", "dd_cnn_get_params", "dd_cnn_guess", "dd_cnn_train_step", "dd_cnn_loss_grad",
+           "dd_cnn_last_error", "dd_cnn_destroy"]
 
 _lib = None
 
@@ -132,6 +134,26 @@ def load(path=LIB_PATH):
     lib.dd_nls_batch_last_error.restype = ctypes.c_char_p
     lib.dd_nls_batch_destroy.argtypes = [vp]
     lib.dd_nls_batch_destroy.restype = None
+    lib.dd_nls_step_guess.argtypes = [vp, vp, vp, ip, ctypes.POINTER(Stats)]
+    lib.dd_nls_step_guess.restype = ip
+    lib.dd_cnn_create.argtypes = [ip, ip, vp, ctypes.POINTER(vp)]
+    lib.dd_cnn_create.restype = ip
+    lib.dd_cnn_num_params.argtypes = [vp]
+    lib.dd_cnn_num_params.restype = ctypes.c_longlong
+    lib.dd_cnn_set_params.argtypes = [vp, vp, ip]
+    lib.dd_cnn_set_params.restype = ip
+    lib.dd_cnn_get_params.argtypes = [vp, vp, ip]
+    lib.dd_cnn_get_params.restype = ip
+    lib.dd_cnn_guess.argtypes = [vp, vp, vp, vp, vp]
+    lib.dd_cnn_guess.restype = ip
+    lib.dd_cnn_train_step.argtypes = [vp, vp, vp, vp, vp, ctypes.c_float, ctypes.POINTER(ctypes.c_double)]
+    lib.dd_cnn_train_step.restype = ip
+    lib.dd_cnn_loss_grad.argtypes = [vp, vp, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_double), ip]
+    lib.dd_cnn_loss_grad.restype = ip
+    lib.dd_cnn_last_error.argtypes = [vp]
+    lib.dd_cnn_last_error.restype = ctypes.c_char_p
+    lib.dd_cnn_destroy.argtypes = [vp]
+    lib.dd_cnn_destroy.restype = None
     _ = dp
     _lib = lib
     return lib
@@ -235,6 +257,13 @@ class Solver:
         st = Stats()
         pu, ku = _ptr(u_out, writable=True)
         self._check(self.lib.dd_nls_step(self.h, nsteps, pu, _kind(ku), ctypes.byref(st)), st)
+        return st.as_dict()
+
+    def step_guess(self, g0, u_out=None):
+        st = Stats()
+        p0, k0 = _ptr(g0)
+        pu, ku = _ptr(u_out, writable=True)
+        self._check(self.lib.dd_nls_step_guess(self.h, p0, pu, _kind(k0, ku), ctypes.byref(st)), st)
         return st.as_dict()
 
     def solve_interface(self, g0=None, g_out=None, v_out=None):
@@ -386,3 +415,78 @@ class Batch:
 
     def __exit__(self, *exc):
         self.close()
+
+
+CNN_LAYERS = ((6, 32), (32, 32), (32, 32), (32, 2))
+
+
+class CNN:
+    """A dd_cnn handle (learned interface guess).  Interface vectors are CUDA complex128
+    tensors of shape (2(N-1), ny+1)."""
+
+    def __init__(self, n_traces, nodes_per_trace, stream=None):
+        self.lib = load()
+        s = None
+        if stream is not None:
+            s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        h = ctypes.c_void_p()
+        rc = self.lib.dd_cnn_create(n_traces, nodes_per_trace, s, ctypes.byref(h))
+        if rc != 0:
+            raise DDNLSError(rc, self.lib.dd_nls_last_error(None).decode())
+        self.h = h
+        self.n = int(self.lib.dd_cnn_num_params(h))
+
+    def _check(self, rc):
+        if rc != 0:
+            raise DDNLSError(rc, self.lib.dd_cnn_last_error(self.h).decode())
+
+    @staticmethod
+    def init_params(seed=0, last_scale=0.0):
+        """He-normal weights, zero biases; the last layer scaled by last_scale (0: the network
+        starts as linear extrapolation)."""
+        rng = np.random.default_rng(seed)
+        out = []
+        for i, (ci, co) in enumerate(CNN_LAYERS):
+            w = rng.standard_normal((co, ci, 3, 3)) * np.sqrt(2.0 / (ci * 9))
+            if i == len(CNN_LAYERS) - 1:
+                w *= last_scale
+            out += [w.ravel(), np.zeros(co)]
+        return np.concatenate(out).astype(np.float32)
+
+    def set_params(self, w):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        assert w.size == self.n
+        self._check(self.lib.dd_cnn_set_params(self.h, w.ctypes.data, PTR_HOST))
+
+    def get_params(self):
+        w = np.zeros(self.n, np.float32)
+        self._check(self.lib.dd_cnn_get_params(self.h, w.ctypes.data, PTR_HOST))
+        return w
+
+    def guess(self, g1, g2, g3, out):
+        self._check(self.lib.dd_cnn_guess(self.h, g1.data_ptr(), g2.data_ptr(), g3.data_ptr(), out.data_ptr()))
+        return out
+
+    def train_step(self, g1, g2, g3, gt, lr=1e-3):
+        loss = ctypes.c_double()
+        self._check(self.lib.dd_cnn_train_step(self.h, g1.data_ptr(), g2.data_ptr(), g3.data_ptr(), gt.data_ptr(),
+                                               lr, ctypes.byref(loss)))
+        return loss.value
+
+    def loss_grad(self, g1, g2, g3, gt):
+        grad = np.zeros(self.n, np.float32)
+        loss = ctypes.c_double()
+        self._check(self.lib.dd_cnn_loss_grad(self.h, g1.data_ptr(), g2.data_ptr(), g3.data_ptr(), gt.data_ptr(),
+                                              grad.ctypes.data, ctypes.byref(loss), PTR_HOST))
+        return loss.value, grad
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dd_cnn_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

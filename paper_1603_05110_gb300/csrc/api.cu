@@ -851,6 +851,26 @@ extern "C" int dd_nls_step(dd_nls* h, int nsteps, double* u_out, int ptr_kind, d
     return DD_NLS_OK;
 }
 
+extern "C" int dd_nls_step_guess(dd_nls* h, const double* g0, double* u_out, int ptr_kind, dd_nls_stats* st) {
+    if (!h) return fail(nullptr, DD_NLS_EINVAL, "dd_nls_step_guess: NULL handle");
+    if (!g0) return fail(h, DD_NLS_EINVAL, "dd_nls_step_guess: NULL guess");
+    if (st) { std::memset(st, 0, sizeof(*st)); st->setup_ms = h->setup_ms; }
+    int rc = load_guess(h, g0, ptr_kind);
+    if (rc) return rc;
+    rc = schwarz(h, st);
+    if (rc) return rc;
+    {
+        ProfScope ps(h, &h->profile.other_ms);
+        CK(launch_commit(h->G, h->zeta, h->u, h->s));
+    }
+    h->have_prev = true;
+    h->step += 1;
+    if (st) { st->steps = 1; rc = diagnostics(h, st); if (rc) return rc; }
+    if (u_out) { rc = download_nodal(h, h->u, u_out, ptr_kind); if (rc) return rc; }
+    CK(cudaStreamSynchronize(h->s));
+    return DD_NLS_OK;
+}
+
 extern "C" int dd_nls_solve_interface(dd_nls* h, const double* g0, double* g_out, double* v_out, int ptr_kind,
                                       dd_nls_stats* st) {
     if (!h) return fail(nullptr, DD_NLS_EINVAL, "dd_nls_solve_interface: NULL handle");

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def declared_symbols():
     src = open(os.path.join(ROOT, "include", "dd_nls.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(dd_nls_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(dd_(?:nls|cnn)_[a-z_]+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")
