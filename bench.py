@@ -130,6 +130,22 @@ def source_sha1():
     return h.hexdigest()
 
 
+# ------------------------------------------------------------------- multi-rank helpers
+def max_over_ranks(value, dist=None, device=None):
+    """The largest value over all ranks (the slowest rank's time); the value itself at N = 1."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, steps, slowest_ms):
+    """Units all ranks processed (world replicas x steps) per second of the slowest rank."""
+    return world * steps / (slowest_ms * 1e-3)
+
+
 # ------------------------------------------------------------------------- oracle timing
 def oracle_strip_sample(w, args, n_strips_timed):
     """Wall time of the oracle's nonlinear strip solves of the first Schwarz iteration of step 1
@@ -237,12 +253,8 @@ def run_ours(args, rank, world, local_rank):
     ms, stats, prof = timed_steps(chosen, args.steps, profile=True)
     barrier()
     clk = clocks.stop()
-    total_ms = sum(ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms * 1e-3)
+    total_ms = max_over_ranks(sum(ms), dist, dev)
+    value = whole_job_rate(world, args.steps, total_ms)
     iters = [s["last_schwarz_iterations"] for s in stats]
     kry = sum(s["krylov_iterations"] for s in stats)
 
