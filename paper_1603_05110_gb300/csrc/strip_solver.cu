@@ -137,6 +137,11 @@ strip_solve_kernel(StripSolveArgs a) {
     const int Nall = Ns + 2 * m * nyn;       // strip nodes, then phi_{e,s} nodes
     const int nchunks = (Nall + blockDim.x - 1) / blockDim.x;
     const float inv_nyn = 1.0f / (float)nyn;
+    // residual phase work items: runs of RX x-nodes per row, then the phi nodes
+    constexpr int RX = 4;
+    const int NR = ((g.nxs + RX - 1) / RX) * nyn;
+    const int NRall = NR + 2 * m * nyn;
+    const int nchunksR = (NRall + blockDim.x - 1) / blockDim.x;
     const long long sbase = si.off;
 
     // edges of this strip
@@ -269,51 +274,97 @@ strip_solve_kernel(StripSolveArgs a) {
 
     for (;; ++nl_it) {
         // ---------------- phase R: coefficients c = w (W + kappa|zeta|^2) and FP64 residual
+        // A work item is a run of RX consecutive x-nodes at one y: the y-direction sums
+        // (My zeta, Ky zeta) of each column are formed once and used by the three nodes that
+        // need them.  ||b||^2 only in the launch's first residual (b is fixed in a launch).
         double loc[4] = {0.0, 0.0, 0.0, 0.0};   // ||res||^2, ||b||^2, rho = r^T z (re, im)
-        for (int ch = rank; ch < nchunks; ch += bps) {
+        T rz_re = 0, rz_im = 0;
+        const bool need_b = nl_it == 0;
+        for (int ch = rank; ch < nchunksR; ch += bps) {
             const int n = ch * blockDim.x + threadIdx.x;
-            if (n >= Nall) continue;
-            if (!PADE || n < Ns) {
-                int ix, iy;
-                split_node(n, nyn, inv_nyn, ix, iy);
-                const long long idx = (long long)ix * P + iy;
-                const Coef1<double> cx = coef1<double>(ix, c, KXd), cy = coef1<double>(iy, ny, KYd);
-                const double2 zc = zeta[idx];
-                const double W = Wn ? Wn[idx] : 0.0;
-                const double wxy = wq(ix, c, g.hx) * wq(iy, ny, g.hy), a2 = zc.x * zc.x + zc.y * zc.y;
-                const double cdiag = wxy * (W + kap * a2);                 // the residual's operator
-                const double cop = wxy * (W + cfac * kap * a2);            // the correction's operator
-                double rre, rim;
-                rho_at(ix, rre, rim);
-                double2 Az = apply_op<double, double2>(zeta, idx, ix, iy, c, ny, P, cx, cy, g.alpha, rre, rim, cdiag);
-                if (PADE) {
-                    const int e = tc_edge(ix);
-                    if (e >= 0)            // B_s phi_s = -i a_s d_s M^G phi_s on the edge rows
-                        for (int s2 = 0; s2 < m; ++s2) {
-                            const double2 mph = edge_mass<double, double2>(phi + ((long long)e * m + s2) * P, iy, ny, cy);
-                            Az = csub(Az, cmul(sig_of(s2), mph));
-                        }
+            if (n >= NRall) continue;
+            if (!PADE || n < NR) {
+                const int seg = n / nyn;
+                const int iy = n - seg * nyn;
+                const int x0 = seg * RX, x1 = min(x0 + RX, g.nxs);
+                const Coef1<double> cy = coef1<double>(iy, ny, KYd);
+                const Coef1<T> cyT = coef1<T>(iy, ny, KYt);
+                const double wy = wq(iy, ny, g.hy);
+                // y-direction sums of column ix at row iy
+                auto colsum = [&](int ix, double2& tM, double2& tK, double2& zc) {
+                    const double2* col = zeta + (long long)ix * P + iy;
+                    zc = col[0];
+                    const double2 am = iy > 0 ? col[-1] : make_double2(0.0, 0.0);
+                    const double2 ap = iy < ny ? col[1] : make_double2(0.0, 0.0);
+                    tM.x = cy.m[0] * am.x + cy.m[1] * zc.x + cy.m[2] * ap.x;
+                    tM.y = cy.m[0] * am.y + cy.m[1] * zc.y + cy.m[2] * ap.y;
+                    tK.x = cy.k[0] * am.x + cy.k[1] * zc.x + cy.k[2] * ap.x;
+                    tK.y = cy.k[0] * am.y + cy.k[1] * zc.y + cy.k[2] * ap.y;
+                };
+                double2 tMm = make_double2(0.0, 0.0), tKm = tMm, tM0, tK0, z0, zdum;
+                if (x0 > 0) colsum(x0 - 1, tMm, tKm, zdum);
+                colsum(x0, tM0, tK0, z0);
+                for (int ix = x0; ix < x1; ++ix) {
+                    double2 tMp = make_double2(0.0, 0.0), tKp = tMp, zp = tMp;
+                    if (ix < c) colsum(ix + 1, tMp, tKp, zp);
+                    const Coef1<double> cx = coef1<double>(ix, c, KXd);
+                    double rre, rim;
+                    rho_at(ix, rre, rim);
+                    // sum over dx of (Bx(ix, ix+dx) tM - Mx(ix, ix+dx) tK), Bx = -Kx + i alpha Mx + rho E
+                    double2 Az = make_double2(0.0, 0.0);
+                    {
+                        const double bre = -cx.k[0], bim = g.alpha * cx.m[0];
+                        Az.x += bre * tMm.x - bim * tMm.y - cx.m[0] * tKm.x;
+                        Az.y += bre * tMm.y + bim * tMm.x - cx.m[0] * tKm.y;
+                    }
+                    {
+                        const double bre = -cx.k[1] + rre, bim = g.alpha * cx.m[1] + rim;
+                        Az.x += bre * tM0.x - bim * tM0.y - cx.m[1] * tK0.x;
+                        Az.y += bre * tM0.y + bim * tM0.x - cx.m[1] * tK0.y;
+                    }
+                    {
+                        const double bre = -cx.k[2], bim = g.alpha * cx.m[2];
+                        Az.x += bre * tMp.x - bim * tMp.y - cx.m[2] * tKp.x;
+                        Az.y += bre * tMp.y + bim * tMp.x - cx.m[2] * tKp.y;
+                    }
+                    const long long idx = (long long)ix * P + iy;
+                    const double W = Wn ? Wn[idx] : 0.0;
+                    const double wxy = wq(ix, c, g.hx) * wy, a2 = z0.x * z0.x + z0.y * z0.y;
+                    const double cdiag = wxy * (W + kap * a2);                 // the residual's operator
+                    const double cop = wxy * (W + cfac * kap * a2);            // the correction's operator
+                    Az.x += cdiag * z0.x;
+                    Az.y += cdiag * z0.y;
+                    if (PADE) {
+                        const int e = tc_edge(ix);
+                        if (e >= 0)            // B_s phi_s = -i a_s d_s M^G phi_s on the edge rows
+                            for (int s2 = 0; s2 < m; ++s2) {
+                                const double2 mph = edge_mass<double, double2>(phi + ((long long)e * m + s2) * P, iy, ny, cy);
+                                Az = csub(Az, cmul(sig_of(s2), mph));
+                            }
+                    }
+                    double2 b = rhs0 ? rhs0[idx] : make_double2(0.0, 0.0);
+                    if (ix == 0 || ix == c || unit_side >= 0) b = csub(b, edge_term(ix, iy, cy));
+                    const double2 res = csub(b, Az);
+                    loc[0] += res.x * res.x + res.y * res.y;
+                    if (need_b) loc[1] += b.x * b.x + b.y * b.y;
+                    const Coef1<T> cxT = coef1<T>(ix, c, KXt);
+                    const T2 rT = cfrom<T2>(make_double2(res.x * inv_s, res.y * inv_s));
+                    const T2 di = diag_inv<T>(cxT, cyT, alphaT, (T)rre, (T)rim, (T)cop);
+                    const T2 zT = cmul(di, rT);
+                    cT[idx] = (T)cop;
+                    r[idx] = rT;
+                    z[idx] = zT;
+                    x[idx] = mk<T2>(0.0, 0.0);
+                    p[idx] = mk<T2>(0.0, 0.0);
+                    q[idx] = mk<T2>(0.0, 0.0);
+                    rz_re += rT.x * zT.x - rT.y * zT.y;
+                    rz_im += rT.x * zT.y + rT.y * zT.x;
+                    tMm = tM0; tKm = tK0;
+                    tM0 = tMp; tK0 = tKp; z0 = zp;
                 }
-                double2 b = rhs0 ? rhs0[idx] : make_double2(0.0, 0.0);
-                b = csub(b, edge_term(ix, iy, cy));
-                const double2 res = csub(b, Az);
-                loc[0] += res.x * res.x + res.y * res.y;
-                loc[1] += b.x * b.x + b.y * b.y;
-                const Coef1<T> cxT = coef1<T>(ix, c, KXt), cyT = coef1<T>(iy, ny, KYt);
-                const T2 rT = cfrom<T2>(make_double2(res.x * inv_s, res.y * inv_s));
-                const T2 di = diag_inv<T>(cxT, cyT, alphaT, (T)rre, (T)rim, (T)cop);
-                const T2 zT = cmul(di, rT);
-                cT[idx] = (T)cop;
-                r[idx] = rT;
-                z[idx] = zT;
-                x[idx] = mk<T2>(0.0, 0.0);
-                p[idx] = mk<T2>(0.0, 0.0);
-                q[idx] = mk<T2>(0.0, 0.0);
-                loc[2] += (double)(rT.x * zT.x - rT.y * zT.y);
-                loc[3] += (double)(rT.x * zT.y + rT.y * zT.x);
             } else {
                 int e, s2, iy;
-                split_phi(n, e, s2, iy);
+                split_phi(n - NR + Ns, e, s2, iy);
                 if (!(e == 0 ? ltc : rtc)) continue;
                 const int ixe = e == 0 ? 0 : c;
                 const long long fi = ((long long)e * m + s2) * P + iy;
@@ -339,10 +390,12 @@ strip_solve_kernel(StripSolveArgs a) {
                 xf[fi] = mk<T2>(0.0, 0.0);
                 pf[fi] = mk<T2>(0.0, 0.0);
                 qf[fi] = mk<T2>(0.0, 0.0);
-                loc[2] += (double)(rT.x * zT.x - rT.y * zT.y);
-                loc[3] += (double)(rT.x * zT.y + rT.y * zT.x);
+                rz_re += rT.x * zT.x - rT.y * zT.y;
+                rz_im += rT.x * zT.y + rT.y * zT.x;
             }
         }
+        loc[2] = (double)rz_re;
+        loc[3] = (double)rz_im;
         block_sum<4>(loc, s_red);
         if (threadIdx.x == 0) { double* sp = slot_ptr(epoch + 1); sp[0] = loc[0]; sp[1] = loc[1]; sp[2] = loc[2]; sp[3] = loc[3]; }
         ++epoch;
@@ -352,7 +405,7 @@ strip_solve_kernel(StripSolveArgs a) {
         group_sum<4>(group_ptr(epoch), bps, tot, s_red);
         lap(4);
         const double rnorm = sqrt(tot[0]);
-        bnorm = sqrt(tot[1]);
+        if (need_b) bnorm = sqrt(tot[1]);
         nres = bnorm > 0.0 ? rnorm / bnorm : rnorm;
         if (!isfinite(tot[0]) || !isfinite(tot[1])) { status = DD_NLS_ENONFINITE; break; }
         if (nres <= nl_tol || rnorm <= floor_abs || rnorm == 0.0) break;
