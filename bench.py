@@ -33,7 +33,7 @@ METRIC = "time steps/s and stencil GB/s at 1e-8 interface residual, chosen vs pl
 
 # DRAM traffic of one strip-solver launch from the committed ncu summary
 # (profiles/strip_solve_nls_well.md), valid only for the source it was taken from.
-NCU_TRAFFIC = {"source_sha1": "1294ebc0c69b9b3b181fc78b8d936b9a30a38b45", "bytes_per_launch": 45.690112e6 + 10.700032e6}
+NCU_TRAFFIC = {"source_sha1": "376ecda55eefe6996a79e850f05694b74d5c0ac4", "bytes_per_launch": 52.061440e6 + 37.389312e6}
 
 
 def parse():

@@ -50,6 +50,7 @@ struct dd_nls {
     double2 *u = nullptr, *zeta = nullptr, *rhs0 = nullptr, *gA = nullptr, *gB = nullptr, *gconv = nullptr;
     double* Wn = nullptr;
     void *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *cT = nullptr;
+    void *w1 = nullptr, *s0 = nullptr, *s1 = nullptr, *dv = nullptr;
     double* part = nullptr;
     unsigned* bar = nullptr;
     int* status = nullptr;
@@ -130,6 +131,7 @@ template <typename T> static cudaError_t dalloc(T** ptr, size_t n) {
 
 static void release(dd_nls* h) {
     void* ptrs[] = {h->u, h->zeta, h->rhs0, h->gA, h->gB, h->gconv, h->Wn, h->x, h->r, h->z, h->p, h->q, h->cT,
+                    h->w1, h->s0, h->s1, h->dv,
                     h->part, h->bar, h->status, h->nl_its, h->kry, h->nl_res, h->err, h->red, h->stage,
                     h->X64, h->X32, h->btype, h->V, h->w, h->tmp, h->hdev, h->xs, h->scratch,
                     h->Cf, h->Ci, h->Cf32, h->Ci32, h->xm, h->fac, h->tkind,
@@ -234,11 +236,16 @@ static int strip_solve(dd_nls* h, StripSolveArgs& a, int nstrips, int nblocks, d
     double bytes = 0.0, flops = 0.0;
     const double nodes = (double)h->G.nxs * h->G.nyn;
     const double s2 = h->fp32 ? 8.0 : 16.0, s1 = h->fp32 ? 4.0 : 8.0;
-    const double bR = 40 + s1 + 5 * s2, bA = 5 * s2 + s1, bB = 7 * s2 + s1, bE = 32 + s2;
+    // per node: residual phase (+ D^-1 and s_-1 for the single-reduction loop), one Krylov
+    // iteration (two passes, or the fused pass of the single-reduction loop), its w_0 = A z_0
+    // pass, the epilogue
+    const bool sr = h->fp32 && h->pade_m == 0;
+    const double bR = 40 + s1 + (sr ? 7 : 5) * s2, bK = sr ? 11 * s2 + s1 : 12 * s2 + 2 * s1;
+    const double bW = sr ? 4 * s2 + s1 : 0.0, bE = 32 + s2;
     for (int j = 0; j < nstrips; ++j) {
         nl += h->h_nl[j];
         kr += h->h_kry[j];
-        bytes += nodes * ((h->h_nl[j] + 1) * bR + h->h_kry[j] * (bA + bB) + h->h_nl[j] * bE);
+        bytes += nodes * ((h->h_nl[j] + 1) * bR + h->h_kry[j] * bK + h->h_nl[j] * (bW + bE));
         flops += nodes * ((h->h_nl[j] + 1) * 110.0 + h->h_kry[j] * 150.0);
     }
     if (h->prof) {
@@ -280,6 +287,7 @@ static StripSolveArgs base_args(dd_nls* h) {
     a.rhs0 = h->rhs0;
     a.Wn = h->Wn;
     a.x = h->x; a.r = h->r; a.z = h->z; a.p = h->p; a.q = h->q; a.cT = h->cT;
+    a.w1 = h->w1; a.s0 = h->s0; a.s1 = h->s1; a.dv = h->dv;
     a.nl_tol = h->P.nl_tol;
     a.inner_tol = h->P.inner_tol;
     a.inner_floor = 0.1 * h->P.nl_tol;
@@ -376,11 +384,12 @@ static int build_Lh(dd_nls* h) {
     // virtual-strip buffers
     const int maxb = strip_solve_max_blocks(h->fp32);
     const long long per_strip = (long long)G.nxs * G.P;
-    const double bytes_per_strip = (double)per_strip * (16 + 5 * (h->fp32 ? 8 : 16) + (h->fp32 ? 4 : 8));
+    const double bytes_per_strip = (double)per_strip * (16 + 9 * (h->fp32 ? 8 : 16) + (h->fp32 ? 4 : 8));
     int chunk = std::max(1, std::min(maxb, (int)std::min(2.0 * nyn, 6e9 / bytes_per_strip)));
     StripSolveArgs a = base_args(h);
     double2* vz = nullptr;
     void *vx = nullptr, *vr = nullptr, *vzz = nullptr, *vp = nullptr, *vq = nullptr, *vc = nullptr;
+    void *vw1 = nullptr, *vs0 = nullptr, *vs1 = nullptr, *vdv = nullptr;
     unsigned* vbar = nullptr;
     int *vstat = nullptr, *vnl = nullptr;
     long long* vkry = nullptr;
@@ -388,7 +397,7 @@ static int build_Lh(dd_nls* h) {
     const size_t s2 = h->fp32 ? sizeof(float2) : sizeof(double2), s1 = h->fp32 ? sizeof(float) : sizeof(double);
     int rc = DD_NLS_OK;
     auto cleanup = [&]() {
-        void* ptrs[] = {vz, vx, vr, vzz, vp, vq, vc, vbar, vstat, vnl, vkry, vres, vpart};
+        void* ptrs[] = {vz, vx, vr, vzz, vp, vq, vc, vw1, vs0, vs1, vdv, vbar, vstat, vnl, vkry, vres, vpart};
         for (void* p : ptrs)
             if (p) cudaFree(p);
     };
@@ -400,6 +409,10 @@ static int build_Lh(dd_nls* h) {
     e = e ? e : cudaMalloc(&vp, chunk * per_strip * s2);
     e = e ? e : cudaMalloc(&vq, chunk * per_strip * s2);
     e = e ? e : cudaMalloc(&vc, chunk * per_strip * s1);
+    e = e ? e : cudaMalloc(&vw1, chunk * per_strip * s2);
+    e = e ? e : cudaMalloc(&vs0, chunk * per_strip * s2);
+    e = e ? e : cudaMalloc(&vs1, chunk * per_strip * s2);
+    e = e ? e : cudaMalloc(&vdv, chunk * per_strip * s2);
     e = e ? e : cudaMalloc(&vbar, chunk * sizeof(unsigned));
     e = e ? e : cudaMalloc(&vstat, chunk * sizeof(int));
     e = e ? e : cudaMalloc(&vnl, chunk * sizeof(int));
@@ -427,6 +440,7 @@ static int build_Lh(dd_nls* h) {
             a.unit_rtc = types[t].second;
             a.zeta = vz; a.rhs0 = nullptr; a.Wn = nullptr; a.gtr = nullptr; a.bscale = nullptr;
             a.x = vx; a.r = vr; a.z = vzz; a.p = vp; a.q = vq; a.cT = vc;
+            a.w1 = vw1; a.s0 = vs0; a.s1 = vs1; a.dv = vdv;
             a.bar = vbar; a.status = vstat; a.nl_its = vnl; a.kry_its = vkry; a.nl_res = vres; a.part = vpart;
             e = cudaMemsetAsync(vz, 0, nv * per_strip * sizeof(double2), h->s);
             if (!e) e = cudaMemsetAsync(vbar, 0, nv * sizeof(unsigned), h->s);
@@ -749,6 +763,10 @@ extern "C" int dd_nls_create(const dd_nls_params* p, const double* V, const doub
     CKC(dalloc((char**)&h->p, h->nfield * s2));
     CKC(dalloc((char**)&h->q, h->nfield * s2));
     CKC(dalloc((char**)&h->cT, h->nfield * s1));
+    CKC(dalloc((char**)&h->w1, h->nfield * s2));
+    CKC(dalloc((char**)&h->s0, h->nfield * s2));
+    CKC(dalloc((char**)&h->s1, h->nfield * s2));
+    CKC(dalloc((char**)&h->dv, h->nfield * s2));
     CKC(dalloc(&h->stage, (size_t)(p->nx + 1) * nyn));
     CKC(dalloc(&h->bar, G.N));
     CKC(dalloc(&h->status, G.N));

@@ -96,6 +96,7 @@ struct dd_nls_batch {
     double2 *u = nullptr, *zeta = nullptr, *rhs0 = nullptr, *gbuf = nullptr;
     double* Wn = nullptr;
     void *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *cT = nullptr;
+    void *w1 = nullptr, *s0 = nullptr, *s1 = nullptr, *dv = nullptr;
     double *part = nullptr, *bscale = nullptr, *bnorm0 = nullptr, *res = nullptr, *nl_res = nullptr;
     double* d_tol = nullptr;        // per-strip nonlinear tolerance of the next launch
     double* h_tol = nullptr;        // pinned mirror
@@ -145,7 +146,8 @@ template <typename T> static cudaError_t zalloc(T** ptr, size_t n) {
 
 static void batch_release(dd_nls_batch* b) {
     void* dev[] = {b->d_geoms, b->d_sinfo, b->d_foff, b->d_goff, b->d_cur, b->d_active, b->u, b->zeta, b->rhs0,
-                   b->gbuf, b->Wn, b->x, b->r, b->z, b->p, b->q, b->cT, b->part, b->bscale, b->bnorm0, b->res,
+                   b->gbuf, b->Wn, b->x, b->r, b->z, b->p, b->q, b->cT, b->w1, b->s0, b->s1, b->dv, b->part,
+                   b->bscale, b->bnorm0, b->res,
                    b->nl_res, b->bar, b->status, b->nl_its, b->err, b->d_blk, b->kry, b->d_tol};
     for (void* p : dev)
         if (p) cudaFree(p);
@@ -211,6 +213,7 @@ static StripSolveArgs batch_args(dd_nls_batch* b) {
     a.Wn = b->Wn;
     a.gtr = b->gbuf;
     a.x = b->x; a.r = b->r; a.z = b->z; a.p = b->p; a.q = b->q; a.cT = b->cT;
+    a.w1 = b->w1; a.s0 = b->s0; a.s1 = b->s1; a.dv = b->dv;
     a.nl_tol = b->P[0].nl_tol;
     a.nl_tol_strip = b->d_tol;
     a.inner_tol = b->P[0].inner_tol;
@@ -384,6 +387,10 @@ extern "C" int dd_nls_batch_create(int n, const dd_nls_params* params, const dou
     BCKC(zalloc((char**)&b->p, b->nfield * s2));
     BCKC(zalloc((char**)&b->q, b->nfield * s2));
     BCKC(zalloc((char**)&b->cT, b->nfield * s1));
+    BCKC(zalloc((char**)&b->w1, b->nfield * s2));
+    BCKC(zalloc((char**)&b->s0, b->nfield * s2));
+    BCKC(zalloc((char**)&b->s1, b->nfield * s2));
+    BCKC(zalloc((char**)&b->dv, b->nfield * s2));
     BCKC(zalloc(&b->gbuf, 2 * b->nI));
     BCKC(zalloc(&b->part, (size_t)16 * maxb + 2048));
     BCKC(zalloc(&b->bscale, n));

@@ -39,6 +39,7 @@ struct StripSolveArgs {
     const double* Wn;        // V/lap per strip node, or NULL (zero)
     const double2* gtr;      // interface traces [2(N-1)][P]
     void *x, *r, *z, *p, *q; // inner Krylov vectors (float2 or double2)
+    void *w1, *s0, *s1, *dv; // single-reduction COCG (Robin): second w buffer, s ping-pong, D^-1
     void* cT;                // c = w (W + kappa|zeta|^2) in inner precision
     double nl_tol, inner_tol, inner_floor;
     const double* nl_tol_strip;   // batched: per-strip nonlinear tolerance (device), or NULL

@@ -139,6 +139,10 @@ extern "C" int dd_nls_step_noalloc(const dd_nls_params* p, const double* V, doub
     void* kp = cv.take<unsigned char>(nfield * s2);
     void* kq = cv.take<unsigned char>(nfield * s2);
     void* kc = cv.take<unsigned char>(nfield * s1);
+    void* kw1 = cv.take<unsigned char>(nfield * s2);
+    void* ks0 = cv.take<unsigned char>(nfield * s2);
+    void* ks1 = cv.take<unsigned char>(nfield * s2);
+    void* kdv = cv.take<unsigned char>(nfield * s2);
     double2* gA = cv.take<double2>(nI);
     double2* gB = cv.take<double2>(nI);
     double* part = cv.take<double>((size_t)16 * std::max(maxb, 512));
@@ -196,6 +200,7 @@ extern "C" int dd_nls_step_noalloc(const dd_nls_params* p, const double* V, doub
     a.rhs0 = rhs0;
     a.Wn = Wn;
     a.x = kx; a.r = kr; a.z = kz; a.p = kp; a.q = kq; a.cT = kc;
+    a.w1 = kw1; a.s0 = ks0; a.s1 = ks1; a.dv = kdv;
     a.nl_tol = p->nl_tol;
     a.inner_tol = p->inner_tol;
     a.inner_floor = 0.1 * p->nl_tol;

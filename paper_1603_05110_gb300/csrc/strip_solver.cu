@@ -67,6 +67,46 @@ __device__ __forceinline__ T2 apply_op(const T2* v, long long idx, int ix, int i
     return acc;
 }
 
+// z_{k+1} = D^{-1}(r_k - alpha (w_k + beta s_{k-1})) at node k (single-reduction COCG)
+template <typename T2>
+__device__ __forceinline__ T2 znext(const T2* rr, const T2* ww, const T2* ss, const T2* dvv, long long k, T2 al, T2 be) {
+    const T2 sv = cfma(be, ss[k], ww[k]);
+    T2 t = rr[k];
+    t.x -= al.x * sv.x - al.y * sv.y;
+    t.y -= al.x * sv.y + al.y * sv.x;
+    return cmul(dvv[k], t);
+}
+// w = A(c) z with z formed on the fly at the 9 stencil nodes (same arithmetic as apply_op)
+template <typename T, typename T2>
+__device__ __forceinline__ T2 apply_op_znext(const T2* rr, const T2* ww, const T2* ss, const T2* dvv, long long idx,
+                                             int ix, int iy, int c, int ny, int P, const Coef1<T>& cx,
+                                             const Coef1<T>& cy, T alpha, T rho_re, T rho_im, T cdiag, T2 al, T2 be,
+                                             T2& zown) {
+    T2 acc = mk<T2>(0.0, 0.0);
+#pragma unroll
+    for (int dx = -1; dx <= 1; ++dx) {
+        if (ix + dx < 0 || ix + dx > c) continue;
+        const long long k0 = idx + (long long)dx * P;
+        const T2 a0 = znext(rr, ww, ss, dvv, k0, al, be);
+        if (dx == 0) zown = a0;
+        const T2 am = iy > 0 ? znext(rr, ww, ss, dvv, k0 - 1, al, be) : mk<T2>(0.0, 0.0);
+        const T2 ap = iy < ny ? znext(rr, ww, ss, dvv, k0 + 1, al, be) : mk<T2>(0.0, 0.0);
+        T2 tM, tK;
+        tM.x = cy.m[0] * am.x + cy.m[1] * a0.x + cy.m[2] * ap.x;
+        tM.y = cy.m[0] * am.y + cy.m[1] * a0.y + cy.m[2] * ap.y;
+        tK.x = cy.k[0] * am.x + cy.k[1] * a0.x + cy.k[2] * ap.x;
+        tK.y = cy.k[0] * am.y + cy.k[1] * a0.y + cy.k[2] * ap.y;
+        const T mx = cx.m[dx + 1];
+        const T bre = -cx.k[dx + 1] + (dx == 0 ? rho_re : (T)0);
+        const T bim = alpha * mx + (dx == 0 ? rho_im : (T)0);
+        acc.x += bre * tM.x - bim * tM.y - mx * tK.x;
+        acc.y += bre * tM.y + bim * tM.x - mx * tK.y;
+    }
+    acc.x += cdiag * zown.x;
+    acc.y += cdiag * zown.y;
+    return acc;
+}
+
 template <typename T>
 __device__ __forceinline__ typename C2<T>::t diag_inv(const Coef1<T>& cx, const Coef1<T>& cy, T alpha, T rho_re,
                                                       T rho_im, T cdiag) {
@@ -172,6 +212,14 @@ strip_solve_kernel(StripSolveArgs a) {
     T2* p = (T2*)a.p + sbase;
     T2* q = (T2*)a.q + sbase;
     T* cT = (T*)a.cT + sbase;
+    // single-reduction COCG (Robin, FP32 inner solve): r and w ping-pong (r|z, q|w1), s
+    // ping-pong, D^-1.  In FP64 the 9-point rebuild of z costs more FP64-pipe time than the
+    // second barrier saves, so the FP64 instance keeps the two-reduction loop.
+    constexpr bool SR = !PADE && sizeof(T) == 4;
+    T2* rbuf[2] = {r, z};
+    T2* wbuf[2] = {q, SR ? (T2*)a.w1 + sbase : nullptr};
+    T2* sbuf[2] = {SR ? (T2*)a.s0 + sbase : nullptr, SR ? (T2*)a.s1 + sbase : nullptr};
+    T2* dv = SR ? (T2*)a.dv + sbase : nullptr;
     // auxiliary unknowns: phi_{e,s}(iy) at ((j*2 + e)*m + s)*P + iy
     const long long fbase = (long long)j * 2 * m * P;
     double2* phi = PADE ? a.phi + fbase : nullptr;
@@ -357,6 +405,10 @@ strip_solve_kernel(StripSolveArgs a) {
                     x[idx] = mk<T2>(0.0, 0.0);
                     p[idx] = mk<T2>(0.0, 0.0);
                     q[idx] = mk<T2>(0.0, 0.0);
+                    if (SR) {
+                        dv[idx] = di;
+                        sbuf[1][idx] = mk<T2>(0.0, 0.0);      // s_{-1}
+                    }
                     rz_re += rT.x * zT.x - rT.y * zT.y;
                     rz_im += rT.x * zT.y + rT.y * zT.x;
                     tMm = tM0; tKm = tK0;
@@ -418,6 +470,131 @@ strip_solve_kernel(StripSolveArgs a) {
         double beta_re = 0.0, beta_im = 0.0;
         // inner stopping test in the scaled units of r
         const double target = fmax(a.inner_tol * rnorm, fmax(inner_floor * bnorm, 0.1 * floor_abs)) * inv_s;
+        if constexpr (SR) {
+            // Single-reduction COCG (the Chronopoulos-Gear arrangement of CG with the unconjugated
+            // bilinear form): s = A p is carried, w = A z is formed in the same pass as the updates
+            // with z_{k+1} rebuilt at the stencil neighbours, so one reduction (gamma = r^T z,
+            // delta = w^T z, ||r||^2) and one barrier per iteration.
+            // w_0 = A z_0, delta_0 = w_0^T z_0
+            T d0r = 0, d0i = 0;
+            const T2 zeroT = mk<T2>(0.0, 0.0);
+            for (int ch = rank; ch < nchunks; ch += bps) {
+                const int n = ch * blockDim.x + threadIdx.x;
+                if (n >= Ns) continue;
+                int ix, iy;
+                split_node(n, nyn, inv_nyn, ix, iy);
+                const long long idx = (long long)ix * P + iy;
+                const Coef1<T> cxT = coef1<T>(ix, c, KXt), cyT = coef1<T>(iy, ny, KYt);
+                T rre, rim;
+                rho_atT(ix, rre, rim);
+                T2 zo;
+                const T2 w0 = apply_op_znext<T, T2>(rbuf[0], sbuf[1], sbuf[1], dv, idx, ix, iy, c, ny, P, cxT, cyT, alphaT, rre,
+                                                    rim, cT[idx], zeroT, zeroT, zo);
+                wbuf[0][idx] = w0;
+                d0r += w0.x * zo.x - w0.y * zo.y;
+                d0i += w0.x * zo.y + w0.y * zo.x;
+            }
+            {
+                T lT[2] = {d0r, d0i};
+                double l2[2];
+                block_sum_t<T, 2>(lT, l2, s_red);
+                if (threadIdx.x == 0) { double* sp = slot_ptr(epoch + 1); sp[0] = l2[0]; sp[1] = l2[1]; sp[2] = 0; sp[3] = 0; }
+            }
+            ++epoch;
+            lap(1);
+            if (!group_barrier(bar, epoch * bps, a.err, &s_flag)) { status = DD_NLS_ETIMEOUT; break; }
+            double dl[4];
+            group_sum<4>(group_ptr(epoch), bps, dl, s_red);
+            lap(4);
+            double gam_r = rho_r, gam_i = rho_i, del_r = dl[0], del_i = dl[1];
+            double dd2 = del_r * del_r + del_i * del_i;
+            if (!(dd2 > 0.0) || !isfinite(dd2)) { status = isfinite(dd2) ? DD_NLS_EBREAKDOWN : DD_NLS_ENONFINITE; break; }
+            double al_r = (gam_r * del_r + gam_i * del_i) / dd2, al_i = (gam_i * del_r - gam_r * del_i) / dd2;
+            double be_r = 0.0, be_i = 0.0;
+            for (int it = 0; it < a.max_inner; ++it) {
+                const int cur = it & 1, nxt = cur ^ 1;
+                const T2* rc = rbuf[cur];
+                const T2* wc = wbuf[cur];
+                const T2* sp = sbuf[nxt];          // s_{k-1}
+                T2* so = sbuf[cur];                // s_k
+                T2* rn_b = rbuf[nxt];
+                T2* wn_b = wbuf[nxt];
+                const T2 alT = mk<T2>(al_r, al_i), beT = mk<T2>(be_r, be_i);
+                T g_r = 0, g_i = 0, dlt_r = 0, dlt_i = 0, rr2 = 0;
+                for (int ch = rank; ch < nchunks; ch += bps) {
+                    const int n = ch * blockDim.x + threadIdx.x;
+                    if (n >= Ns) continue;
+                    int ix, iy;
+                    split_node(n, nyn, inv_nyn, ix, iy);
+                    const long long idx = (long long)ix * P + iy;
+                    const Coef1<T> cxT = coef1<T>(ix, c, KXt), cyT = coef1<T>(iy, ny, KYt);
+                    const T2 zc = cmul(dv[idx], rc[idx]);
+                    const T2 pn = cfma(beT, p[idx], zc);           // p_k = z_k + beta p_{k-1}
+                    const T2 sn = cfma(beT, sp[idx], wc[idx]);     // s_k = w_k + beta s_{k-1}
+                    x[idx] = cfma(alT, pn, x[idx]);
+                    p[idx] = pn;
+                    so[idx] = sn;
+                    T2 rnew = rc[idx];
+                    rnew.x -= alT.x * sn.x - alT.y * sn.y;
+                    rnew.y -= alT.x * sn.y + alT.y * sn.x;
+                    rn_b[idx] = rnew;
+                    T rre, rim;
+                    rho_atT(ix, rre, rim);
+                    T2 zo;
+                    const T2 wn = apply_op_znext<T, T2>(rc, wc, sp, dv, idx, ix, iy, c, ny, P, cxT, cyT, alphaT, rre, rim,
+                                                        cT[idx], alT, beT, zo);
+                    wn_b[idx] = wn;
+                    g_r += rnew.x * zo.x - rnew.y * zo.y;
+                    g_i += rnew.x * zo.y + rnew.y * zo.x;
+                    dlt_r += wn.x * zo.x - wn.y * zo.y;
+                    dlt_i += wn.x * zo.y + wn.y * zo.x;
+                    rr2 += rnew.x * rnew.x + rnew.y * rnew.y;
+                }
+                T lT[4] = {g_r, g_i, dlt_r, dlt_i};
+                double l4[4];
+                block_sum_t<T, 4>(lT, l4, s_red);
+                T lr[1] = {rr2};
+                double l1[1];
+                block_sum_t<T, 1>(lr, l1, s_red);
+                if (threadIdx.x == 0) {
+                    double* spp = slot_ptr(epoch + 1);
+                    spp[0] = l4[0]; spp[1] = l4[1]; spp[2] = l4[2]; spp[3] = l4[3];
+                    // ||r||^2 travels in the other half of the slot ring (slot epoch+3, unused now)
+                    slot_ptr(epoch + 3)[0] = l1[0];
+                }
+                ++epoch;
+                lap(2);
+                if (!group_barrier(bar, epoch * bps, a.err, &s_flag)) { status = DD_NLS_ETIMEOUT; break; }
+                double gg[4];
+                group_sum<4>(group_ptr(epoch), bps, gg, s_red);
+                double rq[1];
+                group_sum<1>(group_ptr(epoch + 2), bps, rq, s_red);
+                lap(4);
+                ++kry;
+                if (!isfinite(rq[0]) || !isfinite(gg[0]) || !isfinite(gg[2])) { status = DD_NLS_ENONFINITE; break; }
+                if (sqrt(rq[0]) <= target) {
+                    // x was advanced in this pass; the solution is complete
+                    break;
+                }
+                // beta_{k+1} = gamma_{k+1}/gamma_k;  alpha_{k+1} = gamma_{k+1}/(delta_{k+1} - beta_{k+1} gamma_{k+1}/alpha_k)
+                const double gk2 = gam_r * gam_r + gam_i * gam_i;
+                if (!(gk2 > 0.0)) { status = DD_NLS_EBREAKDOWN; break; }
+                const double nb_r = (gg[0] * gam_r + gg[1] * gam_i) / gk2, nb_i = (gg[1] * gam_r - gg[0] * gam_i) / gk2;
+                const double a2 = al_r * al_r + al_i * al_i;
+                // t = beta * gamma / alpha
+                const double bg_r = nb_r * gg[0] - nb_i * gg[1], bg_i = nb_r * gg[1] + nb_i * gg[0];
+                const double t_r = (bg_r * al_r + bg_i * al_i) / a2, t_i = (bg_i * al_r - bg_r * al_i) / a2;
+                const double den_r = gg[2] - t_r, den_i = gg[3] - t_i;
+                const double den2 = den_r * den_r + den_i * den_i;
+                if (!(den2 > 0.0) || !isfinite(den2)) { status = isfinite(den2) ? DD_NLS_EBREAKDOWN : DD_NLS_ENONFINITE; break; }
+                al_r = (gg[0] * den_r + gg[1] * den_i) / den2;
+                al_i = (gg[1] * den_r - gg[0] * den_i) / den2;
+                be_r = nb_r;
+                be_i = nb_i;
+                gam_r = gg[0];
+                gam_i = gg[1];
+            }
+        } else
         for (int it = 0; it < a.max_inner; ++it) {
             // phase A: q = A z + beta q, p = z + beta p, partial mu = p^T q
             // (per-thread partials in T: the FP64 pipe is ~1/64 of FP32 on this part)
