@@ -57,7 +57,11 @@ typedef enum {
 enum { DD_NLS_TC_ROBIN = 0, DD_NLS_TC_PADE = 1 };          /* eq. TCSRobin / eq. TCS */
 enum { DD_NLS_BC_SAME = 0, DD_NLS_BC_NEUMANN = 1 };        /* physical x-edges */
 enum { DD_NLS_CLASSICAL = 0, DD_NLS_PRECONDITIONED = 1 };  /* eq. algo_d / eq. algo_pd */
-enum { DD_NLS_FP64 = 0, DD_NLS_FP32_INNER = 1 };           /* inner Krylov precision */
+/* Arithmetic of the strip solves: FP64 throughout; FP32 inner Krylov with the FP64 nonlinear
+ * residual; or FP32 inner Krylov with the residual in double-word arithmetic (pairs of FP32
+ * numbers, about 48 significant bits, on the FP32 pipe; Robin transmission only -- with
+ * S_pade it behaves as DD_NLS_FP32_INNER).  The strip state zeta stays FP64 in every mode. */
+enum { DD_NLS_FP64 = 0, DD_NLS_FP32_INNER = 1, DD_NLS_FP32_DW = 2 };
 enum { DD_NLS_GUESS_ZERO = 0, DD_NLS_GUESS_PREVIOUS = 1 }; /* g_n^0 (Sec. 5) */
 enum { DD_NLS_PTR_HOST = 0, DD_NLS_PTR_DEVICE = 1 };
 /* How P x = y of eq. (algo_pd) is solved: GMRES on the assembled L_h blocks (Sec. 4.2), or
@@ -78,7 +82,8 @@ typedef struct {
     double pade_theta;
     int bc;           /* DD_NLS_BC_SAME: S-bar with zero data on x = xl, xr; or Neumann */
     int algorithm;    /* DD_NLS_CLASSICAL or DD_NLS_PRECONDITIONED */
-    int precision;    /* DD_NLS_FP64, or DD_NLS_FP32_INNER: FP32 Krylov + FP64 residual */
+    int precision;    /* DD_NLS_FP64, DD_NLS_FP32_INNER (FP32 Krylov + FP64 residual) or
+                         DD_NLS_FP32_DW (FP32 Krylov + double-word residual) */
     int guess;        /* interface guess for each step when dd_nls_step is called */
     /* stopping tests */
     double tol;          /* ||R(g)-g|| <= tol*||R(g)|| (or <= tol if tol_absolute) */

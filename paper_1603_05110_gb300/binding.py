@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "libddnls.so")
 TC_ROBIN, TC_PADE = 0, 1
 BC_SAME, BC_NEUMANN = 0, 1
 CLASSICAL, PRECONDITIONED = 0, 1
-FP64, FP32_INNER = 0, 1
+FP64, FP32_INNER, FP32_DW = 0, 1, 2
 GUESS_ZERO, GUESS_PREVIOUS = 0, 1
 PTR_HOST, PTR_DEVICE = 0, 1
 PSOLVE_GMRES, PSOLVE_MODAL = 0, 1

@@ -51,6 +51,9 @@ struct dd_nls {
     double* Wn = nullptr;
     void *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *cT = nullptr;
     void *w1 = nullptr, *s0 = nullptr, *s1 = nullptr, *dv = nullptr;
+    bool dw = false;        // double-word residual (FP32 inner, Robin)
+    float4 *zdw = nullptr, *ddw = nullptr, *bdw = nullptr;
+    float2* wdw = nullptr;
     double* part = nullptr;
     unsigned* bar = nullptr;
     int* status = nullptr;
@@ -131,7 +134,7 @@ template <typename T> static cudaError_t dalloc(T** ptr, size_t n) {
 
 static void release(dd_nls* h) {
     void* ptrs[] = {h->u, h->zeta, h->rhs0, h->gA, h->gB, h->gconv, h->Wn, h->x, h->r, h->z, h->p, h->q, h->cT,
-                    h->w1, h->s0, h->s1, h->dv,
+                    h->w1, h->s0, h->s1, h->dv, h->zdw, h->ddw, h->bdw, h->wdw,
                     h->part, h->bar, h->status, h->nl_its, h->kry, h->nl_res, h->err, h->red, h->stage,
                     h->X64, h->X32, h->btype, h->V, h->w, h->tmp, h->hdev, h->xs, h->scratch,
                     h->Cf, h->Ci, h->Cf32, h->Ci32, h->xm, h->fac, h->tkind,
@@ -241,11 +244,15 @@ static int strip_solve(dd_nls* h, StripSolveArgs& a, int nstrips, int nblocks, d
     // pass, the epilogue
     const bool sr = h->fp32 && h->pade_m == 0;
     const double bR = 40 + s1 + (sr ? 7 : 5) * s2, bK = sr ? 11 * s2 + s1 : 12 * s2 + 2 * s1;
-    const double bW = sr ? 4 * s2 + s1 : 0.0, bE = 32 + s2;
+    // double-word residual: the epilogue updates zeta and the accumulated correction in
+    // double-word form; once per launch a set-up pass (zeta, rhs0, W in; four double-word
+    // fields out) and the FP64 write-back (correction and zeta in, zeta out)
+    const bool dw = h->dw && h->pade_m == 0;
+    const double bW = sr ? 4 * s2 + s1 : 0.0, bE = dw ? 64 + s2 : 32 + s2, bL = dw ? 96 + 48 : 0.0;
     for (int j = 0; j < nstrips; ++j) {
         nl += h->h_nl[j];
         kr += h->h_kry[j];
-        bytes += nodes * ((h->h_nl[j] + 1) * bR + h->h_kry[j] * bK + h->h_nl[j] * (bW + bE));
+        bytes += nodes * (bL + (h->h_nl[j] + 1) * bR + h->h_kry[j] * bK + h->h_nl[j] * (bW + bE));
         flops += nodes * ((h->h_nl[j] + 1) * 110.0 + h->h_kry[j] * 150.0);
     }
     if (h->prof) {
@@ -288,6 +295,7 @@ static StripSolveArgs base_args(dd_nls* h) {
     a.Wn = h->Wn;
     a.x = h->x; a.r = h->r; a.z = h->z; a.p = h->p; a.q = h->q; a.cT = h->cT;
     a.w1 = h->w1; a.s0 = h->s0; a.s1 = h->s1; a.dv = h->dv;
+    a.zdw = h->zdw; a.ddw = h->ddw; a.bdw = h->bdw; a.wdw = h->wdw;
     a.nl_tol = h->P.nl_tol;
     a.inner_tol = h->P.inner_tol;
     a.inner_floor = 0.1 * h->P.nl_tol;
@@ -441,6 +449,7 @@ static int build_Lh(dd_nls* h) {
             a.zeta = vz; a.rhs0 = nullptr; a.Wn = nullptr; a.gtr = nullptr; a.bscale = nullptr;
             a.x = vx; a.r = vr; a.z = vzz; a.p = vp; a.q = vq; a.cT = vc;
             a.w1 = vw1; a.s0 = vs0; a.s1 = vs1; a.dv = vdv;
+            a.zdw = a.ddw = a.bdw = nullptr; a.wdw = nullptr;     // unit-datum solves: FP64 residual
             a.bar = vbar; a.status = vstat; a.nl_its = vnl; a.kry_its = vkry; a.nl_res = vres; a.part = vpart;
             e = cudaMemsetAsync(vz, 0, nv * per_strip * sizeof(double2), h->s);
             if (!e) e = cudaMemsetAsync(vbar, 0, nv * sizeof(unsigned), h->s);
@@ -709,7 +718,7 @@ extern "C" int dd_nls_create(const dd_nls_params* p, const double* V, const doub
         return fail(nullptr, DD_NLS_EINVAL, "dd_nls_create: Pade order m must be in 1..96");
     if (p->tc == DD_NLS_TC_PADE && p->algorithm == DD_NLS_PRECONDITIONED && p->psolve == DD_NLS_PSOLVE_GMRES)
         return fail(nullptr, DD_NLS_EINVAL, "dd_nls_create: S_pade with the preconditioned algorithm uses the modal P solve");
-    if (p->precision != DD_NLS_FP64 && p->precision != DD_NLS_FP32_INNER)
+    if (p->precision != DD_NLS_FP64 && p->precision != DD_NLS_FP32_INNER && p->precision != DD_NLS_FP32_DW)
         return fail(nullptr, DD_NLS_EINVAL, "dd_nls_create: unknown precision");
     if (ptr_kind != DD_NLS_PTR_HOST && ptr_kind != DD_NLS_PTR_DEVICE)
         return fail(nullptr, DD_NLS_EINVAL, "dd_nls_create: unknown ptr_kind");
@@ -723,7 +732,8 @@ extern "C" int dd_nls_create(const dd_nls_params* p, const double* V, const doub
     if (h->P.max_schwarz < 1) h->P.max_schwarz = 1;
     if (h->P.gmres_restart < 1) h->P.gmres_restart = 30;
     h->s = (cudaStream_t)stream;
-    h->fp32 = p->precision == DD_NLS_FP32_INNER;
+    h->fp32 = p->precision != DD_NLS_FP64;
+    h->dw = p->precision == DD_NLS_FP32_DW && p->tc != DD_NLS_TC_PADE;
     Geom& G = h->G;
     G.N = p->n_strips;
     G.nxs = (int)c + 1;
@@ -767,6 +777,12 @@ extern "C" int dd_nls_create(const dd_nls_params* p, const double* V, const doub
     CKC(dalloc((char**)&h->s0, h->nfield * s2));
     CKC(dalloc((char**)&h->s1, h->nfield * s2));
     CKC(dalloc((char**)&h->dv, h->nfield * s2));
+    if (h->dw) {
+        CKC(dalloc(&h->zdw, h->nfield));
+        CKC(dalloc(&h->ddw, h->nfield));
+        CKC(dalloc(&h->bdw, h->nfield));
+        CKC(dalloc(&h->wdw, h->nfield));
+    }
     CKC(dalloc(&h->stage, (size_t)(p->nx + 1) * nyn));
     CKC(dalloc(&h->bar, G.N));
     CKC(dalloc(&h->status, G.N));

@@ -40,6 +40,10 @@ struct StripSolveArgs {
     const double2* gtr;      // interface traces [2(N-1)][P]
     void *x, *r, *z, *p, *q; // inner Krylov vectors (float2 or double2)
     void *w1, *s0, *s1, *dv; // single-reduction COCG (Robin): second w buffer, s ping-pong, D^-1
+    // double-word residual (FP32 Robin, mode 0), all NULL otherwise: zeta and its accumulated
+    // correction (float4 {re.h, re.l, im.h, im.l} per node), the right side b, w W (float2)
+    float4 *zdw, *ddw, *bdw;
+    float2* wdw;
     void* cT;                // c = w (W + kappa|zeta|^2) in inner precision
     double nl_tol, inner_tol, inner_floor;
     const double* nl_tol_strip;   // batched: per-strip nonlinear tolerance (device), or NULL

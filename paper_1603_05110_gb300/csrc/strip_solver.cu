@@ -24,6 +24,7 @@
 // derives the same scalars from the same fixed-order reductions, so all blocks of a strip
 // take the same branches.
 #include "common.cuh"
+#include "dw.cuh"
 #include "kernels.h"
 
 #include <algorithm>
@@ -156,7 +157,7 @@ __device__ __forceinline__ T2 phi_diag_inv(const Coef1<T>& cy, T2 gam, T2 sig, T
     return cinv(cmul(sig, d));
 }
 
-template <typename T, bool PADE, int BS>
+template <typename T, bool PADE, int BS, bool DW = false>
 __global__ void __launch_bounds__(BS, 512 / BS)
 strip_solve_kernel(StripSolveArgs a) {
     using T2 = typename C2<T>::t;
@@ -215,11 +216,24 @@ strip_solve_kernel(StripSolveArgs a) {
     // single-reduction COCG (Robin, FP32 inner solve): r and w ping-pong (r|z, q|w1), s
     // ping-pong, D^-1.  In FP64 the 9-point rebuild of z costs more FP64-pipe time than the
     // second barrier saves, so the FP64 instance keeps the two-reduction loop.
+    // Below a few hundred unknowns COCG exhausts the Krylov space before FP32 reaches the
+    // target, and the single-reduction recurrence for alpha (delta - beta gamma/alpha) then
+    // loses accuracy (FP32 model runs: a few failures in 10^4 random right sides on 4-node
+    // strips, none on 12..544-node strips); such strips take the two-reduction loop.
     constexpr bool SR = !PADE && sizeof(T) == 4;
+    constexpr int kSRMinNodes = 256;
     T2* rbuf[2] = {r, z};
     T2* wbuf[2] = {q, SR ? (T2*)a.w1 + sbase : nullptr};
     T2* sbuf[2] = {SR ? (T2*)a.s0 + sbase : nullptr, SR ? (T2*)a.s1 + sbase : nullptr};
     T2* dv = SR ? (T2*)a.dv + sbase : nullptr;
+    // double-word residual: the nonlinear residual on the FP32 pipe in ~48-bit arithmetic
+    // instead of FP64 (GB300's FP64 rate is ~1/64 of FP32); zeta itself stays FP64 and
+    // receives the accumulated correction once, at the end of the launch
+    static_assert(!DW || SR, "the double-word residual is built for the FP32 Robin solver");
+    float4* zdw = DW ? a.zdw + sbase : nullptr;
+    float4* ddw = DW ? a.ddw + sbase : nullptr;
+    float4* bdw = DW ? a.bdw + sbase : nullptr;
+    const float2* wdw = DW ? a.wdw + sbase : nullptr;
     // auxiliary unknowns: phi_{e,s}(iy) at ((j*2 + e)*m + s)*P + iy
     const long long fbase = (long long)j * 2 * m * P;
     double2* phi = PADE ? a.phi + fbase : nullptr;
@@ -307,31 +321,156 @@ strip_solve_kernel(StripSolveArgs a) {
     auto gam_of = [&](int s2) { return make_double2(a.pade_d[s2].x, g.alpha + a.pade_d[s2].y); };   // i alpha + d_s
     auto sig_of = [&](int s2) { return cmul(make_double2(0.0, 1.0), cmul(a.pade_a[s2], a.pade_d[s2])); };  // i a_s d_s
 
-    // scale of the first correction: the strip's ||(2i/dt) M h|| (FP32 must not see ~1e-111)
+    // scale of the first correction: the strip's ||(2i/dt) M h|| (FP32 must not see ~1e-111),
+    // but at least 1e-6 of the whole problem's: a far-field strip (h ~ 1e-32) whose residual
+    // is set by interface data far above its own h would otherwise overflow FP32
     double bnorm = 0.0;
-    double inv_s = (a.bnorm0 && a.bnorm0[j] > 0.0) ? 1.0 / a.bnorm0[j] : 1.0;
+    const double bscale_inst = a.bscale ? ((volatile const double*)a.bscale)[si.inst] : 0.0;
+    const double s_first = fmax(a.bnorm0 ? a.bnorm0[j] : 0.0, 1e-6 * bscale_inst);
+    double inv_s = s_first > 0.0 ? 1.0 / s_first : 1.0;
     const double nl_tol = a.nl_tol_strip ? a.nl_tol_strip[j] : a.nl_tol;
     const double nl_floor_frac = a.nl_tol_strip ? a.nl_floor_frac * nl_tol / a.nl_tol : a.nl_floor_frac;
     const double inner_floor = a.nl_tol_strip ? 0.1 * nl_tol : a.inner_floor;
-    const double floor_abs = a.bscale ? nl_floor_frac * ((volatile const double*)a.bscale)[si.inst] : 0.0;
+    const double floor_abs = nl_floor_frac * bscale_inst;
     // relaxation of the fixed point: zeta += omega delta, i.e. zeta^q = omega F(zeta^{q-1}) +
     // (1 - omega) zeta^{q-1} (same limit); omega shrinks when a correction does not cut the
     // residual by 10% (the plain iteration diverges for strong nonlinearity)
     double omega = (a.nl_relax > 0.0 && a.nl_relax <= 1.0) ? a.nl_relax : 1.0;
     double rprev = 0.0;
 
-    for (;; ++nl_it) {
+    // Double-word residual constants.  On the uniform mesh the 1D factors are exact multiples
+    // of [1 d 1] (mass, d = 4 inside, 2 at an end) and [-1 e -1] (stiffness, e = 2 / 1), so
+    //   A zeta = -C1 U + i C2 V - C3 Wk + i C5 Tm0 [transmission edge] + c zeta,
+    // with Tm = [1 dy 1] zeta and Tk = [-1 ey -1] zeta along y, U = [-1 ex -1] Tm,
+    // V = [1 dx 1] Tm, Wk = [1 dx 1] Tk along x (exact weights: powers of two), and
+    // C1 = hy/(6hx), C2 = alpha hx hy/36, C3 = hx/(6hy), C5 = p hy/6, c = w W + w kappa|zeta|^2.
+    dw nC1{}, nC2{}, C2{}, nC3{}, nC5{}, C5{}, C6{};
+    float C6f = 0.f;
+    if constexpr (DW) {
+        nC1 = dw_from(-g.hy / (6.0 * g.hx));
+        C2 = dw_from(g.alpha * g.hx * g.hy / 36.0);
+        nC2 = dw_neg(C2);
+        nC3 = dw_from(-g.hx / (6.0 * g.hy));
+        C5 = dw_from(rho_im * g.hy / 6.0);
+        nC5 = dw_neg(C5);
+        C6 = dw_from(g.hx * g.hy * kap);
+        C6f = C6.h;
+        // zeta, b = (2i/dt) M h - M^Gamma Q^T (l; r) and w W in double-word form, ||b||^2
+        double lb[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int ch = rank; ch < nchunks; ch += bps) {
+            const int n = ch * blockDim.x + threadIdx.x;
+            if (n >= Ns) continue;
+            int ix, iy;
+            split_node(n, nyn, inv_nyn, ix, iy);
+            const long long idx = (long long)ix * P + iy;
+            const Coef1<double> cy = coef1<double>(iy, ny, KYd);
+            double2 b = rhs0 ? rhs0[idx] : make_double2(0.0, 0.0);
+            if (ix == 0 || ix == c || unit_side >= 0) b = csub(b, edge_term(ix, iy, cy));
+            lb[0] += b.x * b.x + b.y * b.y;
+            const double2 zv = zeta[idx];
+            const double W = Wn ? Wn[idx] : 0.0;
+            cdw_st(zdw + idx, {dw_from(zv.x), dw_from(zv.y)});
+            cdw_st(ddw + idx, cdw_zero());
+            cdw_st(bdw + idx, {dw_from(b.x), dw_from(b.y)});
+            const dw wv = dw_from(wq(ix, c, g.hx) * wq(iy, ny, g.hy) * W);
+            a.wdw[sbase + idx] = make_float2(wv.h, wv.l);
+        }
+        block_sum<4>(lb, s_red);
+        if (threadIdx.x == 0) { double* sp = slot_ptr(epoch + 1); sp[0] = lb[0]; sp[1] = 0; sp[2] = 0; sp[3] = 0; }
+        ++epoch;
+        if (!group_barrier(bar, epoch * bps, a.err, &s_flag)) status = DD_NLS_ETIMEOUT;
+        if (!status) {
+            double tb[4];
+            group_sum<4>(group_ptr(epoch), bps, tb, s_red);
+            bnorm = sqrt(tb[0]);
+        }
+        lap(0);
+    }
+    // The double-word residual resolves about 1e-14 of ||b||: below kDWFinish the strip folds
+    // its accumulated correction into the FP64 zeta and finishes with the FP64 residual.
+    constexpr double kDWFinish = 1e-12;
+    bool dwr = DW;
+
+    for (; !status; ++nl_it) {
         // ---------------- phase R: coefficients c = w (W + kappa|zeta|^2) and FP64 residual
         // A work item is a run of RX consecutive x-nodes at one y: the y-direction sums
         // (My zeta, Ky zeta) of each column are formed once and used by the three nodes that
         // need them.  ||b||^2 only in the launch's first residual (b is fixed in a launch).
         double loc[4] = {0.0, 0.0, 0.0, 0.0};   // ||res||^2, ||b||^2, rho = r^T z (re, im)
         T rz_re = 0, rz_im = 0;
-        const bool need_b = nl_it == 0;
+        float rr_f = 0.f;                        // double-word residual: ||res||^2 partial
+        const bool need_b = !DW && nl_it == 0;
+        const float inv_sf = DW ? (float)fmin(inv_s, 1e30) : 0.f;
         for (int ch = rank; ch < nchunksR; ch += bps) {
             const int n = ch * blockDim.x + threadIdx.x;
             if (n >= NRall) continue;
-            if (!PADE || n < NR) {
+            if (DW && dwr) {
+                const int seg = n / nyn;
+                const int iy = n - seg * nyn;
+                const int x0 = seg * RX, x1 = min(x0 + RX, g.nxs);
+                const bool ylo = iy > 0, yhi = iy < ny;
+                const float dY = (ylo && yhi) ? 4.f : 2.f, eY = (ylo && yhi) ? 2.f : 1.f;
+                const float qy = (ylo && yhi) ? 1.f : 0.5f;
+                const Coef1<T> cyT = coef1<T>(iy, ny, KYt);
+                // exact-weight y sums of column ix at row iy
+                auto colsum = [&](int ix, cdw& Tm, cdw& Tk, cdw& zc) {
+                    const float4* col = zdw + (long long)ix * P + iy;
+                    zc = cdw_ld(col);
+                    const cdw S = (ylo && yhi) ? cdw_add(cdw_ld(col - 1), cdw_ld(col + 1)) : cdw_ld(ylo ? col - 1 : col + 1);
+                    Tm = cdw_add(S, cdw_pow2(zc, dY));
+                    Tk = cdw_sub(cdw_pow2(zc, eY), S);
+                };
+                cdw Tmm = cdw_zero(), Tkm = cdw_zero(), Tm0, Tk0, z0, zdum;
+                if (x0 > 0) colsum(x0 - 1, Tmm, Tkm, zdum);
+                colsum(x0, Tm0, Tk0, z0);
+                for (int ix = x0; ix < x1; ++ix) {
+                    cdw Tmp = cdw_zero(), Tkp = cdw_zero(), zp = cdw_zero();
+                    if (ix < c) colsum(ix + 1, Tmp, Tkp, zp);
+                    const bool xlo = ix > 0, xhi = ix < c;
+                    const float dX = (xlo && xhi) ? 4.f : 2.f, eX = (xlo && xhi) ? 2.f : 1.f;
+                    const float qxy = ((xlo && xhi) ? 1.f : 0.5f) * qy;
+                    const cdw Q = (xlo && xhi) ? cdw_add(Tmm, Tmp) : (xlo ? Tmm : Tmp);
+                    const cdw Kq = (xlo && xhi) ? cdw_add(Tkm, Tkp) : (xlo ? Tkm : Tkp);
+                    const cdw U = cdw_sub(cdw_pow2(Tm0, eX), Q);
+                    const cdw V = cdw_add(Q, cdw_pow2(Tm0, dX));
+                    const cdw Wk = cdw_add(Kq, cdw_pow2(Tk0, dX));
+                    dw ax = dw_add(dw_add(dw_mul(nC1, U.x), dw_mul(nC2, V.y)), dw_mul(nC3, Wk.x));
+                    dw ay = dw_add(dw_add(dw_mul(nC1, U.y), dw_mul(C2, V.x)), dw_mul(nC3, Wk.y));
+                    if ((ix == 0 && ltc) || (ix == c && rtc)) {
+                        ax = dw_add(ax, dw_mul(nC5, Tm0.y));
+                        ay = dw_add(ay, dw_mul(C5, Tm0.x));
+                    }
+                    const long long idx = (long long)ix * P + iy;
+                    const dw a2 = dw_add(dw_mul(z0.x, z0.x), dw_mul(z0.y, z0.y));
+                    const float2 wv2 = wdw[idx];
+                    const dw cd = dw_add(dw{wv2.x, wv2.y}, dw_mul(dw_pow2(C6, qxy), a2));
+                    ax = dw_add(ax, dw_mul(cd, z0.x));
+                    ay = dw_add(ay, dw_mul(cd, z0.y));
+                    const cdw bv = cdw_ld(bdw + idx);
+                    const dw rx = dw_sub(bv.x, ax), ry = dw_sub(bv.y, ay);
+                    // the correction's operator in the inner precision
+                    const T cop = wv2.x + (T)cfac * (C6f * qxy) * a2.h;
+                    T rre, rim;
+                    rho_atT(ix, rre, rim);
+                    const Coef1<T> cxT = coef1<T>(ix, c, KXt);
+                    const T2 rT = mk<T2>(rx.h * inv_sf, ry.h * inv_sf);
+                    rr_f += rT.x * rT.x + rT.y * rT.y;    // scaled: no underflow of tiny residuals
+                    const T2 di = diag_inv<T>(cxT, cyT, alphaT, rre, rim, cop);
+                    const T2 zT = cmul(di, rT);
+                    cT[idx] = cop;
+                    r[idx] = rT;
+                    z[idx] = zT;
+                    x[idx] = mk<T2>(0.0, 0.0);
+                    p[idx] = mk<T2>(0.0, 0.0);
+                    q[idx] = mk<T2>(0.0, 0.0);
+                    dv[idx] = di;
+                    sbuf[1][idx] = mk<T2>(0.0, 0.0);      // s_{-1}
+                    rz_re += rT.x * zT.x - rT.y * zT.y;
+                    rz_im += rT.x * zT.y + rT.y * zT.x;
+                    Tmm = Tm0; Tkm = Tk0;
+                    Tm0 = Tmp; Tk0 = Tkp; z0 = zp;
+                }
+            } else if (!PADE || n < NR) {
                 const int seg = n / nyn;
                 const int iy = n - seg * nyn;
                 const int x0 = seg * RX, x1 = min(x0 + RX, g.nxs);
@@ -448,6 +587,7 @@ strip_solve_kernel(StripSolveArgs a) {
         }
         loc[2] = (double)rz_re;
         loc[3] = (double)rz_im;
+        if (DW && dwr) loc[0] = (double)rr_f / ((double)inv_sf * (double)inv_sf);
         block_sum<4>(loc, s_red);
         if (threadIdx.x == 0) { double* sp = slot_ptr(epoch + 1); sp[0] = loc[0]; sp[1] = loc[1]; sp[2] = loc[2]; sp[3] = loc[3]; }
         ++epoch;
@@ -462,6 +602,24 @@ strip_solve_kernel(StripSolveArgs a) {
         if (!isfinite(tot[0]) || !isfinite(tot[1])) { status = DD_NLS_ENONFINITE; break; }
         if (nres <= nl_tol || rnorm <= floor_abs || rnorm == 0.0) break;
         if (nl_it >= a.max_nl) { status = DD_NLS_ENOCONV; break; }
+        if (DW && dwr && nres <= kDWFinish) {
+            for (int ch = rank; ch < nchunks; ch += bps) {
+                const int n = ch * blockDim.x + threadIdx.x;
+                if (n >= Ns) continue;
+                int ix, iy;
+                split_node(n, nyn, inv_nyn, ix, iy);
+                const long long idx = (long long)ix * P + iy;
+                const cdw d = cdw_ld(ddw + idx);
+                const double2 zv = zeta[idx];
+                zeta[idx] = make_double2(zv.x + dw_to(d.x), zv.y + dw_to(d.y));
+            }
+            dwr = false;
+            inv_s = 1.0 / rnorm;
+            rprev = INFINITY;
+            ++epoch;
+            if (!group_barrier(bar, epoch * bps, a.err, &s_flag)) { status = DD_NLS_ETIMEOUT; break; }
+            continue;       // the next residual is the FP64 one
+        }
         if (nl_it > 0 && rnorm > 0.9 * rprev) omega = fmax(0.25, 0.6 * omega);
         rprev = rnorm;
 
@@ -470,7 +628,7 @@ strip_solve_kernel(StripSolveArgs a) {
         double beta_re = 0.0, beta_im = 0.0;
         // inner stopping test in the scaled units of r
         const double target = fmax(a.inner_tol * rnorm, fmax(inner_floor * bnorm, 0.1 * floor_abs)) * inv_s;
-        if constexpr (SR) {
+        if (SR && Ns >= kSRMinNodes) {
             // Single-reduction COCG (the Chronopoulos-Gear arrangement of CG with the unconjugated
             // bilinear form): s = A p is carried, w = A z is formed in the same pass as the updates
             // with z_{k+1} rebuilt at the stencil neighbours, so one reduction (gamma = r^T z,
@@ -511,6 +669,8 @@ strip_solve_kernel(StripSolveArgs a) {
             if (!(dd2 > 0.0) || !isfinite(dd2)) { status = isfinite(dd2) ? DD_NLS_EBREAKDOWN : DD_NLS_ENONFINITE; break; }
             double al_r = (gam_r * del_r + gam_i * del_i) / dd2, al_i = (gam_i * del_r - gam_r * del_i) / dd2;
             double be_r = 0.0, be_i = 0.0;
+            double best = INFINITY;     // stagnation guard: least ||r|| so far, iterations since
+            int since = 0;
             for (int it = 0; it < a.max_inner; ++it) {
                 const int cur = it & 1, nxt = cur ^ 1;
                 const T2* rc = rbuf[cur];
@@ -572,13 +732,20 @@ strip_solve_kernel(StripSolveArgs a) {
                 lap(4);
                 ++kry;
                 if (!isfinite(rq[0]) || !isfinite(gg[0]) || !isfinite(gg[2])) { status = DD_NLS_ENONFINITE; break; }
-                if (sqrt(rq[0]) <= target) {
-                    // x was advanced in this pass; the solution is complete
+                const double rk = sqrt(rq[0]);
+                if (rk <= target) break;     // x was advanced in this pass; the solution is complete
+                // A breakdown of the recurrences after the first step, or 32 steps without a 1%
+                // gain, ends the inner solve with the x reached: the nonlinear loop recomputes the
+                // exact residual and starts a new Krylov solve from it.
+                if (rk < 0.99 * best) {
+                    best = rk;
+                    since = 0;
+                } else if (++since >= 32) {
                     break;
                 }
                 // beta_{k+1} = gamma_{k+1}/gamma_k;  alpha_{k+1} = gamma_{k+1}/(delta_{k+1} - beta_{k+1} gamma_{k+1}/alpha_k)
                 const double gk2 = gam_r * gam_r + gam_i * gam_i;
-                if (!(gk2 > 0.0)) { status = DD_NLS_EBREAKDOWN; break; }
+                if (!(gk2 > 0.0)) break;
                 const double nb_r = (gg[0] * gam_r + gg[1] * gam_i) / gk2, nb_i = (gg[1] * gam_r - gg[0] * gam_i) / gk2;
                 const double a2 = al_r * al_r + al_i * al_i;
                 // t = beta * gamma / alpha
@@ -586,7 +753,8 @@ strip_solve_kernel(StripSolveArgs a) {
                 const double t_r = (bg_r * al_r + bg_i * al_i) / a2, t_i = (bg_i * al_r - bg_r * al_i) / a2;
                 const double den_r = gg[2] - t_r, den_i = gg[3] - t_i;
                 const double den2 = den_r * den_r + den_i * den_i;
-                if (!(den2 > 0.0) || !isfinite(den2)) { status = isfinite(den2) ? DD_NLS_EBREAKDOWN : DD_NLS_ENONFINITE; break; }
+                if (!isfinite(den2)) { status = DD_NLS_ENONFINITE; break; }
+                if (!(den2 > 0.0)) break;
                 al_r = (gg[0] * den_r + gg[1] * den_i) / den2;
                 al_i = (gg[1] * den_r - gg[0] * den_i) / den2;
                 be_r = nb_r;
@@ -719,6 +887,21 @@ strip_solve_kernel(StripSolveArgs a) {
         if (status) break;
         // ---------------- zeta += delta (FP64), then every block must see the new zeta
         const double sc = omega / inv_s;
+        if (DW && dwr) {
+            // double-word zeta and the correction accumulated over the launch
+            const dw scd = dw_from(sc);
+            for (int ch = rank; ch < nchunks; ch += bps) {
+                const int n = ch * blockDim.x + threadIdx.x;
+                if (n >= Ns) continue;
+                int ix, iy;
+                split_node(n, nyn, inv_nyn, ix, iy);
+                const long long idx = (long long)ix * P + iy;
+                const T2 dx = x[idx];
+                const cdw cc = {dw_mul_f(scd, dx.x), dw_mul_f(scd, dx.y)};
+                cdw_st(zdw + idx, cdw_add(cdw_ld(zdw + idx), cc));
+                cdw_st(ddw + idx, cdw_add(cdw_ld(ddw + idx), cc));
+            }
+        } else
         for (int ch = rank; ch < nchunks; ch += bps) {
             const int n = ch * blockDim.x + threadIdx.x;
             if (n >= Nall) continue;
@@ -743,6 +926,19 @@ strip_solve_kernel(StripSolveArgs a) {
         if (!group_barrier(bar, epoch * bps, a.err, &s_flag)) { status = DD_NLS_ETIMEOUT; break; }
         lap(4);
     }
+    if (DW && dwr) {
+        // zeta (FP64) += the launch's accumulated correction, own nodes only
+        for (int ch = rank; ch < nchunks; ch += bps) {
+            const int n = ch * blockDim.x + threadIdx.x;
+            if (n >= Ns) continue;
+            int ix, iy;
+            split_node(n, nyn, inv_nyn, ix, iy);
+            const long long idx = (long long)ix * P + iy;
+            const cdw d = cdw_ld(ddw + idx);
+            const double2 zv = zeta[idx];
+            zeta[idx] = make_double2(zv.x + dw_to(d.x), zv.y + dw_to(d.y));
+        }
+    }
     if (a.pcyc && threadIdx.x == 0)
         for (int k = 0; k < 5; ++k) a.pcyc[(size_t)blockIdx.x * 8 + k] = cyc[k];
     if (rank == 0 && threadIdx.x == 0) {
@@ -761,6 +957,8 @@ static cudaError_t launch_strip_solve_t(const StripSolveArgs& args, int nblocks,
     count_launches(1);
     if (a.pade_m > 0)
         return cudaLaunchCooperativeKernel((const void*)strip_solve_kernel<T, true, 256>, grid, dim3(256), params, 0, s);
+    if (sizeof(T) == 4 && a.zdw && a.mode == 0)
+        return cudaLaunchCooperativeKernel((const void*)strip_solve_kernel<float, false, 256, true>, grid, dim3(256), params, 0, s);
     if (bs == 128)
         return cudaLaunchCooperativeKernel((const void*)strip_solve_kernel<T, false, 128>, grid, block, params, 0, s);
     return cudaLaunchCooperativeKernel((const void*)strip_solve_kernel<T, false, 256>, grid, dim3(256), params, 0, s);
