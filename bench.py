@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=4)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--residual", default="fp64", choices=["fp64", "dw"],
+    ap.add_argument("--residual", default="dw", choices=["fp64", "dw"],
                     help="nonlinear residual of the chosen form: FP64, or double-word on the FP32 pipe")
     ap.add_argument("--instances", type=int, default=64)
     ap.add_argument("--max-schwarz", type=int, default=5000)
@@ -352,7 +352,7 @@ def run_ours(args, rank, world, local_rank):
         "krylov_iterations_per_step": kry / args.steps,
         "nl_iterations_per_step": sum(s["nl_iterations"] for s in stats) / args.steps,
         "gmres_iterations_per_step": sum(s["gmres_iterations"] for s in stats) / args.steps,
-        "strip_solve_phase_share": dict(zip(["fp64_residual", "krylov_stencil", "krylov_update", "commit", "waits"],
+        "strip_solve_phase_share": dict(zip(["residual", "krylov_pass1", "krylov_pass2", "epilogue", "waits"],
                                             [c / max(1.0, sum(prof["phase_cycles"])) for c in prof["phase_cycles"]])),
         "time_split_ms_per_step": {"strip_solve": prof["strip_solve_ms"] / args.steps,
                                    "interface": prof["interface_ms"] / args.steps,

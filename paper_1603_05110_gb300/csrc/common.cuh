@@ -204,6 +204,24 @@ __device__ __forceinline__ bool group_barrier(unsigned* ctr, unsigned target, in
 }
 
 // Sum slot values written by the nblk blocks of a group (fixed order); result broadcast.
+// The same sums (same order, same result) formed by warp 0 alone, every lane of which gets
+// them; the caller derives its scalars on one thread and broadcasts what the block needs.
+template <int NV> __device__ __forceinline__ void group_sum_w0(const double* part, int nblk, double (&out)[NV]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) out[k] = 0.0;
+    for (int b0 = 0; b0 < nblk; b0 += 32) {
+        const int b = b0 + lane;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double s = b < nblk ? __ldcg(part + (size_t)b * 4 + k) : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            out[k] += s;
+        }
+    }
+}
+
 template <int NV> __device__ __forceinline__ void group_sum(const double* part, int nblk, double (&out)[NV], double* smem) {
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;

@@ -38,7 +38,17 @@ __device__ __forceinline__ dw dw_add(dw x, dw y) {
     const dw v = fast_two_sum(s.h, __fadd_rn(s.l, t.h));
     return fast_two_sum(v.h, __fadd_rn(t.l, v.l));
 }
+// SloppyDWPlusDW (Algorithm 5 of the same paper): 11 operations instead of 20.  Its relative
+// error is unbounded when x ~ -y, but its absolute error stays within a few u^2 (|x| + |y|)
+// (2Sum is exact; the low words enter with one rounding each), which is the accuracy a
+// residual b - A zeta needs: every term is known to u^2 of its own size, not of the result.
+__device__ __forceinline__ dw dw_add_s(dw x, dw y) {
+    const dw s = two_sum(x.h, y.h);
+    const float w = __fadd_rn(s.l, __fadd_rn(x.l, y.l));
+    return fast_two_sum(s.h, w);
+}
 __device__ __forceinline__ dw dw_neg(dw x) { return {-x.h, -x.l}; }
+__device__ __forceinline__ dw dw_sub_s(dw x, dw y) { return dw_add_s(x, {-y.h, -y.l}); }
 __device__ __forceinline__ dw dw_sub(dw x, dw y) { return dw_add(x, dw_neg(y)); }
 __device__ __forceinline__ dw dw_mul_f(dw x, float y) {
     const float ch = __fmul_rn(x.h, y);
@@ -60,9 +70,29 @@ __device__ __forceinline__ dw dw_from(double v) {
     return {h, __double2float_rn(v - (double)h)};
 }
 __device__ __forceinline__ double dw_to(dw x) { return (double)x.h + (double)x.l; }
+// The same split with integer operations only (GB300 issues FP64 instructions, conversions
+// included, at ~1/64 of the FP32 rate): hi = the leading 24 significant bits of v, truncated;
+// lo = the next 29 bits, rounded to 24 and scaled by 2^(e-1075) in two exact power-of-two
+// steps; then normalized by Fast2Sum.  Exact to 2^-47 relative for 2^-126 <= |v| < 2^128;
+// zero, the FP32-subnormal range and non-finite values take dw_from.
+__device__ __forceinline__ dw dw_from_bits(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned e = (unsigned)(b >> 52) & 0x7ffu;
+    if (e < 897u || e > 1150u) return dw_from(v);
+    const unsigned sgn = (unsigned)(b >> 63) << 31;
+    const unsigned long long m = b & 0xfffffffffffffull;
+    const float h = __uint_as_float(sgn | ((e - 896u) << 23) | (unsigned)(m >> 29));
+    const unsigned k = e >= 949u ? 0u : 64u;
+    const float p1 = __uint_as_float((e + k - 948u) << 23);   // 2^(e - 1075 + k)
+    const float p2 = __uint_as_float((127u - k) << 23);       // 2^-k
+    const float l = __fmul_rn(__fmul_rn(__uint2float_rn((unsigned)(m & 0x1fffffffu)), p1), p2);
+    return fast_two_sum(h, __uint_as_float(__float_as_uint(l) | sgn));
+}
 
 __device__ __forceinline__ cdw cdw_add(const cdw& a, const cdw& b) { return {dw_add(a.x, b.x), dw_add(a.y, b.y)}; }
 __device__ __forceinline__ cdw cdw_sub(const cdw& a, const cdw& b) { return {dw_sub(a.x, b.x), dw_sub(a.y, b.y)}; }
+__device__ __forceinline__ cdw cdw_add_s(const cdw& a, const cdw& b) { return {dw_add_s(a.x, b.x), dw_add_s(a.y, b.y)}; }
+__device__ __forceinline__ cdw cdw_sub_s(const cdw& a, const cdw& b) { return {dw_sub_s(a.x, b.x), dw_sub_s(a.y, b.y)}; }
 __device__ __forceinline__ cdw cdw_pow2(const cdw& a, float p2) { return {dw_pow2(a.x, p2), dw_pow2(a.y, p2)}; }
 __device__ __forceinline__ cdw cdw_zero() { return {{0.f, 0.f}, {0.f, 0.f}}; }
 // storage: one float4 per complex node value {re.h, re.l, im.h, im.l}

@@ -163,6 +163,12 @@ strip_solve_kernel(StripSolveArgs a) {
     using T2 = typename C2<T>::t;
     __shared__ double s_red[64];
     __shared__ int s_flag;
+    // Krylov scalars: the FP64 recurrences run on thread 0 only (FP64 issues at ~1/64 of the
+    // FP32 rate here; eight warps repeating them cost more than the vector work) and reach the
+    // block through shared memory: s_ctl = {0 go on | 1 stop, x accepted | 2 error, status},
+    // s_sc = alpha, beta in the inner precision
+    __shared__ int s_ctl[2];
+    __shared__ T s_sc[4];
 
     const int j = a.blk_strip[blockIdx.x];   // strip of the launch (virtual strip in setup mode)
     const int b0 = a.blk_start[j];
@@ -346,6 +352,7 @@ strip_solve_kernel(StripSolveArgs a) {
     // C1 = hy/(6hx), C2 = alpha hx hy/36, C3 = hx/(6hy), C5 = p hy/6, c = w W + w kappa|zeta|^2.
     dw nC1{}, nC2{}, C2{}, nC3{}, nC5{}, C5{}, C6{};
     float C6f = 0.f;
+    const float cfacf = (float)cfac;
     if constexpr (DW) {
         nC1 = dw_from(-g.hy / (6.0 * g.hx));
         C2 = dw_from(g.alpha * g.hx * g.hy / 36.0);
@@ -355,26 +362,39 @@ strip_solve_kernel(StripSolveArgs a) {
         nC5 = dw_neg(C5);
         C6 = dw_from(g.hx * g.hy * kap);
         C6f = C6.h;
-        // zeta, b = (2i/dt) M h - M^Gamma Q^T (l; r) and w W in double-word form, ||b||^2
-        double lb[4] = {0.0, 0.0, 0.0, 0.0};
+        // zeta, b = (2i/dt) M h - M^Gamma Q^T (l; r) and w W in double-word form, ||b||^2.
+        // Integer splits away from the edge columns (no FP64 instruction there); ||b||^2 in
+        // FP32 in units of the first correction's scale.
+        const dw HXHY = dw_from(g.hx * g.hy);
+        const float bsc = (float)(1.0 / (s_first > 0.0 ? s_first : 1.0));
+        float bb = 0.f;
         for (int ch = rank; ch < nchunks; ch += bps) {
             const int n = ch * blockDim.x + threadIdx.x;
             if (n >= Ns) continue;
             int ix, iy;
             split_node(n, nyn, inv_nyn, ix, iy);
             const long long idx = (long long)ix * P + iy;
-            const Coef1<double> cy = coef1<double>(iy, ny, KYd);
-            double2 b = rhs0 ? rhs0[idx] : make_double2(0.0, 0.0);
-            if (ix == 0 || ix == c || unit_side >= 0) b = csub(b, edge_term(ix, iy, cy));
-            lb[0] += b.x * b.x + b.y * b.y;
+            cdw bv;
+            if (ix == 0 || ix == c || unit_side >= 0) {
+                const Coef1<double> cy = coef1<double>(iy, ny, KYd);
+                double2 b = rhs0 ? rhs0[idx] : make_double2(0.0, 0.0);
+                b = csub(b, edge_term(ix, iy, cy));
+                bv = {dw_from(b.x), dw_from(b.y)};
+            } else {
+                const double2 b = rhs0 ? rhs0[idx] : make_double2(0.0, 0.0);
+                bv = {dw_from_bits(b.x), dw_from_bits(b.y)};
+            }
+            const float bxs = bv.x.h * bsc, bys = bv.y.h * bsc;
+            bb += bxs * bxs + bys * bys;
             const double2 zv = zeta[idx];
-            const double W = Wn ? Wn[idx] : 0.0;
-            cdw_st(zdw + idx, {dw_from(zv.x), dw_from(zv.y)});
+            cdw_st(zdw + idx, {dw_from_bits(zv.x), dw_from_bits(zv.y)});
             cdw_st(ddw + idx, cdw_zero());
-            cdw_st(bdw + idx, {dw_from(b.x), dw_from(b.y)});
-            const dw wv = dw_from(wq(ix, c, g.hx) * wq(iy, ny, g.hy) * W);
+            cdw_st(bdw + idx, bv);
+            const float qxy = ((ix > 0 && ix < c) ? 1.f : 0.5f) * ((iy > 0 && iy < ny) ? 1.f : 0.5f);
+            const dw wv = Wn ? dw_pow2(dw_mul(dw_from_bits(Wn[idx]), HXHY), qxy) : dw{0.f, 0.f};
             a.wdw[sbase + idx] = make_float2(wv.h, wv.l);
         }
+        double lb[4] = {(double)bb / ((double)bsc * (double)bsc), 0.0, 0.0, 0.0};
         block_sum<4>(lb, s_red);
         if (threadIdx.x == 0) { double* sp = slot_ptr(epoch + 1); sp[0] = lb[0]; sp[1] = 0; sp[2] = 0; sp[3] = 0; }
         ++epoch;
@@ -416,9 +436,9 @@ strip_solve_kernel(StripSolveArgs a) {
                 auto colsum = [&](int ix, cdw& Tm, cdw& Tk, cdw& zc) {
                     const float4* col = zdw + (long long)ix * P + iy;
                     zc = cdw_ld(col);
-                    const cdw S = (ylo && yhi) ? cdw_add(cdw_ld(col - 1), cdw_ld(col + 1)) : cdw_ld(ylo ? col - 1 : col + 1);
-                    Tm = cdw_add(S, cdw_pow2(zc, dY));
-                    Tk = cdw_sub(cdw_pow2(zc, eY), S);
+                    const cdw S = (ylo && yhi) ? cdw_add_s(cdw_ld(col - 1), cdw_ld(col + 1)) : cdw_ld(ylo ? col - 1 : col + 1);
+                    Tm = cdw_add_s(S, cdw_pow2(zc, dY));
+                    Tk = cdw_sub_s(cdw_pow2(zc, eY), S);
                 };
                 cdw Tmm = cdw_zero(), Tkm = cdw_zero(), Tm0, Tk0, z0, zdum;
                 if (x0 > 0) colsum(x0 - 1, Tmm, Tkm, zdum);
@@ -429,27 +449,27 @@ strip_solve_kernel(StripSolveArgs a) {
                     const bool xlo = ix > 0, xhi = ix < c;
                     const float dX = (xlo && xhi) ? 4.f : 2.f, eX = (xlo && xhi) ? 2.f : 1.f;
                     const float qxy = ((xlo && xhi) ? 1.f : 0.5f) * qy;
-                    const cdw Q = (xlo && xhi) ? cdw_add(Tmm, Tmp) : (xlo ? Tmm : Tmp);
-                    const cdw Kq = (xlo && xhi) ? cdw_add(Tkm, Tkp) : (xlo ? Tkm : Tkp);
-                    const cdw U = cdw_sub(cdw_pow2(Tm0, eX), Q);
-                    const cdw V = cdw_add(Q, cdw_pow2(Tm0, dX));
-                    const cdw Wk = cdw_add(Kq, cdw_pow2(Tk0, dX));
-                    dw ax = dw_add(dw_add(dw_mul(nC1, U.x), dw_mul(nC2, V.y)), dw_mul(nC3, Wk.x));
-                    dw ay = dw_add(dw_add(dw_mul(nC1, U.y), dw_mul(C2, V.x)), dw_mul(nC3, Wk.y));
+                    const cdw Q = (xlo && xhi) ? cdw_add_s(Tmm, Tmp) : (xlo ? Tmm : Tmp);
+                    const cdw Kq = (xlo && xhi) ? cdw_add_s(Tkm, Tkp) : (xlo ? Tkm : Tkp);
+                    const cdw U = cdw_sub_s(cdw_pow2(Tm0, eX), Q);
+                    const cdw V = cdw_add_s(Q, cdw_pow2(Tm0, dX));
+                    const cdw Wk = cdw_add_s(Kq, cdw_pow2(Tk0, dX));
+                    dw ax = dw_add_s(dw_add_s(dw_mul(nC1, U.x), dw_mul(nC2, V.y)), dw_mul(nC3, Wk.x));
+                    dw ay = dw_add_s(dw_add_s(dw_mul(nC1, U.y), dw_mul(C2, V.x)), dw_mul(nC3, Wk.y));
                     if ((ix == 0 && ltc) || (ix == c && rtc)) {
-                        ax = dw_add(ax, dw_mul(nC5, Tm0.y));
-                        ay = dw_add(ay, dw_mul(C5, Tm0.x));
+                        ax = dw_add_s(ax, dw_mul(nC5, Tm0.y));
+                        ay = dw_add_s(ay, dw_mul(C5, Tm0.x));
                     }
                     const long long idx = (long long)ix * P + iy;
-                    const dw a2 = dw_add(dw_mul(z0.x, z0.x), dw_mul(z0.y, z0.y));
+                    const dw a2 = dw_add_s(dw_mul(z0.x, z0.x), dw_mul(z0.y, z0.y));
                     const float2 wv2 = wdw[idx];
-                    const dw cd = dw_add(dw{wv2.x, wv2.y}, dw_mul(dw_pow2(C6, qxy), a2));
-                    ax = dw_add(ax, dw_mul(cd, z0.x));
-                    ay = dw_add(ay, dw_mul(cd, z0.y));
+                    const dw cd = dw_add_s(dw{wv2.x, wv2.y}, dw_mul(dw_pow2(C6, qxy), a2));
+                    ax = dw_add_s(ax, dw_mul(cd, z0.x));
+                    ay = dw_add_s(ay, dw_mul(cd, z0.y));
                     const cdw bv = cdw_ld(bdw + idx);
-                    const dw rx = dw_sub(bv.x, ax), ry = dw_sub(bv.y, ay);
+                    const dw rx = dw_sub_s(bv.x, ax), ry = dw_sub_s(bv.y, ay);
                     // the correction's operator in the inner precision
-                    const T cop = wv2.x + (T)cfac * (C6f * qxy) * a2.h;
+                    const T cop = wv2.x + cfacf * (C6f * qxy) * a2.h;
                     T rre, rim;
                     rho_atT(ix, rre, rim);
                     const Coef1<T> cxT = coef1<T>(ix, c, KXt);
@@ -624,8 +644,7 @@ strip_solve_kernel(StripSolveArgs a) {
         rprev = rnorm;
 
         // ---------------- inner COCG on A(c) delta = res, Jacobi preconditioner
-        double rho_r = tot[2], rho_i = tot[3];
-        double beta_re = 0.0, beta_im = 0.0;
+        double rho_r = tot[2], rho_i = tot[3];     // thread 0's copy drives the recurrences
         // inner stopping test in the scaled units of r
         const double target = fmax(a.inner_tol * rnorm, fmax(inner_floor * bnorm, 0.1 * floor_abs)) * inv_s;
         if (SR && Ns >= kSRMinNodes) {
@@ -661,16 +680,34 @@ strip_solve_kernel(StripSolveArgs a) {
             ++epoch;
             lap(1);
             if (!group_barrier(bar, epoch * bps, a.err, &s_flag)) { status = DD_NLS_ETIMEOUT; break; }
-            double dl[4];
-            group_sum<4>(group_ptr(epoch), bps, dl, s_red);
-            lap(4);
-            double gam_r = rho_r, gam_i = rho_i, del_r = dl[0], del_i = dl[1];
-            double dd2 = del_r * del_r + del_i * del_i;
-            if (!(dd2 > 0.0) || !isfinite(dd2)) { status = isfinite(dd2) ? DD_NLS_EBREAKDOWN : DD_NLS_ENONFINITE; break; }
-            double al_r = (gam_r * del_r + gam_i * del_i) / dd2, al_i = (gam_i * del_r - gam_r * del_i) / dd2;
-            double be_r = 0.0, be_i = 0.0;
+            // thread-0 state of the recurrences
+            double gam_r = rho_r, gam_i = rho_i, al_r = 0.0, al_i = 0.0, be_r = 0.0, be_i = 0.0;
             double best = INFINITY;     // stagnation guard: least ||r|| so far, iterations since
             int since = 0;
+            if (threadIdx.x < 32) {
+                double dl[4];
+                group_sum_w0<4>(group_ptr(epoch), bps, dl);
+                if (threadIdx.x == 0) {
+                    const double del_r = dl[0], del_i = dl[1];
+                    const double dd2 = del_r * del_r + del_i * del_i;
+                    int ctl = 0, st = 0;
+                    if (!(dd2 > 0.0) || !isfinite(dd2)) {
+                        ctl = 2;
+                        st = isfinite(dd2) ? DD_NLS_EBREAKDOWN : DD_NLS_ENONFINITE;
+                    } else {
+                        al_r = (gam_r * del_r + gam_i * del_i) / dd2;
+                        al_i = (gam_i * del_r - gam_r * del_i) / dd2;
+                    }
+                    s_ctl[0] = ctl;
+                    s_ctl[1] = st;
+                    s_sc[0] = (T)al_r;
+                    s_sc[1] = (T)al_i;
+                }
+            }
+            __syncthreads();
+            lap(4);
+            if (s_ctl[0]) { status = s_ctl[1]; break; }
+            T2 alT = T2{s_sc[0], s_sc[1]}, beT = T2{0, 0};
             for (int it = 0; it < a.max_inner; ++it) {
                 const int cur = it & 1, nxt = cur ^ 1;
                 const T2* rc = rbuf[cur];
@@ -679,7 +716,6 @@ strip_solve_kernel(StripSolveArgs a) {
                 T2* so = sbuf[cur];                // s_k
                 T2* rn_b = rbuf[nxt];
                 T2* wn_b = wbuf[nxt];
-                const T2 alT = mk<T2>(al_r, al_i), beT = mk<T2>(be_r, be_i);
                 T g_r = 0, g_i = 0, dlt_r = 0, dlt_i = 0, rr2 = 0;
                 for (int ch = rank; ch < nchunks; ch += bps) {
                     const int n = ch * blockDim.x + threadIdx.x;
@@ -725,49 +761,80 @@ strip_solve_kernel(StripSolveArgs a) {
                 ++epoch;
                 lap(2);
                 if (!group_barrier(bar, epoch * bps, a.err, &s_flag)) { status = DD_NLS_ETIMEOUT; break; }
-                double gg[4];
-                group_sum<4>(group_ptr(epoch), bps, gg, s_red);
-                double rq[1];
-                group_sum<1>(group_ptr(epoch + 2), bps, rq, s_red);
+                if (threadIdx.x < 32) {
+                    double gg[4], rq[1];
+                    group_sum_w0<4>(group_ptr(epoch), bps, gg);
+                    group_sum_w0<1>(group_ptr(epoch + 2), bps, rq);
+                    if (threadIdx.x == 0) {
+                        int ctl = 0, st = 0;
+                        const double rk = sqrt(rq[0]);
+                        if (!isfinite(rq[0]) || !isfinite(gg[0]) || !isfinite(gg[2])) {
+                            ctl = 2;
+                            st = DD_NLS_ENONFINITE;
+                        } else if (rk <= target) {
+                            ctl = 1;          // x was advanced in this pass; the solution is complete
+                        } else {
+                            // A breakdown of the recurrences after the first step, or 32 steps
+                            // without a 1% gain, ends the inner solve with the x reached: the
+                            // nonlinear loop recomputes the exact residual and starts a new Krylov
+                            // solve from it.
+                            if (rk < 0.99 * best) {
+                                best = rk;
+                                since = 0;
+                            } else if (++since >= 32) {
+                                ctl = 1;
+                            }
+                            // beta_{k+1} = gamma_{k+1}/gamma_k,
+                            // alpha_{k+1} = gamma_{k+1}/(delta_{k+1} - beta_{k+1} gamma_{k+1}/alpha_k)
+                            const double gk2 = gam_r * gam_r + gam_i * gam_i;
+                            if (!ctl && !(gk2 > 0.0)) ctl = 1;
+                            if (!ctl) {
+                                const double nb_r = (gg[0] * gam_r + gg[1] * gam_i) / gk2;
+                                const double nb_i = (gg[1] * gam_r - gg[0] * gam_i) / gk2;
+                                const double a2 = al_r * al_r + al_i * al_i;
+                                const double bg_r = nb_r * gg[0] - nb_i * gg[1], bg_i = nb_r * gg[1] + nb_i * gg[0];
+                                const double t_r = (bg_r * al_r + bg_i * al_i) / a2, t_i = (bg_i * al_r - bg_r * al_i) / a2;
+                                const double den_r = gg[2] - t_r, den_i = gg[3] - t_i;
+                                const double den2 = den_r * den_r + den_i * den_i;
+                                if (!isfinite(den2)) {
+                                    ctl = 2;
+                                    st = DD_NLS_ENONFINITE;
+                                } else if (!(den2 > 0.0)) {
+                                    ctl = 1;
+                                } else {
+                                    al_r = (gg[0] * den_r + gg[1] * den_i) / den2;
+                                    al_i = (gg[1] * den_r - gg[0] * den_i) / den2;
+                                    be_r = nb_r;
+                                    be_i = nb_i;
+                                    gam_r = gg[0];
+                                    gam_i = gg[1];
+                                }
+                            }
+                        }
+                        s_ctl[0] = ctl;
+                        s_ctl[1] = st;
+                        s_sc[0] = (T)al_r;
+                        s_sc[1] = (T)al_i;
+                        s_sc[2] = (T)be_r;
+                        s_sc[3] = (T)be_i;
+                    }
+                }
+                __syncthreads();
                 lap(4);
                 ++kry;
-                if (!isfinite(rq[0]) || !isfinite(gg[0]) || !isfinite(gg[2])) { status = DD_NLS_ENONFINITE; break; }
-                const double rk = sqrt(rq[0]);
-                if (rk <= target) break;     // x was advanced in this pass; the solution is complete
-                // A breakdown of the recurrences after the first step, or 32 steps without a 1%
-                // gain, ends the inner solve with the x reached: the nonlinear loop recomputes the
-                // exact residual and starts a new Krylov solve from it.
-                if (rk < 0.99 * best) {
-                    best = rk;
-                    since = 0;
-                } else if (++since >= 32) {
+                if (s_ctl[0]) {
+                    if (s_ctl[0] == 2) status = s_ctl[1];
                     break;
                 }
-                // beta_{k+1} = gamma_{k+1}/gamma_k;  alpha_{k+1} = gamma_{k+1}/(delta_{k+1} - beta_{k+1} gamma_{k+1}/alpha_k)
-                const double gk2 = gam_r * gam_r + gam_i * gam_i;
-                if (!(gk2 > 0.0)) break;
-                const double nb_r = (gg[0] * gam_r + gg[1] * gam_i) / gk2, nb_i = (gg[1] * gam_r - gg[0] * gam_i) / gk2;
-                const double a2 = al_r * al_r + al_i * al_i;
-                // t = beta * gamma / alpha
-                const double bg_r = nb_r * gg[0] - nb_i * gg[1], bg_i = nb_r * gg[1] + nb_i * gg[0];
-                const double t_r = (bg_r * al_r + bg_i * al_i) / a2, t_i = (bg_i * al_r - bg_r * al_i) / a2;
-                const double den_r = gg[2] - t_r, den_i = gg[3] - t_i;
-                const double den2 = den_r * den_r + den_i * den_i;
-                if (!isfinite(den2)) { status = DD_NLS_ENONFINITE; break; }
-                if (!(den2 > 0.0)) break;
-                al_r = (gg[0] * den_r + gg[1] * den_i) / den2;
-                al_i = (gg[1] * den_r - gg[0] * den_i) / den2;
-                be_r = nb_r;
-                be_i = nb_i;
-                gam_r = gg[0];
-                gam_i = gg[1];
+                alT = T2{s_sc[0], s_sc[1]};
+                beT = T2{s_sc[2], s_sc[3]};
             }
-        } else
+        } else {
+        T2 bT = T2{0, 0};
         for (int it = 0; it < a.max_inner; ++it) {
             // phase A: q = A z + beta q, p = z + beta p, partial mu = p^T q
             // (per-thread partials in T: the FP64 pipe is ~1/64 of FP32 on this part)
             T am_re = 0, am_im = 0;
-            const T2 bT = mk<T2>(beta_re, beta_im);
             for (int ch = rank; ch < nchunks; ch += bps) {
                 const int n = ch * blockDim.x + threadIdx.x;
                 if (n >= Nall) continue;
@@ -817,16 +884,28 @@ strip_solve_kernel(StripSolveArgs a) {
             ++epoch;
             lap(1);
             if (!group_barrier(bar, epoch * bps, a.err, &s_flag)) { status = DD_NLS_ETIMEOUT; break; }
-            double mu[4];
-            group_sum<4>(group_ptr(epoch), bps, mu, s_red);
+            if (threadIdx.x < 32) {
+                double mu[4];
+                group_sum_w0<4>(group_ptr(epoch), bps, mu);
+                if (threadIdx.x == 0) {
+                    const double mu2 = mu[0] * mu[0] + mu[1] * mu[1];
+                    int ctl = 0, st = 0;
+                    if (!(mu2 > 0.0) || !isfinite(mu2)) {
+                        ctl = 2;
+                        st = isfinite(mu2) ? DD_NLS_EBREAKDOWN : DD_NLS_ENONFINITE;
+                    }
+                    // a = rho / mu
+                    s_ctl[0] = ctl;
+                    s_ctl[1] = st;
+                    s_sc[0] = (T)((rho_r * mu[0] + rho_i * mu[1]) / mu2);
+                    s_sc[1] = (T)((rho_i * mu[0] - rho_r * mu[1]) / mu2);
+                }
+            }
+            __syncthreads();
             lap(4);
-            const double mu2 = mu[0] * mu[0] + mu[1] * mu[1];
-            if (!(mu2 > 0.0) || !isfinite(mu2)) { status = isfinite(mu2) ? DD_NLS_EBREAKDOWN : DD_NLS_ENONFINITE; break; }
-            // a = rho / mu
-            const double al_re = (rho_r * mu[0] + rho_i * mu[1]) / mu2;
-            const double al_im = (rho_i * mu[0] - rho_r * mu[1]) / mu2;
-            const T2 alT = mk<T2>(al_re, al_im);
-            const T2 malT = mk<T2>(-al_re, -al_im);
+            if (s_ctl[0]) { status = s_ctl[1]; break; }
+            const T2 alT = T2{s_sc[0], s_sc[1]};
+            const T2 malT = T2{-s_sc[0], -s_sc[1]};
             // phase B: x += a p, r -= a q, z = D^-1 r, partials rho' = r^T z, ||r||^2
             T b0s = 0, b1s = 0, b2s = 0;
             for (int ch = rank; ch < nchunks; ch += bps) {
@@ -871,18 +950,41 @@ strip_solve_kernel(StripSolveArgs a) {
             ++epoch;
             lap(2);
             if (!group_barrier(bar, epoch * bps, a.err, &s_flag)) { status = DD_NLS_ETIMEOUT; break; }
-            double rb[4];
-            group_sum<4>(group_ptr(epoch), bps, rb, s_red);
+            if (threadIdx.x < 32) {
+                double rb[4];
+                group_sum_w0<4>(group_ptr(epoch), bps, rb);
+                if (threadIdx.x == 0) {
+                    int ctl = 0, st = 0;
+                    const double rr2 = rho_r * rho_r + rho_i * rho_i;
+                    if (!isfinite(rb[2])) {
+                        ctl = 2;
+                        st = DD_NLS_ENONFINITE;
+                    } else if (sqrt(rb[2]) <= target) {
+                        ctl = 1;
+                    } else if (!(rr2 > 0.0)) {
+                        ctl = 2;
+                        st = DD_NLS_EBREAKDOWN;
+                    } else {
+                        const double b_re = (rb[0] * rho_r + rb[1] * rho_i) / rr2;
+                        const double b_im = (rb[1] * rho_r - rb[0] * rho_i) / rr2;
+                        rho_r = rb[0];
+                        rho_i = rb[1];
+                        s_sc[2] = (T)b_re;
+                        s_sc[3] = (T)b_im;
+                    }
+                    s_ctl[0] = ctl;
+                    s_ctl[1] = st;
+                }
+            }
+            __syncthreads();
             lap(4);
             ++kry;
-            if (!isfinite(rb[2])) { status = DD_NLS_ENONFINITE; break; }
-            if (sqrt(rb[2]) <= target) break;
-            const double rr2 = rho_r * rho_r + rho_i * rho_i;
-            if (!(rr2 > 0.0)) { status = DD_NLS_EBREAKDOWN; break; }
-            beta_re = (rb[0] * rho_r + rb[1] * rho_i) / rr2;
-            beta_im = (rb[1] * rho_r - rb[0] * rho_i) / rr2;
-            rho_r = rb[0];
-            rho_i = rb[1];
+            if (s_ctl[0]) {
+                if (s_ctl[0] == 2) status = s_ctl[1];
+                break;
+            }
+            bT = T2{s_sc[2], s_sc[3]};
+        }
         }
         if (status) break;
         // ---------------- zeta += delta (FP64), then every block must see the new zeta
