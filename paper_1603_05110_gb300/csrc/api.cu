@@ -239,16 +239,16 @@ static int strip_solve(dd_nls* h, StripSolveArgs& a, int nstrips, int nblocks, d
     double bytes = 0.0, flops = 0.0;
     const double nodes = (double)h->G.nxs * h->G.nyn;
     const double s2 = h->fp32 ? 8.0 : 16.0, s1 = h->fp32 ? 4.0 : 8.0;
-    // per node: residual phase (+ D^-1 and s_-1 for the single-reduction loop), one Krylov
+    // per node: residual phase (r, c and D^-1 only, when the single-reduction loop follows), one Krylov
     // iteration (two passes, or the fused pass of the single-reduction loop), its w_0 = A z_0
     // pass, the epilogue
     const bool sr = h->fp32 && h->pade_m == 0;
-    const double bR = 40 + s1 + (sr ? 7 : 5) * s2, bK = sr ? 11 * s2 + s1 : 12 * s2 + 2 * s1;
+    const double bR = 40 + s1 + (sr ? 2 : 5) * s2, bK = sr ? 11 * s2 + s1 : 12 * s2 + 2 * s1;
     // double-word residual: the epilogue updates zeta and the accumulated correction in
     // double-word form; once per launch a set-up pass (zeta, rhs0, W in; four double-word
     // fields out) and the FP64 write-back (correction and zeta in, zeta out)
     const bool dw = h->dw && h->pade_m == 0;
-    const double bW = sr ? 4 * s2 + s1 : 0.0, bE = dw ? 64 + s2 : 32 + s2, bL = dw ? 96 + 48 : 0.0;
+    const double bW = sr ? 6 * s2 + s1 : 0.0, bE = dw ? 64 + s2 : 32 + s2, bL = dw ? 96 + 48 : 0.0;
     for (int j = 0; j < nstrips; ++j) {
         nl += h->h_nl[j];
         kr += h->h_kry[j];

@@ -228,6 +228,7 @@ strip_solve_kernel(StripSolveArgs a) {
     // strips, none on 12..544-node strips); such strips take the two-reduction loop.
     constexpr bool SR = !PADE && sizeof(T) == 4;
     constexpr int kSRMinNodes = 256;
+    const bool use_sr = SR && Ns >= kSRMinNodes;
     T2* rbuf[2] = {r, z};
     T2* wbuf[2] = {q, SR ? (T2*)a.w1 + sbase : nullptr};
     T2* sbuf[2] = {SR ? (T2*)a.s0 + sbase : nullptr, SR ? (T2*)a.s1 + sbase : nullptr};
@@ -479,12 +480,13 @@ strip_solve_kernel(StripSolveArgs a) {
                     const T2 zT = cmul(di, rT);
                     cT[idx] = cop;
                     r[idx] = rT;
-                    z[idx] = zT;
-                    x[idx] = mk<T2>(0.0, 0.0);
-                    p[idx] = mk<T2>(0.0, 0.0);
-                    q[idx] = mk<T2>(0.0, 0.0);
                     dv[idx] = di;
-                    sbuf[1][idx] = mk<T2>(0.0, 0.0);      // s_{-1}
+                    if (!use_sr) {
+                        z[idx] = zT;
+                        x[idx] = mk<T2>(0.0, 0.0);
+                        p[idx] = mk<T2>(0.0, 0.0);
+                        q[idx] = mk<T2>(0.0, 0.0);
+                    }
                     rz_re += rT.x * zT.x - rT.y * zT.y;
                     rz_im += rT.x * zT.y + rT.y * zT.x;
                     Tmm = Tm0; Tkm = Tk0;
@@ -560,13 +562,13 @@ strip_solve_kernel(StripSolveArgs a) {
                     const T2 zT = cmul(di, rT);
                     cT[idx] = (T)cop;
                     r[idx] = rT;
-                    z[idx] = zT;
-                    x[idx] = mk<T2>(0.0, 0.0);
-                    p[idx] = mk<T2>(0.0, 0.0);
-                    q[idx] = mk<T2>(0.0, 0.0);
-                    if (SR) {
+                    if (use_sr) {
                         dv[idx] = di;
-                        sbuf[1][idx] = mk<T2>(0.0, 0.0);      // s_{-1}
+                    } else {
+                        z[idx] = zT;
+                        x[idx] = mk<T2>(0.0, 0.0);
+                        p[idx] = mk<T2>(0.0, 0.0);
+                        q[idx] = mk<T2>(0.0, 0.0);
                     }
                     rz_re += rT.x * zT.x - rT.y * zT.y;
                     rz_im += rT.x * zT.y + rT.y * zT.x;
@@ -647,7 +649,7 @@ strip_solve_kernel(StripSolveArgs a) {
         double rho_r = tot[2], rho_i = tot[3];     // thread 0's copy drives the recurrences
         // inner stopping test in the scaled units of r
         const double target = fmax(a.inner_tol * rnorm, fmax(inner_floor * bnorm, 0.1 * floor_abs)) * inv_s;
-        if (SR && Ns >= kSRMinNodes) {
+        if (use_sr) {
             // Single-reduction COCG (the Chronopoulos-Gear arrangement of CG with the unconjugated
             // bilinear form): s = A p is carried, w = A z is formed in the same pass as the updates
             // with z_{k+1} rebuilt at the stencil neighbours, so one reduction (gamma = r^T z,
@@ -665,9 +667,14 @@ strip_solve_kernel(StripSolveArgs a) {
                 T rre, rim;
                 rho_atT(ix, rre, rim);
                 T2 zo;
-                const T2 w0 = apply_op_znext<T, T2>(rbuf[0], sbuf[1], sbuf[1], dv, idx, ix, iy, c, ny, P, cxT, cyT, alphaT, rre,
-                                                    rim, cT[idx], zeroT, zeroT, zo);
+                // z_0 = D^-1 r_0 (the rebuild with alpha = beta = 0 reads r only)
+                const T2 w0 = apply_op_znext<T, T2>(rbuf[0], rbuf[0], rbuf[0], dv, idx, ix, iy, c, ny, P, cxT, cyT, alphaT,
+                                                    rre, rim, cT[idx], zeroT, zeroT, zo);
                 wbuf[0][idx] = w0;
+                // the residual pass leaves these to the strips that correct: x = p = s_{-1} = 0
+                x[idx] = zeroT;
+                p[idx] = zeroT;
+                sbuf[1][idx] = zeroT;
                 d0r += w0.x * zo.x - w0.y * zo.y;
                 d0i += w0.x * zo.y + w0.y * zo.x;
             }
