@@ -52,8 +52,10 @@ struct dd_nls {
     void *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *cT = nullptr;
     void *w1 = nullptr, *s0 = nullptr, *s1 = nullptr, *dv = nullptr;
     bool dw = false;        // double-word residual (FP32 inner, Robin)
+    bool dw_res = false;    // the double-word fields hold the strip state of this step
     float4 *zdw = nullptr, *ddw = nullptr, *bdw = nullptr;
     float2* wdw = nullptr;
+    double* bint2 = nullptr;
     double* part = nullptr;
     unsigned* bar = nullptr;
     int* status = nullptr;
@@ -134,7 +136,7 @@ template <typename T> static cudaError_t dalloc(T** ptr, size_t n) {
 
 static void release(dd_nls* h) {
     void* ptrs[] = {h->u, h->zeta, h->rhs0, h->gA, h->gB, h->gconv, h->Wn, h->x, h->r, h->z, h->p, h->q, h->cT,
-                    h->w1, h->s0, h->s1, h->dv, h->zdw, h->ddw, h->bdw, h->wdw,
+                    h->w1, h->s0, h->s1, h->dv, h->zdw, h->ddw, h->bdw, h->wdw, h->bint2,
                     h->part, h->bar, h->status, h->nl_its, h->kry, h->nl_res, h->err, h->red, h->stage,
                     h->X64, h->X32, h->btype, h->V, h->w, h->tmp, h->hdev, h->xs, h->scratch,
                     h->Cf, h->Ci, h->Cf32, h->Ci32, h->xm, h->fac, h->tkind,
@@ -247,8 +249,11 @@ static int strip_solve(dd_nls* h, StripSolveArgs& a, int nstrips, int nblocks, d
     // double-word residual: the epilogue updates zeta and the accumulated correction in
     // double-word form; once per launch a set-up pass (zeta, rhs0, W in; four double-word
     // fields out) and the FP64 write-back (correction and zeta in, zeta out)
+    // (dw_mode 1: set-up only, edge columns written back; dw_mode 2: edge columns only)
     const bool dw = h->dw && h->pade_m == 0;
-    const double bW = sr ? 6 * s2 + s1 : 0.0, bE = dw ? 64 + s2 : 32 + s2, bL = dw ? 96 + 48 : 0.0;
+    const int dm = dw ? a.dw_mode : 0;
+    const double bW = sr ? 6 * s2 + s1 : 0.0, bE = !dw ? 32 + s2 : (dm == 0 ? 64 + s2 : 32 + s2);
+    const double bL = !dw ? 0.0 : (dm == 0 ? 96 + 48 : (dm == 1 ? 80 : 0.0));
     for (int j = 0; j < nstrips; ++j) {
         nl += h->h_nl[j];
         kr += h->h_kry[j];
@@ -295,7 +300,7 @@ static StripSolveArgs base_args(dd_nls* h) {
     a.Wn = h->Wn;
     a.x = h->x; a.r = h->r; a.z = h->z; a.p = h->p; a.q = h->q; a.cT = h->cT;
     a.w1 = h->w1; a.s0 = h->s0; a.s1 = h->s1; a.dv = h->dv;
-    a.zdw = h->zdw; a.ddw = h->ddw; a.bdw = h->bdw; a.wdw = h->wdw;
+    a.zdw = h->zdw; a.ddw = h->ddw; a.bdw = h->bdw; a.wdw = h->wdw; a.bint2 = h->bint2;
     a.nl_tol = h->P.nl_tol;
     a.inner_tol = h->P.inner_tol;
     a.inner_floor = 0.1 * h->P.nl_tol;
@@ -594,6 +599,7 @@ static int schwarz(dd_nls* h, dd_nls_stats* st) {
         CK(launch_finalize(h->part, nb, 1, h->red + 8, h->s));
         CK(launch_sqrt(h->red + 8, h->s));
         CK(cudaMemcpyAsync(h->zeta, h->u, h->nfield * sizeof(double2), cudaMemcpyDeviceToDevice, h->s));   // zeta^0 = h
+        h->dw_res = false;
         if (h->pade_m)        // phi^0 = 0 (eq. localpbS2p)
             CK(cudaMemsetAsync(h->phi, 0, sizeof(double2) * (size_t)G.N * 2 * h->pade_m * G.P, h->s));
         CK(launch_strip_norms(G, h->rhs0, h->bnorm0, h->s));
@@ -623,9 +629,22 @@ static int schwarz(dd_nls* h, dd_nls_stats* st) {
         a.nl_tol = tol_k;
         a.inner_floor = 0.1 * tol_k;
         a.nl_floor_frac = 0.01 * tol_k / std::sqrt((double)G.N);
+        // double-word residual: while the strip tolerance stays at or above its resolution the
+        // double-word fields carry the strip state from launch to launch; a tighter launch
+        // first returns the state to zeta (FP64) and finishes in FP64
+        a.dw_mode = 0;
+        if (h->dw && h->pade_m == 0) {
+            if (tol_k >= kDWFinish) {
+                a.dw_mode = h->dw_res ? 2 : 1;
+            } else if (h->dw_res) {
+                CK(launch_dw_to_zeta(G, h->zdw, h->zeta, h->s));
+                h->dw_res = false;
+            }
+        }
         const int nblk = schedule(h, h->wts, G.N, h->chunks, a);
         int rc = strip_solve(h, a, G.N, nblk, st, true);
         if (rc) return rc;
+        if (a.dw_mode) h->dw_res = true;
         for (int j = 0; j < G.N; ++j) h->wts[j] = 1.0 + (double)h->h_kry[j] + 4.0 * (h->h_nl[j] + 1);
         int nb = 1;
         if (G.N > 1) {
@@ -649,6 +668,10 @@ static int schwarz(dd_nls* h, dd_nls_stats* st) {
         rel_prev = rel;
         // converged only once the strip solves behind R(g) were at full accuracy
         if ((h->P.tol_absolute ? diff : rel) <= h->P.tol && (!adapt || tol_k <= std::max(h->P.nl_tol, h->P.nl_adapt * h->P.tol))) {
+            if (h->dw_res) {
+                CK(launch_dw_to_zeta(G, h->zdw, h->zeta, h->s));
+                h->dw_res = false;
+            }
             if (G.N > 1) CK(cudaMemcpyAsync(h->gconv, gn, h->nI * sizeof(double2), cudaMemcpyDeviceToDevice, h->s));
             h->gA = g;
             h->gB = gn;
@@ -677,6 +700,10 @@ static int schwarz(dd_nls* h, dd_nls_stats* st) {
     }
     h->gA = g;
     h->gB = gn;
+    if (h->dw_res) {
+        CK(launch_dw_to_zeta(G, h->zdw, h->zeta, h->s));
+        h->dw_res = false;
+    }
     return fail(h, DD_NLS_ENOCONV, "Schwarz iteration reached max_schwarz");
 }
 
@@ -782,6 +809,7 @@ extern "C" int dd_nls_create(const dd_nls_params* p, const double* V, const doub
         CKC(dalloc(&h->ddw, h->nfield));
         CKC(dalloc(&h->bdw, h->nfield));
         CKC(dalloc(&h->wdw, h->nfield));
+        CKC(dalloc(&h->bint2, G.N));
     }
     CKC(dalloc(&h->stage, (size_t)(p->nx + 1) * nyn));
     CKC(dalloc(&h->bar, G.N));

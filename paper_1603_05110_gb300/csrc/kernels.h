@@ -44,6 +44,13 @@ struct StripSolveArgs {
     // correction (float4 {re.h, re.l, im.h, im.l} per node), the right side b, w W (float2)
     float4 *zdw, *ddw, *bdw;
     float2* wdw;
+    // 0: zeta (FP64) is the state: set up the double-word fields from it and add the launch's
+    //    correction back at the end.  1: first launch of a step whose strip tolerances stay at
+    //    or above kDWFinish: full set-up, then the double-word fields are the state and only
+    //    the edge columns of zeta (what the trace exchange reads) are written back.
+    //    2: later such launches: only the edge columns of b are refreshed.
+    int dw_mode;
+    double* bint2;           // [strips] ||b||^2 off the edge columns (set in mode 1, read in 2)
     void* cT;                // c = w (W + kappa|zeta|^2) in inner precision
     double nl_tol, inner_tol, inner_floor;
     const double* nl_tol_strip;   // batched: per-strip nonlinear tolerance (device), or NULL
@@ -70,6 +77,11 @@ struct StripSolveArgs {
 
 // cooperative launch of nblocks blocks (a.blk_strip / a.blk_start map blocks to strips)
 cudaError_t launch_strip_solve(const StripSolveArgs& a, int nblocks, bool fp32, cudaStream_t s, int block_size = 256);
+// zeta = the double-word state, every strip node (ends a step run with dw_mode 1/2)
+cudaError_t launch_dw_to_zeta(const Geom& g, const float4* zdw, double2* zeta, cudaStream_t s);
+// The double-word residual resolves about 1e-14 of ||b||: a strip tolerance below this needs the
+// FP64 finish, i.e. dw_mode 0.
+constexpr double kDWFinish = 1e-12;
 int strip_solve_max_blocks(bool fp32);
 int strip_solve_max_blocks_bs(bool fp32, int block_size);   // Robin kernel with 128 or 256 threads
 

@@ -365,51 +365,67 @@ strip_solve_kernel(StripSolveArgs a) {
         C6f = C6.h;
         // zeta, b = (2i/dt) M h - M^Gamma Q^T (l; r) and w W in double-word form, ||b||^2.
         // Integer splits away from the edge columns (no FP64 instruction there); ||b||^2 in
-        // FP32 in units of the first correction's scale.
+        // FP32 in units of the first correction's scale, edge columns apart.
         const dw HXHY = dw_from(g.hx * g.hy);
         const float bsc = (float)(1.0 / (s_first > 0.0 ? s_first : 1.0));
-        float bb = 0.f;
-        for (int ch = rank; ch < nchunks; ch += bps) {
-            const int n = ch * blockDim.x + threadIdx.x;
-            if (n >= Ns) continue;
-            int ix, iy;
-            split_node(n, nyn, inv_nyn, ix, iy);
-            const long long idx = (long long)ix * P + iy;
-            cdw bv;
-            if (ix == 0 || ix == c || unit_side >= 0) {
-                const Coef1<double> cy = coef1<double>(iy, ny, KYd);
-                double2 b = rhs0 ? rhs0[idx] : make_double2(0.0, 0.0);
-                b = csub(b, edge_term(ix, iy, cy));
-                bv = {dw_from(b.x), dw_from(b.y)};
-            } else {
-                const double2 b = rhs0 ? rhs0[idx] : make_double2(0.0, 0.0);
-                bv = {dw_from_bits(b.x), dw_from_bits(b.y)};
-            }
-            const float bxs = bv.x.h * bsc, bys = bv.y.h * bsc;
-            bb += bxs * bxs + bys * bys;
-            const double2 zv = zeta[idx];
-            cdw_st(zdw + idx, {dw_from_bits(zv.x), dw_from_bits(zv.y)});
-            cdw_st(ddw + idx, cdw_zero());
+        float bb = 0.f, be = 0.f;
+        auto edge_b = [&](int ix, int iy, long long idx) {
+            const Coef1<double> cy = coef1<double>(iy, ny, KYd);
+            double2 b = rhs0 ? rhs0[idx] : make_double2(0.0, 0.0);
+            b = csub(b, edge_term(ix, iy, cy));
+            const cdw bv = {dw_from(b.x), dw_from(b.y)};
             cdw_st(bdw + idx, bv);
-            const float qxy = ((ix > 0 && ix < c) ? 1.f : 0.5f) * ((iy > 0 && iy < ny) ? 1.f : 0.5f);
-            const dw wv = Wn ? dw_pow2(dw_mul(dw_from_bits(Wn[idx]), HXHY), qxy) : dw{0.f, 0.f};
-            a.wdw[sbase + idx] = make_float2(wv.h, wv.l);
+            const float bxs = bv.x.h * bsc, bys = bv.y.h * bsc;
+            be += bxs * bxs + bys * bys;
+        };
+        if (a.dw_mode == 2) {
+            // the state and b off the edges are this step's already: refresh b on the edges
+            for (int t = rank * blockDim.x + threadIdx.x; t < 2 * nyn; t += bps * blockDim.x) {
+                const int ix = t < nyn ? 0 : c, iy = t < nyn ? t : t - nyn;
+                edge_b(ix, iy, (long long)ix * P + iy);
+            }
+        } else {
+            for (int ch = rank; ch < nchunks; ch += bps) {
+                const int n = ch * blockDim.x + threadIdx.x;
+                if (n >= Ns) continue;
+                int ix, iy;
+                split_node(n, nyn, inv_nyn, ix, iy);
+                const long long idx = (long long)ix * P + iy;
+                if (ix == 0 || ix == c || unit_side >= 0) {
+                    edge_b(ix, iy, idx);
+                } else {
+                    const double2 b = rhs0 ? rhs0[idx] : make_double2(0.0, 0.0);
+                    const cdw bv = {dw_from_bits(b.x), dw_from_bits(b.y)};
+                    cdw_st(bdw + idx, bv);
+                    const float bxs = bv.x.h * bsc, bys = bv.y.h * bsc;
+                    bb += bxs * bxs + bys * bys;
+                }
+                const double2 zv = zeta[idx];
+                cdw_st(zdw + idx, {dw_from_bits(zv.x), dw_from_bits(zv.y)});
+                if (a.dw_mode == 0) cdw_st(ddw + idx, cdw_zero());
+                const float qxy = ((ix > 0 && ix < c) ? 1.f : 0.5f) * ((iy > 0 && iy < ny) ? 1.f : 0.5f);
+                const dw wv = Wn ? dw_pow2(dw_mul(dw_from_bits(Wn[idx]), HXHY), qxy) : dw{0.f, 0.f};
+                a.wdw[sbase + idx] = make_float2(wv.h, wv.l);
+            }
         }
-        double lb[4] = {(double)bb / ((double)bsc * (double)bsc), 0.0, 0.0, 0.0};
+        const double bs2 = (double)bsc * (double)bsc;
+        double lb[4] = {(double)bb / bs2, (double)be / bs2, 0.0, 0.0};
         block_sum<4>(lb, s_red);
-        if (threadIdx.x == 0) { double* sp = slot_ptr(epoch + 1); sp[0] = lb[0]; sp[1] = 0; sp[2] = 0; sp[3] = 0; }
+        if (threadIdx.x == 0) { double* sp = slot_ptr(epoch + 1); sp[0] = lb[0]; sp[1] = lb[1]; sp[2] = 0; sp[3] = 0; }
         ++epoch;
         if (!group_barrier(bar, epoch * bps, a.err, &s_flag)) status = DD_NLS_ETIMEOUT;
         if (!status) {
             double tb[4];
             group_sum<4>(group_ptr(epoch), bps, tb, s_red);
-            bnorm = sqrt(tb[0]);
+            if (a.dw_mode == 2) tb[0] = a.bint2[j];
+            else if (a.dw_mode == 1 && rank == 0 && threadIdx.x == 0) a.bint2[j] = tb[0];
+            bnorm = sqrt(tb[0] + tb[1]);
         }
         lap(0);
     }
     // The double-word residual resolves about 1e-14 of ||b||: below kDWFinish the strip folds
-    // its accumulated correction into the FP64 zeta and finishes with the FP64 residual.
-    constexpr double kDWFinish = 1e-12;
+    // its accumulated correction into the FP64 zeta and finishes with the FP64 residual (only
+    // with zeta as the state, dw_mode 0; the host keeps tighter tolerances out of modes 1 and 2).
     bool dwr = DW;
 
     for (; !status; ++nl_it) {
@@ -624,7 +640,7 @@ strip_solve_kernel(StripSolveArgs a) {
         if (!isfinite(tot[0]) || !isfinite(tot[1])) { status = DD_NLS_ENONFINITE; break; }
         if (nres <= nl_tol || rnorm <= floor_abs || rnorm == 0.0) break;
         if (nl_it >= a.max_nl) { status = DD_NLS_ENOCONV; break; }
-        if (DW && dwr && nres <= kDWFinish) {
+        if (DW && dwr && a.dw_mode == 0 && nres <= kDWFinish) {
             for (int ch = rank; ch < nchunks; ch += bps) {
                 const int n = ch * blockDim.x + threadIdx.x;
                 if (n >= Ns) continue;
@@ -1008,7 +1024,7 @@ strip_solve_kernel(StripSolveArgs a) {
                 const T2 dx = x[idx];
                 const cdw cc = {dw_mul_f(scd, dx.x), dw_mul_f(scd, dx.y)};
                 cdw_st(zdw + idx, cdw_add(cdw_ld(zdw + idx), cc));
-                cdw_st(ddw + idx, cdw_add(cdw_ld(ddw + idx), cc));
+                if (a.dw_mode == 0) cdw_st(ddw + idx, cdw_add(cdw_ld(ddw + idx), cc));
             }
         } else
         for (int ch = rank; ch < nchunks; ch += bps) {
@@ -1035,7 +1051,15 @@ strip_solve_kernel(StripSolveArgs a) {
         if (!group_barrier(bar, epoch * bps, a.err, &s_flag)) { status = DD_NLS_ETIMEOUT; break; }
         lap(4);
     }
-    if (DW && dwr) {
+    if (DW && dwr && a.dw_mode != 0) {
+        // the double-word fields stay the state; the trace exchange reads the edge columns
+        for (int t = rank * blockDim.x + threadIdx.x; t < 2 * nyn; t += bps * blockDim.x) {
+            const int ix = t < nyn ? 0 : c, iy = t < nyn ? t : t - nyn;
+            const long long idx = (long long)ix * P + iy;
+            const cdw zv = cdw_ld(zdw + idx);
+            zeta[idx] = make_double2(dw_to(zv.x), dw_to(zv.y));
+        }
+    } else if (DW && dwr) {
         // zeta (FP64) += the launch's accumulated correction, own nodes only
         for (int ch = rank; ch < nchunks; ch += bps) {
             const int n = ch * blockDim.x + threadIdx.x;
@@ -1076,6 +1100,22 @@ static cudaError_t launch_strip_solve_t(const StripSolveArgs& args, int nblocks,
 cudaError_t launch_strip_solve(const StripSolveArgs& a, int nblocks, bool fp32, cudaStream_t s, int block_size) {
     return fp32 ? launch_strip_solve_t<float>(a, nblocks, block_size, s)
                 : launch_strip_solve_t<double>(a, nblocks, block_size, s);
+}
+
+__global__ void dw_to_zeta_kernel(Geom g, const float4* __restrict__ zdw, double2* __restrict__ zeta) {
+    const long long total = (long long)g.N * g.sstride();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        if ((int)(i % g.P) >= g.nyn) continue;
+        const cdw v = cdw_ld(zdw + i);
+        zeta[i] = make_double2(dw_to(v.x), dw_to(v.y));
+    }
+}
+cudaError_t launch_dw_to_zeta(const Geom& g, const float4* zdw, double2* zeta, cudaStream_t s) {
+    count_launches(1);
+    const long long total = (long long)g.N * g.sstride();
+    const int nb = (int)std::min<long long>((total + 255) / 256, 152LL * 8);
+    dw_to_zeta_kernel<<<nb, 256, 0, s>>>(g, zdw, zeta);
+    return cudaGetLastError();
 }
 
 int strip_solve_max_blocks_bs(bool fp32, int bs) {

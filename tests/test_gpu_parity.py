@@ -324,3 +324,21 @@ def test_batched_uneven_instances_match_oracle():
         # beta = 900 at dt = 0.002: the plain fixed point diverges; both sides relax it
         ref = run_oracle(w, 2, relax=0.6)
         assert rel(got[i], ref[-1][0]) < 1e-11
+
+
+@pytest.mark.parametrize("case", ["well", "gpe_far"])
+def test_double_word_state_carried_between_launches(case):
+    """Strip tolerances of 1e-12 and above: the double-word fields carry the strip state from
+    one Schwarz launch to the next (only the edge columns go back to FP64 in between, and the
+    whole field at the end of the step).  Interface tolerance 1e-10, so the step agrees with
+    the oracle's (solved to 1e-12) to 1e-8."""
+    if case == "well":
+        w, relax = WELL, 1.0
+    else:
+        w = wl.Workload("gpe_far", -18.0, 18.0, -18.0, 18.0, 36, 30, 6, 0.002, 2, lap=0.5, kappa=-500.0, p=45.0,
+                        potential="trap", datum="ground_noise", seed=1603)
+        relax = 0.6
+    ref = run_oracle(w, 2, algorithm="preconditioned", relax=relax)
+    got = run_gpu(w, 2, tol=1e-10, nl_tol=1e-12, algorithm=binding.PRECONDITIONED, precision=binding.FP32_DW)
+    for (ug, _), (uo, _) in zip(got, ref):
+        assert rel(ug, uo) < 1e-8
