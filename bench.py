@@ -33,7 +33,7 @@ METRIC = "time steps/s and stencil GB/s at 1e-8 interface residual, chosen vs pl
 
 # DRAM traffic of one strip-solver launch from the committed ncu summary
 # (profiles/strip_solve_nls_well.md), valid only for the source it was taken from.
-NCU_TRAFFIC = {"source_sha1": "376ecda55eefe6996a79e850f05694b74d5c0ac4", "bytes_per_launch": 52.061440e6 + 37.389312e6}
+NCU_TRAFFIC = {"source_sha1": "9e47d5895964933c1c05f7d09dab3b1fd6072bcd", "bytes_per_launch": 46.521088e6 + 14.315264e6}
 
 
 def parse():
@@ -127,7 +127,7 @@ def measured_peaks():
 
 def source_sha1():
     h = hashlib.sha1()
-    for f in ("strip_solver.cu", "common.cuh"):
+    for f in ("strip_solver.cu", "common.cuh", "dw.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1603_05110_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
 
@@ -324,8 +324,9 @@ def run_ours(args, rank, world, local_rank):
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
                 "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs",
                 "share_of_step": prof["strip_solve_ms"] / total_ms * world,
-                "note": "algorithmic bytes per node per phase (R, A, B, epilogue) x nodes x phase counts; "
-                        "the step's fields (~90 MB) fit in the 129 MB L2, so this is effective bandwidth"}
+                "note": "algorithmic bytes per node per pass (set-up, residual, Krylov passes, epilogue) x nodes x "
+                        "pass counts; most of the fields stay in the 129 MB L2 between passes, so this is "
+                        "effective bandwidth"}
 
     cpu = None
     if not args.no_cpu and world == 1:

@@ -202,8 +202,8 @@ int dd_nls_step_noalloc(const dd_nls_params* p, const double* V, double* u, cons
  * iteration solves the strips of all instances that have not yet converged in one
  * persistent launch, then updates every instance's interface vector (eq. fluxlr) in one
  * launch; each instance stops at its own `tol`.  Instances may differ in every field of
- * dd_nls_params except `precision`; each must use the classical algorithm with Robin
- * transmission.  An autotuner picks the strip solver's block size and block count for the
+ * dd_nls_params except `precision` (DD_NLS_FP64 or DD_NLS_FP32_INNER); each must use the
+ * classical algorithm with Robin transmission.  An autotuner picks the strip solver's block size and block count for the
  * batch shape the first time a shape is stepped (timed on the first Schwarz iteration).
  * params, V (nullable, or entries NULL) and u0 are arrays of n entries; pointers are host or
  * device per ptr_kind.  Errors: dd_nls_batch_last_error(). */
