@@ -72,6 +72,7 @@ struct dd_nls {
     int* btype = nullptr;
     std::vector<int> btype_h;
     double2 *V = nullptr, *w = nullptr, *tmp = nullptr, *hdev = nullptr, *xs = nullptr;
+    double2* cpart = nullptr;   // cosine-transform partial sums (modal P solve)
     double* scratch = nullptr;
     // S_pade^m (eq. TCS): coefficients and auxiliary unknowns
     int pade_m = 0;
@@ -138,7 +139,7 @@ static void release(dd_nls* h) {
     void* ptrs[] = {h->u, h->zeta, h->rhs0, h->gA, h->gB, h->gconv, h->Wn, h->x, h->r, h->z, h->p, h->q, h->cT,
                     h->w1, h->s0, h->s1, h->dv, h->zdw, h->ddw, h->bdw, h->wdw, h->bint2,
                     h->part, h->bar, h->status, h->nl_its, h->kry, h->nl_res, h->err, h->red, h->stage,
-                    h->X64, h->X32, h->btype, h->V, h->w, h->tmp, h->hdev, h->xs, h->scratch,
+                    h->X64, h->X32, h->btype, h->V, h->w, h->tmp, h->hdev, h->xs, h->scratch, h->cpart,
                     h->Cf, h->Ci, h->Cf32, h->Ci32, h->xm, h->fac, h->tkind,
                     h->pa_dev, h->pd_dev, h->phi, h->xf, h->rf, h->zf, h->pf, h->qf, h->cTf};
     for (void* p : ptrs)
@@ -365,6 +366,7 @@ static int build_modal(dd_nls* h) {
     CK(dalloc(&h->fac, (size_t)9 * std::max(1, G.N - 1) * G.nyn));
     CK(dalloc(&h->tmp, (size_t)h->nI));
     CK(dalloc(&h->xs, (size_t)h->nI));
+    CK(dalloc(&h->cpart, (size_t)8 * h->nI));
     double2* work = nullptr;
     CK(cudaMalloc(&work, sizeof(double2) * (size_t)h->ntypes * G.nyn * 2 * G.nxs));
     cudaEvent_t t0, t1;
@@ -602,7 +604,7 @@ static int schwarz(dd_nls* h, dd_nls_stats* st) {
         h->dw_res = false;
         if (h->pade_m)        // phi^0 = 0 (eq. localpbS2p)
             CK(cudaMemsetAsync(h->phi, 0, sizeof(double2) * (size_t)G.N * 2 * h->pade_m * G.P, h->s));
-        CK(launch_strip_norms(G, h->rhs0, h->bnorm0, h->s));
+        CK(launch_strip_norms(G, h->rhs0, h->bnorm0, h->part, 16 * h->maxb, h->s));
         CK(cudaMemcpyAsync(h->hred + 16, h->bnorm0, sizeof(double) * G.N, cudaMemcpyDeviceToHost, h->s));
         CK(cudaStreamSynchronize(h->s));
     }
@@ -684,7 +686,8 @@ static int schwarz(dd_nls* h, dd_nls_stats* st) {
             ProfScope ps(h, &h->profile.interface_ms);
             if (h->P.psolve == DD_NLS_PSOLVE_MODAL) {
                 CK(launch_sub(h->tmp, g, gn, h->nI, h->s));     // y = g - R(g)
-                CK(launch_modal_apply(G, h->fp32, h->Cf, h->Ci, h->Cf32, h->Ci32, h->fac, h->tmp, h->xs, gn, h->s));
+                CK(launch_modal_apply(G, h->fp32, h->Cf, h->Ci, h->Cf32, h->Ci32, h->fac, h->tmp, h->xs, gn, h->s,
+                                      h->cpart));
                 CK(launch_sub(gn, g, h->xs, h->nI, h->s));
             } else {
                 CK(launch_sub(h->tmp, g, gn, h->nI, h->s));

@@ -4,6 +4,8 @@
 #include "common.cuh"
 #include "kernels.h"
 
+#include <algorithm>
+
 namespace ddnls {
 
 static inline int nblocks(long long n, int bs) { return (int)((n + bs - 1) / bs); }
@@ -98,23 +100,37 @@ cudaError_t launch_rhs0(const Geom& g, const double2* h, double2* rhs0, double* 
     return cudaGetLastError();
 }
 
-__global__ void strip_norms_kernel(Geom g, const double2* __restrict__ rhs0, double* __restrict__ out) {
+// ||rhs0|| per strip: B blocks per strip write partial sums to part (fixed slices of the strip's
+// nodes), one thread per strip adds its B partials in order.  part holds N*B doubles.
+__global__ void strip_norm_parts_kernel(Geom g, const double2* __restrict__ rhs0, int B, double* __restrict__ part) {
     __shared__ double sm[64];
-    const int j = blockIdx.x;
+    const int j = blockIdx.x / B, kb = blockIdx.x - j * B;
     const double2* b = rhs0 + (long long)j * g.sstride();
     const int Ns = g.nxs * g.nyn;
     double v[1] = {0.0};
-    for (int n = threadIdx.x; n < Ns; n += blockDim.x) {
+    for (int n = kb * blockDim.x + threadIdx.x; n < Ns; n += B * blockDim.x) {
         const int ix = n / g.nyn, iy = n - ix * g.nyn;
         const double2 a = b[(long long)ix * g.P + iy];
         v[0] += a.x * a.x + a.y * a.y;
     }
     block_sum<1>(v, sm);
-    if (threadIdx.x == 0) out[j] = sqrt(v[0]);
+    if (threadIdx.x == 0) part[blockIdx.x] = v[0];
 }
-cudaError_t launch_strip_norms(const Geom& g, const double2* rhs0, double* out, cudaStream_t s) {
-    count_launches(1);
-    strip_norms_kernel<<<g.N, 256, 0, s>>>(g, rhs0, out);
+__global__ void strip_norm_sum_kernel(int N, int B, const double* __restrict__ part, double* __restrict__ out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    double acc = 0.0;
+    for (int k = 0; k < B; ++k) acc += part[(long long)j * B + k];
+    out[j] = sqrt(acc);
+}
+cudaError_t launch_strip_norms(const Geom& g, const double2* rhs0, double* out, double* part, int part_cap,
+                               cudaStream_t s) {
+    // as many blocks per strip as the scratch allows, at most 32 (one block per strip before:
+    // 16 blocks for the whole 1024^2 field)
+    const int B = std::max(1, std::min(32, part_cap / std::max(1, g.N)));
+    count_launches(2);
+    strip_norm_parts_kernel<<<g.N * B, 256, 0, s>>>(g, rhs0, B, part);
+    strip_norm_sum_kernel<<<(g.N + 127) / 128, 128, 0, s>>>(g.N, B, part, out);
     return cudaGetLastError();
 }
 

@@ -467,7 +467,7 @@ extern "C" int dd_nls_batch_step(dd_nls_batch* b, int nsteps, dd_nls_stats* stat
             BCK(launch_rhs0(G, b->u + b->foff[i], b->rhs0 + b->foff[i], b->part, &nb, b->s));
             BCK(launch_finalize(b->part, nb, 1, b->bscale + i, b->s));
             BCK(launch_sqrt(b->bscale + i, b->s));
-            BCK(launch_strip_norms(G, b->rhs0 + b->foff[i], b->bnorm0 + b->strip_first[i], b->s));
+            BCK(launch_strip_norms(G, b->rhs0 + b->foff[i], b->bnorm0 + b->strip_first[i], b->part, 16 * b->maxb + 2048, b->s));
             const bool prev = b->P[i].guess == DD_NLS_GUESS_PREVIOUS && b->have_prev[i];
             const size_t gb = sizeof(double2) * (size_t)2 * (G.N - 1) * G.P;
             if (prev) b->cur[i] = b->conv_half[i];

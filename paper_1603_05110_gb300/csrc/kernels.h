@@ -93,7 +93,9 @@ cudaError_t launch_scatter_u(const AuxGeom& g, const double2* glob, double2* str
 cudaError_t launch_gather_u(const AuxGeom& g, const double2* strips, double2* glob, cudaStream_t s);
 cudaError_t launch_scatter_real(const AuxGeom& g, const double* glob, double scale, double* strips, cudaStream_t s);
 // out[j] = ||rhs0|| over strip j (one block per strip)
-cudaError_t launch_strip_norms(const AuxGeom& g, const double2* rhs0, double* out, cudaStream_t s);
+// ||rhs0|| per strip; part: scratch of part_cap doubles (at least N)
+cudaError_t launch_strip_norms(const AuxGeom& g, const double2* rhs0, double* out, double* part, int part_cap,
+                               cudaStream_t s);
 // rhs0 = i alpha M h (per strip); partial sums of ||rhs0||^2 into part[nblk][1]
 cudaError_t launch_rhs0(const AuxGeom& g, const double2* h, double2* rhs0, double* part, int* nblk_out, cudaStream_t s);
 // interface flux update, eq. (fluxlr): writes gnew, partial norms into part[nblk][2].
@@ -125,7 +127,7 @@ cudaError_t launch_modal_setup(const AuxGeom& g, int ntypes, const int* tkind_de
                                const double2* pd = nullptr);
 cudaError_t launch_modal_apply(const AuxGeom& g, bool fp32, const double* Cf, const double* Ci, const float* Cf32,
                                const float* Ci32, const double2* fac, const double2* y, double2* x, double2* tmp,
-                               cudaStream_t s);
+                               cudaStream_t s, void* cpart);   // cpart: 8 x 2(N-1) x P double2 scratch
 
 // GMRES helpers on vectors of length n (complex, FP64)
 cudaError_t launch_dots(const double2* V, long long ld, int k, const double2* w, long long n, double2* out,

@@ -17,6 +17,8 @@
 #include "common.cuh"
 #include "kernels.h"
 
+#include <algorithm>
+
 namespace ddnls {
 
 // C_fwd[k][j] = D_j cos(pi j k/ny) / sigma_k,  C_inv[j][k] = cos(pi j k/ny)
@@ -197,28 +199,33 @@ __global__ void modal_solve_kernel(Geom g, const double2* __restrict__ fac, doub
     }
 }
 
-// out[o][r] = sum_c C[r][c] in[o][c] for the ntr traces of an interface vector (pitch P).
-// Tiles of 32 rows x 8 traces per block; C and the trace tile staged in shared memory.
+// part[kz][o][r] = sum over c in slice kz of C[r][c] in[o][c], for the ntr traces of an interface
+// vector (pitch P).  Tiles of 32 rows x 8 traces per block, C and the trace tile staged in shared
+// memory; the column range is split into kCosSlices slices (grid z) so that a 1025-point
+// transform of 30 traces spreads over ~1000 blocks instead of ~130.
+constexpr int kCosSlices = 8;
 template <typename T>
-__global__ void __launch_bounds__(256) cosine_apply_kernel(int n, int ntr, int P, const T* __restrict__ C,
-                                                          const double2* __restrict__ in, double2* __restrict__ out) {
+__global__ void __launch_bounds__(256) cosine_partial_kernel(int n, int ntr, int P, int klen, const T* __restrict__ C,
+                                                             const double2* __restrict__ in,
+                                                             typename C2<T>::t* __restrict__ part) {
     using T2 = typename C2<T>::t;
     __shared__ T Cs[32][33];
     __shared__ T2 Is[8][32];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int r0 = blockIdx.x * 32, o0 = blockIdx.y * 8;
     const int r = r0 + tx, o = o0 + ty;
+    const int kb = blockIdx.z * klen, ke = min(n, kb + klen);
     T ar = 0, ai = 0;
-    for (int c0 = 0; c0 < n; c0 += 32) {
+    for (int c0 = kb; c0 < ke; c0 += 32) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int rr = r0 + ty * 4 + q, cc = c0 + tx;
-            Cs[ty * 4 + q][tx] = (rr < n && cc < n) ? C[(long long)rr * n + cc] : (T)0;
+            Cs[ty * 4 + q][tx] = (rr < n && cc < ke) ? C[(long long)rr * n + cc] : (T)0;
         }
         {
             const int cc = c0 + tx;
             double2 v = make_double2(0, 0);
-            if (o < ntr && cc < n) v = in[(long long)o * P + cc];
+            if (o < ntr && cc < ke) v = in[(long long)o * P + cc];
             Is[ty][tx] = mk<T2>(v.x, v.y);
         }
         __syncthreads();
@@ -231,7 +238,43 @@ __global__ void __launch_bounds__(256) cosine_apply_kernel(int n, int ntr, int P
         }
         __syncthreads();
     }
-    if (r < n && o < ntr) out[(long long)o * P + r] = make_double2((double)ar, (double)ai);
+    if (r < n && o < ntr) {
+        T2 v;
+        v.x = ar;
+        v.y = ai;
+        part[((long long)blockIdx.z * ntr + o) * P + r] = v;
+    }
+}
+
+// out[o][r] = the slices' partial sums, added in slice order
+template <typename T2>
+__global__ void cosine_reduce_kernel(int n, int ntr, int P, const T2* __restrict__ part, double2* __restrict__ out) {
+    const long long total = (long long)ntr * n;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+        const int o = (int)(t / n), r = (int)(t - (long long)o * n);
+        T2 acc = part[(long long)o * P + r];
+#pragma unroll
+        for (int kz = 1; kz < kCosSlices; ++kz) {
+            const T2 v = part[((long long)kz * ntr + o) * P + r];
+            acc.x += v.x;
+            acc.y += v.y;
+        }
+        out[(long long)o * P + r] = make_double2((double)acc.x, (double)acc.y);
+    }
+}
+
+template <typename T>
+static cudaError_t cosine_apply(int n, int ntr, int P, const T* C, const double2* in, double2* out, void* part,
+                                cudaStream_t s) {
+    using T2 = typename C2<T>::t;
+    const int klen = ((n + kCosSlices - 1) / kCosSlices + 31) / 32 * 32;
+    dim3 grid((n + 31) / 32, (ntr + 7) / 8, kCosSlices);
+    count_launches(2);
+    cosine_partial_kernel<T><<<grid, 256, 0, s>>>(n, ntr, P, klen, C, in, (T2*)part);
+    const long long total = (long long)ntr * n;
+    const int nb = (int)std::min<long long>((total + 255) / 256, 152LL * 8);
+    cosine_reduce_kernel<T2><<<nb, 256, 0, s>>>(n, ntr, P, (const T2*)part, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_modal_setup(const Geom& g, int ntypes, const int* tkind_dev, const int* btype_dev,
@@ -254,15 +297,17 @@ cudaError_t launch_modal_setup(const Geom& g, int ntypes, const int* tkind_dev, 
 
 cudaError_t launch_modal_apply(const Geom& g, bool fp32, const double* Cf, const double* Ci, const float* Cf32,
                                const float* Ci32, const double2* fac, const double2* y, double2* x, double2* tmp,
-                               cudaStream_t s) {
+                               cudaStream_t s, void* cpart) {
     const int ntr = 2 * (g.N - 1);
-    dim3 grid((g.nyn + 31) / 32, (ntr + 7) / 8), block(256);
-    count_launches(3);
-    if (fp32) cosine_apply_kernel<float><<<grid, block, 0, s>>>(g.nyn, ntr, g.P, Cf32, y, tmp);
-    else cosine_apply_kernel<double><<<grid, block, 0, s>>>(g.nyn, ntr, g.P, Cf, y, tmp);
-    modal_solve_kernel<<<(g.nyn + 127) / 128, 128, 0, s>>>(g, fac, tmp);
-    if (fp32) cosine_apply_kernel<float><<<grid, block, 0, s>>>(g.nyn, ntr, g.P, Ci32, tmp, x);
-    else cosine_apply_kernel<double><<<grid, block, 0, s>>>(g.nyn, ntr, g.P, Ci, tmp, x);
+    cudaError_t e = fp32 ? cosine_apply<float>(g.nyn, ntr, g.P, Cf32, y, tmp, cpart, s)
+                         : cosine_apply<double>(g.nyn, ntr, g.P, Cf, y, tmp, cpart, s);
+    if (e != cudaSuccess) return e;
+    // one warp per block: the per-mode sweeps are FP64 chains, spread over as many SMs as possible
+    count_launches(1);
+    modal_solve_kernel<<<(g.nyn + 31) / 32, 32, 0, s>>>(g, fac, tmp);
+    e = fp32 ? cosine_apply<float>(g.nyn, ntr, g.P, Ci32, tmp, x, cpart, s)
+             : cosine_apply<double>(g.nyn, ntr, g.P, Ci, tmp, x, cpart, s);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

@@ -186,7 +186,7 @@ extern "C" int dd_nls_step_noalloc(const dd_nls_params* p, const double* V, doub
     NCK(launch_rhs0(G, us, rhs0, part, &nb, s));
     NCK(launch_finalize(part, nb, 1, red + 8, s));
     NCK(launch_sqrt(red + 8, s));
-    NCK(launch_strip_norms(G, rhs0, bnorm0, s));
+    NCK(launch_strip_norms(G, rhs0, bnorm0, part, 16 * std::max(maxb, 512), s));
     NCK(cudaMemcpyAsync(zeta, us, nfield * sizeof(double2), cudaMemcpyDeviceToDevice, s));
 
     StripSolveArgs a{};
