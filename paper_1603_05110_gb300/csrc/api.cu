@@ -225,7 +225,8 @@ static int schedule(dd_nls* h, const std::vector<double>& w, int nstrips, int ca
     return total;
 }
 
-static int strip_solve(dd_nls* h, StripSolveArgs& a, int nstrips, int nblocks, dd_nls_stats* st, bool count) {
+// Enqueue one strip-solver launch and the copies of its per-strip results (no host wait).
+static int strip_solve_enqueue(dd_nls* h, StripSolveArgs& a, int nstrips, int nblocks) {
     CK(cudaMemsetAsync(h->bar, 0, sizeof(unsigned) * nstrips, h->s));
     CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->s));
     a.pcyc = h->prof ? h->pcyc : nullptr;
@@ -237,6 +238,12 @@ static int strip_solve(dd_nls* h, StripSolveArgs& a, int nstrips, int nblocks, d
     CK(cudaMemcpyAsync(h->h_nl.data(), h->nl_its, sizeof(int) * nstrips, cudaMemcpyDeviceToHost, h->s));
     CK(cudaMemcpyAsync(h->h_kry.data(), h->kry, sizeof(long long) * nstrips, cudaMemcpyDeviceToHost, h->s));
     CK(cudaMemcpyAsync(h->hred + 8, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+    return DD_NLS_OK;
+}
+
+// Wait for the stream, then account for and check the launch enqueued last.
+static int strip_solve_finish(dd_nls* h, const StripSolveArgs& a, int nstrips, int nblocks, dd_nls_stats* st,
+                              bool count) {
     CK(cudaStreamSynchronize(h->s));
     long long nl = 0, kr = 0;
     double bytes = 0.0, flops = 0.0;
@@ -289,6 +296,11 @@ static int strip_solve(dd_nls* h, StripSolveArgs& a, int nstrips, int nblocks, d
             return fail(h, h->h_status[j], buf);
         }
     return DD_NLS_OK;
+}
+
+static int strip_solve(dd_nls* h, StripSolveArgs& a, int nstrips, int nblocks, dd_nls_stats* st, bool count) {
+    const int rc = strip_solve_enqueue(h, a, nstrips, nblocks);
+    return rc ? rc : strip_solve_finish(h, a, nstrips, nblocks, st, count);
 }
 
 static StripSolveArgs base_args(dd_nls* h) {
@@ -644,20 +656,22 @@ static int schwarz(dd_nls* h, dd_nls_stats* st) {
             }
         }
         const int nblk = schedule(h, h->wts, G.N, h->chunks, a);
-        int rc = strip_solve(h, a, G.N, nblk, st, true);
+        // the trace exchange is enqueued behind the strip solve, so one host wait covers both
+        int rc = strip_solve_enqueue(h, a, G.N, nblk);
         if (rc) return rc;
-        if (a.dw_mode) h->dw_res = true;
-        for (int j = 0; j < G.N; ++j) h->wts[j] = 1.0 + (double)h->h_kry[j] + 4.0 * (h->h_nl[j] + 1);
         int nb = 1;
         if (G.N > 1) {
             ProfScope ps(h, &h->profile.interface_ms);
             CK(launch_traces(G, h->zeta, g, gn, h->part, &nb, h->s, h->pade_m, h->phi, h->pa_dev, h->pd_dev));
             CK(launch_finalize(h->part, nb, 2, h->red, h->s));
             CK(cudaMemcpyAsync(h->hred, h->red, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->s));
-            CK(cudaStreamSynchronize(h->s));
         } else {
             h->hred[0] = h->hred[1] = 0.0;
         }
+        rc = strip_solve_finish(h, a, G.N, nblk, st, true);
+        if (rc) return rc;
+        if (a.dw_mode) h->dw_res = true;
+        for (int j = 0; j < G.N; ++j) h->wts[j] = 1.0 + (double)h->h_kry[j] + 4.0 * (h->h_nl[j] + 1);
         const double diff = std::sqrt(h->hred[0]), nrm = std::sqrt(h->hred[1]);
         const double rel = nrm > 0.0 ? diff / nrm : diff;
         if (st) {

@@ -14,10 +14,8 @@ static inline int nblocks(long long n, int bs) { return (int)((n + bs - 1) / bs)
 __global__ void scatter_u_kernel(Geom g, const double2* __restrict__ glob, double2* __restrict__ out) {
     const long long total = (long long)g.N * g.nxs * g.nyn;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
-        const int iy = (int)(t % g.nyn);
-        const long long rest = t / g.nyn;
-        const int ix = (int)(rest % g.nxs);
-        const int j = (int)(rest / g.nxs);
+        int j, ix, iy;
+        split_strip_node(t, g.nxs, g.nyn, j, ix, iy);
         const int ixg = j * (g.nxs - 1) + ix;
         out[(long long)(j * g.nxs + ix) * g.P + iy] = glob[(long long)iy * (g.nx + 1) + ixg];
     }
@@ -25,10 +23,8 @@ __global__ void scatter_u_kernel(Geom g, const double2* __restrict__ glob, doubl
 __global__ void scatter_real_kernel(Geom g, const double* __restrict__ glob, double scale, double* __restrict__ out) {
     const long long total = (long long)g.N * g.nxs * g.nyn;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
-        const int iy = (int)(t % g.nyn);
-        const long long rest = t / g.nyn;
-        const int ix = (int)(rest % g.nxs);
-        const int j = (int)(rest / g.nxs);
+        int j, ix, iy;
+        split_strip_node(t, g.nxs, g.nyn, j, ix, iy);
         const int ixg = j * (g.nxs - 1) + ix;
         out[(long long)(j * g.nxs + ix) * g.P + iy] = scale * glob[(long long)iy * (g.nx + 1) + ixg];
     }
@@ -70,10 +66,8 @@ __global__ void rhs0_kernel(Geom g, const double2* __restrict__ h, double2* __re
     double nv[1] = {0.0};
     const long long total = (long long)g.N * g.nxs * g.nyn;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
-        const int iy = (int)(t % g.nyn);
-        const long long rest = t / g.nyn;
-        const int ix = (int)(rest % g.nxs);
-        const int j = (int)(rest / g.nxs);
+        int j, ix, iy;
+        split_strip_node(t, g.nxs, g.nyn, j, ix, iy);
         const long long idx = (long long)(j * g.nxs + ix) * g.P + iy;
         const Coef1<double> cx = coef1<double>(ix, c, consts_x<double>(g)), cy = coef1<double>(iy, ny, consts_y<double>(g));
         double2 acc = make_double2(0, 0);
@@ -223,10 +217,8 @@ __global__ void commit_kernel(Geom g, const double2* __restrict__ zeta, double2*
     const int c = g.nxs - 1;
     const long long total = (long long)g.N * g.nxs * g.nyn;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
-        const int iy = (int)(t % g.nyn);
-        const long long rest = t / g.nyn;
-        const int ix = (int)(rest % g.nxs);
-        const int j = (int)(rest / g.nxs);
+        int j, ix, iy;
+        split_strip_node(t, g.nxs, g.nyn, j, ix, iy);
         const long long idx = (long long)(j * g.nxs + ix) * g.P + iy;
         const long long src = (ix == 0 && j > 0) ? (long long)((j - 1) * g.nxs + c) * g.P + iy : idx;
         const double2 v = zeta[src];
@@ -250,10 +242,8 @@ __global__ void diagnostics_kernel(Geom g, const double2* __restrict__ u, const 
     const long long total = (long long)g.N * g.nxs * g.nyn;
     double v[2] = {0.0, 0.0};
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
-        const int iy = (int)(t % g.nyn);
-        const long long rest = t / g.nyn;
-        const int ix = (int)(rest % g.nxs);
-        const int j = (int)(rest / g.nxs);
+        int j, ix, iy;
+        split_strip_node(t, g.nxs, g.nyn, j, ix, iy);
         const long long idx = (long long)(j * g.nxs + ix) * g.P + iy;
         const Coef1<double> cx = coef1<double>(ix, c, consts_x<double>(g)), cy = coef1<double>(iy, ny, consts_y<double>(g));
         double2 Mu = make_double2(0, 0), Su = make_double2(0, 0);

@@ -113,6 +113,22 @@ __device__ __forceinline__ void split_node(int n, int nyn, float inv_nyn, int& i
     else if (iy >= nyn) { ix += 1; iy -= nyn; }
 }
 
+// Node t of the strip-field enumeration t = (j nxs + ix) nyn + iy -> (j, ix, iy), with 32-bit
+// divisions while t fits (64-bit ones cost several times more instructions).
+__device__ __forceinline__ void split_strip_node(long long t, int nxs, int nyn, int& j, int& ix, int& iy) {
+    if (t < 0x7fffffffLL) {
+        const unsigned u = (unsigned)t, col = u / (unsigned)nyn, jj = col / (unsigned)nxs;
+        iy = (int)(u - col * (unsigned)nyn);
+        j = (int)jj;
+        ix = (int)(col - jj * (unsigned)nxs);
+    } else {
+        const long long col = t / nyn;
+        iy = (int)(t - col * nyn);
+        j = (int)(col / nxs);
+        ix = (int)(col - (long long)j * nxs);
+    }
+}
+
 // ------------------------------------------------------------------- reductions
 // Sum NV doubles over the block in a fixed order; the result is valid in thread 0.
 template <int NV> __device__ __forceinline__ void block_sum(double (&v)[NV], double* smem) {
