@@ -59,30 +59,54 @@ cudaError_t launch_gather_u(const Geom& g, const double2* strips, double2* glob,
 }
 
 // ------------------------------------------------------------- step right side
+// Both per-step FP64 stencils below walk runs of kRX x-nodes at one row: on the uniform mesh the
+// 1D mass and stiffness rows are exact multiples of [1 d 1] (d = 4 inside, 2 at an end; times
+// h/6) and [-1 e -1] (e = 2 / 1; times 1/h), so the y sums of each column are formed once per
+// column and shared by the run's nodes (about half the FP64 operations of the 9-point loop).
+constexpr int kRX = 4;
+__device__ __forceinline__ void run_item(long long t, const Geom& g, int& j, int& x0, int& x1, int& iy) {
+    const int nseg = (g.nxs + kRX - 1) / kRX;
+    int seg;
+    split_strip_node(t, nseg, g.nyn, j, seg, iy);
+    x0 = seg * kRX;
+    x1 = min(x0 + kRX, g.nxs);
+}
+// y sums of column col at row iy: tm = [1 dy 1] u, tk = [-1 ey -1] u; zc = u(iy)
+__device__ __forceinline__ void col_sums(const double2* col, int iy, int ny, double2& tm, double2& tk, double2& zc) {
+    zc = col[0];
+    const bool lo = iy > 0, hi = iy < ny;
+    const double2 am = lo ? col[-1] : make_double2(0.0, 0.0), ap = hi ? col[1] : make_double2(0.0, 0.0);
+    const double d = (lo && hi) ? 4.0 : 2.0, e = (lo && hi) ? 2.0 : 1.0;
+    const double sx = am.x + ap.x, sy = am.y + ap.y;
+    tm = make_double2(fma(d, zc.x, sx), fma(d, zc.y, sy));
+    tk = make_double2(fma(e, zc.x, -sx), fma(e, zc.y, -sy));
+}
+
 // rhs0 = (2i/dt) M h on every strip (eq. NproblemRobinNL), M = Mx (x) My of the strip.
 __global__ void rhs0_kernel(Geom g, const double2* __restrict__ h, double2* __restrict__ rhs, double* __restrict__ part) {
     __shared__ double sm[64];
     const int c = g.nxs - 1, ny = g.nyn - 1;
+    const double cm = g.hx * g.hy / 36.0;
     double nv[1] = {0.0};
-    const long long total = (long long)g.N * g.nxs * g.nyn;
+    const long long total = (long long)g.N * ((g.nxs + kRX - 1) / kRX) * g.nyn;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
-        int j, ix, iy;
-        split_strip_node(t, g.nxs, g.nyn, j, ix, iy);
-        const long long idx = (long long)(j * g.nxs + ix) * g.P + iy;
-        const Coef1<double> cx = coef1<double>(ix, c, consts_x<double>(g)), cy = coef1<double>(iy, ny, consts_y<double>(g));
-        double2 acc = make_double2(0, 0);
-        for (int dx = -1; dx <= 1; ++dx) {
-            if (ix + dx < 0 || ix + dx > c) continue;
-            for (int dy = -1; dy <= 1; ++dy) {
-                if (iy + dy < 0 || iy + dy > ny) continue;
-                const double w = cx.m[dx + 1] * cy.m[dy + 1];
-                const double2 v = h[idx + (long long)dx * g.P + dy];
-                acc.x += w * v.x;
-                acc.y += w * v.y;
-            }
+        int j, x0, x1, iy;
+        run_item(t, g, j, x0, x1, iy);
+        const double2* base = h + (long long)j * g.sstride() + iy;
+        double2 tmm = make_double2(0.0, 0.0), tm0, tk, zc;
+        if (x0 > 0) col_sums(base + (long long)(x0 - 1) * g.P, iy, ny, tmm, tk, zc);
+        col_sums(base + (long long)x0 * g.P, iy, ny, tm0, tk, zc);
+        for (int ix = x0; ix < x1; ++ix) {
+            double2 tmp = make_double2(0.0, 0.0);
+            if (ix < c) col_sums(base + (long long)(ix + 1) * g.P, iy, ny, tmp, tk, zc);
+            const double dx = (ix > 0 && ix < c) ? 4.0 : 2.0;
+            const double2 acc = make_double2(cm * fma(dx, tm0.x, tmm.x + tmp.x), cm * fma(dx, tm0.y, tmm.y + tmp.y));
+            const long long idx = (long long)j * g.sstride() + (long long)ix * g.P + iy;
+            rhs[idx] = make_double2(-g.alpha * acc.y, g.alpha * acc.x);
+            nv[0] += g.alpha * g.alpha * (acc.x * acc.x + acc.y * acc.y);
+            tmm = tm0;
+            tm0 = tmp;
         }
-        rhs[idx] = make_double2(-g.alpha * acc.y, g.alpha * acc.x);
-        nv[0] += g.alpha * g.alpha * (acc.x * acc.x + acc.y * acc.y);
     }
     block_sum<1>(nv, sm);
     if (threadIdx.x == 0) part[blockIdx.x * 4] = nv[0];
@@ -239,31 +263,35 @@ __global__ void diagnostics_kernel(Geom g, const double2* __restrict__ u, const 
                                    double* __restrict__ part) {
     __shared__ double sm[64];
     const int c = g.nxs - 1, ny = g.nyn - 1;
-    const long long total = (long long)g.N * g.nxs * g.nyn;
+    const double cm = g.hx * g.hy / 36.0, ck = g.hy / (6.0 * g.hx), cl = g.hx / (6.0 * g.hy);
+    const long long total = (long long)g.N * ((g.nxs + kRX - 1) / kRX) * g.nyn;
     double v[2] = {0.0, 0.0};
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
-        int j, ix, iy;
-        split_strip_node(t, g.nxs, g.nyn, j, ix, iy);
-        const long long idx = (long long)(j * g.nxs + ix) * g.P + iy;
-        const Coef1<double> cx = coef1<double>(ix, c, consts_x<double>(g)), cy = coef1<double>(iy, ny, consts_y<double>(g));
-        double2 Mu = make_double2(0, 0), Su = make_double2(0, 0);
-        for (int dx = -1; dx <= 1; ++dx) {
-            if (ix + dx < 0 || ix + dx > c) continue;
-            for (int dy = -1; dy <= 1; ++dy) {
-                if (iy + dy < 0 || iy + dy > ny) continue;
-                const double wm = cx.m[dx + 1] * cy.m[dy + 1];
-                const double ws = cx.k[dx + 1] * cy.m[dy + 1] + cx.m[dx + 1] * cy.k[dy + 1];
-                const double2 a = u[idx + (long long)dx * g.P + dy];
-                Mu.x += wm * a.x; Mu.y += wm * a.y;
-                Su.x += ws * a.x; Su.y += ws * a.y;
-            }
+        int j, x0, x1, iy;
+        run_item(t, g, j, x0, x1, iy);
+        const long long sb = (long long)j * g.sstride() + iy;
+        const double2* base = u + sb;
+        const double wy = wq(iy, ny, g.hy);
+        double2 tmm = make_double2(0.0, 0.0), tkm = tmm, tm0, tk0, z0, zd;
+        if (x0 > 0) col_sums(base + (long long)(x0 - 1) * g.P, iy, ny, tmm, tkm, zd);
+        col_sums(base + (long long)x0 * g.P, iy, ny, tm0, tk0, z0);
+        for (int ix = x0; ix < x1; ++ix) {
+            double2 tmp = make_double2(0.0, 0.0), tkp = tmp, zp = tmp;
+            if (ix < c) col_sums(base + (long long)(ix + 1) * g.P, iy, ny, tmp, tkp, zp);
+            const bool in = ix > 0 && ix < c;
+            const double dx = in ? 4.0 : 2.0, ex = in ? 2.0 : 1.0;
+            // M u = cm [1 dx 1] tm;  S u = ck [-1 ex -1] tm + cl [1 dx 1] tk
+            const double2 Mu = make_double2(cm * fma(dx, tm0.x, tmm.x + tmp.x), cm * fma(dx, tm0.y, tmm.y + tmp.y));
+            const double2 Su = make_double2(ck * fma(ex, tm0.x, -(tmm.x + tmp.x)) + cl * fma(dx, tk0.x, tkm.x + tkp.x),
+                                            ck * fma(ex, tm0.y, -(tmm.y + tmp.y)) + cl * fma(dx, tk0.y, tkm.y + tkp.y));
+            const double a2 = z0.x * z0.x + z0.y * z0.y;
+            const double w = wq(ix, c, g.hx) * wy;
+            const double W = Wn ? Wn[sb + (long long)ix * g.P] : 0.0;
+            v[0] += z0.x * Mu.x + z0.y * Mu.y;
+            v[1] += z0.x * Su.x + z0.y * Su.y - w * W * a2 - 0.5 * g.kap * w * a2 * a2;
+            tmm = tm0; tkm = tk0;
+            tm0 = tmp; tk0 = tkp; z0 = zp;
         }
-        const double2 uc = u[idx];
-        const double a2 = uc.x * uc.x + uc.y * uc.y;
-        const double w = wq(ix, c, g.hx) * wq(iy, ny, g.hy);
-        const double W = Wn ? Wn[idx] : 0.0;
-        v[0] += uc.x * Mu.x + uc.y * Mu.y;
-        v[1] += uc.x * Su.x + uc.y * Su.y - w * W * a2 - 0.5 * g.kap * w * a2 * a2;
     }
     block_sum<2>(v, sm);
     if (threadIdx.x == 0) { part[blockIdx.x * 4 + 0] = v[0]; part[blockIdx.x * 4 + 1] = v[1]; }
