@@ -54,6 +54,10 @@ def parse():
     ap.add_argument("--residual", default="dw", choices=["fp64", "dw"],
                     help="nonlinear residual of the chosen form: FP64, or double-word on the FP32 pipe")
     ap.add_argument("--instances", type=int, default=64)
+    ap.add_argument("--learn-n", type=int, default=256, help="learned_guess: cells per direction")
+    ap.add_argument("--learn-strips", type=int, default=8)
+    ap.add_argument("--learn-steps", type=int, default=160, help="learned_guess: steps generated")
+    ap.add_argument("--learn-epochs", type=int, default=60)
     ap.add_argument("--max-schwarz", type=int, default=5000)
     return ap.parse_args()
 
@@ -460,6 +464,88 @@ def run_batch(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_learned(args, rank, world, local_rank):
+    """Learned interface guess (dd_cnn_*): the plain solver generates a GPE trajectory, the CNN is
+    trained on the device on its converged interface vectors (steps 3 .. 3/4 of the run), and the
+    held-out steps are solved twice from the same state: from the previous step's vector (the
+    paper's guess) and from the network's prediction.  Schwarz iterations and time per step are
+    reported for both; the learned time includes the network's inference."""
+    import torch
+
+    from paper_1603_05110_gb300 import binding, build, workloads as wl
+    if not os.path.exists(binding.LIB_PATH):
+        build.build()
+    binding.load()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    n, dt = args.learn_n, 0.002
+    w = wl.Workload("learned_gpe", -12.0, 12.0, -12.0, 12.0, n, n, args.learn_strips, dt, args.learn_steps, lap=0.5,
+                    kappa=-300.0, p=float(np.sqrt(4 / dt)), potential="trap", datum="ground_noise", seed=1603)
+    prm = solver_params(w, args, binding.FP32_DW if args.residual == "dw" else binding.FP32_INNER)
+    prm["algorithm"] = binding.CLASSICAL
+    ntr = 2 * (w.n_strips - 1)
+    stream = torch.cuda.Stream(device=dev)
+    us, gs = [torch.from_numpy(w.u0()).to(dev)], []
+    t0 = time.perf_counter()
+    with binding.Solver(prm, us[0], torch.from_numpy(w.V()).to(dev), stream=stream) as s:
+        for _ in range(args.learn_steps):
+            out = torch.empty_like(us[0])
+            s.step(1, out)
+            g = torch.empty(ntr, w.ny + 1, dtype=torch.complex128, device=dev)
+            s.get_state(None, g)
+            us.append(out)
+            gs.append(g)
+    gen_s = time.perf_counter() - t0
+    ntrain = (3 * args.learn_steps) // 4
+    net = binding.CNN(ntr, w.ny + 1, stream=stream)
+    net.set_params(binding.CNN.init_params(seed=7, last_scale=0.1))
+    t0 = time.perf_counter()
+    for _ in range(args.learn_epochs):
+        for k in range(3, ntrain):                  # predict g of step k+1 from steps k, k-1, k-2
+            net.train_step(gs[k - 1], gs[k - 2], gs[k - 3], gs[k], lr=3e-4)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    res = {"previous": [], "learned": []}
+    g0 = torch.empty(ntr, w.ny + 1, dtype=torch.complex128, device=dev)
+    with binding.Solver(prm, us[0], torch.from_numpy(w.V()).to(dev), stream=stream) as s:
+        for k in range(ntrain, args.learn_steps - 1):
+            # state u after step k (us[k + 1]); the previous-step guess is gs[k]
+            for kind in ("previous", "learned"):
+                s.set_state(us[k + 1], gs[k], k + 1)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                if kind == "learned":
+                    net.guess(gs[k], gs[k - 1], gs[k - 2], g0)
+                    st = s.solve_interface(g0)
+                else:
+                    st = s.solve_interface(gs[k])
+                e1.record(stream)
+                e1.synchronize()
+                res[kind].append((st["last_schwarz_iterations"], e0.elapsed_time(e1)))
+    net.close()
+    if rank != 0:
+        return
+    its = {k: statistics.mean(v[0] for v in res[k]) for k in res}
+    ms = {k: statistics.mean(v[1] for v in res[k]) for k in res}
+    line = {"metric": METRIC, "value": 1e3 / ms["learned"], "unit": "steps/s", "n_gpus": world,
+            "steps": len(res["learned"]), "warmup": 0, "ms_per_step": ms["learned"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 inner Krylov + " + ("double-word f32x2" if args.residual == "dw" else "f64")
+                     + " residual; CNN bf16 in / f32 accumulate", "data": "synthetic",
+            "config": {"workload": f"learned_guess: GPE trap, beta 300, {n}x{n} cells on (-12,12)^2, {w.n_strips} strips, "
+                                   f"classical Schwarz, Robin p={w.p:.1f}, dt={dt}, interface tol {args.tol:g}; "
+                                   f"{args.learn_steps} generated steps, trained on steps 3..{ntrain - 1}, "
+                                   f"{len(res['learned'])} held-out steps",
+                       "note": "each held-out step solved from the same state with both guesses; no L2 flush"},
+            "schwarz_iterations_per_step": {"previous_guess": its["previous"], "learned_guess": its["learned"]},
+            "ms_per_step_by_guess": {"previous_guess": ms["previous"], "learned_guess": ms["learned"]},
+            "learned_vs_previous_speedup": ms["previous"] / ms["learned"],
+            "generation_s": gen_s, "training_s": train_s, "training_updates": args.learn_epochs * (ntrain - 3)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -469,6 +555,8 @@ def main():
         run_reference(args, rank)
     elif args.workload == "gpe_batch":
         run_batch(args, rank, world, local_rank)
+    elif args.workload == "learned_guess":
+        run_learned(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

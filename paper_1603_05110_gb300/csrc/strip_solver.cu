@@ -228,7 +228,10 @@ strip_solve_kernel(StripSolveArgs a) {
     // strips, none on 12..544-node strips); such strips take the two-reduction loop.
     constexpr bool SR = !PADE && sizeof(T) == 4;
     constexpr int kSRMinNodes = 256;
-    const bool use_sr = SR && Ns >= kSRMinNodes;
+    // A strip whose single-reduction solve stalls (32 steps without a 1% gain) or breaks down
+    // takes the two-reduction loop for the rest of the launch (seen in FP32 on a GPE trap strip
+    // after ~100 steps, where the recurrence for alpha had lost its accuracy).
+    bool use_sr = SR && Ns >= kSRMinNodes;
     T2* rbuf[2] = {r, z};
     T2* wbuf[2] = {q, SR ? (T2*)a.w1 + sbase : nullptr};
     T2* sbuf[2] = {SR ? (T2*)a.s0 + sbase : nullptr, SR ? (T2*)a.s1 + sbase : nullptr};
@@ -799,18 +802,18 @@ strip_solve_kernel(StripSolveArgs a) {
                         } else {
                             // A breakdown of the recurrences after the first step, or 32 steps
                             // without a 1% gain, ends the inner solve with the x reached: the
-                            // nonlinear loop recomputes the exact residual and starts a new Krylov
-                            // solve from it.
+                            // nonlinear loop recomputes the exact residual and continues with the
+                            // two-reduction loop (ctl 3).
                             if (rk < 0.99 * best) {
                                 best = rk;
                                 since = 0;
                             } else if (++since >= 32) {
-                                ctl = 1;
+                                ctl = 3;
                             }
                             // beta_{k+1} = gamma_{k+1}/gamma_k,
                             // alpha_{k+1} = gamma_{k+1}/(delta_{k+1} - beta_{k+1} gamma_{k+1}/alpha_k)
                             const double gk2 = gam_r * gam_r + gam_i * gam_i;
-                            if (!ctl && !(gk2 > 0.0)) ctl = 1;
+                            if (!ctl && !(gk2 > 0.0)) ctl = 3;
                             if (!ctl) {
                                 const double nb_r = (gg[0] * gam_r + gg[1] * gam_i) / gk2;
                                 const double nb_i = (gg[1] * gam_r - gg[0] * gam_i) / gk2;
@@ -823,7 +826,7 @@ strip_solve_kernel(StripSolveArgs a) {
                                     ctl = 2;
                                     st = DD_NLS_ENONFINITE;
                                 } else if (!(den2 > 0.0)) {
-                                    ctl = 1;
+                                    ctl = 3;
                                 } else {
                                     al_r = (gg[0] * den_r + gg[1] * den_i) / den2;
                                     al_i = (gg[1] * den_r - gg[0] * den_i) / den2;
@@ -847,6 +850,7 @@ strip_solve_kernel(StripSolveArgs a) {
                 ++kry;
                 if (s_ctl[0]) {
                     if (s_ctl[0] == 2) status = s_ctl[1];
+                    if (s_ctl[0] == 3) use_sr = false;   // keep x; two-reduction loop from now on
                     break;
                 }
                 alT = T2{s_sc[0], s_sc[1]};

@@ -342,3 +342,22 @@ def test_double_word_state_carried_between_launches(case):
     got = run_gpu(w, 2, tol=1e-10, nl_tol=1e-12, algorithm=binding.PRECONDITIONED, precision=binding.FP32_DW)
     for (ug, _), (uo, _) in zip(got, ref):
         assert rel(ug, uo) < 1e-8
+
+
+def test_fp32_inner_solves_survive_a_long_gpe_trajectory():
+    """GPE trap, beta = 300, 256^2 cells, 8 strips: around step 105 the FP32 single-reduction
+    COCG of one strip stalls (its alpha recurrence loses accuracy); the strip must fall back to the
+    two-reduction loop and the run must track the plain FP64 one."""
+    dt = 0.002
+    w = wl.Workload("gpe_long", -12.0, 12.0, -12.0, 12.0, 256, 256, 8, dt, 110, lap=0.5, kappa=-300.0,
+                    p=float(np.sqrt(4 / dt)), potential="trap", datum="ground_noise", seed=1603)
+    outs = {}
+    for precision in (binding.FP64, binding.FP32_DW):
+        u0 = w.u0()
+        out = np.zeros_like(u0)
+        with binding.Solver(gpu_params(w, tol=1e-8, nl_tol=1e-11, max_schwarz=400, precision=precision), u0,
+                            w.V()) as s:
+            st = s.step(110, out)
+        assert st["steps"] == 110
+        outs[precision] = out
+    assert rel(outs[binding.FP32_DW], outs[binding.FP64]) < 1e-6
