@@ -83,6 +83,7 @@ struct dd_nls {
     double *Cf = nullptr, *Ci = nullptr;
     float *Cf32 = nullptr, *Ci32 = nullptr;
     double2 *xm = nullptr, *fac = nullptr;
+    float2* fac32 = nullptr;    // FP32 copy of the per-mode factors (FP32 forms)
     int* tkind = nullptr;
     // host mirrors
     double* hred = nullptr;          // pinned
@@ -140,7 +141,7 @@ static void release(dd_nls* h) {
                     h->w1, h->s0, h->s1, h->dv, h->zdw, h->ddw, h->bdw, h->wdw, h->bint2,
                     h->part, h->bar, h->status, h->nl_its, h->kry, h->nl_res, h->err, h->red, h->stage,
                     h->X64, h->X32, h->btype, h->V, h->w, h->tmp, h->hdev, h->xs, h->scratch, h->cpart,
-                    h->Cf, h->Ci, h->Cf32, h->Ci32, h->xm, h->fac, h->tkind,
+                    h->Cf, h->Ci, h->Cf32, h->Ci32, h->xm, h->fac, h->fac32, h->tkind,
                     h->pa_dev, h->pd_dev, h->phi, h->xf, h->rf, h->zf, h->pf, h->qf, h->cTf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -387,6 +388,11 @@ static int build_modal(dd_nls* h) {
     cudaEventRecord(t0, h->s);
     cudaError_t e = launch_modal_setup(G, h->ntypes, h->tkind, h->btype, h->Cf, h->Ci, h->Cf32, h->Ci32, h->xm, h->fac,
                                        work, h->s, h->pade_m, h->pa_dev, h->pd_dev);
+    if (e == cudaSuccess && h->fp32) {
+        const size_t nf = (size_t)9 * std::max(1, G.N - 1) * G.nyn;
+        e = cudaMalloc(&h->fac32, nf * sizeof(float2));
+        if (e == cudaSuccess) e = launch_to_float((const double*)h->fac, (float*)h->fac32, 2 * (long long)nf, h->s);
+    }
     cudaEventRecord(t1, h->s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
     float ms = 0.f;
@@ -701,7 +707,7 @@ static int schwarz(dd_nls* h, dd_nls_stats* st) {
             if (h->P.psolve == DD_NLS_PSOLVE_MODAL) {
                 CK(launch_sub(h->tmp, g, gn, h->nI, h->s));     // y = g - R(g)
                 CK(launch_modal_apply(G, h->fp32, h->Cf, h->Ci, h->Cf32, h->Ci32, h->fac, h->tmp, h->xs, gn, h->s,
-                                      h->cpart));
+                                      h->cpart, h->fac32));
                 CK(launch_sub(gn, g, h->xs, h->nI, h->s));
             } else {
                 CK(launch_sub(h->tmp, g, gn, h->nI, h->s));

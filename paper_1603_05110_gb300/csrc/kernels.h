@@ -127,7 +127,9 @@ cudaError_t launch_modal_setup(const AuxGeom& g, int ntypes, const int* tkind_de
                                const double2* pd = nullptr);
 cudaError_t launch_modal_apply(const AuxGeom& g, bool fp32, const double* Cf, const double* Ci, const float* Cf32,
                                const float* Ci32, const double2* fac, const double2* y, double2* x, double2* tmp,
-                               cudaStream_t s, void* cpart);   // cpart: 8 x 2(N-1) x P double2 scratch
+                               cudaStream_t s, void* cpart,    // cpart: 8 x 2(N-1) x P double2 scratch
+                               const float2* fac32 = nullptr); // FP32 factors for the FP32 forms
+cudaError_t launch_to_float(const double* a, float* b, long long n, cudaStream_t s);
 
 // GMRES helpers on vectors of length n (complex, FP64)
 cudaError_t launch_dots(const double2* V, long long ld, int k, const double2* w, long long n, double2* out,

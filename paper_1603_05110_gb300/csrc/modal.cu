@@ -168,33 +168,38 @@ __global__ void modal_factor_kernel(Geom g, const int* __restrict__ btype, const
 }
 
 // y (modal coefficients of the right side, interface layout [2(N-1)][P]) -> x in place.
-__global__ void modal_solve_kernel(Geom g, const double2* __restrict__ fac, double2* __restrict__ y) {
+// Sweeps in the precision of the factors: FP64, or FP32 in the FP32 forms (whose cosine
+// transforms around this solve are FP32 already).
+template <typename T2>
+__global__ void modal_solve_kernel(Geom g, const T2* __restrict__ fac, double2* __restrict__ y) {
     const int n = g.nyn, NI = g.N - 1, P = g.P;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     auto F = [&](int i, int e) { return fac[((long long)i * 9 + e) * n + k]; };
     // forward: Yt_i = Y_i - G_i Yt_{i-1}
-    double2 p0 = make_double2(0, 0), p1 = make_double2(0, 0);
+    auto ld = [&](long long q) { const double2 v = y[q]; return mk<T2>(v.x, v.y); };
+    auto st = [&](long long q, T2 v) { y[q] = make_double2((double)v.x, (double)v.y); };
+    T2 p0 = mk<T2>(0, 0), p1 = mk<T2>(0, 0);
     for (int i = 0; i < NI; ++i) {
-        double2 a = y[(long long)(2 * i) * P + k], b = y[(long long)(2 * i + 1) * P + k];
+        T2 a = ld((long long)(2 * i) * P + k), b = ld((long long)(2 * i + 1) * P + k);
         if (i > 0) {
             a = csub(a, cadd(cmul(F(i, 4), p0), cmul(F(i, 5), p1)));
             b = csub(b, cadd(cmul(F(i, 6), p0), cmul(F(i, 7), p1)));
         }
-        y[(long long)(2 * i) * P + k] = a;
-        y[(long long)(2 * i + 1) * P + k] = b;
+        st((long long)(2 * i) * P + k, a);
+        st((long long)(2 * i + 1) * P + k, b);
         p0 = a;
         p1 = b;
     }
     // backward: U_i = S_i^{-1} (Yt_i - Up_i U_{i+1}),  Up_i U_{i+1} = (up * U_{i+1}[0], 0)
-    double2 n0 = make_double2(0, 0);
+    T2 n0 = mk<T2>(0, 0);
     for (int i = NI - 1; i >= 0; --i) {
-        double2 a = y[(long long)(2 * i) * P + k], b = y[(long long)(2 * i + 1) * P + k];
+        T2 a = ld((long long)(2 * i) * P + k), b = ld((long long)(2 * i + 1) * P + k);
         a = csub(a, cmul(F(i, 8), n0));
-        const double2 u0 = cadd(cmul(F(i, 0), a), cmul(F(i, 1), b));
-        const double2 u1 = cadd(cmul(F(i, 2), a), cmul(F(i, 3), b));
-        y[(long long)(2 * i) * P + k] = u0;
-        y[(long long)(2 * i + 1) * P + k] = u1;
+        const T2 u0 = cadd(cmul(F(i, 0), a), cmul(F(i, 1), b));
+        const T2 u1 = cadd(cmul(F(i, 2), a), cmul(F(i, 3), b));
+        st((long long)(2 * i) * P + k, u0);
+        st((long long)(2 * i + 1) * P + k, u1);
         n0 = u0;
     }
 }
@@ -277,6 +282,12 @@ static cudaError_t cosine_apply(int n, int ntr, int P, const T* C, const double2
     return cudaGetLastError();
 }
 
+cudaError_t launch_to_float(const double* a, float* b, long long n, cudaStream_t s) {
+    count_launches(1);
+    to_float_kernel<<<2048, 256, 0, s>>>(a, b, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_modal_setup(const Geom& g, int ntypes, const int* tkind_dev, const int* btype_dev,
                                double* Cf, double* Ci, float* Cf32, float* Ci32, double2* xm, double2* fac,
                                double2* work, cudaStream_t s, int pade_m, const double2* pa, const double2* pd) {
@@ -297,14 +308,15 @@ cudaError_t launch_modal_setup(const Geom& g, int ntypes, const int* tkind_dev, 
 
 cudaError_t launch_modal_apply(const Geom& g, bool fp32, const double* Cf, const double* Ci, const float* Cf32,
                                const float* Ci32, const double2* fac, const double2* y, double2* x, double2* tmp,
-                               cudaStream_t s, void* cpart) {
+                               cudaStream_t s, void* cpart, const float2* fac32) {
     const int ntr = 2 * (g.N - 1);
     cudaError_t e = fp32 ? cosine_apply<float>(g.nyn, ntr, g.P, Cf32, y, tmp, cpart, s)
                          : cosine_apply<double>(g.nyn, ntr, g.P, Cf, y, tmp, cpart, s);
     if (e != cudaSuccess) return e;
     // one warp per block: the per-mode sweeps are FP64 chains, spread over as many SMs as possible
     count_launches(1);
-    modal_solve_kernel<<<(g.nyn + 31) / 32, 32, 0, s>>>(g, fac, tmp);
+    if (fp32 && fac32) modal_solve_kernel<float2><<<(g.nyn + 31) / 32, 32, 0, s>>>(g, fac32, tmp);
+    else modal_solve_kernel<double2><<<(g.nyn + 31) / 32, 32, 0, s>>>(g, fac, tmp);
     e = fp32 ? cosine_apply<float>(g.nyn, ntr, g.P, Ci32, tmp, x, cpart, s)
              : cosine_apply<double>(g.nyn, ntr, g.P, Ci, tmp, x, cpart, s);
     if (e != cudaSuccess) return e;
