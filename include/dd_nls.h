@@ -60,7 +60,11 @@ enum { DD_NLS_CLASSICAL = 0, DD_NLS_PRECONDITIONED = 1 };  /* eq. algo_d / eq. a
 /* Arithmetic of the strip solves: FP64 throughout; FP32 inner Krylov with the FP64 nonlinear
  * residual; or FP32 inner Krylov with the residual in double-word arithmetic (pairs of FP32
  * numbers, about 48 significant bits, on the FP32 pipe; Robin transmission only -- with
- * S_pade it behaves as DD_NLS_FP32_INNER).  The strip state zeta stays FP64 in every mode. */
+ * S_pade it behaves as DD_NLS_FP32_INNER).  Interface vectors, the Schwarz test, u_n and the
+ * diagnostics are FP64 in every mode.  In the double-word mode a strip whose tolerance is below
+ * 1e-12 finishes with the FP64 residual; while all strip tolerances of a step are 1e-12 or
+ * looser the strip state travels between that step's launches in double-word form and u_n is
+ * rebuilt from it (rounded to ~48 bits) at the end of the step. */
 enum { DD_NLS_FP64 = 0, DD_NLS_FP32_INNER = 1, DD_NLS_FP32_DW = 2 };
 enum { DD_NLS_GUESS_ZERO = 0, DD_NLS_GUESS_PREVIOUS = 1 }; /* g_n^0 (Sec. 5) */
 enum { DD_NLS_PTR_HOST = 0, DD_NLS_PTR_DEVICE = 1 };
