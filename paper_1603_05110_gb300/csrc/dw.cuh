@@ -73,8 +73,9 @@ __device__ __forceinline__ double dw_to(dw x) { return (double)x.h + (double)x.l
 // The same split with integer operations only (GB300 issues FP64 instructions, conversions
 // included, at ~1/64 of the FP32 rate): hi = the leading 24 significant bits of v, truncated;
 // lo = the next 29 bits, rounded to 24 and scaled by 2^(e-1075) in two exact power-of-two
-// steps; then normalized by Fast2Sum.  Exact to 2^-47 relative for 2^-126 <= |v| < 2^128;
-// zero, the FP32-subnormal range and non-finite values take dw_from.
+// steps; then normalized by Fast2Sum.  Exact to 2^-47 relative for 2^-102 <= |v| < 2^128; for
+// 2^-126 <= |v| < 2^-102 the low word is FP32-subnormal and the error stays below 2^-149 in
+// absolute terms; zero, smaller values and non-finite values take dw_from.
 __device__ __forceinline__ dw dw_from_bits(double v) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(v);
     const unsigned e = (unsigned)(b >> 52) & 0x7ffu;
