@@ -33,7 +33,7 @@ METRIC = "time steps/s and stencil GB/s at 1e-8 interface residual, chosen vs pl
 
 # DRAM traffic of one strip-solver launch from the committed ncu summary
 # (profiles/strip_solve_nls_well.md), valid only for the source it was taken from.
-NCU_TRAFFIC = {"source_sha1": "2fb3e6e712101a6bf2be5c043cbafd942163ed5b", "bytes_per_launch": 46.758912e6 + 14.358016e6}
+NCU_TRAFFIC = {"source_sha1": "51e991e1a6dbb0f64a16a43cc5e120063bf4d176", "bytes_per_launch": 46.758912e6 + 14.358016e6}
 
 
 def parse():

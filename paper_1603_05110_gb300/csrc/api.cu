@@ -299,11 +299,6 @@ static int strip_solve_finish(dd_nls* h, const StripSolveArgs& a, int nstrips, i
     return DD_NLS_OK;
 }
 
-static int strip_solve(dd_nls* h, StripSolveArgs& a, int nstrips, int nblocks, dd_nls_stats* st, bool count) {
-    const int rc = strip_solve_enqueue(h, a, nstrips, nblocks);
-    return rc ? rc : strip_solve_finish(h, a, nstrips, nblocks, st, count);
-}
-
 static StripSolveArgs base_args(dd_nls* h) {
     StripSolveArgs a{};
     a.g = h->G;

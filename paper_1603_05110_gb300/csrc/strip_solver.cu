@@ -628,7 +628,9 @@ strip_solve_kernel(StripSolveArgs a) {
         }
         loc[2] = (double)rz_re;
         loc[3] = (double)rz_im;
-        if (DW && dwr) loc[0] = (double)rr_f / ((double)inv_sf * (double)inv_sf);
+        if constexpr (DW) {
+            if (dwr) loc[0] = (double)rr_f / ((double)inv_sf * (double)inv_sf);
+        }
         block_sum<4>(loc, s_red);
         if (threadIdx.x == 0) { double* sp = slot_ptr(epoch + 1); sp[0] = loc[0]; sp[1] = loc[1]; sp[2] = loc[2]; sp[3] = loc[3]; }
         ++epoch;
