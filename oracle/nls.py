@@ -279,11 +279,16 @@ def mono_step(prob, u_prev, tol=1e-13, l=None, r=None, region=None, relax=1.0):
 # Schwarz algorithms
 # ----------------------------------------------------------------------------------------
 class Strips:
-    """Omega cut into N equal x-strips (Sec. 2.1, Fig. figsub3)."""
+    """Omega cut into N equal x-strips (Sec. 2.1, Fig. figsub3).
 
-    def __init__(self, prob, N):
+    ``pool`` (optional, from ``strip_pool``): the strip solves of one Schwarz iteration are
+    independent (one MPI rank per strip in Sec. 4), so they may run in worker processes; the
+    arithmetic is the same either way."""
+
+    def __init__(self, prob, N, pool=None):
         assert prob.nx % N == 0, "strips must be equal"
         self.prob, self.N = prob, N
+        self.pool = pool
         self.c = prob.nx // N
         pk = physical_kind(prob)
         self.regions = [Region(prob, j * self.c, self.c,
@@ -304,9 +309,14 @@ class Strips:
         """R(g) of eq. (algo_d): solve every strip, then the flux update of eq. (fluxlr)."""
         Rg = np.zeros_like(g)
         vs, fp_its = [], []
+        tasks = [(j, *self.data(g, j), reg.restrict(u_prev), tol_fp, relax) for j, reg in enumerate(self.regions)]
+        if self.pool is not None:
+            sols = self.pool.map(_pool_solve, tasks)
+        else:
+            sols = [reg.solve(h, l, r, tol=t, relax=rx) for reg, (_, l, r, h, t, rx) in zip(self.regions, tasks)]
         for j, reg in enumerate(self.regions):
             l, r = self.data(g, j)
-            v, phi, q = reg.solve(reg.restrict(u_prev), l, r, tol=tol_fp, relax=relax)
+            v, phi, q = sols[j]
             vs.append(v)
             fp_its.append(q)
             if j > 0:        # new r_{j-1} = -l_j + 2 S v_j(a_j)
@@ -357,6 +367,91 @@ class Strips:
                 cache[key] = self.strip_blocks(j)
             blocks.append(cache[key])
         return blocks
+
+    # -- exact P^{-1} in the cosine basis ---------------------------------------------------
+    def modal_blocks(self):
+        """Per strip, the entries x1..x4 of its L_h blocks on the cosine modes c_k(iy) =
+        cos(k pi iy / ny), k = 0..ny (each block X^{j,a} is diagonal in that basis: the 1D
+        P1 matrices along y with Neumann ends satisfy K_y c_k = lambda_k M_y c_k).
+
+        On mode k the free strip problem (V = 0, f = 0) of eq. (NproblemRobinNL) becomes the
+        1D problem in x  (i alpha M_x - K_x - lambda_k M_x + i rho_k E) a = -e_edge  for a unit
+        datum on one edge, with rho_k = p (Robin) or, after eliminating phi_s of eq. (TCS_phi)
+        (D_s phi_s = M^Gamma zeta on the edge, diagonal on the modes too),
+        rho_k = sum_s a_s - sum_s a_s d_s / (z_k + d_s), z_k = i alpha - lambda_k (S_pade).
+        The outgoing traces of eq. (fluxlr) are -datum + 2 S v with S v = -i rho_k a(edge).
+        Returns a list over strips of arrays (4, ny+1)."""
+        prob = self.prob
+        ny, c = prob.ny, self.c
+        hy = prob.hy
+        k = np.arange(ny + 1)
+        th = np.pi * k / ny if ny > 0 else np.zeros(1)
+        lam = (6.0 / hy ** 2) * (1.0 - np.cos(th)) / (2.0 + np.cos(th))
+        mx, kx = fem.assemble_p1(c, prob.hx)
+        if prob.tc == "robin":
+            rho = np.full(ny + 1, complex(prob.p))
+        else:
+            a, d = pade_coefficients(prob.m, prob.theta)
+            z = 1j * prob.alpha - lam
+            rho = a.sum() - (a[None, :] * d[None, :] / (z[:, None] + d[None, :])).sum(axis=1)
+        cache, out = {}, []
+        for reg in self.regions:
+            key = (reg.kind["l"], reg.kind["r"])
+            if key not in cache:
+                X = np.zeros((4, ny + 1), complex)
+                for kk in range(ny + 1):
+                    B = 1j * prob.alpha * mx - kx - lam[kk] * mx
+                    if key[0] == "tc":
+                        B[0, 0] += 1j * rho[kk]
+                    if key[1] == "tc":
+                        B[c, c] += 1j * rho[kk]
+                    if key[0] == "tc":
+                        e = np.zeros(c + 1, complex)
+                        e[0] = -1.0
+                        al = np.linalg.solve(B, e)
+                        X[0, kk] = -1.0 - 2j * rho[kk] * al[0]
+                        X[2, kk] = -2j * rho[kk] * al[c]
+                    if key[1] == "tc":
+                        e = np.zeros(c + 1, complex)
+                        e[c] = -1.0
+                        ar = np.linalg.solve(B, e)
+                        X[1, kk] = -2j * rho[kk] * ar[0]
+                        X[3, kk] = -1.0 - 2j * rho[kk] * ar[c]
+                cache[key] = X
+            out.append(cache[key])
+        return out
+
+    def modal_P_solve(self, xm, y):
+        """x with (I - L_h) x = y, exactly: cosine transform of every trace, one dense
+        2(N-1) x 2(N-1) solve per mode with the entries of ``modal_blocks``, back-transform."""
+        ny, N = self.prob.ny, self.N
+        n = 2 * (N - 1)
+        if n == 0:
+            return y.copy()
+        jj = np.arange(ny + 1)
+        Z = np.cos(np.pi * np.outer(jj, jj) / ny) if ny > 0 else np.ones((1, 1))
+        D = np.ones(ny + 1)
+        D[0] = D[-1] = 0.5
+        sig = np.diag((Z.T * D) @ Z)
+        yh = (y * D[None, :]) @ Z / sig[None, :]          # coefficients, (n, ny+1)
+        Pk = np.zeros((ny + 1, n, n), complex)
+        Pk[:, np.arange(n), np.arange(n)] = 1.0
+        for j in range(N):
+            X = xm[j]
+            il = 2 * (j - 1) + 1 if j > 0 else None       # l_j
+            ir = 2 * j if j < N - 1 else None              # r_j
+            if j > 0:                                      # rows of the new r_{j-1}
+                if il is not None:
+                    Pk[:, 2 * (j - 1), il] -= X[0]
+                if ir is not None:
+                    Pk[:, 2 * (j - 1), ir] -= X[1]
+            if j < N - 1:                                  # rows of the new l_{j+1}
+                if il is not None:
+                    Pk[:, 2 * j + 1, il] -= X[2]
+                if ir is not None:
+                    Pk[:, 2 * j + 1, ir] -= X[3]
+        xh = np.linalg.solve(Pk, yh.T[:, :, None])[:, :, 0]    # (ny+1, n)
+        return xh.T @ Z.T
 
     def apply_Lh(self, blocks, x):
         y = np.zeros_like(x)
@@ -414,15 +509,20 @@ class StepInfo:
 
 
 def schwarz_step(prob, N, u_prev, g0=None, algorithm="classical", tol=1e-10, max_iter=2000,
-                 strips=None, Lh=None, tol_fp=1e-13, gmres_tol=1e-13, absolute=False, relax=1.0):
+                 strips=None, Lh=None, tol_fp=1e-13, gmres_tol=1e-13, absolute=False, relax=1.0,
+                 psolve="gmres", modal=None):
     """One time step by the classical (eq. algo_d) or preconditioned (eq. algo_pd) algorithm.
 
     Stops at the first k with ||R(g^k) - g^k|| <= tol * ||R(g^k)|| (or <= tol if
-    ``absolute``) and returns u_n built from v^k (the strip solutions for g^k).
+    ``absolute``) and returns u_n built from v^k (the strip solutions for g^k).  The
+    preconditioned update solves P x = y by GMRES on the L_h blocks (``psolve='gmres'``,
+    Sec. 4.2) or exactly in the cosine basis (``psolve='modal'``, the same P).
     """
     st = strips or Strips(prob, N)
     g = st.zero_g() if g0 is None else np.array(g0, dtype=complex)
-    if algorithm == "preconditioned" and Lh is None:
+    if algorithm == "preconditioned" and psolve == "modal" and modal is None:
+        modal = st.modal_blocks()
+    if algorithm == "preconditioned" and psolve != "modal" and Lh is None:
         Lh = st.build_Lh()
     info = StepInfo()
     for k in range(max_iter):
@@ -438,6 +538,8 @@ def schwarz_step(prob, N, u_prev, g0=None, algorithm="classical", tol=1e-10, max
             break
         if algorithm == "classical":
             g = Rg
+        elif psolve == "modal":
+            g = g - st.modal_P_solve(modal, g - Rg)
         else:
             y = (g - Rg).ravel()
             x, its = gmres(lambda z: z - st.apply_Lh(Lh, z.reshape(g.shape)).ravel(), y,
@@ -449,6 +551,33 @@ def schwarz_step(prob, N, u_prev, g0=None, algorithm="classical", tol=1e-10, max
     info.g = Rg
     v = st.assemble(vs)
     return 2.0 * v - u_prev, v, info
+
+
+# ----------------------------------------------------------------------------------------
+# worker processes for the strip solves (one per strip at a time, as one MPI rank per strip)
+# ----------------------------------------------------------------------------------------
+_WORKER = {}
+
+
+def _pool_init(prob, N):
+    _WORKER["prob"], _WORKER["N"], _WORKER["regions"] = prob, N, {}
+
+
+def _pool_solve(task):
+    j, l, r, h, tol, relax = task
+    regs = _WORKER["regions"]
+    if j not in regs:
+        prob, N = _WORKER["prob"], _WORKER["N"]
+        c = prob.nx // N
+        pk = physical_kind(prob)
+        regs[j] = Region(prob, j * c, c, left=pk if j == 0 else "tc", right=pk if j == N - 1 else "tc")
+    return regs[j].solve(h, l, r, tol=tol, relax=relax)
+
+
+def strip_pool(prob, N, processes):
+    """A process pool (spawn start method) whose workers solve strips of ``prob``."""
+    import multiprocessing as mp
+    return mp.get_context("spawn").Pool(processes, initializer=_pool_init, initargs=(prob, N))
 
 
 # ----------------------------------------------------------------------------------------
