@@ -7,21 +7,33 @@ dt = 0.005, interface residual 1e-8.  The chosen form (FP32 inner Krylov, FP64 r
 interface) is timed against the plain FP64 path on the same GPU.
 
 One "step" is one time step of eq. (CNS): every Schwarz iteration, strip solve, flux update
-and interface GMRES of that step.  Inputs are resident in HBM; L2 is flushed (a 512 MB
+and preconditioned update of that step.  Inputs are resident in HBM; L2 is flushed (a 512 MB
 write) before every timed step; each step is timed with CUDA events on the library's stream.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload nls_well|nls_small|gpe_trap|gpe_batch|learned_guess]
 
 Under torchrun (N > 1) every rank runs an independent replica (the path has no cross-GPU
 exchange on one node here), the slowest rank's time counts, and value = N*K / time.
+
+Roofline of the strip solver (the dominant kernel): algorithmic bytes per Krylov iteration of
+a strip are 68 B/node in FP32 (136 B/node in FP64): one complex stencil apply (read x and c,
+write y: 8 + 4 + 8 B) plus six complex vector streams; the nonlinear residual applies in
+between are counted separately at 40 B/node (the FP64 stencil).  achieved = bytes x nodes per
+strip x strip-Krylov iterations / strip-solver time, against the measured HBM copy bandwidth.
+
+The oracle baselines run the FP64 CPU oracle as it stands, its strip solves spread over the
+host cores by worker processes (one strip per task, like one MPI rank per strip), with the exact
+P^{-1} on the cosine modes for the preconditioned algorithm.
 """
 import argparse
-import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -31,12 +43,13 @@ sys.path.insert(0, ROOT)
 
 METRIC = "time steps/s and stencil GB/s at 1e-8 interface residual, chosen vs plain FP64"
 
-# DRAM traffic of one strip-solver launch from the committed ncu summary
-# (profiles/strip_solve_nls_well.md), valid only for the source it was taken from.
-NCU_TRAFFIC = {"source_sha1": "51e991e1a6dbb0f64a16a43cc5e120063bf4d176", "bytes_per_launch": 46.758912e6 + 14.358016e6}
+# algorithmic bytes per node: one Krylov iteration of a strip (stencil + six vector streams),
+# and one FP64 stencil apply of the nonlinear residual
+KRYLOV_BYTES = {"fp32": 68.0, "fp64": 136.0}
+RESIDUAL_BYTES = 40.0
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -44,8 +57,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="nls_well")
     ap.add_argument("--p", type=float, default=None, help="Robin p (default: the workload's)")
-    ap.add_argument("--tc", default="robin", choices=["robin", "pade"], help="transmission operator")
-    ap.add_argument("--pade-m", type=int, default=4)
+    ap.add_argument("--tc", default=None, choices=["robin", "pade"],
+                    help="transmission operator (default: the workload's, else Robin)")
+    ap.add_argument("--pade-m", type=int, default=None, help="Pade order (default: the workload's, else 4)")
     ap.add_argument("--algorithm", default="workload", choices=["workload", "classical", "preconditioned"])
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--fp64-steps", type=int, default=4)
@@ -59,7 +73,19 @@ def parse():
     ap.add_argument("--learn-steps", type=int, default=160, help="learned_guess: steps generated")
     ap.add_argument("--learn-epochs", type=int, default=60)
     ap.add_argument("--max-schwarz", type=int, default=5000)
-    return ap.parse_args()
+    ap.add_argument("--cpu-budget", type=float, default=30.0,
+                    help="seconds of oracle work for the cpu_baseline sample")
+    ap.add_argument("--ref-budget", type=float, default=150.0,
+                    help="seconds of timed oracle steps in the reference arm")
+    args = ap.parse_args(argv)
+    from paper_1603_05110_gb300 import workloads as wl
+    w = wl.WORKLOADS.get(args.workload)
+    extra = w.extra if w is not None else {}
+    if args.tc is None:
+        args.tc = extra.get("tc", "robin")
+    if args.pade_m is None:
+        args.pade_m = extra.get("pade_m", 4)
+    return args
 
 
 def robin_p(w, args):
@@ -79,7 +105,8 @@ def solver_params(w, args, precision, psolve=None, adapt=0.01):
                 max_inner=4000, max_schwarz=400, gmres_tol=1e-6, gmres_restart=30, gmres_max=300,
                 algorithm=binding.PRECONDITIONED if algorithm_of(w, args) == "preconditioned" else binding.CLASSICAL,
                 tc=binding.TC_PADE if pade else binding.TC_ROBIN, pade_m=getattr(args, "pade_m", 4),
-                precision=precision, guess=binding.GUESS_PREVIOUS)
+                precision=precision, guess=binding.GUESS_PREVIOUS, nl_relax=w.extra.get("relax", 1.0),
+                omega_rot=w.extra.get("omega", 0.0))
 
 
 def describe(w, args):
@@ -94,8 +121,8 @@ class Clocks:
 
     def __init__(self, index):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
-                                 f".clocks_{os.getpid()}.csv")
+        fd, self.path = tempfile.mkstemp(prefix="ddnls_clocks_", suffix=".csv")
+        os.close(fd)
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -145,13 +172,6 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def source_sha1():
-    h = hashlib.sha1()
-    for f in ("strip_solver.cu", "common.cuh", "dw.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_1603_05110_gb300", "csrc", f), "rb").read())
-    return h.hexdigest()
-
-
 # ------------------------------------------------------------------- multi-rank helpers
 def max_over_ranks(value, dist=None, device=None):
     """The largest value over all ranks (the slowest rank's time); the value itself at N = 1."""
@@ -169,56 +189,148 @@ def whole_job_rate(world, steps, slowest_ms):
 
 
 # ------------------------------------------------------------------------- oracle timing
-def oracle_strip_sample(w, args, n_strips_timed):
-    """Wall time of the oracle's nonlinear strip solves of the first Schwarz iteration of step 1
-    (zero interface guess), for the first n_strips_timed strips."""
+def host_info():
+    model = platform.processor() or platform.machine()
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu": model}
+
+
+def oracle_problem(w, args, V=None):
     from oracle import nls
-    prob = nls.Problem(xl=w.xl, xr=w.xr, yb=w.yb, yu=w.yu, nx=w.nx, ny=w.ny, dt=w.dt, V=w.V(),
+    return nls.Problem(xl=w.xl, xr=w.xr, yb=w.yb, yu=w.yu, nx=w.nx, ny=w.ny, dt=w.dt, V=w.V() if V is None else V,
                        kappa=w.kappa, lap=w.lap, p=robin_p(w, args),
                        tc="pade" if getattr(args, "tc", "robin") == "pade" else "robin", m=getattr(args, "pade_m", 4))
-    st = nls.Strips(prob, w.n_strips)
-    u0 = w.u0()
-    g = st.zero_g()
-    times = []
-    for j in range(n_strips_timed):
-        reg = st.regions[j]
-        l, r = st.data(g, j)
-        t0 = time.perf_counter()
-        reg.solve(reg.restrict(u0), l, r, tol=1e-11)
-        times.append(time.perf_counter() - t0)
-    return times
+
+
+def oracle_steps(w, args, n_steps, budget_s, warm_steps=0, max_iter_first=None):
+    """The oracle as it stands on the host cores: strip solves of each Schwarz iteration in worker
+    processes, the exact P^{-1} on the cosine modes (preconditioned), strip fixed points to the
+    chosen form's strip tolerance.  warm_steps untimed steps from u0 (zero guess), then up to
+    n_steps timed steps from the previous step's converged interface vector, stopping once
+    budget_s is spent.  max_iter_first: time only that many Schwarz iterations of the first step
+    (a bounded sample of a step too long to run whole).  Returns a dict of what was timed."""
+    from oracle import nls
+    prob = oracle_problem(w, args)
+    procs = max(1, min(os.cpu_count() or 1, w.n_strips))
+    algorithm = algorithm_of(w, args)
+    relax = w.extra.get("relax", 1.0)
+    out = {"processes": procs, "steps": [], "iterations": [], "setup_s": 0.0}
+    with nls.strip_pool(prob, w.n_strips, procs) as pool:
+        st = nls.Strips(prob, w.n_strips, pool=pool)
+        modal = None
+        if algorithm == "preconditioned":
+            t0 = time.perf_counter()
+            modal = st.modal_blocks()
+            out["setup_s"] = time.perf_counter() - t0
+        u, g = w.u0(), None
+        kw = dict(algorithm=algorithm, tol=args.tol, strips=st, psolve="modal", modal=modal, tol_fp=1e-11,
+                  relax=relax)
+        for _ in range(warm_steps):
+            u, _, info = nls.schwarz_step(prob, w.n_strips, u, g0=g, **kw)
+            g = info.g
+        spent = 0.0
+        for k in range(n_steps):
+            t0 = time.perf_counter()
+            if max_iter_first is not None and k == 0:
+                u, _, info = nls.schwarz_step(prob, w.n_strips, u, g0=g, max_iter=max_iter_first, strict=False, **kw)
+            else:
+                u, _, info = nls.schwarz_step(prob, w.n_strips, u, g0=g, **kw)
+            dt_s = time.perf_counter() - t0
+            out["steps"].append(dt_s)
+            out["iterations"].append(info.iterations)
+            out["converged"] = info.converged
+            g = info.g
+            spent += dt_s
+            if spent >= budget_s or not info.converged:
+                break
+    return out
+
+
+def cpu_baseline_line(w, args, gpu_iters_per_step):
+    """A bounded sample of the oracle on the same workload, scaled to steps/s."""
+    hi = host_info()
+    whole = w.nodes() <= 1.2e6 and w.n_strips <= 64
+    if whole:
+        r = oracle_steps(w, args, 1, args.cpu_budget)
+        t, its = r["steps"][0], r["iterations"][0]
+        value = 1.0 / t
+        sample = (f"one whole oracle step: step 1 of {w.name} from u0 with the zero interface guess "
+                  f"({its} Schwarz iterations, {w.n_strips} strip solves each over {r['processes']} worker "
+                  f"processes, exact modal P^-1), {t:.1f} s; cosine-mode set-up {r['setup_s']:.2f} s not counted; "
+                  f"host {hi['cpu']}, {hi['nproc']} cores")
+    else:
+        k = 2
+        r = oracle_steps(w, args, 1, args.cpu_budget, max_iter_first=k)
+        t, its = r["steps"][0], r["iterations"][0]
+        value = 1.0 / (t / its * gpu_iters_per_step)
+        sample = (f"the first {its} Schwarz iterations of step 1 of {w.name} ({w.n_strips} strip solves each over "
+                  f"{r['processes']} worker processes), {t:.1f} s, scaled to the {gpu_iters_per_step:.1f} Schwarz "
+                  f"iterations per step this run measured on the GPU; host {hi['cpu']}, {hi['nproc']} cores")
+    return {"value": value, "unit": "steps/s", "cores": r["processes"], "kind": "oracle", "sample": sample,
+            "host": hi}
 
 
 def run_reference(args, rank):
-    """The oracle as it stands, on the host cores, on bounded samples of the same workload."""
+    """The oracle as it stands, on the host cores, timed on whole steps of the same workload."""
     from paper_1603_05110_gb300 import workloads as wl
-    w = wl.WORKLOADS[args.workload]
     if rank != 0:
         return
-    iters = ITERS_PER_STEP.get(args.workload)
-    samples = []
-    for k in range(args.warmup + args.steps):
-        t = oracle_strip_sample(w, args, 1)[0]
-        if k >= args.warmup:
-            samples.append(t)
-    t_strip = statistics.mean(samples)
-    step_s = t_strip * w.n_strips * iters
-    value = 1.0 / step_s
+    w = wl.WORKLOADS[args.workload]
+    t_start = time.perf_counter()
+    r = oracle_steps(w, args, max(1, args.steps), args.ref_budget, warm_steps=1)
+    n = len(r["steps"])
+    total = sum(r["steps"])
+    value = n / total
+    hi = host_info()
+    sample = (f"{n} whole oracle steps (steps 2..{n + 1} of {w.name}, each from the previous step's converged "
+              f"interface vector, {statistics.mean(r['iterations']):.1f} Schwarz iterations per step, "
+              f"{w.n_strips} strip solves per iteration over {r['processes']} worker processes, exact modal "
+              f"P^-1); step 1 from u0 untimed; cosine-mode set-up {r['setup_s']:.2f} s not counted; "
+              f"host {hi['cpu']}, {hi['nproc']} cores")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
+            "steps": n, "warmup": 1, "ms_per_step": total / n * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": describe(w, args)},
-            "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle",
-                             "sample": f"each step = one oracle nonlinear strip solve (strip 1 of {w.n_strips}, "
-                                       f"Schwarz iteration 1, step 1), scaled by {w.n_strips} strips x {iters} "
-                                       f"Schwarz iterations per step (the GPU arm's measured mean)"},
-            "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "cpu_baseline": {"value": value, "unit": "steps/s", "cores": r["processes"], "kind": "oracle",
+                             "sample": sample, "host": hi},
+            "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "timed_region_s": total, "wall_s": time.perf_counter() - t_start,
+            "note": f"--steps {args.steps} requested; the oracle times whole steps until {args.ref_budget:g} s "
+                    f"of timed steps are spent"}
     print(json.dumps(line), flush=True)
 
 
-# Schwarz iterations per step of the chosen form, measured by this benchmark on a GB300
-# (used to scale the oracle's per-strip sample to steps/s).
-ITERS_PER_STEP = {"nls_well": 6.0, "nls_small": 20.0, "gpe_trap": 5.0}
+# ---------------------------------------------------------------------------- roofline
+def strip_roofline(prof, stats, w, prec, peaks, peak_kind, nodes_per_strip=None):
+    """The strip solver's achieved bandwidth from algorithmic bytes: KRYLOV_BYTES[prec] per node
+    per strip-Krylov iteration, over the solver's CUDA-event time; the residual applies are listed
+    apart at RESIDUAL_BYTES per node (one per correction plus the final check of each strip in each
+    launch)."""
+    nps = nodes_per_strip if nodes_per_strip is not None else (w.nx // w.n_strips + 1) * (w.ny + 1)
+    launches = max(1, prof["strip_solve_launches"])
+    kry = sum(s["krylov_iterations"] for s in stats)
+    nl = sum(s["nl_iterations"] for s in stats)
+    res_applies = nl + launches * w.n_strips
+    t = prof["strip_solve_ms"] * 1e-3
+    kb = KRYLOV_BYTES[prec] * nps * kry
+    rb = RESIDUAL_BYTES * nps * res_applies
+    out = {"kernel": f"strip_solve_kernel<{'float' if prec == 'fp32' else 'double'}>", "bound": "hbm",
+           "achieved": kb / t / 1e9, "unit": "GB/s",
+           "krylov_bytes_per_launch": kb / launches, "ms_per_launch": prof["strip_solve_ms"] / launches,
+           "strip_krylov_iterations": kry, "residual_applies": res_applies,
+           "achieved_with_residual": (kb + rb) / t / 1e9, "traffic": None,
+           "note": f"{KRYLOV_BYTES[prec]:g} B/node per strip-Krylov iteration x {nps} nodes per strip x "
+                   f"iterations / strip-solver time (CUDA events on the library stream); residual applies at "
+                   f"{RESIDUAL_BYTES:g} B/node in achieved_with_residual; traffic: see the ncu summaries"}
+    if peaks is not None:
+        out.update(peak=peaks["hbm_gbs"], frac=out["achieved"] / peaks["hbm_gbs"], peak_source=f"{peak_kind} hbm_gbs")
+    return out
 
 
 # ---------------------------------------------------------------------------- our arm
@@ -309,8 +421,8 @@ def run_ours(args, rank, world, local_rank):
         fp64 = {"value": args.fp64_steps / (sum(ms64) * 1e-3), "unit": "steps/s",
                 "ms_per_step": sum(ms64) / args.fp64_steps,
                 "schwarz_iterations_per_step": statistics.mean(s["last_schwarz_iterations"] for s in st64),
-                "strip_solve_gbs": prof64["strip_solve_bytes"] / (prof64["strip_solve_ms"] * 1e-3) / 1e9,
-                "strip_solve_gflops": prof64["strip_solve_flops"] / (prof64["strip_solve_ms"] * 1e-3) / 1e9}
+                "strip_solve_gbs": strip_roofline(prof64, st64, w, "fp64", None, None)["achieved"],
+                "strip_solve_ms_per_step": prof64["strip_solve_ms"] / args.fp64_steps}
         # the paper-literal path: FP64, L_h from unit solves, P x = y by GMRES (Robin only: the
         # library solves S_pade's preconditioned update by the modal solve)
         if args.tc == "robin" and algorithm_of(w, args) == "preconditioned":
@@ -340,31 +452,12 @@ def run_ours(args, rank, world, local_rank):
 
     dw_used = args.residual == "dw" and args.tc == "robin"     # S_pade keeps the FP64 residual
     peaks, peak_kind = measured_peaks()
-    launches = prof["strip_solve_launches"]
-    per_launch_ms = prof["strip_solve_ms"] / launches
-    per_launch_bytes = prof["strip_solve_bytes"] / launches
-    achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
-    # the committed capture is of the default configuration's kernel instance
-    captured = args.workload == "nls_well" and args.tc == "robin" and args.residual == "dw"
-    traffic = NCU_TRAFFIC["bytes_per_launch"] if captured and NCU_TRAFFIC["source_sha1"] == source_sha1() else None
-    roofline = {"kernel": "strip_solve_kernel<float>", "bound": "hbm", "achieved": achieved,
-                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs",
-                "share_of_step": prof["strip_solve_ms"] / total_ms * world,
-                "note": "algorithmic bytes per node per pass (set-up, residual, Krylov passes, epilogue) x nodes x "
-                        "pass counts; most of the fields stay in the 129 MB L2 between passes, so this is "
-                        "effective bandwidth"}
+    roofline = strip_roofline(prof, stats, w, "fp32", peaks, peak_kind)
+    roofline["share_of_step"] = prof["strip_solve_ms"] / total_ms * world
 
     cpu = None
     if not args.no_cpu and world == 1:
-        ts = oracle_strip_sample(w, args, 2)
-        t_strip = statistics.mean(ts)
-        ips = statistics.mean(iters)
-        cpu_v = 1.0 / (t_strip * w.n_strips * ips)
-        cpu = {"value": cpu_v, "unit": "steps/s", "cores": 1, "kind": "oracle",
-               "sample": f"oracle nonlinear solves of strips 1-2 of {w.n_strips} (Schwarz iteration 1 of step 1, "
-                         f"{statistics.mean(ts):.2f} s each), scaled by {w.n_strips} strips x {ips:.1f} Schwarz "
-                         f"iterations per step (this run's mean); L_h setup and GMRES not included"}
+        cpu = cpu_baseline_line(w, args, statistics.mean(iters))
 
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
@@ -376,7 +469,7 @@ def run_ours(args, rank, world, local_rank):
                    "form": "chosen: FP32-inner/" + ("double-word" if dw_used else "FP64") + "-refine, "
                            + algorithm_of(w, args),
                    "l2": "flushed (512 MB write) before every timed step", "replicas": world},
-        "stencil_gbs": achieved,
+        "stencil_gbs": roofline["achieved"],
         "schwarz_iterations_per_step": statistics.mean(iters),
         "krylov_iterations_per_step": kry / args.steps,
         "nl_iterations_per_step": sum(s["nl_iterations"] for s in stats) / args.steps,

@@ -114,6 +114,26 @@ typedef struct {
                             residual (at most 1e-6, never below nl_tol), and a step converges
                             only once tol_k <= max(nl_tol, nl_adapt x tol).  Same fixed point,
                             cheaper early Schwarz iterations. */
+    /* Rotating frame of the GPE (Sec. 5.2.1, eq. x1Ax, GPE_Trans, u1u).  The solve runs in the
+     * coordinates x~ = A(t)^T x, A(t) the rotation by omega_rot t, where the rotation term of
+     * eq. (GPE) is absent and the trap becomes time dependent. */
+    double omega_rot;    /* omega of eq. (GPE): the angle of A(t) and the -omega <u, L_z u> term of
+                            the energy (stats.energy_lab) */
+    double trap_gx, trap_gy; /* either > 0: the trap V_trap = (gx^2 x^2 + gy^2 y^2)/2 of eq. (GPE) taken
+                            at (x, y) = A(t_n) x~ is added to the potential (eq. Sch sign: V - V_trap),
+                            and step n solves with W_n = (V_n + V_{n-1})/2 of eq. (CNS), t_n = n dt
+                            (n counts committed steps, see dd_nls_set_state).  0, 0: no trap term */
+    int psolve_modes;    /* modal P solve: only the lowest psolve_modes cosine modes are solved with
+                            (I - L_h); the others take P = I (a partially constructed I - L_h, the
+                            paper's closing suggestion).  0 (default): all modes, the exact P */
+    double wait_limit_ms;  /* bound of every device-side wait between blocks of a strip; on expiry the
+                            call returns DD_NLS_ETIMEOUT and commits nothing.  0 (default): 2000 ms */
+    int solver_layout;   /* 0 (default): FP32 Robin strips whose rows split over a cluster of 16 CTAs fit
+                            in their shared memory are solved one strip per thread-block cluster (the
+                            inner Krylov state on chip, partial sums through distributed shared
+                            memory); other strips by one cooperative launch with global-memory
+                            barriers.  1: always the cooperative launch.  Same arithmetic either way
+                            up to the order of the partial sums. */
 } dd_nls_params;
 
 typedef struct {
@@ -126,8 +146,15 @@ typedef struct {
     double residual;              /* last relative interface residual ||R(g)-g||/||R(g)|| */
     double residual_abs;          /* last absolute interface residual ||R(g)-g|| */
     double mass;                  /* u_n^H M u_n of the last committed step */
-    double energy;                /* u^H S u - u^H M_W u - (kappa/2lap) sum w|u|^4, scaled by 1/lap */
+    double energy;                /* u^H S u - u^H M_W u - (kappa/2lap) sum w|u|^4, scaled by 1/lap, with
+                                     W = V(t_n)/lap the potential at the time of u_n */
     double setup_ms;              /* L_h construction (preconditioned), at create */
+    double lz;                    /* <u_n, L_z u_n>, L_z = -i (x d_y - y d_x) (Sec. 5.2.1): nodal
+                                     quadrature, central differences (one-sided on the boundary) */
+    double energy_lab;            /* the energy of eq. (GPE) (its Hamiltonian), lap u^H S u
+                                     - sum w V(t_n)|u|^2 - (kappa/2) sum w |u|^4 - omega_rot lz; for the
+                                     GPE (lap = 1/2, V = -V_trap, kappa = -beta) this is
+                                     int 1/2|grad u|^2 + V_trap|u|^2 + beta/2 |u|^4 - omega u* L_z u */
 } dd_nls_stats;
 
 /* Device time of the library's kernels, accumulated while profiling is on. */
@@ -146,7 +173,7 @@ typedef struct {
 
 /* Fill *p with defaults: NLS (lap=1, kappa=1), Robin p=1, classical, FP64, previous-step
  * guess, tol 1e-10, nl_tol 1e-13 (max_nl 300), inner_tol 1e-6, GMRES restart 30 / tol 1e-10,
- * modal P solve. */
+ * modal P solve on all modes, no rotation and no trap, 2 s device wait limit. */
 void dd_nls_default_params(dd_nls_params* p);
 
 /* Create a solver.  V: real nodal potential (ny+1)*(nx+1) in the sign of eq. (Sch), or
@@ -183,6 +210,13 @@ int dd_nls_set_state(dd_nls* h, const double* u, const double* g, int step, int 
 int dd_nls_get_blocks(dd_nls* h, int strip, double* x, int ptr_kind);
 int dd_nls_get_modal(dd_nls* h, int strip, double* x, int ptr_kind);
 
+/* The lab-frame field u(t_n, x, y) = u~(t_n, A(t_n)^T (x, y)) of eq. (u1u), t_n = n dt the time of
+ * the current state, on the valid zone (xl/sqrt2, xr/sqrt2) x (yb/sqrt2, yu/sqrt2) of Sec. 5.2.1
+ * (inside every rotated copy A(t) Omega of a square domain centred at the origin): out receives
+ * (ny_out+1) rows of (nx_out+1) complex values, x fastest, the Q1 interpolant of the computed u~
+ * at the rotated points.  Errors: EINVAL for nx_out, ny_out < 1 or a NULL out. */
+int dd_nls_lab_frame(dd_nls* h, int nx_out, int ny_out, double* out, int ptr_kind);
+
 int dd_nls_set_profiling(dd_nls* h, int on);
 int dd_nls_get_profile(dd_nls* h, dd_nls_profile* prof);
 
@@ -198,7 +232,10 @@ int dd_nls_get_profile(dd_nls* h, dd_nls_profile* prof);
  * the converged R(g), the next step's guess) are DEVICE pointers in the layouts above;
  * stream may be NULL.  Every call uses the same array: calls that overlap on the GPU race.
  * The first call on a device looks up the array's address (with that device current); make
- * it before any stream capture.  Errors: dd_nls_last_error(NULL) describes them. */
+ * it before any stream capture.  That address is kept until the process exits, so after a
+ * cudaDeviceReset of the device this entry point must not be called again in that process.
+ * The call waits for its stream once per Schwarz iteration (the host decides convergence).
+ * Errors: dd_nls_last_error(NULL) describes them (one message buffer per host thread). */
 int dd_nls_step_noalloc(const dd_nls_params* p, const double* V, double* u, const double* g0,
                         double* g_out, void* stream, dd_nls_stats* stats);
 

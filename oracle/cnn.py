@@ -13,10 +13,35 @@ library documents):
 * guess g0 = 2 g1 - g2 + s1 (out_re + i out_im); training target for a converged gt:
   (gt - 2 g1 + g2)/s1; loss = mean squared error over the 2 output channels.
 Parameters are packed per layer as weights [Cout][Cin][3][3] then biases [Cout].
+
+Arithmetic: FP64 throughout, or (``bf16=True``) with the operands of every convolution rounded
+to BF16 where the definition puts them -- the features, the weights, the ReLU activations and
+the back-propagated output gradients -- and everything else (accumulation, biases, the loss) in
+FP64.  ``adam_step`` is the Adam update (Kingma & Ba) with bias-corrected moments.
 """
 import numpy as np
 
 LAYERS = ((6, 32), (32, 32), (32, 32), (32, 2))
+
+
+def bf16(a):
+    """Nearest BF16 value (ties to even) of the FP32 rounding of a, returned as float64."""
+    u = np.asarray(a, np.float64).astype(np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _ident(a):
+    return a
+
+
+def adam_step(w, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update at step t (1-based): returns (w, m, v)."""
+    m = b1 * m + (1.0 - b1) * g
+    v = b2 * v + (1.0 - b2) * g * g
+    mh = m / (1.0 - b1 ** t)
+    vh = v / (1.0 - b2 ** t)
+    return w - lr * mh / (np.sqrt(vh) + eps), m, v
 
 
 def unpack(params):
@@ -45,31 +70,34 @@ def conv3x3(x, w, b):
     return y + b[:, None, None]
 
 
-def forward(params, x):
+def forward(params, x, bf16_ops=False):
     """Returns (output, list of (input, pre-activation) per layer)."""
+    R = bf16 if bf16_ops else _ident
     layers = unpack(params)
     cache = []
-    a = x
+    a = R(x)
     for i, (w, b) in enumerate(layers):
-        z = conv3x3(a, w, b)
+        z = conv3x3(a, R(w), b)
         cache.append((a, z))
-        a = z if i == len(layers) - 1 else np.maximum(z, 0.0)
+        a = z if i == len(layers) - 1 else R(np.maximum(z, 0.0))
     return a, cache
 
 
-def loss_grad(params, x, tgt):
+def loss_grad(params, x, tgt, bf16_ops=False):
     """Mean squared error and its gradient with respect to the packed parameters."""
-    out, cache = forward(params, x)
+    R = bf16 if bf16_ops else _ident
+    out, cache = forward(params, x, bf16_ops)
     n = out.size
-    d = 2.0 * (out - tgt) / n
+    d = R(2.0 * (out - tgt) / n)
     loss = float(np.mean((out - tgt) ** 2))
     layers = unpack(params)
     grads = [None] * len(layers)
     for i in reversed(range(len(layers))):
         a, z = cache[i]
         if i != len(layers) - 1:
-            d = d * (z > 0)
+            d = R(d * (z > 0))
         w, b = layers[i]
+        w = R(w)
         C, H, W = a.shape
         ap = np.pad(a, ((0, 0), (1, 1), (1, 1)))
         gw = np.zeros_like(w)
@@ -100,7 +128,7 @@ def features(g1, g2, g3, gt=None):
     return x, tgt, s0, s1
 
 
-def guess(params, g1, g2, g3):
+def guess(params, g1, g2, g3, bf16_ops=False):
     x, _, _, s1 = features(g1, g2, g3)
-    out, _ = forward(params, x)
+    out, _ = forward(params, x, bf16_ops)
     return 2 * g1 - g2 + s1 * (out[0] + 1j * out[1])

@@ -399,24 +399,24 @@ class Strips:
             key = (reg.kind["l"], reg.kind["r"])
             if key not in cache:
                 X = np.zeros((4, ny + 1), complex)
-                for kk in range(ny + 1):
-                    B = 1j * prob.alpha * mx - kx - lam[kk] * mx
-                    if key[0] == "tc":
-                        B[0, 0] += 1j * rho[kk]
-                    if key[1] == "tc":
-                        B[c, c] += 1j * rho[kk]
-                    if key[0] == "tc":
-                        e = np.zeros(c + 1, complex)
-                        e[0] = -1.0
-                        al = np.linalg.solve(B, e)
-                        X[0, kk] = -1.0 - 2j * rho[kk] * al[0]
-                        X[2, kk] = -2j * rho[kk] * al[c]
-                    if key[1] == "tc":
-                        e = np.zeros(c + 1, complex)
-                        e[c] = -1.0
-                        ar = np.linalg.solve(B, e)
-                        X[1, kk] = -2j * rho[kk] * ar[0]
-                        X[3, kk] = -1.0 - 2j * rho[kk] * ar[c]
+                # the ny+1 mode problems as one batch of dense (c+1) x (c+1) solves
+                B = (1j * prob.alpha * mx - kx)[None, :, :] - lam[:, None, None] * mx[None, :, :]
+                if key[0] == "tc":
+                    B[:, 0, 0] += 1j * rho
+                if key[1] == "tc":
+                    B[:, c, c] += 1j * rho
+                if key[0] == "tc":
+                    e = np.zeros((ny + 1, c + 1, 1), complex)
+                    e[:, 0, 0] = -1.0
+                    al = np.linalg.solve(B, e)[:, :, 0]
+                    X[0] = -1.0 - 2j * rho * al[:, 0]
+                    X[2] = -2j * rho * al[:, c]
+                if key[1] == "tc":
+                    e = np.zeros((ny + 1, c + 1, 1), complex)
+                    e[:, c, 0] = -1.0
+                    ar = np.linalg.solve(B, e)[:, :, 0]
+                    X[1] = -2j * rho * ar[:, 0]
+                    X[3] = -1.0 - 2j * rho * ar[:, c]
                 cache[key] = X
             out.append(cache[key])
         return out
@@ -506,17 +506,20 @@ class StepInfo:
     fixed_point_its: list = field(default_factory=list)
     gmres_its: list = field(default_factory=list)
     g: np.ndarray = None                              # R(g) at the last iteration
+    converged: bool = True
 
 
 def schwarz_step(prob, N, u_prev, g0=None, algorithm="classical", tol=1e-10, max_iter=2000,
                  strips=None, Lh=None, tol_fp=1e-13, gmres_tol=1e-13, absolute=False, relax=1.0,
-                 psolve="gmres", modal=None):
+                 psolve="gmres", modal=None, strict=True):
     """One time step by the classical (eq. algo_d) or preconditioned (eq. algo_pd) algorithm.
 
     Stops at the first k with ||R(g^k) - g^k|| <= tol * ||R(g^k)|| (or <= tol if
     ``absolute``) and returns u_n built from v^k (the strip solutions for g^k).  The
     preconditioned update solves P x = y by GMRES on the L_h blocks (``psolve='gmres'``,
-    Sec. 4.2) or exactly in the cosine basis (``psolve='modal'``, the same P).
+    Sec. 4.2) or exactly in the cosine basis (``psolve='modal'``, the same P).  With
+    ``strict=False`` a run that reaches ``max_iter`` returns what it has (info.converged False)
+    instead of raising.
     """
     st = strips or Strips(prob, N)
     g = st.zero_g() if g0 is None else np.array(g0, dtype=complex)
@@ -547,7 +550,9 @@ def schwarz_step(prob, N, u_prev, g0=None, algorithm="classical", tol=1e-10, max
             info.gmres_its.append(its)
             g = g - x.reshape(g.shape)
     else:
-        raise RuntimeError("Schwarz iteration did not converge")
+        if strict:
+            raise RuntimeError("Schwarz iteration did not converge")
+        info.converged = False
     info.g = Rg
     v = st.assemble(vs)
     return 2.0 * v - u_prev, v, info
@@ -575,9 +580,24 @@ def _pool_solve(task):
 
 
 def strip_pool(prob, N, processes):
-    """A process pool (spawn start method) whose workers solve strips of ``prob``."""
+    """A process pool (spawn start method) whose workers solve strips of ``prob``; each worker
+    runs its numerical libraries on one thread, so the pool uses ``processes`` cores."""
     import multiprocessing as mp
-    return mp.get_context("spawn").Pool(processes, initializer=_pool_init, initargs=(prob, N))
+    import os
+    saved = {k: os.environ.get(k) for k in _THREAD_VARS}
+    for k in _THREAD_VARS:
+        os.environ[k] = "1"
+    try:
+        return mp.get_context("spawn").Pool(processes, initializer=_pool_init, initargs=(prob, N))
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+_THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
 
 
 # ----------------------------------------------------------------------------------------

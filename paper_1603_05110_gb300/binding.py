@@ -38,6 +38,8 @@ class Params(ctypes.Structure):
         ("gmres_tol", ctypes.c_double), ("gmres_restart", ctypes.c_int), ("gmres_max", ctypes.c_int),
         ("psolve", ctypes.c_int), ("nl_relax", ctypes.c_double), ("nl_picard", ctypes.c_int),
         ("nl_adapt", ctypes.c_double),
+        ("omega_rot", ctypes.c_double), ("trap_gx", ctypes.c_double), ("trap_gy", ctypes.c_double),
+        ("psolve_modes", ctypes.c_int), ("wait_limit_ms", ctypes.c_double), ("solver_layout", ctypes.c_int),
     ]
 
 
@@ -48,6 +50,7 @@ class Stats(ctypes.Structure):
         ("gmres_iterations", ctypes.c_longlong),
         ("residual", ctypes.c_double), ("residual_abs", ctypes.c_double),
         ("mass", ctypes.c_double), ("energy", ctypes.c_double), ("setup_ms", ctypes.c_double),
+        ("lz", ctypes.c_double), ("energy_lab", ctypes.c_double),
     ]
 
     def as_dict(self):
@@ -76,7 +79,7 @@ SYMBOLS = ["dd_nls_default_params", "dd_nls_create", "dd_nls_step", "dd_nls_solv
            "dd_nls_batch_set_profiling", "dd_nls_batch_get_profile", "dd_nls_batch_last_error",
            "dd_nls_batch_destroy", "dd_nls_step_guess", "dd_cnn_create", "dd_cnn_num_params",
            "dd_cnn_set_params", "dd_cnn_get_params", "dd_cnn_guess", "dd_cnn_train_step", "dd_cnn_loss_grad",
-           "dd_cnn_last_error", "dd_cnn_destroy"]
+           "dd_cnn_last_error", "dd_cnn_destroy", "dd_nls_lab_frame"]
 
 _lib = None
 
@@ -107,6 +110,8 @@ def load(path=LIB_PATH):
     lib.dd_nls_get_blocks.restype = ip
     lib.dd_nls_get_modal.argtypes = [vp, ip, vp, ip]
     lib.dd_nls_get_modal.restype = ip
+    lib.dd_nls_lab_frame.argtypes = [vp, ip, ip, vp, ip]
+    lib.dd_nls_lab_frame.restype = ip
     lib.dd_nls_set_profiling.argtypes = [vp, ip]
     lib.dd_nls_set_profiling.restype = ip
     lib.dd_nls_get_profile.argtypes = [vp, ctypes.POINTER(Profile)]
@@ -297,6 +302,14 @@ class Solver:
         x = np.zeros((4, ne), np.complex128)
         self._check(self.lib.dd_nls_get_modal(self.h, strip, x.ctypes.data, PTR_HOST))
         return x
+
+    def lab_frame(self, nx_out, ny_out, out=None):
+        """u(t_n) in the lab frame on the valid zone, (ny_out+1, nx_out+1) complex values."""
+        if out is None:
+            out = np.zeros((ny_out + 1, nx_out + 1), np.complex128)
+        po, ko = _ptr(out, writable=True)
+        self._check(self.lib.dd_nls_lab_frame(self.h, nx_out, ny_out, po, _kind(ko)))
+        return out
 
     def set_profiling(self, on=True):
         self._check(self.lib.dd_nls_set_profiling(self.h, 1 if on else 0))

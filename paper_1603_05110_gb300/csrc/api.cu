@@ -14,6 +14,7 @@
 #include <cmath>
 #include <complex>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -25,10 +26,12 @@
 using namespace ddnls;
 using cplx = std::complex<double>;
 
-static std::string g_create_error;
+// Text of the last error of a call without a handle (a failed create, the no-allocation step),
+// one buffer per host thread: threads that drive different GPUs do not share it.
+static thread_local char g_create_error[512];
 
 namespace ddnls {
-void set_handle_free_error(const char* msg) { g_create_error = msg; }
+void set_handle_free_error(const char* msg) { std::snprintf(g_create_error, sizeof g_create_error, "%s", msg); }
 }  // namespace ddnls
 
 struct dd_nls {
@@ -49,6 +52,12 @@ struct dd_nls {
     // device state
     double2 *u = nullptr, *zeta = nullptr, *rhs0 = nullptr, *gA = nullptr, *gB = nullptr, *gconv = nullptr;
     double* Wn = nullptr;
+    // rotating trap (time-dependent potential): the static part V/lap and the potential at t_n
+    bool trap = false;
+    double* Ws = nullptr;
+    double* Wt = nullptr;
+    int test_skip = 0;          // test hook: block + 1 that skips its first barrier arrival, once
+    unsigned cl_smem = 0;       // cluster mode: dynamic shared memory per CTA (0: cooperative blocks)
     void *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *cT = nullptr;
     void *w1 = nullptr, *s0 = nullptr, *s1 = nullptr, *dv = nullptr;
     bool dw = false;        // double-word residual (FP32 inner, Robin)
@@ -106,7 +115,7 @@ struct dd_nls {
     } while (0)
 
 static int fail(dd_nls* h, int code, const std::string& msg) {
-    if (h) h->error = msg; else g_create_error = msg;
+    if (h) h->error = msg; else set_handle_free_error(msg.c_str());
     return code;
 }
 
@@ -128,16 +137,26 @@ extern "C" void dd_nls_default_params(dd_nls_params* p) {
     p->psolve = DD_NLS_PSOLVE_MODAL;
     p->nl_relax = 1.0;
     p->nl_adapt = 0.0;
+    p->omega_rot = 0.0;
+    p->trap_gx = p->trap_gy = 0.0;
+    p->psolve_modes = 0;
+    p->wait_limit_ms = 0.0;
+    p->solver_layout = 0;
 }
 
+// Test hook: DD_NLS_TEST_FAIL_ALLOC=k makes the k-th device allocation of the next create fail
+// (as cudaMalloc would when the device is full), so that the clean-up path can be tested.
+static thread_local long long g_alloc_count = 0, g_alloc_fail_at = 0;
+
 template <typename T> static cudaError_t dalloc(T** ptr, size_t n) {
+    if (g_alloc_fail_at > 0 && ++g_alloc_count == g_alloc_fail_at) { *ptr = nullptr; return cudaErrorMemoryAllocation; }
     cudaError_t e = cudaMalloc((void**)ptr, std::max<size_t>(n, 1) * sizeof(T));
     if (e == cudaSuccess) e = cudaMemset(*ptr, 0, std::max<size_t>(n, 1) * sizeof(T));
     return e;
 }
 
 static void release(dd_nls* h) {
-    void* ptrs[] = {h->u, h->zeta, h->rhs0, h->gA, h->gB, h->gconv, h->Wn, h->x, h->r, h->z, h->p, h->q, h->cT,
+    void* ptrs[] = {h->u, h->zeta, h->rhs0, h->gA, h->gB, h->gconv, h->Wn, h->Ws, h->Wt, h->x, h->r, h->z, h->p, h->q, h->cT,
                     h->w1, h->s0, h->s1, h->dv, h->zdw, h->ddw, h->bdw, h->wdw, h->bint2,
                     h->part, h->bar, h->status, h->nl_its, h->kry, h->nl_res, h->err, h->red, h->stage,
                     h->X64, h->X32, h->btype, h->V, h->w, h->tmp, h->hdev, h->xs, h->scratch, h->cpart,
@@ -227,13 +246,35 @@ static int schedule(dd_nls* h, const std::vector<double>& w, int nstrips, int ca
 }
 
 // Enqueue one strip-solver launch and the copies of its per-strip results (no host wait).
+// Cluster mode: one cluster per strip, heaviest strips first (the hardware starts clusters in
+// launch order, so strips that need corrections are not left for a second wave).
+static int schedule_clusters(dd_nls* h, const std::vector<double>& w, int nstrips, StripSolveArgs& a) {
+    std::vector<int> order(nstrips);
+    for (int j = 0; j < nstrips; ++j) order[j] = j;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return w[x] > w[y]; });
+    for (int j = 0; j < nstrips; ++j) h->h_blk[j] = order[j];
+    cudaMemcpyAsync(h->d_blk, h->h_blk, sizeof(int) * nstrips, cudaMemcpyHostToDevice, h->s);
+    a.blk_strip = h->d_blk;
+    a.blk_start = nullptr;
+    a.cluster = 1;
+    a.cluster_smem = h->cl_smem;
+    return nstrips;
+}
+
+// blocks a launch of nblocks (strips in cluster mode) actually runs
+static int physical_blocks(const StripSolveArgs& a, int nblocks) { return a.cluster ? nblocks * kClusterCTAs : nblocks; }
+
 static int strip_solve_enqueue(dd_nls* h, StripSolveArgs& a, int nstrips, int nblocks) {
     CK(cudaMemsetAsync(h->bar, 0, sizeof(unsigned) * nstrips, h->s));
     CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->s));
     a.pcyc = h->prof ? h->pcyc : nullptr;
+    a.test_skip_arrival = h->test_skip <= physical_blocks(a, nblocks) ? h->test_skip : 0;
+    h->test_skip = 0;
     if (h->prof) CK(cudaEventRecord(h->ev0, h->s));
     CK(launch_strip_solve(a, nblocks, h->fp32, h->s));
-    if (h->prof) CK(cudaMemcpyAsync(h->h_pcyc.data(), h->pcyc, sizeof(long long) * 8 * nblocks, cudaMemcpyDeviceToHost, h->s));
+    if (h->prof)
+        CK(cudaMemcpyAsync(h->h_pcyc.data(), h->pcyc, sizeof(long long) * 8 * physical_blocks(a, nblocks),
+                           cudaMemcpyDeviceToHost, h->s));
     if (h->prof) CK(cudaEventRecord(h->ev1, h->s));
     CK(cudaMemcpyAsync(h->h_status.data(), h->status, sizeof(int) * nstrips, cudaMemcpyDeviceToHost, h->s));
     CK(cudaMemcpyAsync(h->h_nl.data(), h->nl_its, sizeof(int) * nstrips, cudaMemcpyDeviceToHost, h->s));
@@ -276,10 +317,11 @@ static int strip_solve_finish(dd_nls* h, const StripSolveArgs& a, int nstrips, i
         h->profile.strip_solve_launches += 1;
         h->profile.strip_solve_bytes += bytes;
         h->profile.strip_solve_flops += flops;
+        const int nb = physical_blocks(a, nblocks);
         for (int k = 0; k < 5; ++k) {
             double sum = 0.0;
-            for (int b = 0; b < nblocks; ++b) sum += (double)h->h_pcyc[(size_t)b * 8 + k];
-            h->profile.phase_cycles[k] += sum / nblocks;
+            for (int b = 0; b < nb; ++b) sum += (double)h->h_pcyc[(size_t)b * 8 + k];
+            h->profile.phase_cycles[k] += sum / nb;
         }
     }
     if (st && count) {
@@ -326,6 +368,7 @@ static StripSolveArgs base_args(dd_nls* h) {
     a.kry_its = h->kry;
     a.nl_res = h->nl_res;
     a.err = h->err;
+    a.wait_ns = (unsigned long long)(h->P.wait_limit_ms > 0.0 ? h->P.wait_limit_ms * 1e6 : 2e9);
     a.pcyc = nullptr;
     a.pade_m = h->pade_m;
     a.phi = h->phi;
@@ -605,8 +648,24 @@ static int gmres(dd_nls* h, const double2* b, double2* x, long long* its_out) {
 // ------------------------------------------------------------- Schwarz step
 // Runs the iteration of the current step from the interface vector in h->gA.
 // On success h->zeta holds v and h->gconv the converged R(g).
+// Trap at the rotating-frame nodes: w0 trap(t0) + w1 trap(t1) added to the static V/lap.
+static TrapArgs trap_args(const dd_nls* h, double t0, double w0, double t1, double w1) {
+    TrapArgs t{};
+    t.gx2 = h->P.trap_gx * h->P.trap_gx;
+    t.gy2 = h->P.trap_gy * h->P.trap_gy;
+    t.inv_lap = 1.0 / h->P.lap;
+    t.c0 = std::cos(h->P.omega_rot * t0); t.s0 = std::sin(h->P.omega_rot * t0); t.w0 = w0;
+    t.c1 = std::cos(h->P.omega_rot * t1); t.s1 = std::sin(h->P.omega_rot * t1); t.w1 = w1;
+    return t;
+}
+
 static int schwarz(dd_nls* h, dd_nls_stats* st) {
     const Geom& G = h->G;
+    if (h->trap) {         // W_n = (V(t_n) + V(t_{n-1}))/2 of eq. (CNS) for the step being solved
+        ProfScope ps(h, &h->profile.other_ms);
+        const double tn = (h->step + 1) * h->P.dt, tp = h->step * h->P.dt;
+        CK(launch_trap_potential(G, h->Ws, h->Wn, trap_args(h, tp, 0.5, tn, 0.5), h->s));
+    }
     {
         ProfScope ps(h, &h->profile.other_ms);
         int nb = 1;
@@ -656,7 +715,7 @@ static int schwarz(dd_nls* h, dd_nls_stats* st) {
                 h->dw_res = false;
             }
         }
-        const int nblk = schedule(h, h->wts, G.N, h->chunks, a);
+        const int nblk = h->cl_smem ? schedule_clusters(h, h->wts, G.N, a) : schedule(h, h->wts, G.N, h->chunks, a);
         // the trace exchange is enqueued behind the strip solve, so one host wait covers both
         int rc = strip_solve_enqueue(h, a, G.N, nblk);
         if (rc) return rc;
@@ -702,7 +761,7 @@ static int schwarz(dd_nls* h, dd_nls_stats* st) {
             if (h->P.psolve == DD_NLS_PSOLVE_MODAL) {
                 CK(launch_sub(h->tmp, g, gn, h->nI, h->s));     // y = g - R(g)
                 CK(launch_modal_apply(G, h->fp32, h->Cf, h->Ci, h->Cf32, h->Ci32, h->fac, h->tmp, h->xs, gn, h->s,
-                                      h->cpart, h->fac32));
+                                      h->cpart, h->fac32, h->P.psolve_modes));
                 CK(launch_sub(gn, g, h->xs, h->nI, h->s));
             } else {
                 CK(launch_sub(h->tmp, g, gn, h->nI, h->s));
@@ -735,21 +794,39 @@ static int load_guess(dd_nls* h, const double* g0, int ptr_kind) {
     return DD_NLS_OK;
 }
 
+// Mass, energy (potential at t_n), <u, L_z u> and the energy of eq. (GPE) of the current u_n.
 static int diagnostics(dd_nls* h, dd_nls_stats* st) {
     ProfScope ps(h, &h->profile.other_ms);
     int nb = 1;
-    CK(launch_diagnostics(h->G, h->u, h->Wn, h->part, &nb, h->s));
-    CK(launch_finalize(h->part, nb, 2, h->red, h->s));
-    CK(cudaMemcpyAsync(h->hred, h->red, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+    const double* W = h->Wn;
+    if (h->trap) {
+        const double tn = h->step * h->P.dt;
+        CK(launch_trap_potential(h->G, h->Ws, h->Wt, trap_args(h, tn, 1.0, tn, 0.0), h->s));
+        W = h->Wt;
+    }
+    CK(launch_diagnostics(h->G, h->u, W, h->part, &nb, h->s));
+    CK(launch_lz(h->G, h->u, h->part, nb, 2, h->s));
+    CK(launch_finalize(h->part, nb, 3, h->red, h->s));
+    CK(cudaMemcpyAsync(h->hred, h->red, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->s));
     CK(cudaStreamSynchronize(h->s));
-    if (st) { st->mass = h->hred[0]; st->energy = h->hred[1]; }
+    if (st) {
+        st->mass = h->hred[0];
+        st->energy = h->hred[1];
+        st->lz = h->hred[2];
+        st->energy_lab = h->P.lap * h->hred[1] - h->P.omega_rot * h->hred[2];
+    }
     return DD_NLS_OK;
 }
 
 // ------------------------------------------------------------------- C-ABI
 extern "C" int dd_nls_create(const dd_nls_params* p, const double* V, const double* u0, int ptr_kind, void* stream,
                              dd_nls** out) {
-    g_create_error.clear();
+    set_handle_free_error("");
+    {
+        const char* fa = std::getenv("DD_NLS_TEST_FAIL_ALLOC");
+        g_alloc_count = 0;
+        g_alloc_fail_at = fa ? std::atoll(fa) : 0;
+    }
     if (!p || !u0 || !out) return fail(nullptr, DD_NLS_EINVAL, "dd_nls_create: NULL params, u0 or out");
     *out = nullptr;
     if (p->nx < 1 || p->ny < 1 || p->n_strips < 1 || p->nx % p->n_strips != 0)
@@ -767,6 +844,10 @@ extern "C" int dd_nls_create(const dd_nls_params* p, const double* V, const doub
         return fail(nullptr, DD_NLS_EINVAL, "dd_nls_create: unknown precision");
     if (ptr_kind != DD_NLS_PTR_HOST && ptr_kind != DD_NLS_PTR_DEVICE)
         return fail(nullptr, DD_NLS_EINVAL, "dd_nls_create: unknown ptr_kind");
+    if (!(p->trap_gx >= 0.0) || !(p->trap_gy >= 0.0) || !std::isfinite(p->omega_rot) || p->psolve_modes < 0 ||
+        !(p->wait_limit_ms >= 0.0) || (p->solver_layout != 0 && p->solver_layout != 1))
+        return fail(nullptr, DD_NLS_EINVAL, "dd_nls_create: need trap_gx, trap_gy >= 0, finite omega_rot, "
+                                            "psolve_modes >= 0, wait_limit_ms >= 0, solver_layout 0 or 1");
     const long long c = p->nx / p->n_strips;
     const long long nyn = (long long)p->ny + 1;
     if (nyn > (1 << 20) || c + 1 > (1 << 20) || (c + 1) * nyn > (1LL << 30))
@@ -791,11 +872,21 @@ extern "C" int dd_nls_create(const dd_nls_params* p, const double* V, const doub
     G.p = p->p;
     G.bc_same = p->bc == DD_NLS_BC_SAME;
     G.nx = p->nx;
+    G.xl = p->xl;
+    G.yb = p->yb;
     G.fill_coefficients();
     h->nfield = (long long)G.N * G.nxs * G.P;
+    h->trap = p->trap_gx > 0.0 || p->trap_gy > 0.0;
     h->nI = std::max<long long>(1, (long long)2 * (G.N - 1) * G.P);
 
-    auto bad = [&](int code) { std::string m = h->error; release(h); delete h; g_create_error = m; return code; };
+    auto bad = [&](int code) {
+        std::string m = h->error;
+        release(h);
+        delete h;
+        set_handle_free_error(m.c_str());
+        g_alloc_fail_at = 0;
+        return code;
+    };
 #define CKC(call)                                                                                   \
     do {                                                                                            \
         cudaError_t e_ = (call);                                                                    \
@@ -809,6 +900,10 @@ extern "C" int dd_nls_create(const dd_nls_params* p, const double* V, const doub
     CKC(dalloc(&h->zeta, h->nfield));
     CKC(dalloc(&h->rhs0, h->nfield));
     CKC(dalloc(&h->Wn, h->nfield));
+    if (h->trap) {
+        CKC(dalloc(&h->Ws, h->nfield));
+        CKC(dalloc(&h->Wt, h->nfield));
+    }
     CKC(dalloc(&h->gA, h->nI));
     CKC(dalloc(&h->gB, h->nI));
     CKC(dalloc(&h->gconv, h->nI));
@@ -851,11 +946,17 @@ extern "C" int dd_nls_create(const dd_nls_params* p, const double* V, const doub
     if (maxb < G.N) { h->error = "dd_nls_create: more strips than co-resident blocks of the strip solver"; return bad(DD_NLS_EINVAL); }
     h->maxb = maxb;
     h->chunks = (int)((G.nxs * (long long)G.nyn + 255) / 256);
+    // cluster mode: FP32 Robin strips whose slab of one CTA fits on chip
+    if (h->fp32 && p->tc == DD_NLS_TC_ROBIN && p->solver_layout == 0) {
+        const unsigned sm = strip_cluster_smem(G.nxs, G.nyn);
+        if (sm && strip_cluster_capacity(h->dw, sm) >= 1) h->cl_smem = sm;
+    }
+    const int maxphys = std::max(maxb, G.N * kClusterCTAs);
     CKC(dalloc(&h->part, (size_t)4 * maxb * 4));
     CKC(dalloc(&h->d_blk, (size_t)2 * maxb + 2));
     CKC(cudaMallocHost((void**)&h->h_blk, sizeof(int) * (2 * maxb + 2)));
     CKC(dalloc(&h->bnorm0, G.N));
-    CKC(dalloc(&h->pcyc, (size_t)8 * maxb));
+    CKC(dalloc(&h->pcyc, (size_t)8 * maxphys));
     if (p->tc == DD_NLS_TC_PADE) {
         // a_s = e^{i theta/2} / (m cos^2 phi_s), d_s = e^{i theta} tan^2 phi_s, phi_s = (2s-1) pi/(4m),
         // s = 1..m (eq. TCS; the sums start at s = 1)
@@ -880,7 +981,7 @@ extern "C" int dd_nls_create(const dd_nls_params* p, const double* V, const doub
         CKC(dalloc((char**)&h->qf, nf * s2));
         CKC(dalloc((char**)&h->cTf, (size_t)G.N * 2 * G.P * s1));
     }
-    h->h_pcyc.assign((size_t)8 * maxb, 0);
+    h->h_pcyc.assign((size_t)8 * maxphys, 0);
 
     if (upload_nodal(h, u0, ptr_kind, h->u)) return bad(DD_NLS_ECUDA);
     if (V) {
@@ -888,6 +989,7 @@ extern "C" int dd_nls_create(const dd_nls_params* p, const double* V, const doub
         CKC(cudaMemcpyAsync(h->stage, V, bytes, ptr_kind == DD_NLS_PTR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->s));
         CKC(launch_scatter_real(G, (const double*)h->stage, 1.0 / p->lap, h->Wn, h->s));
     }
+    if (h->trap) CKC(cudaMemcpyAsync(h->Ws, h->Wn, h->nfield * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
     CKC(cudaStreamSynchronize(h->s));
     if (p->algorithm == DD_NLS_PRECONDITIONED && G.N > 1) {
         if (p->psolve != DD_NLS_PSOLVE_GMRES && p->psolve != DD_NLS_PSOLVE_MODAL) {
@@ -897,6 +999,11 @@ extern "C" int dd_nls_create(const dd_nls_params* p, const double* V, const doub
         int rc = p->psolve == DD_NLS_PSOLVE_MODAL ? build_modal(h) : build_Lh(h);
         if (rc) return bad(rc);
     }
+    {
+        const char* sk = std::getenv("DD_NLS_TEST_SKIP_ARRIVAL");
+        h->test_skip = sk ? std::max(0, std::atoi(sk)) : 0;
+    }
+    g_alloc_fail_at = 0;
     *out = h;
     return DD_NLS_OK;
 #undef CKC
@@ -1002,6 +1109,29 @@ extern "C" int dd_nls_get_modal(dd_nls* h, int strip, double* x, int ptr_kind) {
     return DD_NLS_OK;
 }
 
+extern "C" int dd_nls_lab_frame(dd_nls* h, int nx_out, int ny_out, double* out, int ptr_kind) {
+    if (!h) return fail(nullptr, DD_NLS_EINVAL, "dd_nls_lab_frame: NULL handle");
+    if (nx_out < 1 || ny_out < 1 || !out || (ptr_kind != DD_NLS_PTR_HOST && ptr_kind != DD_NLS_PTR_DEVICE))
+        return fail(h, DD_NLS_EINVAL, "dd_nls_lab_frame: need nx_out, ny_out >= 1, an output and a known ptr_kind");
+    const double t = h->step * h->P.dt, r = std::sqrt(2.0);
+    const double c = std::cos(h->P.omega_rot * t), s = std::sin(h->P.omega_rot * t);
+    const size_t n = (size_t)(nx_out + 1) * (ny_out + 1);
+    double2* dst = (double2*)out;
+    double2* tmp = nullptr;
+    if (ptr_kind == DD_NLS_PTR_HOST) {
+        cudaError_t e = cudaMalloc(&tmp, n * sizeof(double2));
+        if (e != cudaSuccess) return fail(h, DD_NLS_ENOMEM, std::string("dd_nls_lab_frame: ") + cudaGetErrorString(e));
+        dst = tmp;
+    }
+    cudaError_t e = launch_lab_frame(h->G, h->u, nx_out, ny_out, h->P.xl / r, h->P.xr / r, h->P.yb / r, h->P.yu / r,
+                                     c, s, dst, h->s);
+    if (e == cudaSuccess && tmp) e = cudaMemcpyAsync(out, tmp, n * sizeof(double2), cudaMemcpyDeviceToHost, h->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
+    if (tmp) cudaFree(tmp);
+    if (e != cudaSuccess) return fail(h, DD_NLS_ECUDA, std::string("dd_nls_lab_frame: ") + cudaGetErrorString(e));
+    return DD_NLS_OK;
+}
+
 extern "C" int dd_nls_set_profiling(dd_nls* h, int on) {
     if (!h) return fail(nullptr, DD_NLS_EINVAL, "dd_nls_set_profiling: NULL handle");
     h->prof = on != 0;
@@ -1025,5 +1155,5 @@ extern "C" void dd_nls_destroy(dd_nls* h) {
 }
 
 extern "C" const char* dd_nls_last_error(const dd_nls* h) {
-    return h ? h->error.c_str() : g_create_error.c_str();
+    return h ? h->error.c_str() : g_create_error;
 }

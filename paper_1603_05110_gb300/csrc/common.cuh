@@ -55,6 +55,7 @@ struct Geom {
     double p;     // Robin parameter
     int bc_same;  // physical x-edges carry S-bar (1) or Neumann (0)
     int nx;       // cells in x over all strips
+    double xl, yb;   // lower-left corner of Omega (node coordinates x = xl + ixg hx, y = yb + iy hy)
     // 1D P1 coefficients (filled on the host so kernels never divide):
     // mass off-diagonal h/6, diagonal 4h/6 inside and 2h/6 at the ends; stiffness
     // off-diagonal -1/h, diagonal 2/h inside and 1/h at the ends; trapezoid weight h.
@@ -190,24 +191,30 @@ __device__ __forceinline__ unsigned long long globaltimer() {
 }
 
 // Barrier among the nblk co-resident blocks that share *ctr.  The counter only grows:
-// the k-th barrier of a launch waits for k*nblk arrivals.  The wait is bounded (about
-// two seconds of wall time); on time-out it records DD_NLS_ETIMEOUT in *err and returns
-// false, and every caller leaves its loop.
-__device__ __forceinline__ bool group_barrier(unsigned* ctr, unsigned target, int* err, int* s_flag) {
+// the k-th barrier of a launch waits for k*nblk arrivals.  The wait is bounded by limit_ns of
+// wall time (globaltimer); on time-out it records DD_NLS_ETIMEOUT in *err and returns false,
+// and every caller leaves its loop.  A block also stops waiting as soon as another block has
+// recorded the time-out.  arrive = false (a test of the time-out path only) waits without
+// adding this block's arrival.
+__device__ __forceinline__ bool group_barrier(unsigned* ctr, unsigned target, int* err, int* s_flag,
+                                              unsigned long long limit_ns, bool arrive = true) {
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        atomicAdd(ctr, 1u);
+        if (arrive) atomicAdd(ctr, 1u);
         int ok = 1;
         if (ld_acquire(ctr) < target) {
             const unsigned long long t0 = globaltimer();
             unsigned spins = 0;
             while (ld_acquire(ctr) < target) {
                 __nanosleep(64);
-                if ((++spins & 255u) == 0 && globaltimer() - t0 > 2000000000ull) {
-                    atomicExch(err, DD_NLS_ETIMEOUT);
-                    ok = 0;
-                    break;
+                if ((++spins & 255u) == 0) {
+                    if (*(volatile int*)err == DD_NLS_ETIMEOUT) { ok = 0; break; }
+                    if (globaltimer() - t0 > limit_ns) {
+                        atomicExch(err, DD_NLS_ETIMEOUT);
+                        ok = 0;
+                        break;
+                    }
                 }
             }
         }
@@ -217,6 +224,118 @@ __device__ __forceinline__ bool group_barrier(unsigned* ctr, unsigned target, in
     }
     __syncthreads();
     return *s_flag != 0;
+}
+
+// ---------------------------------------------------------- thread-block clusters
+// A strip solved by one cluster: its CTAs exchange partial sums and halo rows through
+// distributed shared memory (DSMEM) instead of global memory.
+constexpr int kClusterCTAs = 16;   // CTAs per cluster (non-portable size, opted in at launch)
+
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+// the shared::cluster address of the same variable in CTA `rank` of the cluster
+__device__ __forceinline__ unsigned mapa(unsigned a, unsigned rank) {
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void st_cluster(unsigned a, double v) {
+    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
+}
+__device__ __forceinline__ void st_release_cluster(unsigned a, unsigned v) {
+    asm volatile("st.release.cluster.shared::cluster.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire_cluster(unsigned a) {
+    unsigned v;
+    asm volatile("ld.acquire.cluster.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ float2 ld_cluster_f2(unsigned a) {
+    float2 v;
+    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ void fence_cluster() { asm volatile("fence.acq_rel.cluster;" ::: "memory"); }
+// all threads of all CTAs of the cluster (hardware barrier; every CTA must reach it)
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Exchange slots of one CTA: the partial sums every CTA of the cluster pushes, by epoch parity.
+struct ClusterSlots {
+    double v[2][kClusterCTAs][6];
+    unsigned flag[2][kClusterCTAs];
+};
+
+// Strip-wide sum over the cluster's CTAs of NV values held by thread 0 (v): lanes q < ncta of
+// warp 0 push the values into slot [parity][this rank] of CTA q and then release the epoch flag;
+// each CTA waits (bounded by limit_ns) until all ncta flags of the epoch have arrived and adds
+// the slots in rank order, so every CTA gets the same sums.  The push follows a fence at cluster
+// scope, so everything this CTA wrote before the call (shared or global memory) is visible to
+// the other CTAs once they return.  Results in out[] of every thread (after a __syncthreads).
+// Returns false on time-out (DD_NLS_ETIMEOUT recorded in *err).
+template <int NV>
+__device__ __forceinline__ bool cluster_allreduce(ClusterSlots& sl, const double (&v)[NV], double (&out)[NV],
+                                                  unsigned epoch, int ncta, int* err, unsigned long long limit_ns,
+                                                  double* s_out, int* s_flag) {
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        const unsigned me = cluster_rank(), par = epoch & 1u;
+        double val[NV > 0 ? NV : 1];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) val[k] = __shfl_sync(0xffffffffu, v[k], 0);
+        if (lane < ncta) {
+            fence_cluster();
+            const unsigned dst = mapa(smem_addr(&sl.v[par][me][0]), (unsigned)lane);
+#pragma unroll
+            for (int k = 0; k < NV; ++k) st_cluster(dst + 8u * k, val[k]);
+            st_release_cluster(mapa(smem_addr(&sl.flag[par][me]), (unsigned)lane), epoch);
+        }
+        int ok = 1;
+        if (lane < ncta) {
+            const unsigned fa = mapa(smem_addr(&sl.flag[par][lane]), me);
+            if (ld_acquire_cluster(fa) != epoch) {
+                const unsigned long long t0 = globaltimer();
+                unsigned spins = 0;
+                while (ld_acquire_cluster(fa) != epoch) {
+                    if ((++spins & 63u) == 0) {
+                        if (*(volatile int*)err == DD_NLS_ETIMEOUT) { ok = 0; break; }
+                        if (globaltimer() - t0 > limit_ns) {
+                            atomicExch(err, DD_NLS_ETIMEOUT);
+                            ok = 0;
+                            break;
+                        }
+                    }
+                }
+            }
+        }
+        ok = __all_sync(0xffffffffu, ok);
+        if (lane == 0) {
+            double acc[NV > 0 ? NV : 1];
+#pragma unroll
+            for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+            if (ok)
+                for (int q = 0; q < ncta; ++q) {
+                    (void)ld_acquire_cluster(mapa(smem_addr(&sl.flag[par][q]), me));
+#pragma unroll
+                    for (int k = 0; k < NV; ++k) acc[k] += sl.v[par][q][k];
+                }
+#pragma unroll
+            for (int k = 0; k < NV; ++k) s_out[k] = acc[k];
+            *s_flag = ok;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) out[k] = s_out[k];
+    const bool ok = *s_flag != 0;
+    __syncthreads();
+    return ok;
 }
 
 // Sum slot values written by the nblk blocks of a group (fixed order); result broadcast.

@@ -66,6 +66,13 @@ struct StripSolveArgs {
     long long* kry_its;      // [strips]
     double* nl_res;          // [strips]
     int* err;                // launch-wide error word
+    unsigned long long wait_ns;   // bound of every device-side wait (0: two seconds)
+    int test_skip_arrival;   // > 0: block test_skip_arrival - 1 skips its first barrier arrival (tests
+                             // of the time-out path); 0 otherwise
+    // cluster mode (FP32 Robin, mode 0): one strip per cluster of kClusterCTAs CTAs of 512 threads,
+    // blk_strip[c] = strip of cluster c, cluster_smem bytes of dynamic shared memory per CTA
+    int cluster;
+    unsigned cluster_smem;
     long long* pcyc;         // [gridDim][8] phase cycles (R, A, B, epilogue, waits) or NULL
     // S_pade^m transmission (eq. TCS): auxiliary unknowns phi_{e,s} on both vertical edges
     int pade_m;              // 0: Robin
@@ -83,6 +90,10 @@ cudaError_t launch_dw_to_zeta(const Geom& g, const float4* zdw, double2* zeta, c
 // FP64 finish, i.e. dw_mode 0.
 constexpr double kDWFinish = 1e-12;
 int strip_solve_max_blocks(bool fp32);
+// Cluster mode: dynamic shared memory of one CTA for a strip of nxs x nyn nodes, 0 when the strip's
+// slab does not fit on chip; clusters that can be resident at once (0: cluster mode unavailable).
+unsigned strip_cluster_smem(int nxs, int nyn);
+int strip_cluster_capacity(bool dw, unsigned smem);
 int strip_solve_max_blocks_bs(bool fp32, int block_size);   // Robin kernel with 128 or 256 threads
 
 // ---- auxiliary kernels (aux_kernels.cu)
@@ -128,8 +139,23 @@ cudaError_t launch_modal_setup(const AuxGeom& g, int ntypes, const int* tkind_de
 cudaError_t launch_modal_apply(const AuxGeom& g, bool fp32, const double* Cf, const double* Ci, const float* Cf32,
                                const float* Ci32, const double2* fac, const double2* y, double2* x, double2* tmp,
                                cudaStream_t s, void* cpart,    // cpart: 8 x 2(N-1) x P double2 scratch
-                               const float2* fac32 = nullptr); // FP32 factors for the FP32 forms
+                               const float2* fac32 = nullptr,  // FP32 factors for the FP32 forms
+                               int kmax = 0);                  // > 0: modes k >= kmax take P = I
 cudaError_t launch_to_float(const double* a, float* b, long long n, cudaStream_t s);
+
+// ---- rotating frame of the GPE (rotating.cu)
+// Wout = Ws + (w0 trap(t0) + w1 trap(t1)) inv_lap, trap(t) = -(gx2 x^2 + gy2 y^2)/2 at A(t) x~,
+// with (c_k, s_k) = (cos w t_k, sin w t_k)
+struct TrapArgs {
+    double gx2, gy2, inv_lap;
+    double c0, s0, w0, c1, s1, w1;
+};
+cudaError_t launch_trap_potential(const Geom& g, const double* Ws, double* Wout, const TrapArgs& t, cudaStream_t s);
+// <u, L_z u> partial sums into part[b*4 + slot], nblk blocks
+cudaError_t launch_lz(const Geom& g, const double2* u, double* part, int nblk, int slot, cudaStream_t s);
+// Q1 interpolant of u (strip layout) at A^T (x, y) on (nxo+1) x (nyo+1) points of (x0,x1) x (y0,y1)
+cudaError_t launch_lab_frame(const Geom& g, const double2* u, int nxo, int nyo, double x0, double x1, double y0,
+                             double y1, double c, double s, double2* out, cudaStream_t st);
 
 // GMRES helpers on vectors of length n (complex, FP64)
 cudaError_t launch_dots(const double2* V, long long ld, int k, const double2* w, long long n, double2* out,

@@ -170,11 +170,13 @@ __global__ void modal_factor_kernel(Geom g, const int* __restrict__ btype, const
 // y (modal coefficients of the right side, interface layout [2(N-1)][P]) -> x in place.
 // Sweeps in the precision of the factors: FP64, or FP32 in the FP32 forms (whose cosine
 // transforms around this solve are FP32 already).
+// Modes k >= kmax (kmax > 0) are left as they are: P = I there (the partially constructed
+// I - L_h of the paper's conclusion, on the low modes only).
 template <typename T2>
-__global__ void modal_solve_kernel(Geom g, const T2* __restrict__ fac, double2* __restrict__ y) {
+__global__ void modal_solve_kernel(Geom g, const T2* __restrict__ fac, double2* __restrict__ y, int kmax) {
     const int n = g.nyn, NI = g.N - 1, P = g.P;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
+    if (k >= n || (kmax > 0 && k >= kmax)) return;
     auto F = [&](int i, int e) { return fac[((long long)i * 9 + e) * n + k]; };
     // forward: Yt_i = Y_i - G_i Yt_{i-1}
     auto ld = [&](long long q) { const double2 v = y[q]; return mk<T2>(v.x, v.y); };
@@ -308,15 +310,15 @@ cudaError_t launch_modal_setup(const Geom& g, int ntypes, const int* tkind_dev, 
 
 cudaError_t launch_modal_apply(const Geom& g, bool fp32, const double* Cf, const double* Ci, const float* Cf32,
                                const float* Ci32, const double2* fac, const double2* y, double2* x, double2* tmp,
-                               cudaStream_t s, void* cpart, const float2* fac32) {
+                               cudaStream_t s, void* cpart, const float2* fac32, int kmax) {
     const int ntr = 2 * (g.N - 1);
     cudaError_t e = fp32 ? cosine_apply<float>(g.nyn, ntr, g.P, Cf32, y, tmp, cpart, s)
                          : cosine_apply<double>(g.nyn, ntr, g.P, Cf, y, tmp, cpart, s);
     if (e != cudaSuccess) return e;
     // one warp per block: the per-mode sweeps are FP64 chains, spread over as many SMs as possible
     count_launches(1);
-    if (fp32 && fac32) modal_solve_kernel<float2><<<(g.nyn + 31) / 32, 32, 0, s>>>(g, fac32, tmp);
-    else modal_solve_kernel<double2><<<(g.nyn + 31) / 32, 32, 0, s>>>(g, fac, tmp);
+    if (fp32 && fac32) modal_solve_kernel<float2><<<(g.nyn + 31) / 32, 32, 0, s>>>(g, fac32, tmp, kmax);
+    else modal_solve_kernel<double2><<<(g.nyn + 31) / 32, 32, 0, s>>>(g, fac, tmp, kmax);
     e = fp32 ? cosine_apply<float>(g.nyn, ntr, g.P, Ci32, tmp, x, cpart, s)
              : cosine_apply<double>(g.nyn, ntr, g.P, Ci, tmp, x, cpart, s);
     if (e != cudaSuccess) return e;

@@ -18,7 +18,10 @@
 //    data, and every buffer that must start at zero is cleared by the call itself;
 //  - the first call on a device looks up the array's device address with
 //    cudaGetSymbolAddress (with that device current); make that first call before any
-//    stream capture.
+//    stream capture.  The address is kept for the life of the process: after a
+//    cudaDeviceReset of that device it is stale, so do not call this entry point again
+//    in a process that has reset the device;
+//  - the call waits for its stream once per Schwarz iteration (the host decides convergence).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -86,7 +89,8 @@ extern "C" int dd_nls_step_noalloc(const dd_nls_params* p, const double* V, doub
     if (p->tc != DD_NLS_TC_ROBIN || p->algorithm != DD_NLS_CLASSICAL)
         return noalloc_fail(DD_NLS_EINVAL, "only the classical algorithm with Robin transmission");
     if (p->precision != DD_NLS_FP64 && p->precision != DD_NLS_FP32_INNER)
-        return noalloc_fail(DD_NLS_EINVAL, "unknown precision");
+        return noalloc_fail(DD_NLS_EINVAL, "precision must be DD_NLS_FP64 or DD_NLS_FP32_INNER "
+                                           "(the double-word form DD_NLS_FP32_DW is not supported here)");
     cudaStream_t s = (cudaStream_t)stream;
     const bool fp32 = p->precision == DD_NLS_FP32_INNER;
 
@@ -115,6 +119,8 @@ extern "C" int dd_nls_step_noalloc(const dd_nls_params* p, const double* V, doub
     G.p = p->p;
     G.bc_same = p->bc == DD_NLS_BC_SAME;
     G.nx = p->nx;
+    G.xl = p->xl;
+    G.yb = p->yb;
     G.fill_coefficients();
     const size_t nfield = (size_t)G.N * G.nxs * G.P;
     const size_t nI = (size_t)2 * (G.N - 1) * G.P + 1;
@@ -217,6 +223,7 @@ extern "C" int dd_nls_step_noalloc(const dd_nls_params* p, const double* V, doub
     a.kry_its = kry;
     a.nl_res = nl_res;
     a.err = err;
+    a.wait_ns = (unsigned long long)(p->wait_limit_ms > 0.0 ? p->wait_limit_ms * 1e6 : 2e9);
     a.pcyc = nullptr;
 
     double2* g = gA;

@@ -29,6 +29,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <type_traits>
 
 namespace ddnls {
 
@@ -77,6 +78,16 @@ __device__ __forceinline__ T2 znext(const T2* rr, const T2* ww, const T2* ss, co
     t.y -= al.x * sv.y + al.y * sv.x;
     return cmul(dvv[k], t);
 }
+// r_{k+1} = r_k - alpha (w_k + beta s_{k-1}) and s_k = w_k + beta s_{k-1}, from values (the same
+// arithmetic as znext, so a neighbour's rebuilt z_{k+1} = D^-1 r_{k+1} matches the owner's)
+template <typename T2>
+__device__ __forceinline__ T2 rnext_v(T2 r, T2 w, T2 s, T2 al, T2 be, T2& sv) {
+    sv = cfma(be, s, w);
+    r.x -= al.x * sv.x - al.y * sv.y;
+    r.y -= al.x * sv.y + al.y * sv.x;
+    return r;
+}
+
 // w = A(c) z with z formed on the fly at the 9 stencil nodes (same arithmetic as apply_op)
 template <typename T, typename T2>
 __device__ __forceinline__ T2 apply_op_znext(const T2* rr, const T2* ww, const T2* ss, const T2* dvv, long long idx,
@@ -157,12 +168,26 @@ __device__ __forceinline__ T2 phi_diag_inv(const Coef1<T>& cy, T2 gam, T2 sig, T
     return cinv(cmul(sig, d));
 }
 
-template <typename T, bool PADE, int BS, bool DW = false>
-__global__ void __launch_bounds__(BS, 512 / BS)
+// Nodes per thread of the on-chip Krylov state in cluster mode (x and r in registers).
+constexpr int kOnChipNPT = 9;
+
+// CLU: one strip per thread-block cluster of kClusterCTAs CTAs (launched with cluster dimensions,
+// no cooperative launch).  The CTAs of a strip exchange partial sums through distributed shared
+// memory instead of global-memory barriers, and the single-reduction COCG keeps the strip's
+// Krylov state on chip: each CTA owns a slab of rows [y0, y1) across the strip's whole width,
+// with x and r in registers, z (with one halo row on each side), w, p, s, D^-1 and c in shared
+// memory; the halo rows of z_{k+1} are rebuilt from the neighbours' exported rows of r_k, w_k,
+// s_{k-1} and D^-1, read through DSMEM, so one cluster exchange per iteration suffices.
+template <typename T, bool PADE, int BS, bool DW = false, bool CLU = false>
+__global__ void __launch_bounds__(BS, CLU ? 1 : 512 / BS)
 strip_solve_kernel(StripSolveArgs a) {
     using T2 = typename C2<T>::t;
     __shared__ double s_red[64];
     __shared__ int s_flag;
+    __shared__ typename std::conditional<CLU, ClusterSlots, char>::type s_cl;
+    __shared__ double s_out[8];
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    static_assert(!CLU || (sizeof(T) == 4 && !PADE), "cluster mode is built for the FP32 Robin solver");
     // Krylov scalars: the FP64 recurrences run on thread 0 only (FP64 issues at ~1/64 of the
     // FP32 rate here; eight warps repeating them cost more than the vector work) and reach the
     // block through shared memory: s_ctl = {0 go on | 1 stop, x accepted | 2 error, status},
@@ -170,10 +195,17 @@ strip_solve_kernel(StripSolveArgs a) {
     __shared__ int s_ctl[2];
     __shared__ T s_sc[4];
 
-    const int j = a.blk_strip[blockIdx.x];   // strip of the launch (virtual strip in setup mode)
-    const int b0 = a.blk_start[j];
-    const int bps = a.blk_start[j + 1] - b0; // blocks of this strip (weighted by the host)
-    const int rank = blockIdx.x - b0;
+    // strip of the launch (virtual strip in setup mode); cluster mode: cluster c solves strip
+    // blk_strip[c] and its CTAs are the strip's blocks
+    const int j = CLU ? a.blk_strip[blockIdx.x / kClusterCTAs] : a.blk_strip[blockIdx.x];
+    const int b0 = CLU ? 0 : a.blk_start[j];
+    const int bps = CLU ? kClusterCTAs : a.blk_start[j + 1] - b0; // blocks of this strip (weighted by the host)
+    const int rank = CLU ? (int)cluster_rank() : (int)blockIdx.x - b0;
+    if constexpr (CLU) {
+        // exchange slots start empty; no CTA pushes before every CTA has cleared its own
+        for (int t = threadIdx.x; t < 2 * kClusterCTAs; t += blockDim.x) (&s_cl.flag[0][0])[t] = 0u;
+        cluster_sync_all();
+    }
     // geometry: the launch's, or the instance's when instances are batched
     const StripInfo si = a.sinfo ? a.sinfo[j] : StripInfo{0, j, (long long)j * a.g.sstride(), 0};
     const Geom g = a.geoms ? a.geoms[si.inst] : a.g;
@@ -256,10 +288,46 @@ strip_solve_kernel(StripSolveArgs a) {
 
     unsigned* bar = a.bar + j;
     unsigned epoch = 0;
+    // bounded waits (a.wait_ns, 0: two seconds); the test hook makes block test_skip_arrival - 1
+    // skip its arrival at its first barrier, so that the wait runs out
+    const unsigned long long wait_ns = a.wait_ns ? a.wait_ns : 2000000000ull;
+    bool skip_arrival = a.test_skip_arrival == (int)blockIdx.x + 1;
+    auto gbar = [&](unsigned target) {
+        const bool ok = group_barrier(bar, target, a.err, &s_flag, wait_ns, !skip_arrival);
+        skip_arrival = false;
+        return ok;
+    };
     const int NB = gridDim.x;
     double* part_base = a.part;
     auto slot_ptr = [&](unsigned e) { return part_base + ((size_t)(e & 3u) * NB + blockIdx.x) * 4; };
     auto group_ptr = [&](unsigned e) { return part_base + ((size_t)(e & 3u) * NB + (size_t)b0) * 4; };
+    unsigned cepoch = 0;     // cluster exchange epoch
+    // strip-wide sum of 4 values held by thread 0 (block sums), broadcast to every thread; also
+    // a barrier of the strip's blocks
+    auto strip_sum4 = [&](const double (&v)[4], double (&out)[4]) -> bool {
+        if constexpr (CLU) {
+            return cluster_allreduce<4>(s_cl, v, out, ++cepoch, bps, a.err, wait_ns, s_out, &s_flag);
+        } else {
+            if (threadIdx.x == 0) {
+                double* sp = slot_ptr(epoch + 1);
+                sp[0] = v[0]; sp[1] = v[1]; sp[2] = v[2]; sp[3] = v[3];
+            }
+            ++epoch;
+            if (!gbar(epoch * bps)) return false;
+            group_sum<4>(group_ptr(epoch), bps, out, s_red);
+            return true;
+        }
+    };
+    auto strip_barrier = [&]() -> bool {
+        if constexpr (CLU) {
+            const double z1[1] = {0.0};
+            double o1[1];
+            return cluster_allreduce<1>(s_cl, z1, o1, ++cepoch, bps, a.err, wait_ns, s_out, &s_flag);
+        } else {
+            ++epoch;
+            return gbar(epoch * bps);
+        }
+    };
 
     // edge coefficient rho: i p (Robin) or i sum_s a_s (S_pade)
     double rho_re = 0.0, rho_im = g.p;
@@ -414,12 +482,9 @@ strip_solve_kernel(StripSolveArgs a) {
         const double bs2 = (double)bsc * (double)bsc;
         double lb[4] = {(double)bb / bs2, (double)be / bs2, 0.0, 0.0};
         block_sum<4>(lb, s_red);
-        if (threadIdx.x == 0) { double* sp = slot_ptr(epoch + 1); sp[0] = lb[0]; sp[1] = lb[1]; sp[2] = 0; sp[3] = 0; }
-        ++epoch;
-        if (!group_barrier(bar, epoch * bps, a.err, &s_flag)) status = DD_NLS_ETIMEOUT;
+        double tb[4];
+        if (!strip_sum4(lb, tb)) status = DD_NLS_ETIMEOUT;
         if (!status) {
-            double tb[4];
-            group_sum<4>(group_ptr(epoch), bps, tb, s_red);
             if (a.dw_mode == 2) tb[0] = a.bint2[j];
             else if (a.dw_mode == 1 && rank == 0 && threadIdx.x == 0) a.bint2[j] = tb[0];
             bnorm = sqrt(tb[0] + tb[1]);
@@ -632,12 +697,9 @@ strip_solve_kernel(StripSolveArgs a) {
             if (dwr) loc[0] = (double)rr_f / ((double)inv_sf * (double)inv_sf);
         }
         block_sum<4>(loc, s_red);
-        if (threadIdx.x == 0) { double* sp = slot_ptr(epoch + 1); sp[0] = loc[0]; sp[1] = loc[1]; sp[2] = loc[2]; sp[3] = loc[3]; }
-        ++epoch;
         lap(0);
-        if (!group_barrier(bar, epoch * bps, a.err, &s_flag)) { status = DD_NLS_ETIMEOUT; break; }
         double tot[4];
-        group_sum<4>(group_ptr(epoch), bps, tot, s_red);
+        if (!strip_sum4(loc, tot)) { status = DD_NLS_ETIMEOUT; break; }
         lap(4);
         const double rnorm = sqrt(tot[0]);
         if (need_b) bnorm = sqrt(tot[1]);
@@ -659,8 +721,7 @@ strip_solve_kernel(StripSolveArgs a) {
             dwr = false;
             inv_s = 1.0 / rnorm;
             rprev = INFINITY;
-            ++epoch;
-            if (!group_barrier(bar, epoch * bps, a.err, &s_flag)) { status = DD_NLS_ETIMEOUT; break; }
+            if (!strip_barrier()) { status = DD_NLS_ETIMEOUT; break; }
             continue;       // the next residual is the FP64 one
         }
         if (nl_it > 0 && rnorm > 0.9 * rprev) omega = fmax(0.25, 0.6 * omega);
@@ -670,7 +731,263 @@ strip_solve_kernel(StripSolveArgs a) {
         double rho_r = tot[2], rho_i = tot[3];     // thread 0's copy drives the recurrences
         // inner stopping test in the scaled units of r
         const double target = fmax(a.inner_tol * rnorm, fmax(inner_floor * bnorm, 0.1 * floor_abs)) * inv_s;
-        if (use_sr) {
+        if (CLU && use_sr) {
+            if constexpr (CLU) {
+            // ---- single-reduction COCG with the Krylov state on chip (one strip per cluster).
+            // Slab of this CTA: rows [y0, y1) of every column; node m < M of the slab is column
+            // m / h, row y0 + m % h, and node k of this thread is m = threadIdx.x + k BS.
+            const int H = (nyn + kClusterCTAs - 1) / kClusterCTAs;
+            const int y0 = min(nyn, rank * H), y1 = min(nyn, y0 + H), h = y1 - y0;
+            const int M = h * g.nxs, ZP = H + 2, NX = g.nxs;
+            const float inv_h = h > 0 ? 1.0f / (float)h : 0.f;
+            float2* Zs = (float2*)s_dyn;                  // z with halo rows: [NX][H + 2]
+            float2* Ws = Zs + (size_t)NX * ZP;            // [NX][H]
+            float2* Ps = Ws + (size_t)NX * H;
+            float2* Ss = Ps + (size_t)NX * H;
+            float2* Ds = Ss + (size_t)NX * H;             // D^-1
+            float2* Ex = Ds + (size_t)NX * H;             // exported rows [2 parity][2 side][r w s D^-1][NX]
+            float* Cs = (float*)(Ex + (size_t)16 * NX);   // c of A(c)
+            auto exp_at = [&](int par, int side, int arr, int ix) { return Ex + ((size_t)(par * 2 + side) * 4 + arr) * NX + ix; };
+            const bool has_up = y0 > 0 && h > 0, has_dn = y1 < nyn && h > 0;
+            const unsigned nb_up = (unsigned)(rank - 1), nb_dn = (unsigned)(rank + 1);
+            T2 rreg[kOnChipNPT], xreg[kOnChipNPT];
+            const T2 zeroT = mk<T2>(0.0, 0.0);
+            // load r_0 (scaled residual), D^-1, c of the residual pass; x = p = s_{-1} = 0
+#pragma unroll
+            for (int k = 0; k < kOnChipNPT; ++k) {
+                const int mm = threadIdx.x + k * BS;
+                rreg[k] = zeroT;
+                xreg[k] = zeroT;
+                if (mm >= M) continue;
+                int ix, il;
+                split_node(mm, h, inv_h, ix, il);
+                const long long idx = (long long)ix * P + y0 + il;
+                const int o = ix * H + il;
+                const T2 dvv = dv[idx];
+                rreg[k] = r[idx];
+                Ds[o] = dvv;
+                Cs[o] = cT[idx];
+                Ps[o] = zeroT;
+                Ss[o] = zeroT;
+                Zs[ix * ZP + il + 1] = cmul(dvv, rreg[k]);
+            }
+            // halo rows of z_0 = D^-1 r_0 from global memory (written by the residual pass)
+            for (int ix = threadIdx.x; ix < NX; ix += BS) {
+                if (has_up) Zs[ix * ZP] = cmul(dv[(long long)ix * P + y0 - 1], r[(long long)ix * P + y0 - 1]);
+                if (has_dn) Zs[ix * ZP + h + 1] = cmul(dv[(long long)ix * P + y1], r[(long long)ix * P + y1]);
+            }
+            __syncthreads();
+            // w_0 = A z_0, delta_0 = w_0^T z_0; export the slab's first and last rows (parity 0)
+            T d0r = 0, d0i = 0;
+#pragma unroll
+            for (int k = 0; k < kOnChipNPT; ++k) {
+                const int mm = threadIdx.x + k * BS;
+                if (mm >= M) continue;
+                int ix, il;
+                split_node(mm, h, inv_h, ix, il);
+                const int iy = y0 + il, o = ix * H + il, zo = ix * ZP + il + 1;
+                const Coef1<T> cxT = coef1<T>(ix, c, KXt), cyT = coef1<T>(iy, ny, KYt);
+                T rre, rim;
+                rho_atT(ix, rre, rim);
+                const T2 w0 = apply_op<T, T2>(Zs, zo, ix, iy, c, ny, ZP, cxT, cyT, alphaT, rre, rim, Cs[o]);
+                const T2 zo_v = Zs[zo];
+                Ws[o] = w0;
+                d0r += w0.x * zo_v.x - w0.y * zo_v.y;
+                d0i += w0.x * zo_v.y + w0.y * zo_v.x;
+                if (il == 0) {
+                    *exp_at(0, 0, 0, ix) = rreg[k]; *exp_at(0, 0, 1, ix) = w0; *exp_at(0, 0, 2, ix) = zeroT; *exp_at(0, 0, 3, ix) = Ds[o];
+                }
+                if (il == h - 1) {
+                    *exp_at(0, 1, 0, ix) = rreg[k]; *exp_at(0, 1, 1, ix) = w0; *exp_at(0, 1, 2, ix) = zeroT; *exp_at(0, 1, 3, ix) = Ds[o];
+                }
+            }
+            // thread-0 state of the recurrences
+            double gam_r = rho_r, gam_i = rho_i, al_r = 0.0, al_i = 0.0, be_r = 0.0, be_i = 0.0;
+            {
+                T lT[2] = {d0r, d0i};
+                double l2[2];
+                block_sum_t<T, 2>(lT, l2, s_red);
+                lap(1);
+                const double l4[4] = {l2[0], l2[1], 0.0, 0.0};
+                double dl[4];
+                if (!strip_sum4(l4, dl)) { status = DD_NLS_ETIMEOUT; break; }
+                if (threadIdx.x == 0) {
+                    const double del_r = dl[0], del_i = dl[1];
+                    const double dd2 = del_r * del_r + del_i * del_i;
+                    int ctl = 0, st = 0;
+                    if (!(dd2 > 0.0) || !isfinite(dd2)) {
+                        ctl = 2;
+                        st = isfinite(dd2) ? DD_NLS_EBREAKDOWN : DD_NLS_ENONFINITE;
+                    } else {
+                        al_r = (gam_r * del_r + gam_i * del_i) / dd2;
+                        al_i = (gam_i * del_r - gam_r * del_i) / dd2;
+                    }
+                    s_ctl[0] = ctl;
+                    s_ctl[1] = st;
+                    s_sc[0] = (T)al_r;
+                    s_sc[1] = (T)al_i;
+                }
+            }
+            __syncthreads();
+            lap(4);
+            if (s_ctl[0]) { status = s_ctl[1]; break; }
+            double best = INFINITY;
+            int since = 0;
+            T2 alT = T2{s_sc[0], s_sc[1]}, beT = T2{0, 0};
+            int cstat = 0;
+            for (int it = 0; it < a.max_inner; ++it) {
+                const int pin = it & 1, pout = pin ^ 1;
+                // phase 1: p_k = z_k + beta p_{k-1}, s_k = w_k + beta s_{k-1}, x += alpha p_k,
+                // r_{k+1} = r_k - alpha s_k, z_{k+1} = D^-1 r_{k+1}
+#pragma unroll
+                for (int k = 0; k < kOnChipNPT; ++k) {
+                    const int mm = threadIdx.x + k * BS;
+                    if (mm >= M) continue;
+                    int ix, il;
+                    split_node(mm, h, inv_h, ix, il);
+                    const int o = ix * H + il;
+                    const T2 dvv = Ds[o];
+                    const T2 pn = cfma(beT, Ps[o], cmul(dvv, rreg[k]));
+                    T2 sn;
+                    rreg[k] = rnext_v(rreg[k], Ws[o], Ss[o], alT, beT, sn);
+                    xreg[k] = cfma(alT, pn, xreg[k]);
+                    Ps[o] = pn;
+                    Ss[o] = sn;
+                    Zs[ix * ZP + il + 1] = cmul(dvv, rreg[k]);
+                }
+                // halo rows of z_{k+1}, rebuilt from the neighbours' exported r_k, w_k, s_{k-1}, D^-1
+                for (int ix = threadIdx.x; ix < NX; ix += BS) {
+                    if (has_up) {
+                        T2 sv;
+                        const T2 rr = rnext_v(ld_cluster_f2(mapa(smem_addr(exp_at(pin, 1, 0, ix)), nb_up)),
+                                              ld_cluster_f2(mapa(smem_addr(exp_at(pin, 1, 1, ix)), nb_up)),
+                                              ld_cluster_f2(mapa(smem_addr(exp_at(pin, 1, 2, ix)), nb_up)), alT, beT, sv);
+                        Zs[ix * ZP] = cmul(ld_cluster_f2(mapa(smem_addr(exp_at(pin, 1, 3, ix)), nb_up)), rr);
+                    }
+                    if (has_dn) {
+                        T2 sv;
+                        const T2 rr = rnext_v(ld_cluster_f2(mapa(smem_addr(exp_at(pin, 0, 0, ix)), nb_dn)),
+                                              ld_cluster_f2(mapa(smem_addr(exp_at(pin, 0, 1, ix)), nb_dn)),
+                                              ld_cluster_f2(mapa(smem_addr(exp_at(pin, 0, 2, ix)), nb_dn)), alT, beT, sv);
+                        Zs[ix * ZP + h + 1] = cmul(ld_cluster_f2(mapa(smem_addr(exp_at(pin, 0, 3, ix)), nb_dn)), rr);
+                    }
+                }
+                __syncthreads();
+                // phase 2: w_{k+1} = A z_{k+1}; gamma = r^T z, delta = w^T z, ||r||^2; export rows
+                T g_r = 0, g_i = 0, dlt_r = 0, dlt_i = 0, rr2 = 0;
+#pragma unroll
+                for (int k = 0; k < kOnChipNPT; ++k) {
+                    const int mm = threadIdx.x + k * BS;
+                    if (mm >= M) continue;
+                    int ix, il;
+                    split_node(mm, h, inv_h, ix, il);
+                    const int iy = y0 + il, o = ix * H + il, zo = ix * ZP + il + 1;
+                    const Coef1<T> cxT = coef1<T>(ix, c, KXt), cyT = coef1<T>(iy, ny, KYt);
+                    T rre, rim;
+                    rho_atT(ix, rre, rim);
+                    const T2 wn = apply_op<T, T2>(Zs, zo, ix, iy, c, ny, ZP, cxT, cyT, alphaT, rre, rim, Cs[o]);
+                    const T2 zz = Zs[zo], rv = rreg[k];
+                    Ws[o] = wn;
+                    g_r += rv.x * zz.x - rv.y * zz.y;
+                    g_i += rv.x * zz.y + rv.y * zz.x;
+                    dlt_r += wn.x * zz.x - wn.y * zz.y;
+                    dlt_i += wn.x * zz.y + wn.y * zz.x;
+                    rr2 += rv.x * rv.x + rv.y * rv.y;
+                    if (il == 0) {
+                        *exp_at(pout, 0, 0, ix) = rv; *exp_at(pout, 0, 1, ix) = wn; *exp_at(pout, 0, 2, ix) = Ss[o]; *exp_at(pout, 0, 3, ix) = Ds[o];
+                    }
+                    if (il == h - 1) {
+                        *exp_at(pout, 1, 0, ix) = rv; *exp_at(pout, 1, 1, ix) = wn; *exp_at(pout, 1, 2, ix) = Ss[o]; *exp_at(pout, 1, 3, ix) = Ds[o];
+                    }
+                }
+                T lT[4] = {g_r, g_i, dlt_r, dlt_i};
+                double l4[4];
+                block_sum_t<T, 4>(lT, l4, s_red);
+                T lr[1] = {rr2};
+                double l1[1];
+                block_sum_t<T, 1>(lr, l1, s_red);
+                lap(2);
+                // one exchange per iteration: gamma, delta and ||r||^2; the rows exported above are
+                // visible to the neighbours once it completes
+                double gg[5];
+                {
+                    const double v5[5] = {l4[0], l4[1], l4[2], l4[3], l1[0]};
+                    if (!cluster_allreduce<5>(s_cl, v5, gg, ++cepoch, bps, a.err, wait_ns, s_out, &s_flag)) {
+                        cstat = DD_NLS_ETIMEOUT;
+                        break;
+                    }
+                }
+                if (threadIdx.x == 0) {
+                    int ctl = 0, st = 0;
+                    const double rk = sqrt(gg[4]);
+                    if (!isfinite(gg[4]) || !isfinite(gg[0]) || !isfinite(gg[2])) {
+                        ctl = 2;
+                        st = DD_NLS_ENONFINITE;
+                    } else if (rk <= target) {
+                        ctl = 1;
+                    } else {
+                        if (rk < 0.99 * best) {
+                            best = rk;
+                            since = 0;
+                        } else if (++since >= 32) {
+                            ctl = 3;
+                        }
+                        const double gk2 = gam_r * gam_r + gam_i * gam_i;
+                        if (!ctl && !(gk2 > 0.0)) ctl = 3;
+                        if (!ctl) {
+                            const double nb_r = (gg[0] * gam_r + gg[1] * gam_i) / gk2;
+                            const double nb_i = (gg[1] * gam_r - gg[0] * gam_i) / gk2;
+                            const double a2 = al_r * al_r + al_i * al_i;
+                            const double bg_r = nb_r * gg[0] - nb_i * gg[1], bg_i = nb_r * gg[1] + nb_i * gg[0];
+                            const double t_r = (bg_r * al_r + bg_i * al_i) / a2, t_i = (bg_i * al_r - bg_r * al_i) / a2;
+                            const double den_r = gg[2] - t_r, den_i = gg[3] - t_i;
+                            const double den2 = den_r * den_r + den_i * den_i;
+                            if (!isfinite(den2)) {
+                                ctl = 2;
+                                st = DD_NLS_ENONFINITE;
+                            } else if (!(den2 > 0.0)) {
+                                ctl = 3;
+                            } else {
+                                al_r = (gg[0] * den_r + gg[1] * den_i) / den2;
+                                al_i = (gg[1] * den_r - gg[0] * den_i) / den2;
+                                be_r = nb_r;
+                                be_i = nb_i;
+                                gam_r = gg[0];
+                                gam_i = gg[1];
+                            }
+                        }
+                    }
+                    s_ctl[0] = ctl;
+                    s_ctl[1] = st;
+                    s_sc[0] = (T)al_r;
+                    s_sc[1] = (T)al_i;
+                    s_sc[2] = (T)be_r;
+                    s_sc[3] = (T)be_i;
+                }
+                __syncthreads();
+                lap(4);
+                ++kry;
+                if (s_ctl[0]) {
+                    if (s_ctl[0] == 2) cstat = s_ctl[1];
+                    if (s_ctl[0] == 3) use_sr = false;   // keep x; two-reduction loop from now on
+                    break;
+                }
+                alT = T2{s_sc[0], s_sc[1]};
+                beT = T2{s_sc[2], s_sc[3]};
+            }
+            // x of the slab back to global memory, then every CTA sees the whole correction
+#pragma unroll
+            for (int k = 0; k < kOnChipNPT; ++k) {
+                const int mm = threadIdx.x + k * BS;
+                if (mm >= M) continue;
+                int ix, il;
+                split_node(mm, h, inv_h, ix, il);
+                x[(long long)ix * P + y0 + il] = xreg[k];
+            }
+            if (cstat) { status = cstat; break; }
+            if (!strip_barrier()) { status = DD_NLS_ETIMEOUT; break; }
+            }
+        } else if (use_sr) {
             // Single-reduction COCG (the Chronopoulos-Gear arrangement of CG with the unconjugated
             // bilinear form): s = A p is carried, w = A z is formed in the same pass as the updates
             // with z_{k+1} rebuilt at the stencil neighbours, so one reduction (gamma = r^T z,
@@ -707,7 +1024,7 @@ strip_solve_kernel(StripSolveArgs a) {
             }
             ++epoch;
             lap(1);
-            if (!group_barrier(bar, epoch * bps, a.err, &s_flag)) { status = DD_NLS_ETIMEOUT; break; }
+            if (!gbar(epoch * bps)) { status = DD_NLS_ETIMEOUT; break; }
             // thread-0 state of the recurrences
             double gam_r = rho_r, gam_i = rho_i, al_r = 0.0, al_i = 0.0, be_r = 0.0, be_i = 0.0;
             double best = INFINITY;     // stagnation guard: least ||r|| so far, iterations since
@@ -788,7 +1105,7 @@ strip_solve_kernel(StripSolveArgs a) {
                 }
                 ++epoch;
                 lap(2);
-                if (!group_barrier(bar, epoch * bps, a.err, &s_flag)) { status = DD_NLS_ETIMEOUT; break; }
+                if (!gbar(epoch * bps)) { status = DD_NLS_ETIMEOUT; break; }
                 if (threadIdx.x < 32) {
                     double gg[4], rq[1];
                     group_sum_w0<4>(group_ptr(epoch), bps, gg);
@@ -909,13 +1226,18 @@ strip_solve_kernel(StripSolveArgs a) {
             T lmT[2] = {am_re, am_im};
             double lm[2];
             block_sum_t<T, 2>(lmT, lm, s_red);
-            if (threadIdx.x == 0) { double* sp = slot_ptr(epoch + 1); sp[0] = lm[0]; sp[1] = lm[1]; sp[2] = 0; sp[3] = 0; }
-            ++epoch;
             lap(1);
-            if (!group_barrier(bar, epoch * bps, a.err, &s_flag)) { status = DD_NLS_ETIMEOUT; break; }
+            double mu[4];
+            if constexpr (CLU) {
+                const double lm4[4] = {lm[0], lm[1], 0.0, 0.0};
+                if (!strip_sum4(lm4, mu)) { status = DD_NLS_ETIMEOUT; break; }
+            } else {
+                if (threadIdx.x == 0) { double* sp = slot_ptr(epoch + 1); sp[0] = lm[0]; sp[1] = lm[1]; sp[2] = 0; sp[3] = 0; }
+                ++epoch;
+                if (!gbar(epoch * bps)) { status = DD_NLS_ETIMEOUT; break; }
+                if (threadIdx.x < 32) group_sum_w0<4>(group_ptr(epoch), bps, mu);
+            }
             if (threadIdx.x < 32) {
-                double mu[4];
-                group_sum_w0<4>(group_ptr(epoch), bps, mu);
                 if (threadIdx.x == 0) {
                     const double mu2 = mu[0] * mu[0] + mu[1] * mu[1];
                     int ctl = 0, st = 0;
@@ -975,13 +1297,18 @@ strip_solve_kernel(StripSolveArgs a) {
             T lbT[3] = {b0s, b1s, b2s};
             double lb[3];
             block_sum_t<T, 3>(lbT, lb, s_red);
-            if (threadIdx.x == 0) { double* sp = slot_ptr(epoch + 1); sp[0] = lb[0]; sp[1] = lb[1]; sp[2] = lb[2]; sp[3] = 0; }
-            ++epoch;
             lap(2);
-            if (!group_barrier(bar, epoch * bps, a.err, &s_flag)) { status = DD_NLS_ETIMEOUT; break; }
+            double rb[4];
+            if constexpr (CLU) {
+                const double lb4[4] = {lb[0], lb[1], lb[2], 0.0};
+                if (!strip_sum4(lb4, rb)) { status = DD_NLS_ETIMEOUT; break; }
+            } else {
+                if (threadIdx.x == 0) { double* sp = slot_ptr(epoch + 1); sp[0] = lb[0]; sp[1] = lb[1]; sp[2] = lb[2]; sp[3] = 0; }
+                ++epoch;
+                if (!gbar(epoch * bps)) { status = DD_NLS_ETIMEOUT; break; }
+                if (threadIdx.x < 32) group_sum_w0<4>(group_ptr(epoch), bps, rb);
+            }
             if (threadIdx.x < 32) {
-                double rb[4];
-                group_sum_w0<4>(group_ptr(epoch), bps, rb);
                 if (threadIdx.x == 0) {
                     int ctl = 0, st = 0;
                     const double rr2 = rho_r * rho_r + rho_i * rho_i;
@@ -1052,9 +1379,8 @@ strip_solve_kernel(StripSolveArgs a) {
             }
         }
         inv_s = 1.0 / rnorm;           // scale of the next correction
-        ++epoch;
         lap(3);
-        if (!group_barrier(bar, epoch * bps, a.err, &s_flag)) { status = DD_NLS_ETIMEOUT; break; }
+        if (!strip_barrier()) { status = DD_NLS_ETIMEOUT; break; }
         lap(4);
     }
     if (DW && dwr && a.dw_mode != 0) {
@@ -1086,6 +1412,49 @@ strip_solve_kernel(StripSolveArgs a) {
         a.kry_its[j] = kry;
         a.nl_res[j] = nres;
     }
+    // no CTA leaves while another may still read its shared memory or push into it
+    if constexpr (CLU) cluster_sync_all();
+}
+
+unsigned strip_cluster_smem(int nxs, int nyn) {
+    const long long H = (nyn + kClusterCTAs - 1) / kClusterCTAs;
+    if ((long long)nxs * H > 512LL * kOnChipNPT) return 0;
+    const long long bytes = 8LL * nxs * (H + 2) + 4 * 8LL * nxs * H + 16 * 8LL * nxs + 4LL * nxs * H;
+    return bytes <= 200 * 1024 ? (unsigned)bytes : 0u;
+}
+
+// Cluster kernels: opt in to 16-CTA clusters and to the dynamic shared memory they need.
+static void* cluster_kernel(bool dw) {
+    return dw ? (void*)strip_solve_kernel<float, false, 512, true, true>
+              : (void*)strip_solve_kernel<float, false, 512, false, true>;
+}
+static cudaError_t cluster_prepare(bool dw, unsigned smem) {
+    const void* k = cluster_kernel(dw);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return e;
+}
+static void cluster_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* at, int nstrips, unsigned smem, cudaStream_t s) {
+    cfg = cudaLaunchConfig_t{};
+    cfg.gridDim = dim3(nstrips * kClusterCTAs);
+    cfg.blockDim = dim3(512);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = kClusterCTAs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+}
+int strip_cluster_capacity(bool dw, unsigned smem) {
+    if (smem == 0 || cluster_prepare(dw, smem) != cudaSuccess) { cudaGetLastError(); return 0; }
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute at[1];
+    cluster_config(cfg, at, 1, smem, nullptr);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, cluster_kernel(dw), &cfg) != cudaSuccess) { cudaGetLastError(); return 0; }
+    return n;
 }
 
 template <typename T>
@@ -1094,6 +1463,17 @@ static cudaError_t launch_strip_solve_t(const StripSolveArgs& args, int nblocks,
     void* params[] = {&a};
     dim3 grid(nblocks), block(bs);
     count_launches(1);
+    if (sizeof(T) == 4 && a.cluster && a.mode == 0 && a.pade_m == 0) {
+        // nblocks = strips: one cluster per strip, clusters independent (no cooperative launch)
+        const bool dw = a.zdw != nullptr;
+        cudaError_t e = cluster_prepare(dw, a.cluster_smem);
+        if (e != cudaSuccess) return e;
+        cudaLaunchConfig_t cfg;
+        cudaLaunchAttribute at[1];
+        cluster_config(cfg, at, nblocks, a.cluster_smem, s);
+        return dw ? cudaLaunchKernelEx(&cfg, strip_solve_kernel<float, false, 512, true, true>, a)
+                  : cudaLaunchKernelEx(&cfg, strip_solve_kernel<float, false, 512, false, true>, a);
+    }
     if (a.pade_m > 0)
         return cudaLaunchCooperativeKernel((const void*)strip_solve_kernel<T, true, 256>, grid, dim3(256), params, 0, s);
     if (sizeof(T) == 4 && a.zdw && a.mode == 0)

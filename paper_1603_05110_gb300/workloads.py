@@ -14,7 +14,9 @@ Workloads (sizes are cells; nodes are cells + 1 per direction):
                 {1, 2, 4}, dt = 0.005, 200 steps, same u0 (the initial datum is not stated
                 for this case; the nls_small datum is used).
 * gpe_trap   -- GPE, harmonic trap V_trap = (x^2+y^2)/2, beta = 500, on (-16,16)^2,
-                2048 x 2048 cells, 32 strips, dt = 0.001, 500 steps;
+                2048 x 2048 cells, 32 strips, dt = 0.001, 500 steps, S_pade^8 transmission,
+                preconditioned, rotation omega = 0.4 (isotropic trap: the rotating-frame
+                potential does not change, omega enters the energy);
                 u0 = pi^{-1/2} exp(-(x^2+y^2)/2) exp(i eps xi), eps = 1e-3, xi ~ U[-1,1]
                 per node from numpy's PCG64 with seed 1603.
 * gpe_batch  -- 64 independent GPE instances on (-16,16)^2, dt = 0.002, 100 steps, Robin
@@ -83,7 +85,8 @@ NLS_SMALL = Workload("nls_small", -8.0, 8.0, -8.0, 8.0, 128, 128, 2, 0.01, 10, p
 NLS_WELL = Workload("nls_well", -32.0, 32.0, -32.0, 32.0, 1024, 1024, 16, 0.005, 200, p=2.0,
                     algorithm="preconditioned", potential="well")
 GPE_TRAP = Workload("gpe_trap", -16.0, 16.0, -16.0, 16.0, 2048, 2048, 32, 0.001, 500, lap=0.5,
-                    kappa=-500.0, p=2.0 * np.sqrt(1.0 / 0.001), potential="trap", datum="ground_noise")
+                    kappa=-500.0, p=2.0 * np.sqrt(1.0 / 0.001), algorithm="preconditioned", potential="trap",
+                    datum="ground_noise", extra={"tc": "pade", "pade_m": 8, "omega": 0.4})
 
 WORKLOADS = {w.name: w for w in (NLS_SMALL, NLS_WELL, GPE_TRAP)}
 

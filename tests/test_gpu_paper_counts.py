@@ -1,0 +1,63 @@
+"""The paper's printed iteration counts (Sec. 5.1, Table Influence_p_NL_2_32) through the library.
+
+Setup of Sec. 5.1: Omega = (-16,16) x (-8,8), dx = 1/128, dy = 1/8 (4096 x 128 cells), the cubic
+NLS with V = 0 and f = |u|^2, u0 = exp(-x^2 - y^2 - 0.5 i x), dt = 0.01, Robin p on the interfaces
+and the physical edges, the first time step from the zero interface vector, stopping at
+||g^{k+1} - g^k|| < 1e-10 (absolute).  The classical counts are printed for p = 5, 10, ..., 50 at
+N = 2 and N = 32; the preconditioned algorithm needs 6 at every p.  The paper states neither the
+scaling of its norm nor its quadrature, so this is a soft pin: within 3 of the printed count, and
+the U shape with its minimum at p = 15.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_1603_05110_gb300 import binding  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+P = [5, 10, 15, 20, 25, 30, 35, 40, 45, 50]
+PRINTED = {2: [57, 35, 32, 36, 41, 46, 53, 59, 66, 73], 32: [57, 35, 33, 36, 41, 47, 53, 60, 66, 73]}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1603_05110_gb300 import build
+    build.build()
+    binding.load()
+
+
+def setup(N, p, algorithm):
+    prm = dict(xl=-16.0, xr=16.0, yb=-8.0, yu=8.0, nx=4096, ny=128, n_strips=N, dt=0.01, lap=1.0, kappa=1.0,
+               p=float(p), tol=1e-10, tol_absolute=1, max_schwarz=400, nl_tol=1e-13, guess=binding.GUESS_ZERO,
+               algorithm=algorithm, precision=binding.FP64)
+    x = -16.0 + np.arange(4097) / 128.0
+    y = -8.0 + np.arange(129) / 8.0
+    X, Y = np.meshgrid(x, y, indexing="xy")
+    return prm, np.exp(-X ** 2 - Y ** 2 - 0.5j * X)
+
+
+@pytest.mark.parametrize("N", [2, 32])
+def test_classical_counts_follow_the_printed_table(N):
+    counts = []
+    for p in P:
+        prm, u0 = setup(N, p, binding.CLASSICAL)
+        with binding.Solver(prm, u0) as s:
+            counts.append(s.solve_interface()["last_schwarz_iterations"])
+    print(f"N={N} classical, p=5..50: {counts} (printed {PRINTED[N]})")
+    assert all(abs(c - q) <= 3 for c, q in zip(counts, PRINTED[N])), counts
+    assert int(np.argmin(counts)) == 2
+
+
+@pytest.mark.parametrize("N", [2, 32])
+def test_preconditioned_counts_are_about_six_at_every_p(N):
+    counts = []
+    for p in P:
+        prm, u0 = setup(N, p, binding.PRECONDITIONED)
+        with binding.Solver(prm, u0) as s:
+            counts.append(s.solve_interface()["last_schwarz_iterations"])
+    print(f"N={N} preconditioned, p=5..50: {counts} (printed 6)")
+    assert all(abs(c - 6) <= 3 for c in counts), counts

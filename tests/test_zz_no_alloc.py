@@ -54,6 +54,23 @@ def test_two_noalloc_steps_match_the_ordinary_step(precision):
         torch.cuda.synchronize()
         assert rel(u.cpu().numpy(), ref[k]) < 1e-11
         g.copy_(g_next)
+    # the property the entry point exists for: further steps change neither the device's free
+    # memory nor torch's pool
+    torch.cuda.synchronize()
+    free0, reserved0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_reserved()
+    for _ in range(3):
+        binding.step_noalloc(prm, u, Vd, g0=g, g_out=g_next)
+        g.copy_(g_next)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0 and torch.cuda.memory_reserved() == reserved0
+
+
+def test_noalloc_rejects_the_double_word_form_by_name():
+    w = wl.scaled(wl.NLS_SMALL, 48, 37, n_strips=3)
+    u = torch.zeros(w.ny + 1, w.nx + 1, dtype=torch.complex128, device="cuda:0")
+    with pytest.raises(binding.DDNLSError) as e:
+        binding.step_noalloc(gpu_params(w, precision=binding.FP32_DW), u)
+    assert e.value.code == 1 and "FP32_DW" in str(e.value)
 
 
 def test_noalloc_rejects_a_problem_beyond_its_memory():
