@@ -27,6 +27,7 @@ host cores by worker processes (one strip per task, like one MPI rank per strip)
 P^{-1} on the cosine modes for the preconditioned algorithm.
 """
 import argparse
+import copy
 import json
 import os
 import platform
@@ -509,7 +510,8 @@ def run_batch(args, rank, world, local_rank):
     prms = []
     for w in ws:
         d = solver_params(w, args, binding.FP32_INNER)
-        d.update(p=w.p, algorithm=binding.CLASSICAL, tol=args.tol, max_schwarz=args.max_schwarz, nl_tol=1e-13)
+        d.update(p=w.p, algorithm=binding.CLASSICAL, tol=args.tol, max_schwarz=args.max_schwarz, nl_tol=1e-13,
+                 omega_rot=w.extra["omega"])
         prms.append(d)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -536,9 +538,56 @@ def run_batch(args, rank, world, local_rank):
     clk = clocks.stop()
     prof = b.profile()
     bs, nblk = b.tuning()
+    # e2e through the C-ABI with pinned host buffers: every instance's u_{n-1} in, step, every u_n out
+    hu = [torch.empty(w.ny + 1, w.nx + 1, dtype=torch.complex128, pin_memory=True) for w in ws]
+    for i in range(len(ws)):
+        b.get_u(i, hu[i].numpy())
+    e2e_steps = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for i in range(len(ws)):
+            b.set_u(i, hu[i].numpy())
+        b.step(1)
+        for i in range(len(ws)):
+            b.get_u(i, hu[i].numpy())
+    e2e_s = time.perf_counter() - t0
     b.close()
     total_ms = sum(ms)
     nodes = sum(w.nodes() for w in ws)
+    io_bytes = 16 * nodes
+    # roofline: 68 B/node per strip-Krylov iteration of each instance's strips
+    kb = 0.0
+    for st in stats:
+        for w, s1 in zip(ws, st):
+            kb += KRYLOV_BYTES["fp32"] * (w.nx // w.n_strips + 1) * (w.ny + 1) * s1["krylov_iterations"]
+    peaks, peak_kind = measured_peaks()
+    t_strip = prof["strip_solve_ms"] * 1e-3
+    roofline = {"kernel": "strip_solve_kernel<float> (batched)", "bound": "hbm", "achieved": kb / t_strip / 1e9,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": kb / t_strip / 1e9 / peaks["hbm_gbs"],
+                "peak_source": f"{peak_kind} hbm_gbs", "traffic": None,
+                "share_of_step": prof["strip_solve_ms"] / total_ms,
+                "note": "68 B/node per strip-Krylov iteration x each instance's nodes per strip / strip-solver time"}
+    its_mean = statistics.mean(statistics.mean(s2["last_schwarz_iterations"] for s2 in st) for st in stats)
+    cpu = None
+    if not args.no_cpu and world == 1:
+        # bounded sample: the first 2 Schwarz iterations of step 1 of four instances (strip solves over
+        # the host cores), scaled by each instance's Schwarz iterations per step measured here
+        per_inst = []
+        hi = host_info()
+        for i in (0, 1, 2, 3):
+            w = copy.deepcopy(ws[i])
+            w.extra["relax"] = 0.6          # the oracle's plain fixed point diverges for the strongest beta
+            a2 = parse(["--workload", "nls_well", "--tol", str(args.tol)])
+            a2.p, a2.algorithm, a2.tc = w.p, "classical", "robin"
+            r = oracle_steps(w, a2, 1, args.cpu_budget, max_iter_first=2)
+            its_i = statistics.mean(st[i]["last_schwarz_iterations"] for st in stats)
+            per_inst.append(r["steps"][0] / r["iterations"][0] * its_i)
+        inst_s = statistics.mean(per_inst)
+        cpu = {"value": 1.0 / inst_s, "unit": "instance-steps/s", "cores": r["processes"], "kind": "oracle",
+               "sample": f"the first 2 Schwarz iterations of step 1 of instances 0-3 (strip solves over {r['processes']} "
+                         f"worker processes), scaled by each instance's Schwarz iterations per step measured on the "
+                         f"GPU ({statistics.mean(per_inst):.1f} s per instance-step); host {hi['cpu']}, {hi['nproc']} cores",
+               "host": hi}
     line = {"metric": METRIC, "value": len(ws) * args.steps / (total_ms * 1e-3), "unit": "instance-steps/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -549,10 +598,12 @@ def run_batch(args, rank, world, local_rank):
                        "l2": "flushed (512 MB write) before every timed step"},
             "autotuned": {"block_size": bs, "blocks_per_launch": nblk, "first_call_s": warm_s},
             "schwarz_iterations_per_step_max": max(max(s2["last_schwarz_iterations"] for s2 in st) for st in stats),
-            "schwarz_iterations_per_step_mean": statistics.mean(statistics.mean(s2["last_schwarz_iterations"] for s2 in st)
-                                                                for st in stats),
+            "schwarz_iterations_per_step_mean": its_mean,
             "strip_solve_ms_per_step": prof["strip_solve_ms"] / args.steps,
             "strip_solve_launches_per_step": prof["strip_solve_launches"] / args.steps,
+            "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": {"value": len(ws) * e2e_steps / e2e_s, "unit": "instance-steps/s", "h2d_bytes_per_step": io_bytes,
+                    "d2h_bytes_per_step": io_bytes},
             "gpu_launches": prof["kernel_launches"], "clocks": clk}
     print(json.dumps(line), flush=True)
 

@@ -128,12 +128,12 @@ typedef struct {
                             paper's closing suggestion).  0 (default): all modes, the exact P */
     double wait_limit_ms;  /* bound of every device-side wait between blocks of a strip; on expiry the
                             call returns DD_NLS_ETIMEOUT and commits nothing.  0 (default): 2000 ms */
-    int solver_layout;   /* 0 (default): FP32 Robin strips whose rows split over a cluster of 16 CTAs fit
-                            in their shared memory are solved one strip per thread-block cluster (the
-                            inner Krylov state on chip, partial sums through distributed shared
-                            memory); other strips by one cooperative launch with global-memory
-                            barriers.  1: always the cooperative launch.  Same arithmetic either way
-                            up to the order of the partial sums. */
+    int solver_layout;   /* 0 (default) and 1: one cooperative launch over all strips, blocks split among
+                            strips by expected work, global-memory barriers.  2: FP32 Robin strips whose
+                            rows split over a cluster of 16 CTAs fit in their shared memory are solved
+                            one strip per thread-block cluster (inner Krylov state on chip, partial sums
+                            through distributed shared memory, double-word scalar recurrences); other
+                            strips as in 0.  The converged step is the same either way. */
 } dd_nls_params;
 
 typedef struct {
@@ -255,6 +255,9 @@ int dd_nls_batch_create(int n, const dd_nls_params* params, const double* const*
 int dd_nls_batch_step(dd_nls_batch* b, int nsteps, dd_nls_stats* stats);
 /* u_n of instance i, nodal layout above. */
 int dd_nls_batch_get_u(dd_nls_batch* b, int i, double* u, int ptr_kind);
+/* Replace the state u_{n-1} of instance i (nodal layout above); the interface guess of the next
+ * step is kept.  Host pointers go through a staging buffer the batch owns. */
+int dd_nls_batch_set_u(dd_nls_batch* b, int i, const double* u, int ptr_kind);
 /* The autotuner's choice: threads per block and blocks per launch (0 before the first step). */
 int dd_nls_batch_tuning(dd_nls_batch* b, int* block_size, int* blocks);
 int dd_nls_batch_set_profiling(dd_nls_batch* b, int on);

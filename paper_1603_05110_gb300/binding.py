@@ -79,7 +79,7 @@ SYMBOLS = ["dd_nls_default_params", "dd_nls_create", "dd_nls_step", "dd_nls_solv
            "dd_nls_batch_set_profiling", "dd_nls_batch_get_profile", "dd_nls_batch_last_error",
            "dd_nls_batch_destroy", "dd_nls_step_guess", "dd_cnn_create", "dd_cnn_num_params",
            "dd_cnn_set_params", "dd_cnn_get_params", "dd_cnn_guess", "dd_cnn_train_step", "dd_cnn_loss_grad",
-           "dd_cnn_last_error", "dd_cnn_destroy", "dd_nls_lab_frame"]
+           "dd_cnn_last_error", "dd_cnn_destroy", "dd_nls_lab_frame", "dd_nls_batch_set_u"]
 
 _lib = None
 
@@ -129,6 +129,8 @@ def load(path=LIB_PATH):
     lib.dd_nls_batch_step.restype = ip
     lib.dd_nls_batch_get_u.argtypes = [vp, ip, vp, ip]
     lib.dd_nls_batch_get_u.restype = ip
+    lib.dd_nls_batch_set_u.argtypes = [vp, ip, vp, ip]
+    lib.dd_nls_batch_set_u.restype = ip
     lib.dd_nls_batch_tuning.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.dd_nls_batch_tuning.restype = ip
     lib.dd_nls_batch_set_profiling.argtypes = [vp, ip]
@@ -398,6 +400,12 @@ class Batch:
         po, ko = _ptr(out, writable=True)
         self._check(self.lib.dd_nls_batch_get_u(self.h, i, po, ko))
         return out
+
+    def set_u(self, i, u):
+        if isinstance(u, np.ndarray):
+            u = np.ascontiguousarray(u, dtype=np.complex128)
+        pu, ku = _ptr(u)
+        self._check(self.lib.dd_nls_batch_set_u(self.h, i, pu, ku))
 
     def tuning(self):
         a, b = ctypes.c_int(), ctypes.c_int()

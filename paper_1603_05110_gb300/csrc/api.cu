@@ -845,9 +845,9 @@ extern "C" int dd_nls_create(const dd_nls_params* p, const double* V, const doub
     if (ptr_kind != DD_NLS_PTR_HOST && ptr_kind != DD_NLS_PTR_DEVICE)
         return fail(nullptr, DD_NLS_EINVAL, "dd_nls_create: unknown ptr_kind");
     if (!(p->trap_gx >= 0.0) || !(p->trap_gy >= 0.0) || !std::isfinite(p->omega_rot) || p->psolve_modes < 0 ||
-        !(p->wait_limit_ms >= 0.0) || (p->solver_layout != 0 && p->solver_layout != 1))
+        !(p->wait_limit_ms >= 0.0) || p->solver_layout < 0 || p->solver_layout > 2)
         return fail(nullptr, DD_NLS_EINVAL, "dd_nls_create: need trap_gx, trap_gy >= 0, finite omega_rot, "
-                                            "psolve_modes >= 0, wait_limit_ms >= 0, solver_layout 0 or 1");
+                                            "psolve_modes >= 0, wait_limit_ms >= 0, solver_layout 0, 1 or 2");
     const long long c = p->nx / p->n_strips;
     const long long nyn = (long long)p->ny + 1;
     if (nyn > (1 << 20) || c + 1 > (1 << 20) || (c + 1) * nyn > (1LL << 30))
@@ -947,7 +947,7 @@ extern "C" int dd_nls_create(const dd_nls_params* p, const double* V, const doub
     h->maxb = maxb;
     h->chunks = (int)((G.nxs * (long long)G.nyn + 255) / 256);
     // cluster mode: FP32 Robin strips whose slab of one CTA fits on chip
-    if (h->fp32 && p->tc == DD_NLS_TC_ROBIN && p->solver_layout == 0) {
+    if (h->fp32 && p->tc == DD_NLS_TC_ROBIN && p->solver_layout == 2) {
         const unsigned sm = strip_cluster_smem(G.nxs, G.nyn);
         if (sm && strip_cluster_capacity(h->dw, sm) >= 1) h->cl_smem = sm;
     }

@@ -120,6 +120,7 @@ struct dd_nls_batch {
     int blocks = 1;                 // blocks per launch chosen by the autotuner
     bool tuned = false;
     bool prof = false;
+    double2* stage = nullptr;       // nodal staging buffer of the largest instance (host IO)
     long long launch_base = 0;
     dd_nls_profile profile{};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -148,7 +149,7 @@ static void batch_release(dd_nls_batch* b) {
     void* dev[] = {b->d_geoms, b->d_sinfo, b->d_foff, b->d_goff, b->d_cur, b->d_active, b->u, b->zeta, b->rhs0,
                    b->gbuf, b->Wn, b->x, b->r, b->z, b->p, b->q, b->cT, b->w1, b->s0, b->s1, b->dv, b->part,
                    b->bscale, b->bnorm0, b->res,
-                   b->nl_res, b->bar, b->status, b->nl_its, b->err, b->d_blk, b->kry, b->d_tol};
+                   b->nl_res, b->bar, b->status, b->nl_its, b->err, b->d_blk, b->kry, b->d_tol, b->stage};
     for (void* p : dev)
         if (p) cudaFree(p);
     void* host[] = {b->h_blk, b->h_cur, b->h_active, b->h_res, b->h_bn, b->h_tol};
@@ -432,8 +433,8 @@ extern "C" int dd_nls_batch_create(int n, const dd_nls_params* params, const dou
     // inputs: one staging buffer of the largest nodal field, per instance scatter
     size_t maxnodes = 0;
     for (int i = 0; i < n; ++i) maxnodes = std::max(maxnodes, (size_t)(params[i].nx + 1) * (params[i].ny + 1));
-    double2* stage = nullptr;
-    BCKC(cudaMalloc(&stage, sizeof(double2) * maxnodes));
+    BCKC(cudaMalloc(&b->stage, sizeof(double2) * maxnodes));
+    double2* stage = b->stage;
     const cudaMemcpyKind kind = ptr_kind == DD_NLS_PTR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < n && e == cudaSuccess; ++i) {
@@ -446,7 +447,6 @@ extern "C" int dd_nls_batch_create(int n, const dd_nls_params* params, const dou
         }
         if (!e) e = cudaStreamSynchronize(b->s);
     }
-    cudaFree(stage);
     BCKC(e);
     *out = b;
     return DD_NLS_OK;
@@ -555,16 +555,24 @@ extern "C" int dd_nls_batch_step(dd_nls_batch* b, int nsteps, dd_nls_stats* stat
 extern "C" int dd_nls_batch_get_u(dd_nls_batch* b, int i, double* u, int ptr_kind) {
     if (!b || i < 0 || i >= b->n || !u) return bfail(b, DD_NLS_EINVAL, "dd_nls_batch_get_u: bad arguments");
     const size_t nodes = (size_t)(b->P[i].nx + 1) * (b->P[i].ny + 1);
-    double2* stage = nullptr;
     if (ptr_kind == DD_NLS_PTR_DEVICE) {
         BCK(launch_gather_u(b->G[i], b->u + b->foff[i], (double2*)u, b->s));
     } else {
-        BCK(cudaMalloc(&stage, sizeof(double2) * nodes));
-        cudaError_t e = launch_gather_u(b->G[i], b->u + b->foff[i], stage, b->s);
-        if (!e) e = cudaMemcpyAsync(u, stage, sizeof(double2) * nodes, cudaMemcpyDeviceToHost, b->s);
-        if (!e) e = cudaStreamSynchronize(b->s);
-        cudaFree(stage);
-        BCK(e);
+        BCK(launch_gather_u(b->G[i], b->u + b->foff[i], b->stage, b->s));
+        BCK(cudaMemcpyAsync(u, b->stage, sizeof(double2) * nodes, cudaMemcpyDeviceToHost, b->s));
+    }
+    BCK(cudaStreamSynchronize(b->s));
+    return DD_NLS_OK;
+}
+
+extern "C" int dd_nls_batch_set_u(dd_nls_batch* b, int i, const double* u, int ptr_kind) {
+    if (!b || i < 0 || i >= b->n || !u) return bfail(b, DD_NLS_EINVAL, "dd_nls_batch_set_u: bad arguments");
+    const size_t nodes = (size_t)(b->P[i].nx + 1) * (b->P[i].ny + 1);
+    if (ptr_kind == DD_NLS_PTR_DEVICE) {
+        BCK(launch_scatter_u(b->G[i], (const double2*)u, b->u + b->foff[i], b->s));
+    } else {
+        BCK(cudaMemcpyAsync(b->stage, u, sizeof(double2) * nodes, cudaMemcpyHostToDevice, b->s));
+        BCK(launch_scatter_u(b->G[i], b->stage, b->u + b->foff[i], b->s));
     }
     BCK(cudaStreamSynchronize(b->s));
     return DD_NLS_OK;

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include "../../include/dd_nls.h"
+#include "dw.cuh"
 
 namespace ddnls {
 
@@ -336,6 +337,108 @@ __device__ __forceinline__ bool cluster_allreduce(ClusterSlots& sl, const double
     const bool ok = *s_flag != 0;
     __syncthreads();
     return ok;
+}
+
+// The same exchange for double-word values (pairs of FP32 numbers, ~48 bits): the sums over the
+// cluster are formed with the accurate double-word addition in rank order, so every CTA gets the
+// same result without any FP64 instruction (GB300 runs FP64 at ~1/64 of the FP32 rate, and these
+// exchanges sit on the critical path of every Krylov iteration).  v valid in thread 0; out in
+// every thread.
+struct __align__(16) ClusterSlotsDW {
+    float v[2][kClusterCTAs][12];
+    unsigned flag[2][kClusterCTAs];
+};
+template <int NV>
+__device__ __forceinline__ bool cluster_allreduce_dw(ClusterSlotsDW& sl, const dw (&v)[NV], dw (&out)[NV],
+                                                     unsigned epoch, int ncta, int* err, unsigned long long limit_ns,
+                                                     float* s_out, int* s_flag) {
+    static_assert(NV <= 6, "six double words per slot");
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        const unsigned me = cluster_rank(), par = epoch & 1u;
+        float vh[NV], vl[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            vh[k] = __shfl_sync(0xffffffffu, v[k].h, 0);
+            vl[k] = __shfl_sync(0xffffffffu, v[k].l, 0);
+        }
+        if (lane < ncta) {
+            fence_cluster();
+            const unsigned dst = mapa(smem_addr(&sl.v[par][me][0]), (unsigned)lane);
+#pragma unroll
+            for (int k = 0; k < NV; ++k)
+                asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(dst + 8u * k), "f"(vh[k]), "f"(vl[k]) : "memory");
+            st_release_cluster(mapa(smem_addr(&sl.flag[par][me]), (unsigned)lane), epoch);
+        }
+        int ok = 1;
+        if (lane < ncta) {
+            const unsigned fa = mapa(smem_addr(&sl.flag[par][lane]), me);
+            if (ld_acquire_cluster(fa) != epoch) {
+                const unsigned long long t0 = globaltimer();
+                unsigned spins = 0;
+                while (ld_acquire_cluster(fa) != epoch) {
+                    if ((++spins & 63u) == 0) {
+                        if (*(volatile int*)err == DD_NLS_ETIMEOUT) { ok = 0; break; }
+                        if (globaltimer() - t0 > limit_ns) {
+                            atomicExch(err, DD_NLS_ETIMEOUT);
+                            ok = 0;
+                            break;
+                        }
+                    }
+                }
+            }
+        }
+        ok = __all_sync(0xffffffffu, ok);
+        if (lane == 0) {
+            dw acc[NV];
+#pragma unroll
+            for (int k = 0; k < NV; ++k) acc[k] = {0.f, 0.f};
+            if (ok)
+                for (int q = 0; q < ncta; ++q) {
+                    (void)ld_acquire_cluster(mapa(smem_addr(&sl.flag[par][q]), me));
+#pragma unroll
+                    for (int k = 0; k < NV; ++k) acc[k] = dw_add(acc[k], {sl.v[par][q][2 * k], sl.v[par][q][2 * k + 1]});
+                }
+#pragma unroll
+            for (int k = 0; k < NV; ++k) { s_out[2 * k] = acc[k].h; s_out[2 * k + 1] = acc[k].l; }
+            *s_flag = ok;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) out[k] = {s_out[2 * k], s_out[2 * k + 1]};
+    const bool ok = *s_flag != 0;
+    __syncthreads();
+    return ok;
+}
+
+// Block sum of NV FP32 values: warp shuffles in FP32, then the warps' partials added in
+// double words by warp 0 (fixed order); valid in thread 0.  smem: 16 * NV floats at least.
+template <int NV>
+__device__ __forceinline__ void block_sum_dw(float (&v)[NV], dw (&out)[NV], float* smem) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) smem[wid * NV + k] = v[k];
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            dw s = {lane < nw ? smem[lane * NV + k] : 0.f, 0.f};
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const dw t = {__shfl_down_sync(0xffffffffu, s.h, o), __shfl_down_sync(0xffffffffu, s.l, o)};
+                s = dw_add(s, t);
+            }
+            out[k] = s;
+        }
+    }
+    __syncthreads();
 }
 
 // Sum slot values written by the nblk blocks of a group (fixed order); result broadcast.

@@ -90,7 +90,33 @@ __device__ __forceinline__ dw dw_from_bits(double v) {
     return fast_two_sum(h, __uint_as_float(__float_as_uint(l) | sgn));
 }
 
+// 1/b: the FP32 reciprocal r0 refined by one Newton step carried in double words,
+// r = r0 + r0 (1 - b r0); relative error O(u^2) while b and 1/b stay normal
+__device__ __forceinline__ dw dw_recip(dw b) {
+    const float r0 = __frcp_rn(b.h);
+    const dw e = dw_sub({1.f, 0.f}, dw_mul_f(b, r0));
+    return dw_add({r0, 0.f}, dw_mul_f(e, r0));
+}
+
 __device__ __forceinline__ cdw cdw_add(const cdw& a, const cdw& b) { return {dw_add(a.x, b.x), dw_add(a.y, b.y)}; }
+// complex products and quotients of double words (the Krylov scalar recurrences)
+__device__ __forceinline__ cdw cdw_mul(const cdw& a, const cdw& b) {
+    return {dw_sub(dw_mul(a.x, b.x), dw_mul(a.y, b.y)), dw_add(dw_mul(a.x, b.y), dw_mul(a.y, b.x))};
+}
+__device__ __forceinline__ dw cdw_abs2(const cdw& a) { return dw_add(dw_mul(a.x, a.x), dw_mul(a.y, a.y)); }
+// a / b = a conj(b) / |b|^2 with b scaled by a power of two so that |b|^2 neither overflows nor
+// underflows; b = 0 gives a non-finite result
+__device__ __forceinline__ cdw cdw_div(const cdw& a, const cdw& b) {
+    const float m = fmaxf(fabsf(b.x.h), fabsf(b.y.h));
+    int e = 0;
+    if (m > 0.f && m < INFINITY) e = ((__float_as_int(m) >> 23) & 0xff) - 127;
+    e = max(-120, min(120, e));
+    const float p2 = __int_as_float((127 - e) << 23);   // 2^-e
+    const cdw bs = {dw_pow2(b.x, p2), dw_pow2(b.y, p2)};
+    const dw inv = dw_recip(cdw_abs2(bs));
+    const cdw t = cdw_mul(a, {bs.x, dw_neg(bs.y)});
+    return {dw_pow2(dw_mul(t.x, inv), p2), dw_pow2(dw_mul(t.y, inv), p2)};
+}
 __device__ __forceinline__ cdw cdw_sub(const cdw& a, const cdw& b) { return {dw_sub(a.x, b.x), dw_sub(a.y, b.y)}; }
 __device__ __forceinline__ cdw cdw_add_s(const cdw& a, const cdw& b) { return {dw_add_s(a.x, b.x), dw_add_s(a.y, b.y)}; }
 __device__ __forceinline__ cdw cdw_sub_s(const cdw& a, const cdw& b) { return {dw_sub_s(a.x, b.x), dw_sub_s(a.y, b.y)}; }

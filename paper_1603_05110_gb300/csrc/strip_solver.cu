@@ -185,6 +185,7 @@ strip_solve_kernel(StripSolveArgs a) {
     __shared__ double s_red[64];
     __shared__ int s_flag;
     __shared__ typename std::conditional<CLU, ClusterSlots, char>::type s_cl;
+    __shared__ typename std::conditional<CLU, ClusterSlotsDW, char>::type s_cld;
     __shared__ double s_out[8];
     extern __shared__ __align__(16) unsigned char s_dyn[];
     static_assert(!CLU || (sizeof(T) == 4 && !PADE), "cluster mode is built for the FP32 Robin solver");
@@ -203,7 +204,10 @@ strip_solve_kernel(StripSolveArgs a) {
     const int rank = CLU ? (int)cluster_rank() : (int)blockIdx.x - b0;
     if constexpr (CLU) {
         // exchange slots start empty; no CTA pushes before every CTA has cleared its own
-        for (int t = threadIdx.x; t < 2 * kClusterCTAs; t += blockDim.x) (&s_cl.flag[0][0])[t] = 0u;
+        for (int t = threadIdx.x; t < 2 * kClusterCTAs; t += blockDim.x) {
+            (&s_cl.flag[0][0])[t] = 0u;
+            (&s_cld.flag[0][0])[t] = 0u;
+        }
         cluster_sync_all();
     }
     // geometry: the launch's, or the instance's when instances are batched
@@ -801,37 +805,40 @@ strip_solve_kernel(StripSolveArgs a) {
                     *exp_at(0, 1, 0, ix) = rreg[k]; *exp_at(0, 1, 1, ix) = w0; *exp_at(0, 1, 2, ix) = zeroT; *exp_at(0, 1, 3, ix) = Ds[o];
                 }
             }
-            // thread-0 state of the recurrences
-            double gam_r = rho_r, gam_i = rho_i, al_r = 0.0, al_i = 0.0, be_r = 0.0, be_i = 0.0;
+            // thread-0 state of the recurrences, in double words (no FP64 on the iteration path)
+            cdw gam = {dw_from(rho_r), dw_from(rho_i)}, al = cdw_zero(), be = cdw_zero();
+            float* s_outf = (float*)s_out;
+            const float target2 = (float)(target * target);
             {
-                T lT[2] = {d0r, d0i};
-                double l2[2];
-                block_sum_t<T, 2>(lT, l2, s_red);
+                float lT[2] = {d0r, d0i};
+                dw l2[2];
+                block_sum_dw<2>(lT, l2, (float*)s_red);
                 lap(1);
-                const double l4[4] = {l2[0], l2[1], 0.0, 0.0};
-                double dl[4];
-                if (!strip_sum4(l4, dl)) { status = DD_NLS_ETIMEOUT; break; }
+                dw dl[2];
+                if (!cluster_allreduce_dw<2>(s_cld, l2, dl, ++cepoch, bps, a.err, wait_ns, s_outf, &s_flag)) {
+                    status = DD_NLS_ETIMEOUT;
+                    break;
+                }
                 if (threadIdx.x == 0) {
-                    const double del_r = dl[0], del_i = dl[1];
-                    const double dd2 = del_r * del_r + del_i * del_i;
+                    const cdw del = {dl[0], dl[1]};
+                    const float dd2 = cdw_abs2(del).h;
                     int ctl = 0, st = 0;
-                    if (!(dd2 > 0.0) || !isfinite(dd2)) {
+                    if (!(dd2 > 0.f) || !isfinite(dd2)) {
                         ctl = 2;
                         st = isfinite(dd2) ? DD_NLS_EBREAKDOWN : DD_NLS_ENONFINITE;
                     } else {
-                        al_r = (gam_r * del_r + gam_i * del_i) / dd2;
-                        al_i = (gam_i * del_r - gam_r * del_i) / dd2;
+                        al = cdw_div(gam, del);
                     }
                     s_ctl[0] = ctl;
                     s_ctl[1] = st;
-                    s_sc[0] = (T)al_r;
-                    s_sc[1] = (T)al_i;
+                    s_sc[0] = al.x.h;
+                    s_sc[1] = al.y.h;
                 }
             }
             __syncthreads();
             lap(4);
             if (s_ctl[0]) { status = s_ctl[1]; break; }
-            double best = INFINITY;
+            float best2 = INFINITY;      // stagnation guard on ||r||^2
             int since = 0;
             T2 alT = T2{s_sc[0], s_sc[1]}, beT = T2{0, 0};
             int cstat = 0;
@@ -900,69 +907,60 @@ strip_solve_kernel(StripSolveArgs a) {
                         *exp_at(pout, 1, 0, ix) = rv; *exp_at(pout, 1, 1, ix) = wn; *exp_at(pout, 1, 2, ix) = Ss[o]; *exp_at(pout, 1, 3, ix) = Ds[o];
                     }
                 }
-                T lT[4] = {g_r, g_i, dlt_r, dlt_i};
-                double l4[4];
-                block_sum_t<T, 4>(lT, l4, s_red);
-                T lr[1] = {rr2};
-                double l1[1];
-                block_sum_t<T, 1>(lr, l1, s_red);
+                float lT[5] = {g_r, g_i, dlt_r, dlt_i, rr2};
+                dw l5[5];
+                block_sum_dw<5>(lT, l5, (float*)s_red);
                 lap(2);
                 // one exchange per iteration: gamma, delta and ||r||^2; the rows exported above are
                 // visible to the neighbours once it completes
-                double gg[5];
-                {
-                    const double v5[5] = {l4[0], l4[1], l4[2], l4[3], l1[0]};
-                    if (!cluster_allreduce<5>(s_cl, v5, gg, ++cepoch, bps, a.err, wait_ns, s_out, &s_flag)) {
-                        cstat = DD_NLS_ETIMEOUT;
-                        break;
-                    }
+                dw gg[5];
+                if (!cluster_allreduce_dw<5>(s_cld, l5, gg, ++cepoch, bps, a.err, wait_ns, s_outf, &s_flag)) {
+                    cstat = DD_NLS_ETIMEOUT;
+                    break;
                 }
                 if (threadIdx.x == 0) {
                     int ctl = 0, st = 0;
-                    const double rk = sqrt(gg[4]);
-                    if (!isfinite(gg[4]) || !isfinite(gg[0]) || !isfinite(gg[2])) {
+                    const cdw gk = {gg[0], gg[1]}, dk = {gg[2], gg[3]};
+                    const float rr = gg[4].h;
+                    if (!isfinite(rr) || !isfinite(gk.x.h) || !isfinite(gk.y.h) || !isfinite(dk.x.h) || !isfinite(dk.y.h)) {
                         ctl = 2;
                         st = DD_NLS_ENONFINITE;
-                    } else if (rk <= target) {
-                        ctl = 1;
+                    } else if (rr <= target2) {
+                        ctl = 1;          // x was advanced in this pass; the solution is complete
                     } else {
-                        if (rk < 0.99 * best) {
-                            best = rk;
+                        // a breakdown of the recurrences after the first step, or 32 steps without a
+                        // 1% gain in ||r||, ends the inner solve with the x reached (ctl 3)
+                        if (rr < 0.9801f * best2) {
+                            best2 = rr;
                             since = 0;
                         } else if (++since >= 32) {
                             ctl = 3;
                         }
-                        const double gk2 = gam_r * gam_r + gam_i * gam_i;
-                        if (!ctl && !(gk2 > 0.0)) ctl = 3;
+                        if (!ctl && !(cdw_abs2(gam).h > 0.f)) ctl = 3;
                         if (!ctl) {
-                            const double nb_r = (gg[0] * gam_r + gg[1] * gam_i) / gk2;
-                            const double nb_i = (gg[1] * gam_r - gg[0] * gam_i) / gk2;
-                            const double a2 = al_r * al_r + al_i * al_i;
-                            const double bg_r = nb_r * gg[0] - nb_i * gg[1], bg_i = nb_r * gg[1] + nb_i * gg[0];
-                            const double t_r = (bg_r * al_r + bg_i * al_i) / a2, t_i = (bg_i * al_r - bg_r * al_i) / a2;
-                            const double den_r = gg[2] - t_r, den_i = gg[3] - t_i;
-                            const double den2 = den_r * den_r + den_i * den_i;
+                            // beta_{k+1} = gamma_{k+1}/gamma_k,
+                            // alpha_{k+1} = gamma_{k+1}/(delta_{k+1} - beta_{k+1} gamma_{k+1}/alpha_k)
+                            const cdw nb = cdw_div(gk, gam);
+                            const cdw den = cdw_sub(dk, cdw_div(cdw_mul(nb, gk), al));
+                            const float den2 = cdw_abs2(den).h;
                             if (!isfinite(den2)) {
                                 ctl = 2;
                                 st = DD_NLS_ENONFINITE;
-                            } else if (!(den2 > 0.0)) {
+                            } else if (!(den2 > 0.f)) {
                                 ctl = 3;
                             } else {
-                                al_r = (gg[0] * den_r + gg[1] * den_i) / den2;
-                                al_i = (gg[1] * den_r - gg[0] * den_i) / den2;
-                                be_r = nb_r;
-                                be_i = nb_i;
-                                gam_r = gg[0];
-                                gam_i = gg[1];
+                                al = cdw_div(gk, den);
+                                be = nb;
+                                gam = gk;
                             }
                         }
                     }
                     s_ctl[0] = ctl;
                     s_ctl[1] = st;
-                    s_sc[0] = (T)al_r;
-                    s_sc[1] = (T)al_i;
-                    s_sc[2] = (T)be_r;
-                    s_sc[3] = (T)be_i;
+                    s_sc[0] = al.x.h;
+                    s_sc[1] = al.y.h;
+                    s_sc[2] = be.x.h;
+                    s_sc[3] = be.y.h;
                 }
                 __syncthreads();
                 lap(4);

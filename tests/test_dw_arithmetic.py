@@ -150,3 +150,64 @@ def test_integer_split_is_exact_to_2_pow_minus_47():
             worst_abs = max(worst_abs, float(err))
     assert worst_rel <= 2.0 ** -47, worst_rel
     assert worst_abs <= 2.0 ** -149, worst_abs
+
+
+def mul_f(x, y):
+    """DWTimesFP (the dw_mul_f sequence): x double word, y float."""
+    ch = f32(x[0] * y)
+    cl1 = fma32(x[0], y, -ch)
+    return fast_two_sum(ch, fma32(x[1], y, cl1))
+
+
+def rcp32(v):
+    """The correctly rounded FP32 reciprocal (rounding the exact rational once)."""
+    q = F(1) / F(float(v))
+    lo = f32(float(q))                      # nearest double, then float: fix the rare double rounding
+    cands = [lo, np.nextafter(lo, f32(np.inf)), np.nextafter(lo, f32(-np.inf))]
+    return min(cands, key=lambda c: (abs(F(float(c)) - q), int(np.frombuffer(np.float32(c).tobytes(), np.uint32)[0]) & 1))
+
+
+def recip(b):
+    """dw_recip: r0 = rcp(b.h), e = 1 - b r0 in double words, r = r0 + e r0."""
+    r0 = rcp32(b[0])
+    e = add_accurate((f32(1.0), f32(0.0)), tuple(-t for t in mul_f(b, r0)))
+    return add_accurate((r0, f32(0.0)), mul_f(e, r0))
+
+
+def test_double_word_reciprocal_relative_error():
+    rng = np.random.default_rng(6)
+    worst = 0.0
+    for _ in range(4000):
+        b = dw(rng.standard_normal() * 10.0 ** rng.uniform(-15, 15))
+        r = recip(b)
+        worst = max(worst, float(abs(val(r) * val(b) - 1)) / U2)
+    assert worst <= 6.0, worst
+
+
+def cdiv(a, b):
+    """cdw_div without its power-of-two scaling (operands of moderate size): a conj(b) / |b|^2."""
+    ax, ay = a
+    bx, by = b
+    abs2 = add_accurate(mul(bx, bx), mul(by, by))
+    inv = recip(abs2)
+    tx = add_accurate(mul(ax, bx), mul(ay, by))
+    ty = add_accurate(mul(ay, bx), tuple(-t for t in mul(ax, by)))
+    return mul(tx, inv), mul(ty, inv)
+
+
+def test_complex_double_word_quotient_relative_error():
+    """The Krylov scalar recurrences divide complex double words: about 2^-44 relative at worst
+    (a few u^2 per operation), the accuracy FP64 scalars had for these recurrences' purpose."""
+    rng = np.random.default_rng(7)
+    worst = 0.0
+    for _ in range(1500):
+        a = (dw(rng.standard_normal() * 10.0 ** rng.uniform(-4, 4)), dw(rng.standard_normal() * 10.0 ** rng.uniform(-4, 4)))
+        b = (dw(rng.standard_normal() * 10.0 ** rng.uniform(-4, 4)), dw(rng.standard_normal() * 10.0 ** rng.uniform(-4, 4)))
+        qx, qy = cdiv(a, b)
+        num_x, num_y = val(a[0]) * val(b[0]) + val(a[1]) * val(b[1]), val(a[1]) * val(b[0]) - val(a[0]) * val(b[1])
+        den = val(b[0]) ** 2 + val(b[1]) ** 2
+        ex, ey = num_x / den, num_y / den
+        mag = abs(complex(float(ex), float(ey)))
+        err = abs(complex(float(val(qx) - ex), float(val(qy) - ey))) / mag
+        worst = max(worst, err)
+    assert worst <= 2.0 ** -43, worst

@@ -367,11 +367,11 @@ def test_fp32_inner_solves_survive_a_long_gpe_trajectory():
 @pytest.mark.parametrize("algorithm", ["classical", "preconditioned"])
 def test_cluster_and_cooperative_layouts_reach_the_oracle_step(precision, algorithm):
     """FP32 Robin strips are solved one strip per thread-block cluster when they fit on chip
-    (solver_layout 0) or by the cooperative launch (solver_layout 1); both reach the oracle's step."""
+    (solver_layout 2) or by the cooperative launch (solver_layout 0); both reach the oracle's step."""
     w = WELL if algorithm == "preconditioned" else SMALL
     ref = run_oracle(w, 2, algorithm=algorithm)
     alg = binding.PRECONDITIONED if algorithm == "preconditioned" else binding.CLASSICAL
-    for layout in (0, 1):
+    for layout in (0, 2):
         got = run_gpu(w, 2, tol=TOL, algorithm=alg, precision=precision, solver_layout=layout)
         for (ug, _), (uo, _) in zip(got, ref):
             assert rel(ug, uo) < 1e-10, (layout, rel(ug, uo))
@@ -382,6 +382,6 @@ def test_cluster_layout_on_strips_wider_than_a_cta_slab():
     256+ nodes take the on-chip single-reduction COCG."""
     w = wl.scaled(wl.NLS_WELL, 96, 160, n_strips=4, xl=-8.0, xr=8.0, yb=-9.0, yu=9.0, dt=0.02, p=3.0)
     ref = run_oracle(w, 2, algorithm="preconditioned")
-    got = run_gpu(w, 2, tol=TOL, algorithm=binding.PRECONDITIONED, precision=binding.FP32_DW)
+    got = run_gpu(w, 2, tol=TOL, algorithm=binding.PRECONDITIONED, precision=binding.FP32_DW, solver_layout=2)
     for (ug, _), (uo, _) in zip(got, ref):
         assert rel(ug, uo) < 1e-10
