@@ -266,11 +266,11 @@ def cpu_baseline_line(w, args, gpu_iters_per_step):
                   f"processes, exact modal P^-1), {t:.1f} s; cosine-mode set-up {r['setup_s']:.2f} s not counted; "
                   f"host {hi['cpu']}, {hi['nproc']} cores")
     else:
-        k = 2
+        k = 1
         r = oracle_steps(w, args, 1, args.cpu_budget, max_iter_first=k)
         t, its = r["steps"][0], r["iterations"][0]
         value = 1.0 / (t / its * gpu_iters_per_step)
-        sample = (f"the first {its} Schwarz iterations of step 1 of {w.name} ({w.n_strips} strip solves each over "
+        sample = (f"the first {its} Schwarz iteration(s) of step 1 of {w.name} ({w.n_strips} strip solves each over "
                   f"{r['processes']} worker processes), {t:.1f} s, scaled to the {gpu_iters_per_step:.1f} Schwarz "
                   f"iterations per step this run measured on the GPU; host {hi['cpu']}, {hi['nproc']} cores")
     return {"value": value, "unit": "steps/s", "cores": r["processes"], "kind": "oracle", "sample": sample,

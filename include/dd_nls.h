@@ -128,12 +128,13 @@ typedef struct {
                             paper's closing suggestion).  0 (default): all modes, the exact P */
     double wait_limit_ms;  /* bound of every device-side wait between blocks of a strip; on expiry the
                             call returns DD_NLS_ETIMEOUT and commits nothing.  0 (default): 2000 ms */
-    int solver_layout;   /* 0 (default) and 1: one cooperative launch over all strips, blocks split among
-                            strips by expected work, global-memory barriers.  2: FP32 Robin strips whose
-                            rows split over a cluster of 16 CTAs fit in their shared memory are solved
-                            one strip per thread-block cluster (inner Krylov state on chip, partial sums
-                            through distributed shared memory, double-word scalar recurrences); other
-                            strips as in 0.  The converged step is the same either way. */
+    int solver_layout;   /* 0 (default) and 2: FP32 Robin strips whose rows, split over a cluster of 16
+                            CTAs, fit in their shared memory are solved one strip per thread-block
+                            cluster (inner Krylov state on chip, partial sums through distributed shared
+                            memory, double-word scalar recurrences); everything else as in 1.
+                            1: one cooperative launch over all strips, blocks split among strips by
+                            expected work, global-memory barriers.  The converged step is the same
+                            either way. */
 } dd_nls_params;
 
 typedef struct {

@@ -374,6 +374,15 @@ static StripSolveArgs base_args(dd_nls* h) {
     a.phi = h->phi;
     a.xf = h->xf; a.rf = h->rf; a.zf = h->zf; a.pf = h->pf; a.qf = h->qf; a.cTf = h->cTf;
     for (int s2 = 0; s2 < h->pade_m; ++s2) { a.pade_a[s2] = h->pade_a[s2]; a.pade_d[s2] = h->pade_d[s2]; }
+    // edge coefficient: i p (Robin) or i sum_s a_s (S_pade)
+    double rre = 0.0, rim = h->G.p;
+    if (h->pade_m) {
+        double sre = 0.0, sim = 0.0;
+        for (int s2 = 0; s2 < h->pade_m; ++s2) { sre += h->pade_a[s2].x; sim += h->pade_a[s2].y; }
+        rre = -sim;
+        rim = sre;
+    }
+    fill_fp32_constants(a, h->G, rre, rim, h->G.kap);
     return a;
 }
 
@@ -947,7 +956,7 @@ extern "C" int dd_nls_create(const dd_nls_params* p, const double* V, const doub
     h->maxb = maxb;
     h->chunks = (int)((G.nxs * (long long)G.nyn + 255) / 256);
     // cluster mode: FP32 Robin strips whose slab of one CTA fits on chip
-    if (h->fp32 && p->tc == DD_NLS_TC_ROBIN && p->solver_layout == 2) {
+    if (h->fp32 && p->tc == DD_NLS_TC_ROBIN && p->solver_layout != 1) {
         const unsigned sm = strip_cluster_smem(G.nxs, G.nyn);
         if (sm && strip_cluster_capacity(h->dw, sm) >= 1) h->cl_smem = sm;
     }

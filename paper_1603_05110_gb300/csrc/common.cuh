@@ -62,11 +62,21 @@ struct Geom {
     // off-diagonal -1/h, diagonal 2/h inside and 1/h at the ends; trapezoid weight h.
     double mxo, mxi, mxe, kxo, kxi, kxe;
     double myo, myi, mye, kyo, kyi, kye;
+    // FP32 copies for the FP32 kernels, rounded once here: a conversion from FP64 in a kernel
+    // runs on the FP64 pipe (~1/64 of the FP32 rate on GB300), and the compiler may repeat
+    // such conversions inside loops instead of keeping their results in registers
+    float cf[12];            // mxo mxi mxe kxo kxi kxe myo myi mye kyo kyi kye
+    float alpha_f, p_f;
+    // after hx, hy, alpha and p are set
     __host__ void fill_coefficients() {
         mxo = hx / 6.0; mxi = 4.0 * hx / 6.0; mxe = 2.0 * hx / 6.0;
         kxo = -1.0 / hx; kxi = 2.0 / hx; kxe = 1.0 / hx;
         myo = hy / 6.0; myi = 4.0 * hy / 6.0; mye = 2.0 * hy / 6.0;
         kyo = -1.0 / hy; kyi = 2.0 / hy; kye = 1.0 / hy;
+        const double d[12] = {mxo, mxi, mxe, kxo, kxi, kxe, myo, myi, mye, kyo, kyi, kye};
+        for (int i = 0; i < 12; ++i) cf[i] = (float)d[i];
+        alpha_f = (float)alpha;
+        p_f = (float)p;
     }
     __host__ __device__ long long sstride() const { return (long long)nxs * P; }
     __host__ __device__ int c() const { return nxs - 1; }
@@ -82,12 +92,27 @@ template <typename T> struct Coef1 {
 template <typename T> struct Coef1Consts {
     T mo, mi, me, ko, ki, ke;
 };
-template <typename T> __device__ __forceinline__ Coef1Consts<T> consts_x(const Geom& g) {
-    return {(T)g.mxo, (T)g.mxi, (T)g.mxe, (T)g.kxo, (T)g.kxi, (T)g.kxe};
+template <typename T> __device__ __forceinline__ Coef1Consts<T> consts_x(const Geom& g);
+template <typename T> __device__ __forceinline__ Coef1Consts<T> consts_y(const Geom& g);
+template <> __device__ __forceinline__ Coef1Consts<double> consts_x<double>(const Geom& g) {
+    return {g.mxo, g.mxi, g.mxe, g.kxo, g.kxi, g.kxe};
 }
-template <typename T> __device__ __forceinline__ Coef1Consts<T> consts_y(const Geom& g) {
-    return {(T)g.myo, (T)g.myi, (T)g.mye, (T)g.kyo, (T)g.kyi, (T)g.kye};
+template <> __device__ __forceinline__ Coef1Consts<double> consts_y<double>(const Geom& g) {
+    return {g.myo, g.myi, g.mye, g.kyo, g.kyi, g.kye};
 }
+template <> __device__ __forceinline__ Coef1Consts<float> consts_x<float>(const Geom& g) {
+    return {g.cf[0], g.cf[1], g.cf[2], g.cf[3], g.cf[4], g.cf[5]};
+}
+template <> __device__ __forceinline__ Coef1Consts<float> consts_y<float>(const Geom& g) {
+    return {g.cf[6], g.cf[7], g.cf[8], g.cf[9], g.cf[10], g.cf[11]};
+}
+// alpha = 2/(lap dt) and the Robin p in the working precision (no conversion in the kernel)
+template <typename T> __device__ __forceinline__ T alpha_t(const Geom& g);
+template <> __device__ __forceinline__ double alpha_t<double>(const Geom& g) { return g.alpha; }
+template <> __device__ __forceinline__ float alpha_t<float>(const Geom& g) { return g.alpha_f; }
+template <typename T> __device__ __forceinline__ T p_t(const Geom& g);
+template <> __device__ __forceinline__ double p_t<double>(const Geom& g) { return g.p; }
+template <> __device__ __forceinline__ float p_t<float>(const Geom& g) { return g.p_f; }
 template <typename T> __device__ __forceinline__ Coef1<T> coef1(int i, int n, const Coef1Consts<T>& k) {
     Coef1<T> c;
     const bool lo = (i > 0), hi = (i < n);
@@ -278,11 +303,12 @@ struct ClusterSlots {
 // the slots in rank order, so every CTA gets the same sums.  The push follows a fence at cluster
 // scope, so everything this CTA wrote before the call (shared or global memory) is visible to
 // the other CTAs once they return.  Results in out[] of every thread (after a __syncthreads).
-// Returns false on time-out (DD_NLS_ETIMEOUT recorded in *err).
+// Returns false on time-out (DD_NLS_ETIMEOUT recorded in *err).  push = false (a test hook)
+// leaves this CTA's values and flags out, so that every CTA's wait runs out.
 template <int NV>
 __device__ __forceinline__ bool cluster_allreduce(ClusterSlots& sl, const double (&v)[NV], double (&out)[NV],
                                                   unsigned epoch, int ncta, int* err, unsigned long long limit_ns,
-                                                  double* s_out, int* s_flag) {
+                                                  double* s_out, int* s_flag, bool push = true) {
     __syncthreads();
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
@@ -290,7 +316,7 @@ __device__ __forceinline__ bool cluster_allreduce(ClusterSlots& sl, const double
         double val[NV > 0 ? NV : 1];
 #pragma unroll
         for (int k = 0; k < NV; ++k) val[k] = __shfl_sync(0xffffffffu, v[k], 0);
-        if (lane < ncta) {
+        if (lane < ncta && push) {
             fence_cluster();
             const unsigned dst = mapa(smem_addr(&sl.v[par][me][0]), (unsigned)lane);
 #pragma unroll

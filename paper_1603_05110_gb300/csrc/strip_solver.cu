@@ -310,7 +310,9 @@ strip_solve_kernel(StripSolveArgs a) {
     // a barrier of the strip's blocks
     auto strip_sum4 = [&](const double (&v)[4], double (&out)[4]) -> bool {
         if constexpr (CLU) {
-            return cluster_allreduce<4>(s_cl, v, out, ++cepoch, bps, a.err, wait_ns, s_out, &s_flag);
+            const bool ok = cluster_allreduce<4>(s_cl, v, out, ++cepoch, bps, a.err, wait_ns, s_out, &s_flag, !skip_arrival);
+            skip_arrival = false;
+            return ok;
         } else {
             if (threadIdx.x == 0) {
                 double* sp = slot_ptr(epoch + 1);
@@ -326,7 +328,9 @@ strip_solve_kernel(StripSolveArgs a) {
         if constexpr (CLU) {
             const double z1[1] = {0.0};
             double o1[1];
-            return cluster_allreduce<1>(s_cl, z1, o1, ++cepoch, bps, a.err, wait_ns, s_out, &s_flag);
+            const bool ok = cluster_allreduce<1>(s_cl, z1, o1, ++cepoch, bps, a.err, wait_ns, s_out, &s_flag, !skip_arrival);
+            skip_arrival = false;
+            return ok;
         } else {
             ++epoch;
             return gbar(epoch * bps);
@@ -343,7 +347,7 @@ strip_solve_kernel(StripSolveArgs a) {
     }
     const Coef1Consts<double> KXd = consts_x<double>(g), KYd = consts_y<double>(g);
     const Coef1Consts<T> KXt = consts_x<T>(g), KYt = consts_y<T>(g);
-    const T alphaT = (T)g.alpha;
+    const T alphaT = alpha_t<T>(g);
     const double kap = a.mode == 0 ? g.kap : 0.0;
     // correction operator: the complex-linear part of the Jacobian of kappa|z|^2 z (2 kappa|z|^2),
     // or the frozen operator of the fixed point (kappa|z|^2)
@@ -366,7 +370,11 @@ strip_solve_kernel(StripSolveArgs a) {
         re = im = 0.0;
         if ((ix == 0 && ltc) || (ix == c && rtc)) { re = rho_re; im = rho_im; }
     };
-    const T rho_reT = (T)rho_re, rho_imT = (T)rho_im;
+    // the edge coefficient in the working precision, rounded on the host (Robin: i p of the strip's
+    // instance; S_pade: i sum a_s)
+    T rho_reT = (T)0, rho_imT = p_t<T>(g);
+    if constexpr (sizeof(T) == 4 && PADE) { rho_reT = a.rho_f[0]; rho_imT = a.rho_f[1]; }
+    else if constexpr (PADE) { rho_reT = (T)rho_re; rho_imT = (T)rho_im; }
     auto rho_atT = [&](int ix, T& re, T& im) {
         re = im = (T)0;
         if ((ix == 0 && ltc) || (ix == c && rtc)) { re = rho_reT; im = rho_imT; }
@@ -428,20 +436,21 @@ strip_solve_kernel(StripSolveArgs a) {
     // C1 = hy/(6hx), C2 = alpha hx hy/36, C3 = hx/(6hy), C5 = p hy/6, c = w W + w kappa|zeta|^2.
     dw nC1{}, nC2{}, C2{}, nC3{}, nC5{}, C5{}, C6{};
     float C6f = 0.f;
-    const float cfacf = (float)cfac;
+    const float cfacf = a.nl_picard ? 1.f : 2.f;
     if constexpr (DW) {
-        nC1 = dw_from(-g.hy / (6.0 * g.hx));
-        C2 = dw_from(g.alpha * g.hx * g.hy / 36.0);
+        // double-word constants split on the host (no FP64 conversion in the kernel)
+        nC1 = {a.dwk[0], a.dwk[1]};
+        C2 = {a.dwk[2], a.dwk[3]};
         nC2 = dw_neg(C2);
-        nC3 = dw_from(-g.hx / (6.0 * g.hy));
-        C5 = dw_from(rho_im * g.hy / 6.0);
+        nC3 = {a.dwk[4], a.dwk[5]};
+        C5 = {a.dwk[6], a.dwk[7]};
         nC5 = dw_neg(C5);
-        C6 = dw_from(g.hx * g.hy * kap);
+        if (a.mode == 0) C6 = {a.dwk[8], a.dwk[9]};
         C6f = C6.h;
         // zeta, b = (2i/dt) M h - M^Gamma Q^T (l; r) and w W in double-word form, ||b||^2.
         // Integer splits away from the edge columns (no FP64 instruction there); ||b||^2 in
         // FP32 in units of the first correction's scale, edge columns apart.
-        const dw HXHY = dw_from(g.hx * g.hy);
+        const dw HXHY = {a.dwk[10], a.dwk[11]};
         const float bsc = (float)(1.0 / (s_first > 0.0 ? s_first : 1.0));
         float bb = 0.f, be = 0.f;
         auto edge_b = [&](int ix, int iy, long long idx) {
@@ -562,7 +571,9 @@ strip_solve_kernel(StripSolveArgs a) {
                     T rre, rim;
                     rho_atT(ix, rre, rim);
                     const Coef1<T> cxT = coef1<T>(ix, c, KXt);
-                    const T2 rT = mk<T2>(rx.h * inv_sf, ry.h * inv_sf);
+                    T2 rT;
+                    rT.x = rx.h * inv_sf;
+                    rT.y = ry.h * inv_sf;
                     rr_f += rT.x * rT.x + rT.y * rT.y;    // scaled: no underflow of tiny residuals
                     const T2 di = diag_inv<T>(cxT, cyT, alphaT, rre, rim, cop);
                     const T2 zT = cmul(di, rT);
@@ -756,6 +767,15 @@ strip_solve_kernel(StripSolveArgs a) {
             const unsigned nb_up = (unsigned)(rank - 1), nb_dn = (unsigned)(rank + 1);
             T2 rreg[kOnChipNPT], xreg[kOnChipNPT];
             const T2 zeroT = mk<T2>(0.0, 0.0);
+            // r holds res * inv_s, scaled for the launch's first correction; a later correction
+            // (a strip near convergence) is far smaller, and the FP32 squares of the recurrences
+            // (|delta|^2, ||r||^2) would underflow.  Rescale by the power of two sf2 that brings
+            // ||r|| to [1/2, 1): exact, and the correction's scale inv_s takes the same factor.
+            int e2 = 0;
+            (void)frexp(rnorm * inv_s, &e2);
+            e2 = max(-120, min(120, e2));
+            const float sf2 = __int_as_float((127 - e2) << 23);   // 2^-e2
+            const T2 sf2v = T2{sf2, 0.f};
             // load r_0 (scaled residual), D^-1, c of the residual pass; x = p = s_{-1} = 0
 #pragma unroll
             for (int k = 0; k < kOnChipNPT; ++k) {
@@ -768,7 +788,8 @@ strip_solve_kernel(StripSolveArgs a) {
                 const long long idx = (long long)ix * P + y0 + il;
                 const int o = ix * H + il;
                 const T2 dvv = dv[idx];
-                rreg[k] = r[idx];
+                const T2 r0 = r[idx];
+                rreg[k] = T2{r0.x * sf2, r0.y * sf2};
                 Ds[o] = dvv;
                 Cs[o] = cT[idx];
                 Ps[o] = zeroT;
@@ -777,8 +798,8 @@ strip_solve_kernel(StripSolveArgs a) {
             }
             // halo rows of z_0 = D^-1 r_0 from global memory (written by the residual pass)
             for (int ix = threadIdx.x; ix < NX; ix += BS) {
-                if (has_up) Zs[ix * ZP] = cmul(dv[(long long)ix * P + y0 - 1], r[(long long)ix * P + y0 - 1]);
-                if (has_dn) Zs[ix * ZP + h + 1] = cmul(dv[(long long)ix * P + y1], r[(long long)ix * P + y1]);
+                if (has_up) Zs[ix * ZP] = cmul(cmul(dv[(long long)ix * P + y0 - 1], r[(long long)ix * P + y0 - 1]), sf2v);
+                if (has_dn) Zs[ix * ZP + h + 1] = cmul(cmul(dv[(long long)ix * P + y1], r[(long long)ix * P + y1]), sf2v);
             }
             __syncthreads();
             // w_0 = A z_0, delta_0 = w_0^T z_0; export the slab's first and last rows (parity 0)
@@ -806,9 +827,10 @@ strip_solve_kernel(StripSolveArgs a) {
                 }
             }
             // thread-0 state of the recurrences, in double words (no FP64 on the iteration path)
-            cdw gam = {dw_from(rho_r), dw_from(rho_i)}, al = cdw_zero(), be = cdw_zero();
+            const double sf2d = (double)sf2;
+            cdw gam = {dw_from(rho_r * sf2d * sf2d), dw_from(rho_i * sf2d * sf2d)}, al = cdw_zero(), be = cdw_zero();
             float* s_outf = (float*)s_out;
-            const float target2 = (float)(target * target);
+            const float target2 = (float)((target * sf2d) * (target * sf2d));
             {
                 float lT[2] = {d0r, d0i};
                 dw l2[2];
@@ -982,6 +1004,7 @@ strip_solve_kernel(StripSolveArgs a) {
                 split_node(mm, h, inv_h, ix, il);
                 x[(long long)ix * P + y0 + il] = xreg[k];
             }
+            inv_s *= sf2d;      // x is the correction in units of 1/(inv_s sf2)
             if (cstat) { status = cstat; break; }
             if (!strip_barrier()) { status = DD_NLS_ETIMEOUT; break; }
             }
@@ -1412,6 +1435,22 @@ strip_solve_kernel(StripSolveArgs a) {
     }
     // no CTA leaves while another may still read its shared memory or push into it
     if constexpr (CLU) cluster_sync_all();
+}
+
+static void dw_split(double v, float* out) {
+    const float h = (float)v;
+    out[0] = h;
+    out[1] = (float)(v - (double)h);
+}
+void fill_fp32_constants(StripSolveArgs& a, const Geom& g, double rho_re, double rho_im, double kap) {
+    a.rho_f[0] = (float)rho_re;
+    a.rho_f[1] = (float)rho_im;
+    dw_split(-g.hy / (6.0 * g.hx), a.dwk + 0);
+    dw_split(g.alpha * g.hx * g.hy / 36.0, a.dwk + 2);
+    dw_split(-g.hx / (6.0 * g.hy), a.dwk + 4);
+    dw_split(rho_im * g.hy / 6.0, a.dwk + 6);
+    dw_split(g.hx * g.hy * kap, a.dwk + 8);
+    dw_split(g.hx * g.hy, a.dwk + 10);
 }
 
 unsigned strip_cluster_smem(int nxs, int nyn) {

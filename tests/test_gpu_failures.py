@@ -3,7 +3,9 @@
 * A bounded device wait that runs out: block 1 of a strip skips its first barrier arrival (test
   hook DD_NLS_TEST_SKIP_ARRIVAL, one launch only) and the wait limit is 5 ms; every block gives up,
   the call returns DD_NLS_ETIMEOUT, nothing is committed, and the next call on the same handle
-  steps normally.
+  steps normally.  In FP64 the wait is the cooperative launch's global-memory barrier; in FP32
+  with the double-word residual it is the exchange of a thread-block cluster (CTA 1 of strip 0's
+  cluster pushes nothing).
 * An exact breakdown of the inner COCG: a strip whose first residual r satisfies r^T D^{-1} r = 0
   exactly (two edge nodes of equal diagonal with residuals -3 and -3i, made exact by a mesh of
   hy = 6 where the edge mass is the integer matrix [[2, 1], [1, 2]]); the recurrence cannot form
@@ -33,9 +35,10 @@ def _lib():
     binding.load()
 
 
-def test_a_wait_that_runs_out_returns_etimeout_and_the_handle_stays_usable(monkeypatch):
+@pytest.mark.parametrize("precision", [binding.FP64, binding.FP32_DW])
+def test_a_wait_that_runs_out_returns_etimeout_and_the_handle_stays_usable(monkeypatch, precision):
     w = SMALL
-    prm = gpu_params(w, tol=1e-12, wait_limit_ms=5.0)
+    prm = gpu_params(w, tol=1e-12, wait_limit_ms=5.0, precision=precision)
     ref = np.zeros_like(w.u0())
     with binding.Solver(prm, w.u0(), w.V()) as s:
         s.step(1, ref)

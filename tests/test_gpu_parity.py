@@ -367,11 +367,12 @@ def test_fp32_inner_solves_survive_a_long_gpe_trajectory():
 @pytest.mark.parametrize("algorithm", ["classical", "preconditioned"])
 def test_cluster_and_cooperative_layouts_reach_the_oracle_step(precision, algorithm):
     """FP32 Robin strips are solved one strip per thread-block cluster when they fit on chip
-    (solver_layout 2) or by the cooperative launch (solver_layout 0); both reach the oracle's step."""
+    (solver_layout 2, also the default) or by the cooperative launch (solver_layout 1); both reach
+    the oracle's step."""
     w = WELL if algorithm == "preconditioned" else SMALL
     ref = run_oracle(w, 2, algorithm=algorithm)
     alg = binding.PRECONDITIONED if algorithm == "preconditioned" else binding.CLASSICAL
-    for layout in (0, 2):
+    for layout in (1, 2):
         got = run_gpu(w, 2, tol=TOL, algorithm=alg, precision=precision, solver_layout=layout)
         for (ug, _), (uo, _) in zip(got, ref):
             assert rel(ug, uo) < 1e-10, (layout, rel(ug, uo))
