@@ -299,8 +299,8 @@ struct ClusterSlots {
 
 // Strip-wide sum over the cluster's CTAs of NV values held by thread 0 (v): lanes q < ncta of
 // warp 0 push the values into slot [parity][this rank] of CTA q and then release the epoch flag;
-// each CTA waits (bounded by limit_ns) until all ncta flags of the epoch have arrived and adds
-// the slots in rank order, so every CTA gets the same sums.  The push follows a fence at cluster
+// each CTA waits (bounded by limit_ns) until all ncta flags of the epoch have arrived and sums
+// the slots over a lane tree of fixed shape, so every CTA gets the same sums.  The push follows a fence at cluster
 // scope, so everything this CTA wrote before the call (shared or global memory) is visible to
 // the other CTAs once they return.  Results in out[] of every thread (after a __syncthreads).
 // Returns false on time-out (DD_NLS_ETIMEOUT recorded in *err).  push = false (a test hook)
@@ -342,16 +342,16 @@ __device__ __forceinline__ bool cluster_allreduce(ClusterSlots& sl, const double
             }
         }
         ok = __all_sync(0xffffffffu, ok);
+        // lane q holds CTA q's values (read after its own acquire of flag q); a tree of fixed
+        // shape over the lanes gives every CTA the same sums
+        double acc[NV > 0 ? NV : 1];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) acc[k] = (ok && lane < ncta) ? sl.v[par][lane][k] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
         if (lane == 0) {
-            double acc[NV > 0 ? NV : 1];
-#pragma unroll
-            for (int k = 0; k < NV; ++k) acc[k] = 0.0;
-            if (ok)
-                for (int q = 0; q < ncta; ++q) {
-                    (void)ld_acquire_cluster(mapa(smem_addr(&sl.flag[par][q]), me));
-#pragma unroll
-                    for (int k = 0; k < NV; ++k) acc[k] += sl.v[par][q][k];
-                }
 #pragma unroll
             for (int k = 0; k < NV; ++k) s_out[k] = acc[k];
             *s_flag = ok;
@@ -366,7 +366,7 @@ __device__ __forceinline__ bool cluster_allreduce(ClusterSlots& sl, const double
 }
 
 // The same exchange for double-word values (pairs of FP32 numbers, ~48 bits): the sums over the
-// cluster are formed with the accurate double-word addition in rank order, so every CTA gets the
+// cluster are formed with the accurate double-word addition over a fixed lane tree, so every CTA gets the
 // same result without any FP64 instruction (GB300 runs FP64 at ~1/64 of the FP32 rate, and these
 // exchanges sit on the critical path of every Krylov iteration).  v valid in thread 0; out in
 // every thread.
@@ -416,16 +416,20 @@ __device__ __forceinline__ bool cluster_allreduce_dw(ClusterSlotsDW& sl, const d
             }
         }
         ok = __all_sync(0xffffffffu, ok);
+        // lane q holds CTA q's values (read after its own acquire of flag q); a tree of fixed
+        // shape over the lanes, in double words, gives every CTA the same sums
+        dw acc[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k)
+            acc[k] = (ok && lane < ncta) ? dw{sl.v[par][lane][2 * k], sl.v[par][lane][2 * k + 1]} : dw{0.f, 0.f};
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) {
+                const dw t = {__shfl_down_sync(0xffffffffu, acc[k].h, o), __shfl_down_sync(0xffffffffu, acc[k].l, o)};
+                acc[k] = dw_add(acc[k], t);
+            }
         if (lane == 0) {
-            dw acc[NV];
-#pragma unroll
-            for (int k = 0; k < NV; ++k) acc[k] = {0.f, 0.f};
-            if (ok)
-                for (int q = 0; q < ncta; ++q) {
-                    (void)ld_acquire_cluster(mapa(smem_addr(&sl.flag[par][q]), me));
-#pragma unroll
-                    for (int k = 0; k < NV; ++k) acc[k] = dw_add(acc[k], {sl.v[par][q][2 * k], sl.v[par][q][2 * k + 1]});
-                }
 #pragma unroll
             for (int k = 0; k < NV; ++k) { s_out[2 * k] = acc[k].h; s_out[2 * k + 1] = acc[k].l; }
             *s_flag = ok;

@@ -69,6 +69,48 @@ __device__ __forceinline__ T2 apply_op(const T2* v, long long idx, int ix, int i
     return acc;
 }
 
+// The 9-point stencil of A(c) at a node off the strip's edges and off the y-boundary (uniform
+// mesh): four complex weights, W(dx, dy) = Bx(dx) My(dy) - Mx(dx) Ky(dy) with Bx = -Kx + i alpha Mx,
+// for the corners (ac), the x-neighbours (bx), the y-neighbours (ay) and the centre (bc, plus c).
+// The same operator as apply_op there, in about a third of its arithmetic.
+template <typename T2> struct Interior9 {
+    T2 ac, bx, ay, bc;
+};
+template <typename T, typename T2>
+__device__ __forceinline__ Interior9<T2> interior9(const Coef1Consts<T>& kx, const Coef1Consts<T>& ky, T alpha) {
+    Interior9<T2> w;
+    w.ac.x = -kx.ko * ky.mo - kx.mo * ky.ko;
+    w.ac.y = alpha * kx.mo * ky.mo;
+    w.bx.x = -kx.ko * ky.mi - kx.mo * ky.ki;
+    w.bx.y = alpha * kx.mo * ky.mi;
+    w.ay.x = -kx.ki * ky.mo - kx.mi * ky.ko;
+    w.ay.y = alpha * kx.mi * ky.mo;
+    w.bc.x = -kx.ki * ky.mi - kx.mi * ky.ki;
+    w.bc.y = alpha * kx.mi * ky.mi;
+    return w;
+}
+template <typename T, typename T2>
+__device__ __forceinline__ T2 apply_interior(const T2* v, int idx, int P, const Interior9<T2>& w, T cdiag) {
+    const T2* l = v + idx - P;
+    const T2* m = v + idx;
+    const T2* r = v + idx + P;
+    const T2 c0 = m[0];
+    T2 sc, sx, sy;
+    sc.x = (l[-1].x + l[1].x) + (r[-1].x + r[1].x);
+    sc.y = (l[-1].y + l[1].y) + (r[-1].y + r[1].y);
+    sx.x = l[0].x + r[0].x;
+    sx.y = l[0].y + r[0].y;
+    sy.x = m[-1].x + m[1].x;
+    sy.y = m[-1].y + m[1].y;
+    const T bcx = w.bc.x + cdiag;
+    T2 acc;
+    acc.x = w.ac.x * sc.x - w.ac.y * sc.y + w.bx.x * sx.x - w.bx.y * sx.y + w.ay.x * sy.x - w.ay.y * sy.y +
+            bcx * c0.x - w.bc.y * c0.y;
+    acc.y = w.ac.x * sc.y + w.ac.y * sc.x + w.bx.x * sx.y + w.bx.y * sx.x + w.ay.x * sy.y + w.ay.y * sy.x +
+            bcx * c0.y + w.bc.y * c0.x;
+    return acc;
+}
+
 // z_{k+1} = D^{-1}(r_k - alpha (w_k + beta s_{k-1})) at node k (single-reduction COCG)
 template <typename T2>
 __device__ __forceinline__ T2 znext(const T2* rr, const T2* ww, const T2* ss, const T2* dvv, long long k, T2 al, T2 be) {
@@ -176,8 +218,9 @@ constexpr int kOnChipNPT = 9;
 // memory instead of global-memory barriers, and the single-reduction COCG keeps the strip's
 // Krylov state on chip: each CTA owns a slab of rows [y0, y1) across the strip's whole width,
 // with x and r in registers, z (with one halo row on each side), w, p, s, D^-1 and c in shared
-// memory; the halo rows of z_{k+1} are rebuilt from the neighbours' exported rows of r_k, w_k,
-// s_{k-1} and D^-1, read through DSMEM, so one cluster exchange per iteration suffices.
+// memory; the halo rows of z_{k+1} are rebuilt from the neighbours' exported rows of r_k, w_k and
+// s_{k-1}, read through DSMEM, and their D^-1 (fixed during a solve, read once), so one cluster
+// exchange per iteration suffices.
 template <typename T, bool PADE, int BS, bool DW = false, bool CLU = false>
 __global__ void __launch_bounds__(BS, CLU ? 1 : 512 / BS)
 strip_solve_kernel(StripSolveArgs a) {
@@ -211,8 +254,8 @@ strip_solve_kernel(StripSolveArgs a) {
         cluster_sync_all();
     }
     // geometry: the launch's, or the instance's when instances are batched
-    const StripInfo si = a.sinfo ? a.sinfo[j] : StripInfo{0, j, (long long)j * a.g.sstride(), 0};
-    const Geom g = a.geoms ? a.geoms[si.inst] : a.g;
+    const StripInfo si = (!CLU && a.sinfo) ? a.sinfo[j] : StripInfo{0, j, (long long)j * a.g.sstride(), 0};
+    const Geom g = (!CLU && a.geoms) ? a.geoms[si.inst] : a.g;   // cluster launches are never batched
     const int jl = si.jloc;                  // strip index inside its instance
     const int nyn = g.nyn, ny = nyn - 1, c = g.nxs - 1, P = g.P;
     const int Ns = g.nxs * nyn;
@@ -414,19 +457,34 @@ strip_solve_kernel(StripSolveArgs a) {
     // scale of the first correction: the strip's ||(2i/dt) M h|| (FP32 must not see ~1e-111),
     // but at least 1e-6 of the whole problem's: a far-field strip (h ~ 1e-32) whose residual
     // is set by interface data far above its own h would otherwise overflow FP32
-    double bnorm = 0.0;
-    const double bscale_inst = a.bscale ? ((volatile const double*)a.bscale)[si.inst] : 0.0;
-    const double s_first = fmax(a.bnorm0 ? a.bnorm0[j] : 0.0, 1e-6 * bscale_inst);
-    double inv_s = s_first > 0.0 ? 1.0 / s_first : 1.0;
-    const double nl_tol = a.nl_tol_strip ? a.nl_tol_strip[j] : a.nl_tol;
-    const double nl_floor_frac = a.nl_tol_strip ? a.nl_floor_frac * nl_tol / a.nl_tol : a.nl_floor_frac;
-    const double inner_floor = a.nl_tol_strip ? 0.1 * nl_tol : a.inner_floor;
-    const double floor_abs = nl_floor_frac * bscale_inst;
+    //
+    // The scalar control of the nonlinear iteration (norms, tolerances, scales, relaxation) runs
+    // on thread 0 in FP64 and reaches the block through shared memory: FP64 issues at ~1/64 of
+    // the FP32 rate here, and sixteen warps repeating divisions and square roots would occupy
+    // the FP64 pipe for longer than the vector work of a light strip.
+    __shared__ double s_nld[2];   // inv_s, the correction's scale sc
+    __shared__ float s_nlf[4];    // inv_s in FP32 (clamped), sf2 (on-chip rescale), sc as a double word
+    __shared__ int s_nli[2];      // decision, status
+    double bnorm = 0.0, s_first = 0.0, nl_tol = 0.0, inner_floor = 0.0, floor_abs = 0.0, rnorm0 = 0.0;
     // relaxation of the fixed point: zeta += omega delta, i.e. zeta^q = omega F(zeta^{q-1}) +
     // (1 - omega) zeta^{q-1} (same limit); omega shrinks when a correction does not cut the
     // residual by 10% (the plain iteration diverges for strong nonlinearity)
-    double omega = (a.nl_relax > 0.0 && a.nl_relax <= 1.0) ? a.nl_relax : 1.0;
-    double rprev = 0.0;
+    double omega = 1.0, rprev = 0.0;
+    if (threadIdx.x == 0) {
+        const double bscale_inst = a.bscale ? ((volatile const double*)a.bscale)[si.inst] : 0.0;
+        s_first = fmax(a.bnorm0 ? a.bnorm0[j] : 0.0, 1e-6 * bscale_inst);
+        nl_tol = a.nl_tol_strip ? a.nl_tol_strip[j] : a.nl_tol;
+        const double nl_floor_frac = a.nl_tol_strip ? a.nl_floor_frac * nl_tol / a.nl_tol : a.nl_floor_frac;
+        inner_floor = a.nl_tol_strip ? 0.1 * nl_tol : a.inner_floor;
+        floor_abs = nl_floor_frac * bscale_inst;
+        omega = (a.nl_relax > 0.0 && a.nl_relax <= 1.0) ? a.nl_relax : 1.0;
+        const double is0 = s_first > 0.0 ? 1.0 / s_first : 1.0;
+        s_nld[0] = is0;
+        s_nlf[0] = (float)fmin(is0, 1e30);
+    }
+    __syncthreads();
+    double inv_s = s_nld[0];      // every thread's copy follows thread 0's
+    float inv_sf = s_nlf[0];
 
     // Double-word residual constants.  On the uniform mesh the 1D factors are exact multiples
     // of [1 d 1] (mass, d = 4 inside, 2 at an end) and [-1 e -1] (stiffness, e = 2 / 1), so
@@ -451,7 +509,7 @@ strip_solve_kernel(StripSolveArgs a) {
         // Integer splits away from the edge columns (no FP64 instruction there); ||b||^2 in
         // FP32 in units of the first correction's scale, edge columns apart.
         const dw HXHY = {a.dwk[10], a.dwk[11]};
-        const float bsc = (float)(1.0 / (s_first > 0.0 ? s_first : 1.0));
+        const float bsc = (float)inv_s;
         float bb = 0.f, be = 0.f;
         auto edge_b = [&](int ix, int iy, long long idx) {
             const Coef1<double> cy = coef1<double>(iy, ny, KYd);
@@ -462,44 +520,53 @@ strip_solve_kernel(StripSolveArgs a) {
             const float bxs = bv.x.h * bsc, bys = bv.y.h * bsc;
             be += bxs * bxs + bys * bys;
         };
-        if (a.dw_mode == 2) {
-            // the state and b off the edges are this step's already: refresh b on the edges
-            for (int t = rank * blockDim.x + threadIdx.x; t < 2 * nyn; t += bps * blockDim.x) {
-                const int ix = t < nyn ? 0 : c, iy = t < nyn ? t : t - nyn;
-                edge_b(ix, iy, (long long)ix * P + iy);
-            }
-        } else {
+        // zeta, its accumulated correction and w W of one node in double-word form
+        auto init_node = [&](int ix, int iy, long long idx) {
+            const double2 zv = zeta[idx];
+            cdw_st(zdw + idx, {dw_from_bits(zv.x), dw_from_bits(zv.y)});
+            if (a.dw_mode == 0) cdw_st(ddw + idx, cdw_zero());
+            const float qxy = ((ix > 0 && ix < c) ? 1.f : 0.5f) * ((iy > 0 && iy < ny) ? 1.f : 0.5f);
+            const dw wv = Wn ? dw_pow2(dw_mul(dw_from_bits(Wn[idx]), HXHY), qxy) : dw{0.f, 0.f};
+            a.wdw[sbase + idx] = make_float2(wv.h, wv.l);
+        };
+        // the 2 nyn edge nodes (FP64 data term) in equal shares over the strip's blocks
+        const int ne = 2 * nyn, epc = (ne + bps - 1) / bps;
+        for (int t = rank * epc + threadIdx.x; t < min(ne, (rank + 1) * epc); t += blockDim.x) {
+            const int ix = t < nyn ? 0 : c, iy = t < nyn ? t : t - nyn;
+            const long long idx = (long long)ix * P + iy;
+            edge_b(ix, iy, idx);
+            if (a.dw_mode != 2) init_node(ix, iy, idx);
+        }
+        // the state and b off the edges: this step's already in dw_mode 2
+        if (a.dw_mode != 2) {
             for (int ch = rank; ch < nchunks; ch += bps) {
                 const int n = ch * blockDim.x + threadIdx.x;
                 if (n >= Ns) continue;
                 int ix, iy;
                 split_node(n, nyn, inv_nyn, ix, iy);
+                if (ix == 0 || ix == c) continue;
                 const long long idx = (long long)ix * P + iy;
-                if (ix == 0 || ix == c || unit_side >= 0) {
-                    edge_b(ix, iy, idx);
-                } else {
-                    const double2 b = rhs0 ? rhs0[idx] : make_double2(0.0, 0.0);
-                    const cdw bv = {dw_from_bits(b.x), dw_from_bits(b.y)};
-                    cdw_st(bdw + idx, bv);
-                    const float bxs = bv.x.h * bsc, bys = bv.y.h * bsc;
-                    bb += bxs * bxs + bys * bys;
-                }
-                const double2 zv = zeta[idx];
-                cdw_st(zdw + idx, {dw_from_bits(zv.x), dw_from_bits(zv.y)});
-                if (a.dw_mode == 0) cdw_st(ddw + idx, cdw_zero());
-                const float qxy = ((ix > 0 && ix < c) ? 1.f : 0.5f) * ((iy > 0 && iy < ny) ? 1.f : 0.5f);
-                const dw wv = Wn ? dw_pow2(dw_mul(dw_from_bits(Wn[idx]), HXHY), qxy) : dw{0.f, 0.f};
-                a.wdw[sbase + idx] = make_float2(wv.h, wv.l);
+                const double2 b = rhs0 ? rhs0[idx] : make_double2(0.0, 0.0);
+                const cdw bv = {dw_from_bits(b.x), dw_from_bits(b.y)};
+                cdw_st(bdw + idx, bv);
+                const float bxs = bv.x.h * bsc, bys = bv.y.h * bsc;
+                bb += bxs * bxs + bys * bys;
+                init_node(ix, iy, idx);
             }
         }
-        const double bs2 = (double)bsc * (double)bsc;
-        double lb[4] = {(double)bb / bs2, (double)be / bs2, 0.0, 0.0};
-        block_sum<4>(lb, s_red);
-        double tb[4];
+        float lbT[2] = {bb, be};
+        dw lb2[2];
+        block_sum_dw<2>(lbT, lb2, (float*)s_red);
+        double lb[4] = {0.0, 0.0, 0.0, 0.0}, tb[4];
+        if (threadIdx.x == 0) {
+            const double bs2 = (double)bsc * (double)bsc;
+            lb[0] = dw_to(lb2[0]) / bs2;
+            lb[1] = dw_to(lb2[1]) / bs2;
+        }
         if (!strip_sum4(lb, tb)) status = DD_NLS_ETIMEOUT;
-        if (!status) {
+        if (!status && threadIdx.x == 0) {
             if (a.dw_mode == 2) tb[0] = a.bint2[j];
-            else if (a.dw_mode == 1 && rank == 0 && threadIdx.x == 0) a.bint2[j] = tb[0];
+            else if (a.dw_mode == 1 && rank == 0) a.bint2[j] = tb[0];
             bnorm = sqrt(tb[0] + tb[1]);
         }
         lap(0);
@@ -518,7 +585,6 @@ strip_solve_kernel(StripSolveArgs a) {
         T rz_re = 0, rz_im = 0;
         float rr_f = 0.f;                        // double-word residual: ||res||^2 partial
         const bool need_b = !DW && nl_it == 0;
-        const float inv_sf = DW ? (float)fmin(inv_s, 1e30) : 0.f;
         for (int ch = rank; ch < nchunksR; ch += bps) {
             const int n = ch * blockDim.x + threadIdx.x;
             if (n >= NRall) continue;
@@ -706,23 +772,78 @@ strip_solve_kernel(StripSolveArgs a) {
                 rz_im += rT.x * zT.y + rT.y * zT.x;
             }
         }
-        loc[2] = (double)rz_re;
-        loc[3] = (double)rz_im;
-        if constexpr (DW) {
-            if (dwr) loc[0] = (double)rr_f / ((double)inv_sf * (double)inv_sf);
+        bool fp32_sums = false;
+        if constexpr (DW) fp32_sums = dwr;
+        if (fp32_sums) {
+            // the double-word residual's partials are FP32 (scaled units): block sum in double
+            // words on the FP32 pipe, conversion to FP64 by thread 0 alone
+            float lT[3] = {rr_f, (float)rz_re, (float)rz_im};
+            dw l3[3];
+            block_sum_dw<3>(lT, l3, (float*)s_red);
+            if (threadIdx.x == 0) {
+                const double isf = (double)inv_sf;
+                loc[0] = dw_to(l3[0]) / (isf * isf);
+                loc[1] = 0.0;
+                loc[2] = dw_to(l3[1]);
+                loc[3] = dw_to(l3[2]);
+            }
+        } else {
+            loc[2] = (double)rz_re;
+            loc[3] = (double)rz_im;
+            block_sum<4>(loc, s_red);
         }
-        block_sum<4>(loc, s_red);
         lap(0);
         double tot[4];
         if (!strip_sum4(loc, tot)) { status = DD_NLS_ETIMEOUT; break; }
         lap(4);
-        const double rnorm = sqrt(tot[0]);
-        if (need_b) bnorm = sqrt(tot[1]);
-        nres = bnorm > 0.0 ? rnorm / bnorm : rnorm;
-        if (!isfinite(tot[0]) || !isfinite(tot[1])) { status = DD_NLS_ENONFINITE; break; }
-        if (nres <= nl_tol || rnorm <= floor_abs || rnorm == 0.0) break;
-        if (nl_it >= a.max_nl) { status = DD_NLS_ENOCONV; break; }
-        if (DW && dwr && a.dw_mode == 0 && nres <= kDWFinish) {
+        // thread 0 decides: 0 go on, 1 converged, 2 error (status), 3 leave the double-word residual
+        double rho_r = 0.0, rho_i = 0.0, target = 0.0;     // thread 0's: they drive the recurrences
+        if (threadIdx.x == 0) {
+            const double rnorm = sqrt(tot[0]);
+            if (need_b) bnorm = sqrt(tot[1]);
+            nres = bnorm > 0.0 ? rnorm / bnorm : rnorm;
+            int ctl = 0, st = 0;
+            if (!isfinite(tot[0]) || !isfinite(tot[1])) {
+                ctl = 2;
+                st = DD_NLS_ENONFINITE;
+            } else if (nres <= nl_tol || rnorm <= floor_abs || rnorm == 0.0) {
+                ctl = 1;
+            } else if (nl_it >= a.max_nl) {
+                ctl = 2;
+                st = DD_NLS_ENOCONV;
+            } else if (DW && dwr && a.dw_mode == 0 && nres <= kDWFinish) {
+                ctl = 3;
+                inv_s = 1.0 / rnorm;
+                rprev = INFINITY;
+                s_nld[0] = inv_s;
+                s_nlf[0] = (float)fmin(inv_s, 1e30);
+            } else {
+                if (nl_it > 0 && rnorm > 0.9 * rprev) omega = fmax(0.25, 0.6 * omega);
+                rprev = rnorm;
+                rnorm0 = rnorm;
+                rho_r = tot[2];
+                rho_i = tot[3];
+                // inner stopping test in the scaled units of r
+                target = fmax(a.inner_tol * rnorm, fmax(inner_floor * bnorm, 0.1 * floor_abs)) * inv_s;
+                // r holds res * inv_s, scaled for the launch's first correction; a later one (a
+                // strip near convergence) is far smaller, and FP32 squares of the on-chip
+                // recurrences (|delta|^2, ||r||^2) would underflow: the power of two sf2 brings
+                // ||r|| to [1/2, 1) there (exact; the correction's scale takes the same factor)
+                int e2 = 0;
+                (void)frexp(rnorm * inv_s, &e2);
+                e2 = max(-120, min(120, e2));
+                s_nlf[1] = __int_as_float((127 - e2) << 23);   // 2^-e2
+            }
+            s_nli[0] = ctl;
+            s_nli[1] = st;
+        }
+        __syncthreads();
+        {
+            const int ctl = s_nli[0];
+            if (ctl == 1) break;
+            if (ctl == 2) { status = s_nli[1]; break; }
+        }
+        if (DW && dwr && s_nli[0] == 3) {
             for (int ch = rank; ch < nchunks; ch += bps) {
                 const int n = ch * blockDim.x + threadIdx.x;
                 if (n >= Ns) continue;
@@ -734,18 +855,13 @@ strip_solve_kernel(StripSolveArgs a) {
                 zeta[idx] = make_double2(zv.x + dw_to(d.x), zv.y + dw_to(d.y));
             }
             dwr = false;
-            inv_s = 1.0 / rnorm;
-            rprev = INFINITY;
+            inv_s = s_nld[0];
+            inv_sf = s_nlf[0];
             if (!strip_barrier()) { status = DD_NLS_ETIMEOUT; break; }
             continue;       // the next residual is the FP64 one
         }
-        if (nl_it > 0 && rnorm > 0.9 * rprev) omega = fmax(0.25, 0.6 * omega);
-        rprev = rnorm;
 
         // ---------------- inner COCG on A(c) delta = res, Jacobi preconditioner
-        double rho_r = tot[2], rho_i = tot[3];     // thread 0's copy drives the recurrences
-        // inner stopping test in the scaled units of r
-        const double target = fmax(a.inner_tol * rnorm, fmax(inner_floor * bnorm, 0.1 * floor_abs)) * inv_s;
         if (CLU && use_sr) {
             if constexpr (CLU) {
             // ---- single-reduction COCG with the Krylov state on chip (one strip per cluster).
@@ -760,21 +876,25 @@ strip_solve_kernel(StripSolveArgs a) {
             float2* Ps = Ws + (size_t)NX * H;
             float2* Ss = Ps + (size_t)NX * H;
             float2* Ds = Ss + (size_t)NX * H;             // D^-1
-            float2* Ex = Ds + (size_t)NX * H;             // exported rows [2 parity][2 side][r w s D^-1][NX]
+            float2* Ex = Ds + (size_t)NX * H;             // exported rows [2 parity][2 side][r w s][NX]
+            float2* Dh = Ex + (size_t)12 * NX;            // D^-1 of the halo rows [up, down][NX]
             float* Cs = (float*)(Ex + (size_t)16 * NX);   // c of A(c)
-            auto exp_at = [&](int par, int side, int arr, int ix) { return Ex + ((size_t)(par * 2 + side) * 4 + arr) * NX + ix; };
+            auto exp_at = [&](int par, int side, int arr, int ix) { return Ex + ((size_t)(par * 2 + side) * 3 + arr) * NX + ix; };
+            const Interior9<T2> W9 = interior9<T, T2>(KXt, KYt, alphaT);
+            // w = A(c) z at slab node (ix, iy): the interior stencil off the edges, else the general one
+            auto apply_at = [&](int ix, int iy, int zo, T cdg) -> T2 {
+                if (ix > 0 && ix < c && iy > 0 && iy < ny) return apply_interior<T, T2>(Zs, zo, ZP, W9, cdg);
+                const Coef1<T> cxT = coef1<T>(ix, c, KXt), cyT = coef1<T>(iy, ny, KYt);
+                T rre, rim;
+                rho_atT(ix, rre, rim);
+                return apply_op<T, T2>(Zs, zo, ix, iy, c, ny, ZP, cxT, cyT, alphaT, rre, rim, cdg);
+            };
             const bool has_up = y0 > 0 && h > 0, has_dn = y1 < nyn && h > 0;
             const unsigned nb_up = (unsigned)(rank - 1), nb_dn = (unsigned)(rank + 1);
             T2 rreg[kOnChipNPT], xreg[kOnChipNPT];
             const T2 zeroT = mk<T2>(0.0, 0.0);
-            // r holds res * inv_s, scaled for the launch's first correction; a later correction
-            // (a strip near convergence) is far smaller, and the FP32 squares of the recurrences
-            // (|delta|^2, ||r||^2) would underflow.  Rescale by the power of two sf2 that brings
-            // ||r|| to [1/2, 1): exact, and the correction's scale inv_s takes the same factor.
-            int e2 = 0;
-            (void)frexp(rnorm * inv_s, &e2);
-            e2 = max(-120, min(120, e2));
-            const float sf2 = __int_as_float((127 - e2) << 23);   // 2^-e2
+            // r rescaled by the power of two sf2 (thread 0's choice above)
+            const float sf2 = s_nlf[1];
             const T2 sf2v = T2{sf2, 0.f};
             // load r_0 (scaled residual), D^-1, c of the residual pass; x = p = s_{-1} = 0
 #pragma unroll
@@ -796,10 +916,19 @@ strip_solve_kernel(StripSolveArgs a) {
                 Ss[o] = zeroT;
                 Zs[ix * ZP + il + 1] = cmul(dvv, rreg[k]);
             }
-            // halo rows of z_0 = D^-1 r_0 from global memory (written by the residual pass)
+            // halo rows of z_0 = D^-1 r_0 and their D^-1 (fixed during the solve) from global memory
+            // (written by the residual pass)
             for (int ix = threadIdx.x; ix < NX; ix += BS) {
-                if (has_up) Zs[ix * ZP] = cmul(cmul(dv[(long long)ix * P + y0 - 1], r[(long long)ix * P + y0 - 1]), sf2v);
-                if (has_dn) Zs[ix * ZP + h + 1] = cmul(cmul(dv[(long long)ix * P + y1], r[(long long)ix * P + y1]), sf2v);
+                if (has_up) {
+                    const T2 du = dv[(long long)ix * P + y0 - 1];
+                    Dh[ix] = du;
+                    Zs[ix * ZP] = cmul(cmul(du, r[(long long)ix * P + y0 - 1]), sf2v);
+                }
+                if (has_dn) {
+                    const T2 dd = dv[(long long)ix * P + y1];
+                    Dh[NX + ix] = dd;
+                    Zs[ix * ZP + h + 1] = cmul(cmul(dd, r[(long long)ix * P + y1]), sf2v);
+                }
             }
             __syncthreads();
             // w_0 = A z_0, delta_0 = w_0^T z_0; export the slab's first and last rows (parity 0)
@@ -811,26 +940,28 @@ strip_solve_kernel(StripSolveArgs a) {
                 int ix, il;
                 split_node(mm, h, inv_h, ix, il);
                 const int iy = y0 + il, o = ix * H + il, zo = ix * ZP + il + 1;
-                const Coef1<T> cxT = coef1<T>(ix, c, KXt), cyT = coef1<T>(iy, ny, KYt);
-                T rre, rim;
-                rho_atT(ix, rre, rim);
-                const T2 w0 = apply_op<T, T2>(Zs, zo, ix, iy, c, ny, ZP, cxT, cyT, alphaT, rre, rim, Cs[o]);
+                const T2 w0 = apply_at(ix, iy, zo, Cs[o]);
                 const T2 zo_v = Zs[zo];
                 Ws[o] = w0;
                 d0r += w0.x * zo_v.x - w0.y * zo_v.y;
                 d0i += w0.x * zo_v.y + w0.y * zo_v.x;
                 if (il == 0) {
-                    *exp_at(0, 0, 0, ix) = rreg[k]; *exp_at(0, 0, 1, ix) = w0; *exp_at(0, 0, 2, ix) = zeroT; *exp_at(0, 0, 3, ix) = Ds[o];
+                    *exp_at(0, 0, 0, ix) = rreg[k]; *exp_at(0, 0, 1, ix) = w0; *exp_at(0, 0, 2, ix) = zeroT;
                 }
                 if (il == h - 1) {
-                    *exp_at(0, 1, 0, ix) = rreg[k]; *exp_at(0, 1, 1, ix) = w0; *exp_at(0, 1, 2, ix) = zeroT; *exp_at(0, 1, 3, ix) = Ds[o];
+                    *exp_at(0, 1, 0, ix) = rreg[k]; *exp_at(0, 1, 1, ix) = w0; *exp_at(0, 1, 2, ix) = zeroT;
                 }
             }
             // thread-0 state of the recurrences, in double words (no FP64 on the iteration path)
-            const double sf2d = (double)sf2;
-            cdw gam = {dw_from(rho_r * sf2d * sf2d), dw_from(rho_i * sf2d * sf2d)}, al = cdw_zero(), be = cdw_zero();
+            cdw gam = cdw_zero(), al = cdw_zero(), be = cdw_zero();
+            float target2 = 0.f;
+            if (threadIdx.x == 0) {
+                const double sf2d = (double)sf2;
+                gam = {dw_from(rho_r * sf2d * sf2d), dw_from(rho_i * sf2d * sf2d)};
+                target2 = (float)((target * sf2d) * (target * sf2d));
+                inv_s *= sf2d;      // x is the correction in units of 1/(inv_s sf2)
+            }
             float* s_outf = (float*)s_out;
-            const float target2 = (float)((target * sf2d) * (target * sf2d));
             {
                 float lT[2] = {d0r, d0i};
                 dw l2[2];
@@ -884,21 +1015,21 @@ strip_solve_kernel(StripSolveArgs a) {
                     Ss[o] = sn;
                     Zs[ix * ZP + il + 1] = cmul(dvv, rreg[k]);
                 }
-                // halo rows of z_{k+1}, rebuilt from the neighbours' exported r_k, w_k, s_{k-1}, D^-1
+                // halo rows of z_{k+1}, rebuilt from the neighbours' exported r_k, w_k, s_{k-1}
                 for (int ix = threadIdx.x; ix < NX; ix += BS) {
                     if (has_up) {
                         T2 sv;
                         const T2 rr = rnext_v(ld_cluster_f2(mapa(smem_addr(exp_at(pin, 1, 0, ix)), nb_up)),
                                               ld_cluster_f2(mapa(smem_addr(exp_at(pin, 1, 1, ix)), nb_up)),
                                               ld_cluster_f2(mapa(smem_addr(exp_at(pin, 1, 2, ix)), nb_up)), alT, beT, sv);
-                        Zs[ix * ZP] = cmul(ld_cluster_f2(mapa(smem_addr(exp_at(pin, 1, 3, ix)), nb_up)), rr);
+                        Zs[ix * ZP] = cmul(Dh[ix], rr);
                     }
                     if (has_dn) {
                         T2 sv;
                         const T2 rr = rnext_v(ld_cluster_f2(mapa(smem_addr(exp_at(pin, 0, 0, ix)), nb_dn)),
                                               ld_cluster_f2(mapa(smem_addr(exp_at(pin, 0, 1, ix)), nb_dn)),
                                               ld_cluster_f2(mapa(smem_addr(exp_at(pin, 0, 2, ix)), nb_dn)), alT, beT, sv);
-                        Zs[ix * ZP + h + 1] = cmul(ld_cluster_f2(mapa(smem_addr(exp_at(pin, 0, 3, ix)), nb_dn)), rr);
+                        Zs[ix * ZP + h + 1] = cmul(Dh[NX + ix], rr);
                     }
                 }
                 __syncthreads();
@@ -911,10 +1042,7 @@ strip_solve_kernel(StripSolveArgs a) {
                     int ix, il;
                     split_node(mm, h, inv_h, ix, il);
                     const int iy = y0 + il, o = ix * H + il, zo = ix * ZP + il + 1;
-                    const Coef1<T> cxT = coef1<T>(ix, c, KXt), cyT = coef1<T>(iy, ny, KYt);
-                    T rre, rim;
-                    rho_atT(ix, rre, rim);
-                    const T2 wn = apply_op<T, T2>(Zs, zo, ix, iy, c, ny, ZP, cxT, cyT, alphaT, rre, rim, Cs[o]);
+                    const T2 wn = apply_at(ix, iy, zo, Cs[o]);
                     const T2 zz = Zs[zo], rv = rreg[k];
                     Ws[o] = wn;
                     g_r += rv.x * zz.x - rv.y * zz.y;
@@ -923,10 +1051,10 @@ strip_solve_kernel(StripSolveArgs a) {
                     dlt_i += wn.x * zz.y + wn.y * zz.x;
                     rr2 += rv.x * rv.x + rv.y * rv.y;
                     if (il == 0) {
-                        *exp_at(pout, 0, 0, ix) = rv; *exp_at(pout, 0, 1, ix) = wn; *exp_at(pout, 0, 2, ix) = Ss[o]; *exp_at(pout, 0, 3, ix) = Ds[o];
+                        *exp_at(pout, 0, 0, ix) = rv; *exp_at(pout, 0, 1, ix) = wn; *exp_at(pout, 0, 2, ix) = Ss[o];
                     }
                     if (il == h - 1) {
-                        *exp_at(pout, 1, 0, ix) = rv; *exp_at(pout, 1, 1, ix) = wn; *exp_at(pout, 1, 2, ix) = Ss[o]; *exp_at(pout, 1, 3, ix) = Ds[o];
+                        *exp_at(pout, 1, 0, ix) = rv; *exp_at(pout, 1, 1, ix) = wn; *exp_at(pout, 1, 2, ix) = Ss[o];
                     }
                 }
                 float lT[5] = {g_r, g_i, dlt_r, dlt_i, rr2};
@@ -1004,7 +1132,6 @@ strip_solve_kernel(StripSolveArgs a) {
                 split_node(mm, h, inv_h, ix, il);
                 x[(long long)ix * P + y0 + il] = xreg[k];
             }
-            inv_s *= sf2d;      // x is the correction in units of 1/(inv_s sf2)
             if (cstat) { status = cstat; break; }
             if (!strip_barrier()) { status = DD_NLS_ETIMEOUT; break; }
             }
@@ -1365,10 +1492,22 @@ strip_solve_kernel(StripSolveArgs a) {
         }
         if (status) break;
         // ---------------- zeta += delta (FP64), then every block must see the new zeta
-        const double sc = omega / inv_s;
+        // thread 0: the correction's scale sc = omega / inv_s and the next correction's inv_s
+        if (threadIdx.x == 0) {
+            const double sc0 = omega / inv_s;
+            const dw scd0 = dw_from(sc0);
+            s_nld[1] = sc0;
+            s_nlf[2] = scd0.h;
+            s_nlf[3] = scd0.l;
+            inv_s = 1.0 / rnorm0;
+            s_nld[0] = inv_s;
+            s_nlf[0] = (float)fmin(inv_s, 1e30);
+        }
+        __syncthreads();
+        const double sc = s_nld[1];
         if (DW && dwr) {
             // double-word zeta and the correction accumulated over the launch
-            const dw scd = dw_from(sc);
+            const dw scd = {s_nlf[2], s_nlf[3]};
             for (int ch = rank; ch < nchunks; ch += bps) {
                 const int n = ch * blockDim.x + threadIdx.x;
                 if (n >= Ns) continue;
@@ -1399,7 +1538,8 @@ strip_solve_kernel(StripSolveArgs a) {
                 phi[fi] = make_double2(phi[fi].x + sc * dx.x, phi[fi].y + sc * dx.y);
             }
         }
-        inv_s = 1.0 / rnorm;           // scale of the next correction
+        inv_s = s_nld[0];              // scale of the next correction
+        inv_sf = s_nlf[0];
         lap(3);
         if (!strip_barrier()) { status = DD_NLS_ETIMEOUT; break; }
         lap(4);
@@ -1500,7 +1640,7 @@ static cudaError_t launch_strip_solve_t(const StripSolveArgs& args, int nblocks,
     void* params[] = {&a};
     dim3 grid(nblocks), block(bs);
     count_launches(1);
-    if (sizeof(T) == 4 && a.cluster && a.mode == 0 && a.pade_m == 0) {
+    if (sizeof(T) == 4 && a.cluster && a.mode == 0 && a.pade_m == 0 && !a.geoms && !a.sinfo) {
         // nblocks = strips: one cluster per strip, clusters independent (no cooperative launch)
         const bool dw = a.zdw != nullptr;
         cudaError_t e = cluster_prepare(dw, a.cluster_smem);
