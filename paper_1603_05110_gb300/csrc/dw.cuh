@@ -117,6 +117,19 @@ __device__ __forceinline__ cdw cdw_div(const cdw& a, const cdw& b) {
     const cdw t = cdw_mul(a, {bs.x, dw_neg(bs.y)});
     return {dw_pow2(dw_mul(t.x, inv), p2), dw_pow2(dw_mul(t.y, inv), p2)};
 }
+// 1 / b = conj(b) / |b|^2, with b scaled by a power of two as in cdw_div
+__device__ __forceinline__ cdw cdw_recip(const cdw& b) {
+    const float m = fmaxf(fabsf(b.x.h), fabsf(b.y.h));
+    int e = 0;
+    if (m > 0.f && m < INFINITY) e = ((__float_as_int(m) >> 23) & 0xff) - 127;
+    e = max(-120, min(120, e));
+    const float p2 = __int_as_float((127 - e) << 23);   // 2^-e
+    const cdw bs = {dw_pow2(b.x, p2), dw_pow2(b.y, p2)};
+    const dw inv = dw_recip(cdw_abs2(bs));
+    return {dw_pow2(dw_mul(bs.x, inv), p2), dw_pow2(dw_mul(dw_neg(bs.y), inv), p2)};
+}
+__device__ __forceinline__ bool cdw_nonzero(const cdw& a) { return a.x.h != 0.f || a.y.h != 0.f; }
+__device__ __forceinline__ bool cdw_finite(const cdw& a) { return isfinite(a.x.h) && isfinite(a.y.h); }
 __device__ __forceinline__ cdw cdw_sub(const cdw& a, const cdw& b) { return {dw_sub(a.x, b.x), dw_sub(a.y, b.y)}; }
 __device__ __forceinline__ cdw cdw_add_s(const cdw& a, const cdw& b) { return {dw_add_s(a.x, b.x), dw_add_s(a.y, b.y)}; }
 __device__ __forceinline__ cdw cdw_sub_s(const cdw& a, const cdw& b) { return {dw_sub_s(a.x, b.x), dw_sub_s(a.y, b.y)}; }

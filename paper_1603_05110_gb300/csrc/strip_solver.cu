@@ -238,6 +238,8 @@ strip_solve_kernel(StripSolveArgs a) {
     // s_sc = alpha, beta in the inner precision
     __shared__ int s_ctl[2];
     __shared__ T s_sc[4];
+    __shared__ float s_kr[24];    // thread 0's state of the on-chip recurrences (cluster mode)
+    __shared__ int s_kri;
 
     // strip of the launch (virtual strip in setup mode); cluster mode: cluster c solves strip
     // blk_strip[c] and its CTAs are the strip's blocks
@@ -398,7 +400,20 @@ strip_solve_kernel(StripSolveArgs a) {
 
     int status = 0, nl_it = 0;
     long long kry = 0;
-    double nres = 0.0;
+    // thread 0's scalars of the nonlinear control live in shared memory: as registers they would
+    // be live (and spilled) in every thread across the Krylov loops
+    __shared__ double s_t0[12];
+    double& nres = s_t0[0];
+    double& bnorm = s_t0[1];
+    double& nl_tol = s_t0[2];
+    double& inner_floor = s_t0[3];
+    double& floor_abs = s_t0[4];
+    double& rnorm0 = s_t0[5];
+    double& omega = s_t0[6];       // relaxation (below)
+    double& rprev = s_t0[7];
+    double& rho_r = s_t0[8];       // rho = r^T z and the inner target: they drive the recurrences
+    double& rho_i = s_t0[9];
+    double& target = s_t0[10];
     // optional phase timing (thread 0, SM clock cycles): R, A, B, epilogue compute; waits
     long long cyc[5] = {0, 0, 0, 0, 0};
     long long tmark = clock64();
@@ -465,14 +480,13 @@ strip_solve_kernel(StripSolveArgs a) {
     __shared__ double s_nld[2];   // inv_s, the correction's scale sc
     __shared__ float s_nlf[4];    // inv_s in FP32 (clamped), sf2 (on-chip rescale), sc as a double word
     __shared__ int s_nli[2];      // decision, status
-    double bnorm = 0.0, s_first = 0.0, nl_tol = 0.0, inner_floor = 0.0, floor_abs = 0.0, rnorm0 = 0.0;
     // relaxation of the fixed point: zeta += omega delta, i.e. zeta^q = omega F(zeta^{q-1}) +
     // (1 - omega) zeta^{q-1} (same limit); omega shrinks when a correction does not cut the
     // residual by 10% (the plain iteration diverges for strong nonlinearity)
-    double omega = 1.0, rprev = 0.0;
     if (threadIdx.x == 0) {
+        nres = bnorm = rnorm0 = rprev = rho_r = rho_i = target = 0.0;
         const double bscale_inst = a.bscale ? ((volatile const double*)a.bscale)[si.inst] : 0.0;
-        s_first = fmax(a.bnorm0 ? a.bnorm0[j] : 0.0, 1e-6 * bscale_inst);
+        const double s_first = fmax(a.bnorm0 ? a.bnorm0[j] : 0.0, 1e-6 * bscale_inst);
         nl_tol = a.nl_tol_strip ? a.nl_tol_strip[j] : a.nl_tol;
         const double nl_floor_frac = a.nl_tol_strip ? a.nl_floor_frac * nl_tol / a.nl_tol : a.nl_floor_frac;
         inner_floor = a.nl_tol_strip ? 0.1 * nl_tol : a.inner_floor;
@@ -797,7 +811,6 @@ strip_solve_kernel(StripSolveArgs a) {
         if (!strip_sum4(loc, tot)) { status = DD_NLS_ETIMEOUT; break; }
         lap(4);
         // thread 0 decides: 0 go on, 1 converged, 2 error (status), 3 leave the double-word residual
-        double rho_r = 0.0, rho_i = 0.0, target = 0.0;     // thread 0's: they drive the recurrences
         if (threadIdx.x == 0) {
             const double rnorm = sqrt(tot[0]);
             if (need_b) bnorm = sqrt(tot[1]);
@@ -871,14 +884,16 @@ strip_solve_kernel(StripSolveArgs a) {
             const int y0 = min(nyn, rank * H), y1 = min(nyn, y0 + H), h = y1 - y0;
             const int M = h * g.nxs, ZP = H + 2, NX = g.nxs;
             const float inv_h = h > 0 ? 1.0f / (float)h : 0.f;
-            float2* Zs = (float2*)s_dyn;                  // z with halo rows: [NX][H + 2]
-            float2* Ws = Zs + (size_t)NX * ZP;            // [NX][H]
-            float2* Ps = Ws + (size_t)NX * H;
-            float2* Ss = Ps + (size_t)NX * H;
-            float2* Ds = Ss + (size_t)NX * H;             // D^-1
-            float2* Ex = Ds + (size_t)NX * H;             // exported rows [2 parity][2 side][r w s][NX]
-            float2* Dh = Ex + (size_t)12 * NX;            // D^-1 of the halo rows [up, down][NX]
-            float* Cs = (float*)(Ex + (size_t)16 * NX);   // c of A(c)
+            // disjoint arrays of the dynamic shared memory (restrict: loads of one node may be
+            // scheduled ahead of the stores of the previous one)
+            float2* __restrict__ Zs = (float2*)s_dyn;                  // z with halo rows: [NX][H + 2]
+            float2* __restrict__ Ws = (float2*)s_dyn + (size_t)NX * ZP;            // [NX][H]
+            float2* __restrict__ Ps = (float2*)s_dyn + (size_t)NX * (ZP + H);
+            float2* __restrict__ Ss = (float2*)s_dyn + (size_t)NX * (ZP + 2 * H);
+            float2* __restrict__ Ds = (float2*)s_dyn + (size_t)NX * (ZP + 3 * H);  // D^-1
+            float2* __restrict__ Ex = (float2*)s_dyn + (size_t)NX * (ZP + 4 * H);  // exported rows [2 parity][2 side][r w s][NX]
+            float2* __restrict__ Dh = Ex + (size_t)12 * NX;            // D^-1 of the halo rows [up, down][NX]
+            float* __restrict__ Cs = (float*)(Ex + (size_t)16 * NX);   // c of A(c)
             auto exp_at = [&](int par, int side, int arr, int ix) { return Ex + ((size_t)(par * 2 + side) * 3 + arr) * NX + ix; };
             const Interior9<T2> W9 = interior9<T, T2>(KXt, KYt, alphaT);
             // w = A(c) z at slab node (ix, iy): the interior stencil off the edges, else the general one
@@ -952,13 +967,24 @@ strip_solve_kernel(StripSolveArgs a) {
                     *exp_at(0, 1, 0, ix) = rreg[k]; *exp_at(0, 1, 1, ix) = w0; *exp_at(0, 1, 2, ix) = zeroT;
                 }
             }
-            // thread-0 state of the recurrences, in double words (no FP64 on the iteration path)
-            cdw gam = cdw_zero(), al = cdw_zero(), be = cdw_zero();
-            float target2 = 0.f;
+            // thread-0 state of the recurrences, in double words (no FP64 on the iteration path),
+            // kept in shared memory (no registers in the other threads): gamma_k, 1/gamma_k,
+            // q_k = 1/(gamma_k alpha_k), alpha_k, beta_k, the stopping bound and the stagnation guard
+            cdw& gam = *reinterpret_cast<cdw*>(s_kr);
+            cdw& ig = *reinterpret_cast<cdw*>(s_kr + 4);
+            cdw& qk = *reinterpret_cast<cdw*>(s_kr + 8);
+            cdw& al = *reinterpret_cast<cdw*>(s_kr + 12);
+            cdw& be = *reinterpret_cast<cdw*>(s_kr + 16);
+            float& target2 = s_kr[20];
+            float& best2 = s_kr[21];      // least ||r||^2 so far
+            int& since = s_kri;           // iterations since it fell by 1%
             if (threadIdx.x == 0) {
                 const double sf2d = (double)sf2;
                 gam = {dw_from(rho_r * sf2d * sf2d), dw_from(rho_i * sf2d * sf2d)};
+                ig = qk = al = be = cdw_zero();
                 target2 = (float)((target * sf2d) * (target * sf2d));
+                best2 = INFINITY;
+                since = 0;
                 inv_s *= sf2d;      // x is the correction in units of 1/(inv_s sf2)
             }
             float* s_outf = (float*)s_out;
@@ -980,7 +1006,12 @@ strip_solve_kernel(StripSolveArgs a) {
                         ctl = 2;
                         st = isfinite(dd2) ? DD_NLS_EBREAKDOWN : DD_NLS_ENONFINITE;
                     } else {
-                        al = cdw_div(gam, del);
+                        al = cdw_mul(gam, cdw_recip(del));     // alpha_0 = gamma_0 / delta_0
+                        if (cdw_nonzero(gam)) {
+                            const cdw rg2 = cdw_recip(cdw_mul(gam, gam));
+                            ig = cdw_mul(gam, rg2);
+                            qk = cdw_mul(del, rg2);
+                        }
                     }
                     s_ctl[0] = ctl;
                     s_ctl[1] = st;
@@ -991,8 +1022,6 @@ strip_solve_kernel(StripSolveArgs a) {
             __syncthreads();
             lap(4);
             if (s_ctl[0]) { status = s_ctl[1]; break; }
-            float best2 = INFINITY;      // stagnation guard on ||r||^2
-            int since = 0;
             T2 alT = T2{s_sc[0], s_sc[1]}, beT = T2{0, 0};
             int cstat = 0;
             for (int it = 0; it < a.max_inner; ++it) {
@@ -1086,21 +1115,25 @@ strip_solve_kernel(StripSolveArgs a) {
                         } else if (++since >= 32) {
                             ctl = 3;
                         }
-                        if (!ctl && !(cdw_abs2(gam).h > 0.f)) ctl = 3;
+                        if (!ctl && !cdw_nonzero(gam)) ctl = 3;
                         if (!ctl) {
-                            // beta_{k+1} = gamma_{k+1}/gamma_k,
-                            // alpha_{k+1} = gamma_{k+1}/(delta_{k+1} - beta_{k+1} gamma_{k+1}/alpha_k)
-                            const cdw nb = cdw_div(gk, gam);
-                            const cdw den = cdw_sub(dk, cdw_div(cdw_mul(nb, gk), al));
-                            const float den2 = cdw_abs2(den).h;
-                            if (!isfinite(den2)) {
+                            // beta_{k+1} = gamma_{k+1}/gamma_k and
+                            // alpha_{k+1} = gamma_{k+1}/(delta_{k+1} - beta_{k+1} gamma_{k+1}/alpha_k),
+                            // the latter as gamma_{k+1}/(delta_{k+1} - gamma_{k+1}^2 q_k): two
+                            // independent reciprocals per step instead of three chained quotients
+                            const cdw g2 = cdw_mul(gk, gk);
+                            const cdw den = cdw_sub(dk, cdw_mul(g2, qk));
+                            if (!cdw_finite(den) || !cdw_finite(g2)) {
                                 ctl = 2;
                                 st = DD_NLS_ENONFINITE;
-                            } else if (!(den2 > 0.f)) {
+                            } else if (!cdw_nonzero(den) || !cdw_nonzero(g2)) {
                                 ctl = 3;
                             } else {
-                                al = cdw_div(gk, den);
-                                be = nb;
+                                const cdw r1 = cdw_recip(den), r2 = cdw_recip(g2);
+                                be = cdw_mul(gk, ig);
+                                al = cdw_mul(gk, r1);
+                                qk = cdw_mul(den, r2);
+                                ig = cdw_mul(gk, r2);
                                 gam = gk;
                             }
                         }

@@ -211,3 +211,75 @@ def test_complex_double_word_quotient_relative_error():
         err = abs(complex(float(val(qx) - ex), float(val(qy) - ey))) / mag
         worst = max(worst, err)
     assert worst <= 2.0 ** -43, worst
+
+
+def cmul(a, b):
+    """cdw_mul: (ax bx - ay by) + i (ax by + ay bx) with double-word products and sums."""
+    (ax, ay), (bx, by) = a, b
+    return (add_accurate(mul(ax, bx), tuple(-t for t in mul(ay, by))), add_accurate(mul(ax, by), mul(ay, bx)))
+
+
+def crecip(b):
+    """cdw_recip without its power-of-two scaling: conj(b) / |b|^2."""
+    bx, by = b
+    inv = recip(add_accurate(mul(bx, bx), mul(by, by)))
+    return mul(bx, inv), mul(tuple(-t for t in by), inv)
+
+
+def cval(a):
+    return complex(float(val(a[0])), float(val(a[1])))
+
+
+def test_two_reciprocal_recurrence_matches_the_quotient_form():
+    """The single-reduction COCG scalars (Chronopoulos-Gear form of CG, unconjugated): from gamma_k,
+    delta_k the quotient form gives beta_{k+1} = gamma_{k+1}/gamma_k and alpha_{k+1} =
+    gamma_{k+1}/(delta_{k+1} - beta_{k+1} gamma_{k+1}/alpha_k).  The on-chip solver carries
+    q_k = 1/(gamma_k alpha_k) and 1/gamma_k instead (two independent reciprocals per step).  Over
+    40-step sequences of random complex gamma, delta the double-word version stays within 2^-38 of
+    the quotient form evaluated exactly."""
+    rng = np.random.default_rng(11)
+    worst = 0.0
+    for _ in range(30):
+        cz = lambda: complex(rng.standard_normal(), rng.standard_normal()) * 10.0 ** rng.uniform(-2, 2)
+        g0, d0 = cz(), cz()
+        # exact (rational) reference of the quotient form
+        G0, D0 = (F(g0.real), F(g0.imag)), (F(d0.real), F(d0.imag))
+
+        def qmul(a, b):
+            return (a[0] * b[0] - a[1] * b[1], a[0] * b[1] + a[1] * b[0])
+
+        def qdiv(a, b):
+            den = b[0] * b[0] + b[1] * b[1]
+            return ((a[0] * b[0] + a[1] * b[1]) / den, (a[1] * b[0] - a[0] * b[1]) / den)
+
+        gam_x = (dw(g0.real), dw(g0.imag))
+        del_x = (dw(d0.real), dw(d0.imag))
+        Gk = (val(gam_x[0]), val(gam_x[1]))
+        Ak = qdiv(Gk, (val(del_x[0]), val(del_x[1])))
+        # double-word state
+        al = cmul(gam_x, crecip(del_x))
+        rg2 = crecip(cmul(gam_x, gam_x))
+        ig = cmul(gam_x, rg2)
+        qk = cmul(del_x, rg2)
+        gam = gam_x
+        for _k in range(40):
+            g1, d1 = cz(), cz()
+            gk = (dw(g1.real), dw(g1.imag))
+            dk = (dw(d1.real), dw(d1.imag))
+            G1, D1 = (val(gk[0]), val(gk[1])), (val(dk[0]), val(dk[1]))
+            B1 = qdiv(G1, Gk)
+            t = qdiv(qmul(B1, G1), Ak)
+            A1 = qdiv(G1, (D1[0] - t[0], D1[1] - t[1]))
+            g2 = cmul(gk, gk)
+            m = cmul(g2, qk)
+            den = (add_accurate(dk[0], tuple(-v for v in m[0])), add_accurate(dk[1], tuple(-v for v in m[1])))
+            r1, r2 = crecip(den), crecip(g2)
+            be = cmul(gk, ig)
+            al = cmul(gk, r1)
+            qk = cmul(den, r2)
+            ig = cmul(gk, r2)
+            for got, ref in ((al, A1), (be, B1)):
+                rv = complex(float(ref[0]), float(ref[1]))
+                worst = max(worst, abs(cval(got) - rv) / abs(rv))
+            Gk, Ak = G1, A1
+    assert worst <= 2.0 ** -38, worst
