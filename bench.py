@@ -69,6 +69,10 @@ def parse(argv=None):
     ap.add_argument("--residual", default="dw", choices=["fp64", "dw"],
                     help="nonlinear residual of the chosen form: FP64, or double-word on the FP32 pipe")
     ap.add_argument("--instances", type=int, default=64)
+    ap.add_argument("--batch-form", default="chosen", choices=["chosen", "classical"],
+                    help="gpe_batch: preconditioned + double-word residual (chosen) or classical + FP32 inner")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="nls_well: skip the gpe_trap and gpe_batch lines nested under 'configs'")
     ap.add_argument("--learn-n", type=int, default=256, help="learned_guess: cells per direction")
     ap.add_argument("--learn-strips", type=int, default=8)
     ap.add_argument("--learn-steps", type=int, default=160, help="learned_guess: steps generated")
@@ -490,9 +494,26 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": prof["kernel_launches"],
         "clocks": clk,
     }
-    print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+    return line
+
+
+def extra_configs(args, local_rank):
+    """The other single-GPU configurations, run after the headline one with fewer steps: the GPE
+    trap with S_pade (gpe_trap) and the batched GPE instances (gpe_batch), each with its own
+    roofline, oracle sample, e2e and clocks."""
+    out = {}
+    common = ["--warmup", "3", "--no-fp64", "--cpu-budget", str(args.cpu_budget), "--tol", str(args.tol)]
+    if args.no_cpu:
+        common.append("--no-cpu")
+    for name, steps in (("gpe_trap", max(2, min(args.steps, 5))), ("gpe_batch", max(2, min(args.steps, 3)))):
+        a = parse(["--workload", name, "--steps", str(steps)] + common)
+        try:
+            out[name] = run_batch(a, 0, 1, local_rank) if name == "gpe_batch" else run_ours(a, 0, 1, local_rank)
+        except Exception as e:          # a failed extra line must not cost the headline line
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+    return out
 
 
 def run_batch(args, rank, world, local_rank):
@@ -507,11 +528,14 @@ def run_batch(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     ws = wl.gpe_batch(args.instances)
+    chosen = args.batch_form == "chosen"
     prms = []
     for w in ws:
-        d = solver_params(w, args, binding.FP32_INNER)
-        d.update(p=w.p, algorithm=binding.CLASSICAL, tol=args.tol, max_schwarz=args.max_schwarz, nl_tol=1e-13,
-                 omega_rot=w.extra["omega"])
+        # chosen: preconditioned Schwarz (modal P^-1 per instance) with the double-word residual;
+        # classical: the plain algorithm with the FP64 residual
+        d = solver_params(w, args, binding.FP32_DW if chosen else binding.FP32_INNER)
+        d.update(p=w.p, algorithm=binding.PRECONDITIONED if chosen else binding.CLASSICAL, tol=args.tol,
+                 max_schwarz=args.max_schwarz, nl_tol=1e-11 if chosen else 1e-13, omega_rot=w.extra["omega"])
         prms.append(d)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -578,7 +602,7 @@ def run_batch(args, rank, world, local_rank):
             w = copy.deepcopy(ws[i])
             w.extra["relax"] = 0.6          # the oracle's plain fixed point diverges for the strongest beta
             a2 = parse(["--workload", "nls_well", "--tol", str(args.tol)])
-            a2.p, a2.algorithm, a2.tc = w.p, "classical", "robin"
+            a2.p, a2.algorithm, a2.tc = w.p, "preconditioned" if chosen else "classical", "robin"
             r = oracle_steps(w, a2, 1, args.cpu_budget, max_iter_first=2)
             its_i = statistics.mean(st[i]["last_schwarz_iterations"] for st in stats)
             per_inst.append(r["steps"][0] / r["iterations"][0] * its_i)
@@ -591,10 +615,14 @@ def run_batch(args, rank, world, local_rank):
     line = {"metric": METRIC, "value": len(ws) * args.steps / (total_ms * 1e-3), "unit": "instance-steps/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 inner Krylov + f64 residual/interface", "data": "synthetic",
+            "dtype": "f32 inner Krylov + " + ("double-word f32x2" if chosen else "f64") + " residual, f64 interface",
+            "data": "synthetic",
             "config": {"workload": f"gpe_batch: {len(ws)} GPE instances, meshes {min(w.nx for w in ws)}^2..{max(w.nx for w in ws)}^2 "
                                    f"cells, {sum(w.n_strips for w in ws)} strips, {nodes/1e6:.1f} M nodes, dt 0.002, "
-                                   f"classical Robin, tol {args.tol:g}",
+                                   + ("preconditioned (modal P^-1 per instance)" if chosen else "classical")
+                                   + f" Robin, tol {args.tol:g}",
+                       "form": "chosen: FP32-inner/double-word-refine, preconditioned" if chosen
+                               else "classical, FP32-inner/FP64-refine",
                        "l2": "flushed (512 MB write) before every timed step"},
             "autotuned": {"block_size": bs, "blocks_per_launch": nblk, "first_call_s": warm_s},
             "schwarz_iterations_per_step_max": max(max(s2["last_schwarz_iterations"] for s2 in st) for st in stats),
@@ -605,7 +633,7 @@ def run_batch(args, rank, world, local_rank):
             "e2e": {"value": len(ws) * e2e_steps / e2e_s, "unit": "instance-steps/s", "h2d_bytes_per_step": io_bytes,
                     "d2h_bytes_per_step": io_bytes},
             "gpu_launches": prof["kernel_launches"], "clocks": clk}
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def run_learned(args, rank, world, local_rank):
@@ -708,11 +736,17 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank)
     elif args.workload == "gpe_batch":
-        run_batch(args, rank, world, local_rank)
+        line = run_batch(args, rank, world, local_rank)
+        if line is not None and rank == 0:
+            print(json.dumps(line), flush=True)
     elif args.workload == "learned_guess":
         run_learned(args, rank, world, local_rank)
     else:
-        run_ours(args, rank, world, local_rank)
+        line = run_ours(args, rank, world, local_rank)
+        if line is not None:
+            if world == 1 and args.workload == "nls_well" and not args.no_extra:
+                line["configs"] = extra_configs(args, local_rank)
+            print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":

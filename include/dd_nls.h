@@ -244,9 +244,13 @@ int dd_nls_step_noalloc(const dd_nls_params* p, const double* V, double* u, cons
  * iteration solves the strips of all instances that have not yet converged in one
  * persistent launch, then updates every instance's interface vector (eq. fluxlr) in one
  * launch; each instance stops at its own `tol`.  Instances may differ in every field of
- * dd_nls_params except `precision` (DD_NLS_FP64 or DD_NLS_FP32_INNER); each must use the
- * classical algorithm with Robin transmission.  An autotuner picks the strip solver's block size and block count for the
- * batch shape the first time a shape is stepped (timed on the first Schwarz iteration).
+ * dd_nls_params except `precision` (DD_NLS_FP64, DD_NLS_FP32_INNER or DD_NLS_FP32_DW; the
+ * latter needs nl_tol >= 1e-12).  Each uses Robin transmission and either the classical
+ * algorithm (eq. algo_d) or the preconditioned one (eq. algo_pd) with psolve =
+ * DD_NLS_PSOLVE_MODAL (the exact P^-1 on cosine modes, one set of factors per instance, built
+ * at create; nl_adapt and psolve_modes apply as in dd_nls_step).  An autotuner picks the
+ * strip solver's block size and block count for the batch shape the first time a shape is
+ * stepped (timed on the first Schwarz iteration).
  * params, V (nullable, or entries NULL) and u0 are arrays of n entries; pointers are host or
  * device per ptr_kind.  Errors: dd_nls_batch_last_error(). */
 typedef struct dd_nls_batch dd_nls_batch;

@@ -382,7 +382,7 @@ static StripSolveArgs base_args(dd_nls* h) {
         rre = -sim;
         rim = sre;
     }
-    fill_fp32_constants(a, h->G, rre, rim, h->G.kap);
+    fill_fp32_constants(a, rre, rim);
     return a;
 }
 

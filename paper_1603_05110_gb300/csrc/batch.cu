@@ -8,8 +8,11 @@
 // pass) and the number of co-resident blocks once per batch shape by timing the candidates on
 // the first Schwarz iteration.
 //
-// Scope: classical algorithm (eq. algo_d), Robin transmission (eq. TCSRobin), one precision
-// for the whole batch.
+// Scope: Robin transmission (eq. TCSRobin); per instance the classical algorithm (eq. algo_d) or
+// the preconditioned one (eq. algo_pd) with the exact P^-1 on cosine modes (Sec. 4.2; one set of
+// modal factors per instance); one precision for the whole batch (FP64, FP32 inner with the
+// FP64 residual, or FP32 inner with the double-word residual, whose fields then carry every
+// strip's state from launch to launch within a step).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -120,6 +123,22 @@ struct dd_nls_batch {
     int blocks = 1;                 // blocks per launch chosen by the autotuner
     bool tuned = false;
     bool prof = false;
+    bool dw = false;                // double-word residual (FP32 inner)
+    // exact P^-1 of a preconditioned instance (modal.cu): strip types, cosine transforms, the
+    // per-mode block-Thomas factors, scratch
+    struct Modal {
+        int ntypes = 0;
+        int *btype = nullptr, *tkind = nullptr;
+        double *Cf = nullptr, *Ci = nullptr;
+        float *Cf32 = nullptr, *Ci32 = nullptr;
+        double2 *xm = nullptr, *fac = nullptr, *tmp = nullptr, *xs = nullptr, *cpart = nullptr;
+        float2* fac32 = nullptr;
+    };
+    std::vector<Modal> modal;
+    std::vector<double> tolk;       // strip tolerance of each instance in the next launch
+    float4 *zdw = nullptr, *bdw = nullptr;   // double-word state and right side
+    float2* wdw = nullptr;                   // w W in double words
+    double* bint2 = nullptr;                 // ||b||^2 off the edges per strip
     double2* stage = nullptr;       // nodal staging buffer of the largest instance (host IO)
     long long launch_base = 0;
     dd_nls_profile profile{};
@@ -151,6 +170,14 @@ static void batch_release(dd_nls_batch* b) {
                    b->bscale, b->bnorm0, b->res,
                    b->nl_res, b->bar, b->status, b->nl_its, b->err, b->d_blk, b->kry, b->d_tol, b->stage};
     for (void* p : dev)
+        if (p) cudaFree(p);
+    for (auto& m : b->modal) {
+        void* md[] = {m.btype, m.tkind, m.Cf, m.Ci, m.Cf32, m.Ci32, m.xm, m.fac, m.tmp, m.xs, m.cpart, m.fac32};
+        for (void* p : md)
+            if (p) cudaFree(p);
+    }
+    void* dwp[] = {b->zdw, b->bdw, b->wdw, b->bint2};
+    for (void* p : dwp)
         if (p) cudaFree(p);
     void* host[] = {b->h_blk, b->h_cur, b->h_active, b->h_res, b->h_bn, b->h_tol};
     for (void* p : host)
@@ -203,7 +230,7 @@ static std::vector<std::vector<int>> batch_waves(dd_nls_batch* b, int total) {
 static StripSolveArgs batch_args(dd_nls_batch* b) {
     StripSolveArgs a{};
     a.g = b->G[0];
-    fill_fp32_constants(a, a.g, 0.0, a.g.p, a.g.kap);   // Robin only; per-instance p comes from geoms
+    fill_fp32_constants(a, 0.0, a.g.p);   // Robin only; per-instance p comes from geoms
     a.geoms = b->d_geoms;
     a.sinfo = b->d_sinfo;
     a.blk_strip = b->d_blk;
@@ -233,6 +260,16 @@ static StripSolveArgs batch_args(dd_nls_batch* b) {
     a.kry_its = b->kry;
     a.nl_res = b->nl_res;
     a.err = b->err;
+    if (b->dw) {
+        // modes 1 (first launch of a step: state and right side from zeta and rhs0) and 2 (the
+        // double-word fields already hold this step's state); set per launch by the caller
+        a.zdw = b->zdw;
+        a.bdw = b->bdw;
+        a.wdw = b->wdw;
+        a.ddw = nullptr;
+        a.bint2 = b->bint2;
+        a.dw_mode = 1;
+    }
     return a;
 }
 
@@ -248,7 +285,7 @@ static int batch_solve(dd_nls_batch* b, StripSolveArgs& a, int nblk, float* ms_o
     }
     BCK(cudaMemcpyAsync(b->d_sinfo, b->sinfo.data(), sizeof(StripInfo) * b->nstrips, cudaMemcpyHostToDevice, b->s));
     BCK(cudaMemcpyAsync(b->d_blk, b->h_blk, sizeof(int) * (b->maxb + b->nstrips + 1), cudaMemcpyHostToDevice, b->s));
-    for (int j = 0; j < b->nstrips; ++j) b->h_tol[j] = b->P[b->sinfo[j].inst].nl_tol;   // classical: fixed
+    for (int j = 0; j < b->nstrips; ++j) b->h_tol[j] = b->tolk[b->sinfo[j].inst];
     BCK(cudaMemcpyAsync(b->d_tol, b->h_tol, sizeof(double) * b->nstrips, cudaMemcpyHostToDevice, b->s));
     BCK(cudaMemsetAsync(b->bar, 0, sizeof(unsigned) * b->nstrips, b->s));
     BCK(cudaMemsetAsync(b->err, 0, sizeof(int), b->s));
@@ -272,7 +309,7 @@ static int batch_solve(dd_nls_batch* b, StripSolveArgs& a, int nblk, float* ms_o
 // Pick (block size, blocks per launch) for this batch shape: time one Schwarz iteration of the
 // first step with each candidate, from the same starting state.
 static int autotune(dd_nls_batch* b, std::vector<double>& w) {
-    TuneKey key{b->n, b->nstrips, b->fp32 ? 1 : 0, b->nfield};
+    TuneKey key{b->n, b->nstrips, b->dw ? 2 : (b->fp32 ? 1 : 0), b->nfield};
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tuned.find(key);
@@ -292,6 +329,7 @@ static int autotune(dd_nls_batch* b, std::vector<double>& w) {
         const int mb = strip_solve_max_blocks_bs(b->fp32, c.bs);
         const int blocks = std::max(1, (int)(mb * c.occ));
         if (blocks > mb || blocks > maxb_all) continue;
+        if (b->dw && c.bs != 256) continue;      // the double-word kernel is built for 256 threads
         b->bs = c.bs;
         BCK(cudaMemcpyAsync(b->zeta, b->u, sizeof(double2) * b->nfield, cudaMemcpyDeviceToDevice, b->s));
         float ms = 0.f;
@@ -314,6 +352,49 @@ static int autotune(dd_nls_batch* b, std::vector<double>& w) {
     return DD_NLS_OK;
 }
 
+// The exact P^-1 of instance i (eq. algo_pd, Sec. 4.2): strip types by edge kinds (equal strips
+// share their L_h blocks), the diagonal of L_h in the cosine basis and the per-mode factors.
+static int batch_modal_build(dd_nls_batch* b, int i) {
+    const Geom& G = b->G[i];
+    dd_nls_batch::Modal& m = b->modal[i];
+    std::vector<std::pair<int, int>> types;
+    std::vector<int> bt(G.N);
+    for (int j = 0; j < G.N; ++j) {
+        const auto key = std::make_pair((j > 0 || G.bc_same) ? 1 : 0, (j < G.N - 1 || G.bc_same) ? 1 : 0);
+        auto it = std::find(types.begin(), types.end(), key);
+        if (it == types.end()) { types.push_back(key); bt[j] = (int)types.size() - 1; }
+        else bt[j] = (int)(it - types.begin());
+    }
+    m.ntypes = (int)types.size();
+    std::vector<int> tk(2 * m.ntypes);
+    for (int t = 0; t < m.ntypes; ++t) { tk[2 * t] = types[t].first; tk[2 * t + 1] = types[t].second; }
+    const long long nn = (long long)G.nyn * G.nyn, nIi = 2LL * (G.N - 1) * G.P;
+    const size_t nf = (size_t)9 * std::max(1, G.N - 1) * G.nyn;
+    BCK(zalloc(&m.btype, G.N));
+    BCK(zalloc(&m.tkind, tk.size()));
+    BCK(cudaMemcpy(m.btype, bt.data(), sizeof(int) * G.N, cudaMemcpyHostToDevice));
+    BCK(cudaMemcpy(m.tkind, tk.data(), sizeof(int) * tk.size(), cudaMemcpyHostToDevice));
+    BCK(zalloc(&m.Cf, nn));
+    BCK(zalloc(&m.Ci, nn));
+    if (b->fp32) { BCK(zalloc(&m.Cf32, nn)); BCK(zalloc(&m.Ci32, nn)); }
+    BCK(zalloc(&m.xm, (size_t)m.ntypes * 4 * G.nyn));
+    BCK(zalloc(&m.fac, nf));
+    BCK(zalloc(&m.tmp, nIi));
+    BCK(zalloc(&m.xs, nIi));
+    BCK(zalloc(&m.cpart, 8 * nIi));
+    double2* work = nullptr;
+    BCK(cudaMalloc(&work, sizeof(double2) * (size_t)m.ntypes * G.nyn * 2 * G.nxs));
+    cudaError_t e = launch_modal_setup(G, m.ntypes, m.tkind, m.btype, m.Cf, m.Ci, m.Cf32, m.Ci32, m.xm, m.fac, work, b->s);
+    if (e == cudaSuccess && b->fp32) {
+        e = cudaMalloc(&m.fac32, nf * sizeof(float2));
+        if (e == cudaSuccess) e = launch_to_float((const double*)m.fac, (float*)m.fac32, 2 * (long long)nf, b->s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->s);
+    cudaFree(work);
+    if (e != cudaSuccess) return bfail(b, DD_NLS_ECUDA, std::string("batched modal set-up: ") + cudaGetErrorString(e));
+    return DD_NLS_OK;
+}
+
 extern "C" int dd_nls_batch_create(int n, const dd_nls_params* params, const double* const* V,
                                    const double* const* u0, int ptr_kind, void* stream, dd_nls_batch** out) {
     dd_nls_batch* b = nullptr;
@@ -324,10 +405,15 @@ extern "C" int dd_nls_batch_create(int n, const dd_nls_params* params, const dou
         const dd_nls_params& p = params[i];
         if (!u0[i] || p.nx < 1 || p.ny < 1 || p.n_strips < 1 || p.nx % p.n_strips)
             return bfail(nullptr, DD_NLS_EINVAL, "dd_nls_batch_create: instance with bad sizes");
-        if (p.tc != DD_NLS_TC_ROBIN || p.algorithm != DD_NLS_CLASSICAL || !(p.p > 0))
-            return bfail(nullptr, DD_NLS_EINVAL, "dd_nls_batch_create: batches take the classical algorithm with Robin p > 0");
-        if (p.precision != prec || (prec != DD_NLS_FP64 && prec != DD_NLS_FP32_INNER))
+        if (p.tc != DD_NLS_TC_ROBIN || !(p.p > 0))
+            return bfail(nullptr, DD_NLS_EINVAL, "dd_nls_batch_create: batches take Robin transmission with p > 0");
+        if (p.algorithm != DD_NLS_CLASSICAL && (p.algorithm != DD_NLS_PRECONDITIONED || p.psolve != DD_NLS_PSOLVE_MODAL))
+            return bfail(nullptr, DD_NLS_EINVAL,
+                         "dd_nls_batch_create: the classical algorithm, or the preconditioned one with the modal P solve");
+        if (p.precision != prec || (prec != DD_NLS_FP64 && prec != DD_NLS_FP32_INNER && prec != DD_NLS_FP32_DW))
             return bfail(nullptr, DD_NLS_EINVAL, "dd_nls_batch_create: one precision for the whole batch");
+        if (prec == DD_NLS_FP32_DW && !(p.nl_tol >= kDWFinish))
+            return bfail(nullptr, DD_NLS_EINVAL, "dd_nls_batch_create: the double-word residual needs nl_tol >= 1e-12");
         if (!(p.xr > p.xl) || !(p.yu > p.yb) || !(p.dt > 0) || !(p.lap > 0))
             return bfail(nullptr, DD_NLS_EINVAL, "dd_nls_batch_create: bad domain or time step");
     }
@@ -343,7 +429,8 @@ extern "C" int dd_nls_batch_create(int n, const dd_nls_params* params, const dou
     } while (0)
     b->n = n;
     b->s = (cudaStream_t)stream;
-    b->fp32 = prec == DD_NLS_FP32_INNER;
+    b->fp32 = prec != DD_NLS_FP64;
+    b->dw = prec == DD_NLS_FP32_DW;
     b->P.assign(params, params + n);
     b->G.resize(n);
     b->foff.resize(n);
@@ -412,6 +499,14 @@ extern "C" int dd_nls_batch_create(int n, const dd_nls_params* params, const dou
     BCKC(zalloc(&b->d_cur, n));
     BCKC(zalloc(&b->d_active, n));
     BCKC(zalloc(&b->d_tol, b->nstrips));
+    b->tolk.assign(n, 0.0);
+    for (int i = 0; i < n; ++i) b->tolk[i] = params[i].nl_tol;
+    if (b->dw) {
+        BCKC(zalloc(&b->zdw, b->nfield));
+        BCKC(zalloc(&b->bdw, b->nfield));
+        BCKC(zalloc(&b->wdw, b->nfield));
+        BCKC(zalloc(&b->bint2, b->nstrips));
+    }
     BCKC(cudaMallocHost((void**)&b->h_tol, sizeof(double) * b->nstrips));
     b->rel_prev.assign(n, 1.0);
     BCKC(cudaMallocHost((void**)&b->h_blk, sizeof(int) * (maxb + b->nstrips + 2)));
@@ -449,6 +544,12 @@ extern "C" int dd_nls_batch_create(int n, const dd_nls_params* params, const dou
         if (!e) e = cudaStreamSynchronize(b->s);
     }
     BCKC(e);
+    b->modal.resize(n);
+    for (int i = 0; i < n; ++i)
+        if (params[i].algorithm == DD_NLS_PRECONDITIONED && b->G[i].N > 1) {
+            const int rc = batch_modal_build(b, i);
+            if (rc) return bad(rc);
+        }
     *out = b;
     return DD_NLS_OK;
 #undef BCKC
@@ -479,6 +580,9 @@ extern "C" int dd_nls_batch_step(dd_nls_batch* b, int nsteps, dd_nls_stats* stat
             b->h_active[i] = 1;
             b->rel_prev[i] = 1.0;
         }
+        auto adapt_of = [&](int i) {
+            return b->P[i].algorithm == DD_NLS_PRECONDITIONED && b->P[i].nl_adapt > 0.0 && b->G[i].N > 1;
+        };
         BCK(cudaMemcpyAsync(b->zeta, b->u, sizeof(double2) * b->nfield, cudaMemcpyDeviceToDevice, b->s));
         BCK(cudaMemcpyAsync(b->h_bn, b->bnorm0, sizeof(double) * b->nstrips, cudaMemcpyDeviceToHost, b->s));
         BCK(cudaStreamSynchronize(b->s));
@@ -495,9 +599,16 @@ extern "C" int dd_nls_batch_step(dd_nls_batch* b, int nsteps, dd_nls_stats* stat
         int nact = b->n;
         std::vector<int> its(b->n, 0);
         for (int k = 0; k < max_it && nact > 0; ++k) {
+            // strip tolerance per instance: nl_tol, or for a preconditioned instance with
+            // nl_adapt > 0 the inexact solves of the single-instance path (nl_adapt x the last
+            // relative interface residual, at most 1e-6, down to nl_tol)
+            for (int i = 0; i < b->n; ++i)
+                b->tolk[i] = adapt_of(i) ? std::max(b->P[i].nl_tol, std::min(1e-6, b->P[i].nl_adapt * b->rel_prev[i]))
+                                         : b->P[i].nl_tol;
             for (const auto& wave : batch_waves(b, b->blocks)) {
                 const int nblk = batch_schedule(b, w, wave, b->blocks);
                 StripSolveArgs a = batch_args(b);
+                if (b->dw) a.dw_mode = k == 0 ? 1 : 2;
                 float ms = 0.f;
                 int rc = batch_solve(b, a, nblk, &ms);
                 if (rc) return rc;
@@ -532,13 +643,27 @@ extern "C" int dd_nls_batch_step(dd_nls_batch* b, int nsteps, dd_nls_stats* stat
                 if (!std::isfinite(diff) || !std::isfinite(nrm)) return bfail(b, DD_NLS_ENONFINITE, "non-finite interface residual");
                 if (stats) { stats[i].residual = rel; stats[i].residual_abs = diff; stats[i].schwarz_iterations += 1;
                              stats[i].last_schwarz_iterations = k + 1; }
-                b->cur[i] ^= 1;                       // the new R(g) is the next g
+                const int old = b->cur[i];
+                b->cur[i] ^= 1;                       // the new R(g) is the next g (classical)
                 b->rel_prev[i] = rel;
-                if ((b->P[i].tol_absolute ? diff : rel) <= b->P[i].tol || b->G[i].N == 1) {
+                const bool full = !adapt_of(i) || b->tolk[i] <= std::max(b->P[i].nl_tol, b->P[i].nl_adapt * b->P[i].tol);
+                if (((b->P[i].tol_absolute ? diff : rel) <= b->P[i].tol && full) || b->G[i].N == 1) {
                     // zeta holds v for g^k; R(g^k) (now current) is the next step's guess
                     b->conv_half[i] = b->cur[i];
                     b->h_active[i] = 0;
                     --nact;
+                    if (b->dw) BCK(launch_dw_to_zeta(b->G[i], b->zdw + b->foff[i], b->zeta + b->foff[i], b->s));
+                } else if (b->P[i].algorithm == DD_NLS_PRECONDITIONED) {
+                    // g^{k+1} = g^k - P^{-1} (g^k - R(g^k))  (eq. algo_pd), into the half of R(g^k)
+                    const Geom& G = b->G[i];
+                    dd_nls_batch::Modal& m = b->modal[i];
+                    const long long nIi = 2LL * (G.N - 1) * G.P;
+                    double2* gk = b->gbuf + b->goff[i] + (old ? half : 0);
+                    double2* gr = b->gbuf + b->goff[i] + (old ? 0 : half);
+                    BCK(launch_sub(m.tmp, gk, gr, nIi, b->s));               // y = g - R(g)
+                    BCK(launch_modal_apply(G, b->fp32, m.Cf, m.Ci, m.Cf32, m.Ci32, m.fac, m.tmp, m.xs, gr, b->s,
+                                           m.cpart, m.fac32, b->P[i].psolve_modes));
+                    BCK(launch_sub(gr, gk, m.xs, nIi, b->s));                // g^{k+1} = g - x
                 }
             }
         }

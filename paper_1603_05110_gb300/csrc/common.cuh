@@ -67,7 +67,10 @@ struct Geom {
     // such conversions inside loops instead of keeping their results in registers
     float cf[12];            // mxo mxi mxe kxo kxi kxe myo myi mye kyo kyi kye
     float alpha_f, p_f;
-    // after hx, hy, alpha and p are set
+    // the double-word residual's constants (hi, lo pairs) for Robin transmission: -hy/(6hx),
+    // alpha hx hy/36, -hx/(6hy), p hy/6, hx hy kappa, hx hy
+    float dwk[12];
+    // after hx, hy, alpha, kap and p are set
     __host__ void fill_coefficients() {
         mxo = hx / 6.0; mxi = 4.0 * hx / 6.0; mxe = 2.0 * hx / 6.0;
         kxo = -1.0 / hx; kxi = 2.0 / hx; kxe = 1.0 / hx;
@@ -77,6 +80,11 @@ struct Geom {
         for (int i = 0; i < 12; ++i) cf[i] = (float)d[i];
         alpha_f = (float)alpha;
         p_f = (float)p;
+        const double k[6] = {-hy / (6.0 * hx), alpha * hx * hy / 36.0, -hx / (6.0 * hy), p * hy / 6.0, hx * hy * kap, hx * hy};
+        for (int i = 0; i < 6; ++i) {
+            dwk[2 * i] = (float)k[i];
+            dwk[2 * i + 1] = (float)(k[i] - (double)dwk[2 * i]);
+        }
     }
     __host__ __device__ long long sstride() const { return (long long)nxs * P; }
     __host__ __device__ int c() const { return nxs - 1; }

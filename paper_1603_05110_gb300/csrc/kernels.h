@@ -16,10 +16,8 @@ void count_launches(int n);
 constexpr int kMaxPade = 96;   // largest Pade order m of eq. (TCS) the kernels take
 
 struct StripSolveArgs;
-struct Geom;
-// Fill the FP32 constants of a strip-solver launch (rho_f, dwk) for geometry g, edge coefficient
-// i (rho_re + i rho_im) and kappa/lap = kap.
-void fill_fp32_constants(StripSolveArgs& a, const Geom& g, double rho_re, double rho_im, double kap);
+// Fill the FP32 edge coefficient of a strip-solver launch: i (rho_re + i rho_im).
+void fill_fp32_constants(StripSolveArgs& a, double rho_re, double rho_im);
 
 // Batched instances: strip j of the launch belongs to instance `inst` (its own geometry),
 // is strip `jloc` of that instance, and its fields start at element `off` of the field arrays;
@@ -79,11 +77,8 @@ struct StripSolveArgs {
     // blk_strip[c] = strip of cluster c, cluster_smem bytes of dynamic shared memory per CTA
     int cluster;
     unsigned cluster_smem;
-    // FP32 constants rounded on the host: the S_pade edge coefficient i sum a_s (re, im) and the
-    // double-word residual's constants (hi, lo pairs): -hy/(6hx), alpha hx hy/36, -hx/(6hy),
-    // p hy/6, hx hy kappa, hx hy
+    // the S_pade edge coefficient i sum a_s (re, im) rounded to FP32 on the host
     float rho_f[2];
-    float dwk[12];
     long long* pcyc;         // [gridDim][8] phase cycles (R, A, B, epilogue, waits) or NULL
     // S_pade^m transmission (eq. TCS): auxiliary unknowns phi_{e,s} on both vertical edges
     int pade_m;              // 0: Robin

@@ -256,8 +256,11 @@ strip_solve_kernel(StripSolveArgs a) {
         cluster_sync_all();
     }
     // geometry: the launch's, or the instance's when instances are batched
-    const StripInfo si = (!CLU && a.sinfo) ? a.sinfo[j] : StripInfo{0, j, (long long)j * a.g.sstride(), 0};
-    const Geom g = (!CLU && a.geoms) ? a.geoms[si.inst] : a.g;   // cluster launches are never batched
+    // batched instances (per-instance geometry) take the cooperative Robin kernels only; the
+    // others read the geometry from the kernel parameters
+    constexpr bool kBatchable = !CLU && !PADE;
+    const StripInfo si = (kBatchable && a.sinfo) ? a.sinfo[j] : StripInfo{0, j, (long long)j * a.g.sstride(), 0};
+    const Geom g = (kBatchable && a.geoms) ? a.geoms[si.inst] : a.g;
     const int jl = si.jloc;                  // strip index inside its instance
     const int nyn = g.nyn, ny = nyn - 1, c = g.nxs - 1, P = g.P;
     const int Ns = g.nxs * nyn;
@@ -322,7 +325,7 @@ strip_solve_kernel(StripSolveArgs a) {
     // receives the accumulated correction once, at the end of the launch
     static_assert(!DW || SR, "the double-word residual is built for the FP32 Robin solver");
     float4* zdw = DW ? a.zdw + sbase : nullptr;
-    float4* ddw = DW ? a.ddw + sbase : nullptr;
+    float4* ddw = (DW && a.ddw) ? a.ddw + sbase : nullptr;   // dw_mode 0 only
     float4* bdw = DW ? a.bdw + sbase : nullptr;
     const float2* wdw = DW ? a.wdw + sbase : nullptr;
     // auxiliary unknowns: phi_{e,s}(iy) at ((j*2 + e)*m + s)*P + iy
@@ -468,6 +471,16 @@ strip_solve_kernel(StripSolveArgs a) {
     };
     auto gam_of = [&](int s2) { return make_double2(a.pade_d[s2].x, g.alpha + a.pade_d[s2].y); };   // i alpha + d_s
     auto sig_of = [&](int s2) { return cmul(make_double2(0.0, 1.0), cmul(a.pade_a[s2], a.pade_d[s2])); };  // i a_s d_s
+    // the same coefficients in the inner precision, formed once per launch (an FP64 product and
+    // conversion per phi node and Krylov iteration would occupy the FP64 pipe)
+    __shared__ T2 s_pgam[PADE ? kMaxPade : 1], s_psig[PADE ? kMaxPade : 1];
+    if constexpr (PADE) {
+        for (int s2 = threadIdx.x; s2 < m; s2 += blockDim.x) {
+            s_pgam[s2] = cfrom<T2>(gam_of(s2));
+            s_psig[s2] = cfrom<T2>(sig_of(s2));
+        }
+        __syncthreads();
+    }
 
     // scale of the first correction: the strip's ||(2i/dt) M h|| (FP32 must not see ~1e-111),
     // but at least 1e-6 of the whole problem's: a far-field strip (h ~ 1e-32) whose residual
@@ -510,19 +523,19 @@ strip_solve_kernel(StripSolveArgs a) {
     float C6f = 0.f;
     const float cfacf = a.nl_picard ? 1.f : 2.f;
     if constexpr (DW) {
-        // double-word constants split on the host (no FP64 conversion in the kernel)
-        nC1 = {a.dwk[0], a.dwk[1]};
-        C2 = {a.dwk[2], a.dwk[3]};
+        // double-word constants split on the host (Geom::fill_coefficients; no FP64 conversion here)
+        nC1 = {g.dwk[0], g.dwk[1]};
+        C2 = {g.dwk[2], g.dwk[3]};
         nC2 = dw_neg(C2);
-        nC3 = {a.dwk[4], a.dwk[5]};
-        C5 = {a.dwk[6], a.dwk[7]};
+        nC3 = {g.dwk[4], g.dwk[5]};
+        C5 = {g.dwk[6], g.dwk[7]};
         nC5 = dw_neg(C5);
-        if (a.mode == 0) C6 = {a.dwk[8], a.dwk[9]};
+        if (a.mode == 0) C6 = {g.dwk[8], g.dwk[9]};
         C6f = C6.h;
         // zeta, b = (2i/dt) M h - M^Gamma Q^T (l; r) and w W in double-word form, ||b||^2.
         // Integer splits away from the edge columns (no FP64 instruction there); ||b||^2 in
         // FP32 in units of the first correction's scale, edge columns apart.
-        const dw HXHY = {a.dwk[10], a.dwk[11]};
+        const dw HXHY = {g.dwk[10], g.dwk[11]};
         const float bsc = (float)inv_s;
         float bb = 0.f, be = 0.f;
         auto edge_b = [&](int ix, int iy, long long idx) {
@@ -1378,7 +1391,7 @@ strip_solve_kernel(StripSolveArgs a) {
                         if (e >= 0)
                             for (int s2 = 0; s2 < m; ++s2) {
                                 const T2 mph = edge_mass<T, T2>(zf + ((long long)e * m + s2) * P, iy, ny, cyT);
-                                Az = csub(Az, cmul(cfrom<T2>(sig_of(s2)), mph));
+                                Az = csub(Az, cmul(s_psig[s2], mph));
                             }
                     }
                     const T2 qn = cfma(bT, q[idx], Az);
@@ -1395,7 +1408,7 @@ strip_solve_kernel(StripSolveArgs a) {
                     const long long fi = ((long long)e * m + s2) * P + iy;
                     const Coef1<T> cyT = coef1<T>(iy, ny, KYt);
                     const T2 J = phi_row<T, T2>(z + (long long)ixe * P, zf + ((long long)e * m + s2) * P, iy, ny, cyT,
-                                                cfrom<T2>(gam_of(s2)), cfrom<T2>(sig_of(s2)), cTf[(long long)e * P + iy]);
+                                                s_pgam[s2], s_psig[s2], cTf[(long long)e * P + iy]);
                     const T2 qn = cfma(bT, qf[fi], J);
                     const T2 pn = cfma(bT, pf[fi], zf[fi]);
                     qf[fi] = qn;
@@ -1467,7 +1480,7 @@ strip_solve_kernel(StripSolveArgs a) {
                     xf[fi] = cfma(alT, pf[fi], xf[fi]);
                     rn = cfma(malT, qf[fi], rf[fi]);
                     rf[fi] = rn;
-                    const T2 di = phi_diag_inv<T, T2>(cyT, cfrom<T2>(gam_of(s2)), cfrom<T2>(sig_of(s2)), cTf[(long long)e * P + iy]);
+                    const T2 di = phi_diag_inv<T, T2>(cyT, s_pgam[s2], s_psig[s2], cTf[(long long)e * P + iy]);
                     zn = cmul(di, rn);
                     zf[fi] = zn;
                 }
@@ -1610,20 +1623,9 @@ strip_solve_kernel(StripSolveArgs a) {
     if constexpr (CLU) cluster_sync_all();
 }
 
-static void dw_split(double v, float* out) {
-    const float h = (float)v;
-    out[0] = h;
-    out[1] = (float)(v - (double)h);
-}
-void fill_fp32_constants(StripSolveArgs& a, const Geom& g, double rho_re, double rho_im, double kap) {
+void fill_fp32_constants(StripSolveArgs& a, double rho_re, double rho_im) {
     a.rho_f[0] = (float)rho_re;
     a.rho_f[1] = (float)rho_im;
-    dw_split(-g.hy / (6.0 * g.hx), a.dwk + 0);
-    dw_split(g.alpha * g.hx * g.hy / 36.0, a.dwk + 2);
-    dw_split(-g.hx / (6.0 * g.hy), a.dwk + 4);
-    dw_split(rho_im * g.hy / 6.0, a.dwk + 6);
-    dw_split(g.hx * g.hy * kap, a.dwk + 8);
-    dw_split(g.hx * g.hy, a.dwk + 10);
 }
 
 unsigned strip_cluster_smem(int nxs, int nyn) {
@@ -1684,8 +1686,10 @@ static cudaError_t launch_strip_solve_t(const StripSolveArgs& args, int nblocks,
         return dw ? cudaLaunchKernelEx(&cfg, strip_solve_kernel<float, false, 512, true, true>, a)
                   : cudaLaunchKernelEx(&cfg, strip_solve_kernel<float, false, 512, false, true>, a);
     }
-    if (a.pade_m > 0)
+    if (a.pade_m > 0) {
+        if (a.geoms || a.sinfo) return cudaErrorInvalidValue;   // S_pade strips are never batched
         return cudaLaunchCooperativeKernel((const void*)strip_solve_kernel<T, true, 256>, grid, dim3(256), params, 0, s);
+    }
     if (sizeof(T) == 4 && a.zdw && a.mode == 0)
         return cudaLaunchCooperativeKernel((const void*)strip_solve_kernel<float, false, 256, true>, grid, dim3(256), params, 0, s);
     if (bs == 128)
@@ -1731,10 +1735,12 @@ int strip_solve_max_blocks(bool fp32) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     // the smaller of the Robin and S_pade instances, so one schedule fits both
-    int per2 = 0;
+    int per2 = 0, per3 = 0;
     if (fp32) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, strip_solve_kernel<float, false, 256>, 256, 0);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, strip_solve_kernel<float, true, 256>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per3, strip_solve_kernel<float, false, 256, true>, 256, 0);
+        per2 = std::min(per2, per3);
     } else {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, strip_solve_kernel<double, false, 256>, 256, 0);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, strip_solve_kernel<double, true, 256>, 256, 0);

@@ -326,6 +326,37 @@ def test_batched_uneven_instances_match_oracle():
         assert rel(got[i], ref[-1][0]) < 1e-11
 
 
+@pytest.mark.parametrize("precision", [binding.FP64, binding.FP32_DW])
+def test_batched_preconditioned_and_classical_instances_match_oracle(precision):
+    """A batch mixing preconditioned instances (eq. algo_pd, modal P^-1 per instance, nl_adapt)
+    with classical ones, in FP64 and in FP32 with the double-word residual (its fields carry the
+    strip states between launches): every instance reaches the oracle's steps.  FP64 at interface
+    tolerance 1e-12 agrees to 1e-11; the double-word form at 1e-10 (strip tolerance 1e-12) to 1e-8."""
+    shapes = [(24, 20, 3, -120.0, "preconditioned"), (30, 17, 5, -400.0, "preconditioned"),
+              (16, 33, 2, -250.0, "classical"), (40, 41, 4, -250.0, "preconditioned")]
+    ws = [wl.Workload(f"bp{i}", -4.0, 4.0, -4.0, 4.0, nx, ny, N, 0.002, 2, lap=0.5, kappa=k, p=45.0,
+                      potential="trap", datum="ground_noise", seed=1700 + i)
+          for i, (nx, ny, N, k, _) in enumerate(shapes)]
+    dw = precision == binding.FP32_DW
+    tol = 1e-10 if dw else TOL
+    prms = [gpu_params(w, tol=tol, nl_tol=1e-12 if dw else 1e-14, precision=precision, nl_adapt=0.01,
+                       algorithm=binding.PRECONDITIONED if sh[4] == "preconditioned" else binding.CLASSICAL,
+                       psolve=binding.PSOLVE_MODAL)
+            for w, sh in zip(ws, shapes)]
+    with binding.Batch(prms, [w.u0() for w in ws], [w.V() for w in ws]) as b:
+        its = []
+        for step in range(2):
+            st = b.step(1)
+            its.append([st[i]["last_schwarz_iterations"] for i in range(len(ws))])
+        got = [b.get_u(i) for i in range(len(ws))]
+    for i, (w, sh) in enumerate(zip(ws, shapes)):
+        ref = run_oracle(w, 2, algorithm=sh[4], tol=tol)
+        assert rel(got[i], ref[-1][0]) < (1e-8 if dw else 1e-11), (i, rel(got[i], ref[-1][0]))
+        # the same Schwarz iteration counts as the oracle's, within the inexact early solves
+        for step in range(2):
+            assert abs(its[step][i] - ref[step][1].iterations) <= 2, (i, step, its, ref[step][1].iterations)
+
+
 @pytest.mark.parametrize("case", ["well", "gpe_far"])
 def test_double_word_state_carried_between_launches(case):
     """Strip tolerances of 1e-12 and above: the double-word fields carry the strip state from
