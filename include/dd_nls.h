@@ -113,7 +113,9 @@ typedef struct {
                             algorithm only: tol_k = nl_adapt x the last relative interface
                             residual (at most 1e-6, never below nl_tol), and a step converges
                             only once tol_k <= max(nl_tol, nl_adapt x tol).  Same fixed point,
-                            cheaper early Schwarz iterations. */
+                            cheaper early Schwarz iterations.  A Schwarz iteration that does not
+                            cut the relative interface residual by 4x ends the inexact solves
+                            for the rest of the step. */
     /* Rotating frame of the GPE (Sec. 5.2.1, eq. x1Ax, GPE_Trans, u1u).  The solve runs in the
      * coordinates x~ = A(t)^T x, A(t) the rotation by omega_rot t, where the rotation term of
      * eq. (GPE) is absent and the trap becomes time dependent. */

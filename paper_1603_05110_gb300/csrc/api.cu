@@ -701,13 +701,15 @@ static int schwarz(dd_nls* h, dd_nls_stats* st) {
     double2* g = h->gA;
     double2* gn = h->gB;
     double rel_prev = 1.0;
+    // nl_adapt > 0 with the preconditioned algorithm: inexact strip solves while the interface
+    // residual is large (nl_adapt x the last relative residual, at most 1e-6, down to nl_tol);
+    // same fixed point, cheaper early iterations.  The classical algorithm contracts too slowly
+    // (0.98-0.99 per iteration) to absorb that perturbation.  An iteration that does not cut the
+    // interface residual by 4x ends the inexact solves for the rest of the step (strongly
+    // nonlinear strips can stall the preconditioned iteration at the inexact solves' level).
+    bool adapt = h->P.algorithm == DD_NLS_PRECONDITIONED && h->P.nl_adapt > 0.0;
     for (int k = 0; k < h->P.max_schwarz; ++k) {
         a.gtr = g;
-        // nl_adapt > 0 with the preconditioned algorithm: inexact strip solves while the interface
-        // residual is large (nl_adapt x the last relative residual, at most 1e-6, down to
-        // nl_tol); same fixed point, cheaper early iterations.  The classical algorithm contracts
-        // too slowly (0.98-0.99 per iteration) to absorb that perturbation.
-        const bool adapt = h->P.algorithm == DD_NLS_PRECONDITIONED && h->P.nl_adapt > 0.0;
         const double tol_k = adapt ? std::max(h->P.nl_tol, std::min(1e-6, h->P.nl_adapt * rel_prev)) : h->P.nl_tol;
         a.nl_tol = tol_k;
         a.inner_floor = 0.1 * tol_k;
@@ -750,6 +752,7 @@ static int schwarz(dd_nls* h, dd_nls_stats* st) {
             st->residual_abs = diff;
         }
         if (!std::isfinite(diff) || !std::isfinite(nrm)) return fail(h, DD_NLS_ENONFINITE, "interface residual is not finite");
+        const bool stalled = adapt && k > 0 && rel > 0.25 * rel_prev;
         rel_prev = rel;
         // converged only once the strip solves behind R(g) were at full accuracy
         if ((h->P.tol_absolute ? diff : rel) <= h->P.tol && (!adapt || tol_k <= std::max(h->P.nl_tol, h->P.nl_adapt * h->P.tol))) {
@@ -783,6 +786,7 @@ static int schwarz(dd_nls* h, dd_nls_stats* st) {
             }
             std::swap(g, gn);
         }
+        if (stalled) adapt = false;
     }
     h->gA = g;
     h->gB = gn;

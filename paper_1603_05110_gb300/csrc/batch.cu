@@ -580,9 +580,12 @@ extern "C" int dd_nls_batch_step(dd_nls_batch* b, int nsteps, dd_nls_stats* stat
             b->h_active[i] = 1;
             b->rel_prev[i] = 1.0;
         }
-        auto adapt_of = [&](int i) {
-            return b->P[i].algorithm == DD_NLS_PRECONDITIONED && b->P[i].nl_adapt > 0.0 && b->G[i].N > 1;
-        };
+        // inexact strip solves per instance until an iteration fails to cut its interface
+        // residual by 4x (as in dd_nls_step)
+        std::vector<char> adapt_on(b->n);
+        for (int i = 0; i < b->n; ++i)
+            adapt_on[i] = b->P[i].algorithm == DD_NLS_PRECONDITIONED && b->P[i].nl_adapt > 0.0 && b->G[i].N > 1;
+        auto adapt_of = [&](int i) { return adapt_on[i] != 0; };
         BCK(cudaMemcpyAsync(b->zeta, b->u, sizeof(double2) * b->nfield, cudaMemcpyDeviceToDevice, b->s));
         BCK(cudaMemcpyAsync(b->h_bn, b->bnorm0, sizeof(double) * b->nstrips, cudaMemcpyDeviceToHost, b->s));
         BCK(cudaStreamSynchronize(b->s));
@@ -645,8 +648,10 @@ extern "C" int dd_nls_batch_step(dd_nls_batch* b, int nsteps, dd_nls_stats* stat
                              stats[i].last_schwarz_iterations = k + 1; }
                 const int old = b->cur[i];
                 b->cur[i] ^= 1;                       // the new R(g) is the next g (classical)
+                const bool stalled = adapt_of(i) && k > 0 && rel > 0.25 * b->rel_prev[i];
                 b->rel_prev[i] = rel;
                 const bool full = !adapt_of(i) || b->tolk[i] <= std::max(b->P[i].nl_tol, b->P[i].nl_adapt * b->P[i].tol);
+                if (stalled) adapt_on[i] = 0;
                 if (((b->P[i].tol_absolute ? diff : rel) <= b->P[i].tol && full) || b->G[i].N == 1) {
                     // zeta holds v for g^k; R(g^k) (now current) is the next step's guess
                     b->conv_half[i] = b->cur[i];
