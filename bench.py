@@ -49,6 +49,35 @@ METRIC = "time steps/s and stencil GB/s at 1e-8 interface residual, chosen vs pl
 KRYLOV_BYTES = {"fp32": 68.0, "fp64": 136.0}
 RESIDUAL_BYTES = 40.0
 
+# DRAM traffic of the strip solver per launch (dram__bytes_read.sum + dram__bytes_write.sum from one
+# ncu capture, the mean over every strip-solver launch of
+#     python bench.py [--workload W] --steps 5 --warmup 3 --no-fp64 --no-cpu --no-extra
+# for nls_well, --steps 3 for gpe_trap) and the hash of the kernel sources it was measured on; a
+# figure is reported only while those sources are unchanged (null once the kernel changed).
+KERNEL_SOURCES = ["strip_solver.cu", "common.cuh", "dw.cuh", "kernels.h"]
+STRIP_TRAFFIC = {"nls_well": (47.25e6, "c03c07aedcd4c73b")}
+
+
+def kernel_sources_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1603_05110_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload):
+    t = STRIP_TRAFFIC.get(workload)
+    if t is None:
+        return None, "no ncu capture of this workload"
+    try:
+        same = kernel_sources_hash() == t[1]
+    except OSError:
+        same = False
+    if not same:
+        return None, "the kernel sources changed since the ncu capture"
+    return t[0], "ncu: mean DRAM bytes (read + write) per strip-solver launch of this workload"
 
 def parse(argv=None):
     ap = argparse.ArgumentParser()
@@ -73,10 +102,12 @@ def parse(argv=None):
                     help="gpe_batch: preconditioned + double-word residual (chosen) or classical + FP32 inner")
     ap.add_argument("--no-extra", action="store_true",
                     help="nls_well: skip the gpe_trap and gpe_batch lines nested under 'configs'")
-    ap.add_argument("--learn-n", type=int, default=256, help="learned_guess: cells per direction")
-    ap.add_argument("--learn-strips", type=int, default=8)
-    ap.add_argument("--learn-steps", type=int, default=160, help="learned_guess: steps generated")
-    ap.add_argument("--learn-epochs", type=int, default=60)
+    ap.add_argument("--learn-n", type=int, default=1024, help="learned_guess: cells per direction")
+    ap.add_argument("--learn-strips", type=int, default=32)
+    ap.add_argument("--learn-train", type=int, default=2000, help="learned_guess: training steps generated")
+    ap.add_argument("--learn-traj", type=int, default=4, help="learned_guess: training trajectories (one beta each)")
+    ap.add_argument("--learn-eval", type=int, default=500, help="learned_guess: held-out steps")
+    ap.add_argument("--learn-epochs", type=int, default=3)
     ap.add_argument("--max-schwarz", type=int, default=5000)
     ap.add_argument("--cpu-budget", type=float, default=30.0,
                     help="seconds of oracle work for the cpu_baseline sample")
@@ -332,7 +363,9 @@ def strip_roofline(prof, stats, w, prec, peaks, peak_kind, nodes_per_strip=None)
            "achieved_with_residual": (kb + rb) / t / 1e9, "traffic": None,
            "note": f"{KRYLOV_BYTES[prec]:g} B/node per strip-Krylov iteration x {nps} nodes per strip x "
                    f"iterations / strip-solver time (CUDA events on the library stream); residual applies at "
-                   f"{RESIDUAL_BYTES:g} B/node in achieved_with_residual; traffic: see the ncu summaries"}
+                   f"{RESIDUAL_BYTES:g} B/node in achieved_with_residual"}
+    if prec == "fp32":
+        out["traffic"], out["traffic_source"] = measured_traffic(w.name)
     if peaks is not None:
         out.update(peak=peaks["hbm_gbs"], frac=out["achieved"] / peaks["hbm_gbs"], peak_source=f"{peak_kind} hbm_gbs")
     return out
@@ -500,17 +533,20 @@ def run_ours(args, rank, world, local_rank):
 
 
 def extra_configs(args, local_rank):
-    """The other single-GPU configurations, run after the headline one with fewer steps: the GPE
-    trap with S_pade (gpe_trap) and the batched GPE instances (gpe_batch), each with its own
-    roofline, oracle sample, e2e and clocks."""
+    """The other single-GPU configurations, run after the headline one: the GPE trap with S_pade
+    (gpe_trap) and the batched GPE instances (gpe_batch), with fewer steps, each with its own
+    roofline, oracle sample, e2e and clocks; and the learned interface guess at its full size
+    (learned_guess: 2000 training steps, 500 held-out steps)."""
     out = {}
     common = ["--warmup", "3", "--no-fp64", "--cpu-budget", str(args.cpu_budget), "--tol", str(args.tol)]
     if args.no_cpu:
         common.append("--no-cpu")
-    for name, steps in (("gpe_trap", max(2, min(args.steps, 5))), ("gpe_batch", max(2, min(args.steps, 3)))):
+    runs = {"gpe_trap": run_ours, "gpe_batch": run_batch, "learned_guess": run_learned}
+    for name, steps in (("gpe_trap", max(2, min(args.steps, 5))), ("gpe_batch", max(2, min(args.steps, 3))),
+                        ("learned_guess", 1)):
         a = parse(["--workload", name, "--steps", str(steps)] + common)
         try:
-            out[name] = run_batch(a, 0, 1, local_rank) if name == "gpe_batch" else run_ours(a, 0, 1, local_rank)
+            out[name] = runs[name](a, 0, 1, local_rank)
         except Exception as e:          # a failed extra line must not cost the headline line
             out[name] = {"error": f"{type(e).__name__}: {e}"}
     return out
@@ -636,54 +672,100 @@ def run_batch(args, rank, world, local_rank):
     return line
 
 
+def learned_workload(args, beta, seed):
+    """The GPE trap of the gpe_trap configuration at learn_n^2 cells and learn_strips strips
+    (S_pade m = 8, Omega_rot 0.4, preconditioned), with the given beta."""
+    from paper_1603_05110_gb300 import workloads as wl
+    n, dt = args.learn_n, 0.001
+    return wl.Workload("learned_gpe", -16.0, 16.0, -16.0, 16.0, n, n, args.learn_strips, dt, 1, lap=0.5,
+                       kappa=-beta, p=2.0 * float(np.sqrt(1.0 / dt)), algorithm="preconditioned", potential="trap",
+                       datum="ground_noise", seed=seed, extra={"tc": "pade", "pade_m": 8, "omega": 0.4})
+
+
 def run_learned(args, rank, world, local_rank):
-    """Learned interface guess (dd_cnn_*): the plain solver generates a GPE trajectory, the CNN is
-    trained on the device on its converged interface vectors (steps 3 .. 3/4 of the run), and the
-    held-out steps are solved twice from the same state: from the previous step's vector (the
-    paper's guess) and from the network's prediction.  Schwarz iterations and time per step are
-    reported for both; the learned time includes the network's inference."""
+    """Learned interface guess (dd_cnn_*) on the GPE trap at 1024^2 cells with 32 strips: the plain
+    solver generates training trajectories at seeded beta in [200, 800] (learn_train steps over
+    learn_traj trajectories), the CNN is trained on the device to predict each step's converged
+    interface vector from the previous three (a correction to the previous vector, the paper's
+    guess), and a held-out trajectory at its own beta is solved step by step from the same state
+    with four guesses: zero, the previous vector, linear extrapolation and the network's.  Schwarz
+    iterations and time per step are reported for each; the learned time includes inference."""
     import torch
 
-    from paper_1603_05110_gb300 import binding, build, workloads as wl
+    from paper_1603_05110_gb300 import binding, build
     if not os.path.exists(binding.LIB_PATH):
         build.build()
     binding.load()
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    n, dt = args.learn_n, 0.002
-    w = wl.Workload("learned_gpe", -12.0, 12.0, -12.0, 12.0, n, n, args.learn_strips, dt, args.learn_steps, lap=0.5,
-                    kappa=-300.0, p=float(np.sqrt(4 / dt)), potential="trap", datum="ground_noise", seed=1603)
-    prm = solver_params(w, args, binding.FP32_DW if args.residual == "dw" else binding.FP32_INNER)
-    prm["algorithm"] = binding.CLASSICAL
-    ntr = 2 * (w.n_strips - 1)
+    rng = np.random.default_rng(1603)
+    betas = [float(b) for b in rng.uniform(200.0, 800.0, args.learn_traj + 1)]
+    args.tc, args.pade_m = "pade", 8
     stream = torch.cuda.Stream(device=dev)
-    us, gs = [torch.from_numpy(w.u0()).to(dev)], []
+
+    def params_of(w):
+        prm = solver_params(w, args, binding.FP32_DW if args.residual == "dw" else binding.FP32_INNER)
+        prm["omega_rot"] = w.extra["omega"]
+        return prm
+
+    def trajectory(w, steps, keep_states=True):
+        """States after steps 0..steps (keep_states) and the converged interface vectors of steps
+        1..steps."""
+        ntr = 2 * (w.n_strips - 1)
+        us, gs = [torch.from_numpy(w.u0()).to(dev)], []
+        its = []
+        with binding.Solver(params_of(w), us[0], torch.from_numpy(w.V()).to(dev), stream=stream) as s:
+            for _ in range(steps):
+                out = torch.empty_like(us[0])
+                its.append(s.step(1, out)["last_schwarz_iterations"])
+                g = torch.empty(ntr, w.ny + 1, dtype=torch.complex128, device=dev)
+                s.get_state(None, g)
+                if keep_states:
+                    us.append(out)
+                gs.append(g)
+        return us, gs, its
+
+    # ---- training data: learn_traj trajectories, one beta each
     t0 = time.perf_counter()
-    with binding.Solver(prm, us[0], torch.from_numpy(w.V()).to(dev), stream=stream) as s:
-        for _ in range(args.learn_steps):
-            out = torch.empty_like(us[0])
-            s.step(1, out)
-            g = torch.empty(ntr, w.ny + 1, dtype=torch.complex128, device=dev)
-            s.get_state(None, g)
-            us.append(out)
-            gs.append(g)
+    per = max(4, args.learn_train // args.learn_traj)
+    train = []                                   # (g_{k-1}, g_{k-2}, g_{k-3}, g_k)
+    gen_its = []
+    for t in range(args.learn_traj):
+        w = learned_workload(args, betas[t], 1603 + t)
+        _, gs, its = trajectory(w, per, keep_states=False)
+        gen_its += its
+        train += [(gs[k - 1], gs[k - 2], gs[k - 3], gs[k]) for k in range(3, len(gs))]
     gen_s = time.perf_counter() - t0
-    ntrain = (3 * args.learn_steps) // 4
-    net = binding.CNN(ntr, w.ny + 1, stream=stream)
+    # ---- held-out trajectory (its own beta); its states are the starting points of the solves
+    w = learned_workload(args, betas[-1], 1603 + args.learn_traj)
+    t0 = time.perf_counter()
+    us, gs, _ = trajectory(w, args.learn_eval + 4)
+    gen_s += time.perf_counter() - t0
+    ntr = 2 * (w.n_strips - 1)
+    # ---- training on the device (Adam), shuffled samples, learning rate halved each epoch
+    net = binding.CNN(ntr, w.ny + 1, stream=stream, base=binding.CNN.BASE_PREVIOUS)
     net.set_params(binding.CNN.init_params(seed=7, last_scale=0.1))
     t0 = time.perf_counter()
-    for _ in range(args.learn_epochs):
-        for k in range(3, ntrain):                  # predict g of step k+1 from steps k, k-1, k-2
-            net.train_step(gs[k - 1], gs[k - 2], gs[k - 3], gs[k], lr=3e-4)
+    losses = []
+    order_rng = np.random.default_rng(7)
+    for ep in range(args.learn_epochs):
+        lr = 1e-3 * 0.5 ** ep
+        for i in order_rng.permutation(len(train)):
+            losses.append(net.train_step(*train[i], lr=lr))
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
-    res = {"previous": [], "extrapolated": [], "learned": []}
+    del train
+
+    # ---- held-out steps: each solved from the same state with each guess
+    kinds = ("zero", "previous", "extrapolated", "learned")
+    res = {k: [] for k in kinds}
     g0 = torch.empty(ntr, w.ny + 1, dtype=torch.complex128, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    with binding.Solver(prm, us[0], torch.from_numpy(w.V()).to(dev), stream=stream) as s:
-        for k in range(ntrain, args.learn_steps - 1):
-            # state u after step k (us[k + 1]); the previous-step guess is gs[k]
-            for kind in ("previous", "extrapolated", "learned"):
+    clocks = Clocks(local_rank)
+    with binding.Solver(params_of(w), us[0], torch.from_numpy(w.V()).to(dev), stream=stream) as s:
+        for k in range(3, 3 + args.learn_eval):
+            # state after step k + 1 (us[k + 1]); the step to solve is k + 2, whose vector is gs[k + 1]
+            for kind in kinds:
                 s.set_state(us[k + 1], gs[k], k + 1)
                 with torch.cuda.stream(stream):
                     flush.zero_()           # every solve starts from a cold L2
@@ -698,34 +780,44 @@ def run_learned(args, rank, world, local_rank):
                     with torch.cuda.stream(stream):     # the solver reads g0 on this stream
                         g0.copy_(2 * gs[k] - gs[k - 1])
                     st = s.solve_interface(g0)
+                elif kind == "zero":
+                    with torch.cuda.stream(stream):
+                        g0.zero_()
+                    st = s.solve_interface(g0)
                 else:
                     st = s.solve_interface(gs[k])
                 e1.record(stream)
                 e1.synchronize()
                 res[kind].append((st["last_schwarz_iterations"], e0.elapsed_time(e1)))
+    clk = clocks.stop()
     net.close()
     if rank != 0:
-        return
+        return None
     its = {k: statistics.mean(v[0] for v in res[k]) for k in res}
     ms = {k: statistics.mean(v[1] for v in res[k]) for k in res}
+    nl = len(losses)
     line = {"metric": METRIC, "value": 1e3 / ms["learned"], "unit": "steps/s", "n_gpus": world,
             "steps": len(res["learned"]), "warmup": 0, "ms_per_step": ms["learned"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 inner Krylov + " + ("double-word f32x2" if args.residual == "dw" else "f64")
-                     + " residual; CNN bf16 in / f32 accumulate", "data": "synthetic",
-            "config": {"workload": f"learned_guess: GPE trap, beta 300, {n}x{n} cells on (-12,12)^2, {w.n_strips} strips, "
-                                   f"classical Schwarz, Robin p={w.p:.1f}, dt={dt}, interface tol {args.tol:g}; "
-                                   f"{args.learn_steps} generated steps, trained on steps 3..{ntrain - 1}, "
-                                   f"{len(res['learned'])} held-out steps",
+            "dtype": "f32 inner Krylov + f64 residual (S_pade); CNN bf16 operands / f32 accumulate", "data": "synthetic",
+            "config": {"workload": f"learned_guess: GPE trap, {w.nx}x{w.ny} cells on (-16,16)^2, {w.n_strips} strips, "
+                                   f"preconditioned Schwarz, S_pade m=8, Omega_rot 0.4, dt={w.dt}, interface tol {args.tol:g}; "
+                                   f"training: {args.learn_traj} trajectories x {per} steps at beta "
+                                   + ", ".join(f"{b:.0f}" for b in betas[:-1])
+                                   + f"; held out: {len(res['learned'])} steps at beta {betas[-1]:.0f}",
                        "note": "each held-out step solved from the same state with each guess; L2 flushed "
-                               "(512 MB write) before every timed solve"},
-            "schwarz_iterations_per_step": {"previous_guess": its["previous"], "extrapolated_guess": its["extrapolated"],
-                                            "learned_guess": its["learned"]},
-            "ms_per_step_by_guess": {"previous_guess": ms["previous"], "extrapolated_guess": ms["extrapolated"],
-                                     "learned_guess": ms["learned"]},
+                               "(512 MB write) before every timed solve; the network predicts a correction to "
+                               "the previous step's vector"},
+            "schwarz_iterations_per_step": {f"{k}_guess": its[k] for k in kinds},
+            "ms_per_step_by_guess": {f"{k}_guess": ms[k] for k in kinds},
             "learned_vs_previous_speedup": ms["previous"] / ms["learned"],
-            "generation_s": gen_s, "training_s": train_s, "training_updates": args.learn_epochs * (ntrain - 3)}
-    print(json.dumps(line), flush=True)
+            "learned_vs_zero_speedup": ms["zero"] / ms["learned"],
+            "training": {"updates": nl, "epochs": args.learn_epochs, "samples": nl // max(1, args.learn_epochs),
+                         "loss_first_100": statistics.mean(losses[:100]) if losses else None,
+                         "loss_last_100": statistics.mean(losses[-100:]) if losses else None, "seconds": train_s},
+            "generation_s": gen_s, "generation_schwarz_iterations_mean": statistics.mean(gen_its),
+            "clocks": clk}
+    return line
 
 
 def main():
@@ -740,7 +832,9 @@ def main():
         if line is not None and rank == 0:
             print(json.dumps(line), flush=True)
     elif args.workload == "learned_guess":
-        run_learned(args, rank, world, local_rank)
+        line = run_learned(args, rank, world, local_rank)
+        if line is not None:
+            print(json.dumps(line), flush=True)
     else:
         line = run_ours(args, rank, world, local_rank)
         if line is not None:

@@ -276,16 +276,19 @@ void dd_nls_batch_destroy(dd_nls_batch* b);
  * previous converged vector, Sec. 5).  A 4-layer CNN (3x3 convolutions 6->32->32->32->2, ReLU,
  * BF16 operands with FP32 accumulation on the tensor cores) maps the last three converged
  * interface vectors of a problem with n_traces = 2(N-1) traces of nodes_per_trace = ny+1
- * nodes to a correction of linear extrapolation:
- *     g0 = 2 g1 - g2 + s1 * net(g1/s0, (g1-g2)/s1, (g2-g3)/s1),
- * s0 = rms(g1), s1 = rms(g1-g2) (g1 the most recent).  Interface vectors are DEVICE pointers
+ * nodes to a correction of a base guess:
+ *     g0 = g1 + e (g1 - g2) + s1 * net(g1/s0, (g1-g2)/s1, (g2-g3)/s1),
+ * s0 = rms(g1), s1 = rms(g1-g2) (g1 the most recent), e = 1 (linear extrapolation, the default)
+ * or e = 0 (the paper's previous-step vector), chosen by dd_cnn_set_base (EINVAL otherwise).  Interface vectors are DEVICE pointers
  * in the ABI layout.  Parameters: one FP32 array of dd_cnn_num_params() values, per layer the
  * weights [Cout][Cin][3][3] then the biases [Cout]; the caller supplies the initial values.
  * dd_cnn_train_step: one Adam step (lr, betas 0.9/0.999) on the squared error of the
  * correction for the target vector gt; loss (nullable) receives the mean squared error.
  * dd_cnn_loss_grad: the same loss and its gradient (host or device per ptr_kind), no update. */
 typedef struct dd_cnn dd_cnn;
+enum { DD_CNN_BASE_PREVIOUS = 0, DD_CNN_BASE_EXTRAPOLATE = 1 };
 int dd_cnn_create(int n_traces, int nodes_per_trace, void* stream, dd_cnn** out);
+int dd_cnn_set_base(dd_cnn* c, int base);
 long long dd_cnn_num_params(const dd_cnn* c);
 int dd_cnn_set_params(dd_cnn* c, const float* w, int ptr_kind);
 int dd_cnn_get_params(dd_cnn* c, float* w, int ptr_kind);

@@ -115,20 +115,22 @@ def loss_grad(params, x, tgt, bf16_ops=False):
     return loss, pack(grads)
 
 
-def features(g1, g2, g3, gt=None):
-    """(x, target or None, s0, s1) for complex interface images g of shape (2(N-1), ny+1)."""
+def features(g1, g2, g3, gt=None, e=1.0):
+    """(x, target or None, s0, s1) for complex interface images g of shape (2(N-1), ny+1); the
+    target is the correction to the base guess g1 + e (g1 - g2) (e = 1 linear extrapolation,
+    e = 0 the previous-step vector), in units of s1."""
     s0 = np.sqrt(np.mean(np.abs(g1) ** 2)) + 1e-300
     s1 = np.sqrt(np.mean(np.abs(g1 - g2) ** 2)) + 1e-300
     parts = [g1 / s0, (g1 - g2) / s1, (g2 - g3) / s1]
     x = np.stack([f for p in parts for f in (p.real, p.imag)])
     tgt = None
     if gt is not None:
-        t = (gt - 2 * g1 + g2) / s1
+        t = (gt - g1 - e * (g1 - g2)) / s1
         tgt = np.stack([t.real, t.imag])
     return x, tgt, s0, s1
 
 
-def guess(params, g1, g2, g3, bf16_ops=False):
-    x, _, _, s1 = features(g1, g2, g3)
+def guess(params, g1, g2, g3, bf16_ops=False, e=1.0):
+    x, _, _, s1 = features(g1, g2, g3, e=e)
     out, _ = forward(params, x, bf16_ops)
-    return 2 * g1 - g2 + s1 * (out[0] + 1j * out[1])
+    return g1 + e * (g1 - g2) + s1 * (out[0] + 1j * out[1])

@@ -79,7 +79,7 @@ SYMBOLS = ["dd_nls_default_params", "dd_nls_create", "dd_nls_step", "dd_nls_solv
            "dd_nls_batch_set_profiling", "dd_nls_batch_get_profile", "dd_nls_batch_last_error",
            "dd_nls_batch_destroy", "dd_nls_step_guess", "dd_cnn_create", "dd_cnn_num_params",
            "dd_cnn_set_params", "dd_cnn_get_params", "dd_cnn_guess", "dd_cnn_train_step", "dd_cnn_loss_grad",
-           "dd_cnn_last_error", "dd_cnn_destroy", "dd_nls_lab_frame", "dd_nls_batch_set_u"]
+           "dd_cnn_last_error", "dd_cnn_destroy", "dd_nls_lab_frame", "dd_nls_batch_set_u", "dd_cnn_set_base"]
 
 _lib = None
 
@@ -147,6 +147,8 @@ def load(path=LIB_PATH):
     lib.dd_cnn_create.restype = ip
     lib.dd_cnn_num_params.argtypes = [vp]
     lib.dd_cnn_num_params.restype = ctypes.c_longlong
+    lib.dd_cnn_set_base.argtypes = [vp, ip]
+    lib.dd_cnn_set_base.restype = ip
     lib.dd_cnn_set_params.argtypes = [vp, vp, ip]
     lib.dd_cnn_set_params.restype = ip
     lib.dd_cnn_get_params.argtypes = [vp, vp, ip]
@@ -445,7 +447,9 @@ class CNN:
     """A dd_cnn handle (learned interface guess).  Interface vectors are CUDA complex128
     tensors of shape (2(N-1), ny+1)."""
 
-    def __init__(self, n_traces, nodes_per_trace, stream=None):
+    BASE_PREVIOUS, BASE_EXTRAPOLATE = 0, 1
+
+    def __init__(self, n_traces, nodes_per_trace, stream=None, base=1):
         self.lib = load()
         s = None
         if stream is not None:
@@ -456,6 +460,8 @@ class CNN:
             raise DDNLSError(rc, self.lib.dd_nls_last_error(None).decode())
         self.h = h
         self.n = int(self.lib.dd_cnn_num_params(h))
+        if base != self.BASE_EXTRAPOLATE:
+            self._check(self.lib.dd_cnn_set_base(h, int(base)))
 
     def _check(self, rc):
         if rc != 0:

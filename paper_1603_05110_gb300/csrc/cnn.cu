@@ -6,10 +6,11 @@
 // Sec. 2.3) and W = ny+1 columns, and 6 channels
 //     g_{n-1}/s0,  (g_{n-1} - g_{n-2})/s1,  (g_{n-2} - g_{n-3})/s1    (real and imaginary parts),
 // s0 = rms(g_{n-1}), s1 = rms(g_{n-1} - g_{n-2}).  The network (3x3 convolutions 6->32->32->32->2,
-// ReLU between) outputs a correction to linear extrapolation:
-//     g_n^0 = 2 g_{n-1} - g_{n-2} + s1 * out.
-// With zero last-layer weights it is linear extrapolation; trained on converged vectors of the
-// plain solver it learns the rest.  The Schwarz iteration converges from any guess, so the guess
+// ReLU between) outputs a correction to a base guess, linear extrapolation (e = 1, default) or
+// the paper's previous-step vector (e = 0, dd_cnn_set_base):
+//     g_n^0 = g_{n-1} + e (g_{n-1} - g_{n-2}) + s1 * out.
+// With zero last-layer weights it is the base; trained on converged vectors of the plain solver
+// it learns the rest.  The Schwarz iteration converges from any guess, so the guess
 // only changes the iteration count.
 //
 // Arithmetic: activations and weights in BF16, accumulation in FP32, on the tensor cores through
@@ -235,10 +236,11 @@ __global__ void guess_norms_kernel(const double2* __restrict__ g1, const double2
         out[1] = sqrt(v[1] / nn) + 1e-300;      // s1
     }
 }
-// x[6][n] (bf16) and, when gt != NULL, the training target tgt[2][n] = (gt - 2 g1 + g2)/s1
+// x[6][n] (bf16) and, when gt != NULL, the training target tgt[2][n] = (gt - g1 - e (g1 - g2))/s1
 __global__ void guess_features_kernel(const double2* __restrict__ g1, const double2* __restrict__ g2,
                                       const double2* __restrict__ g3, const double2* __restrict__ gt, long long n,
-                                      const double* __restrict__ s, __nv_bfloat16* __restrict__ x, float* __restrict__ tgt) {
+                                      const double* __restrict__ s, double e, __nv_bfloat16* __restrict__ x,
+                                      float* __restrict__ tgt) {
     const double s0 = s[0], s1 = s[1];
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const double2 a = g1[i], b = g2[i], c = g3[i];
@@ -250,18 +252,18 @@ __global__ void guess_features_kernel(const double2* __restrict__ g1, const doub
         x[5 * n + i] = __float2bfloat16((float)((b.y - c.y) / s1));
         if (gt) {
             const double2 t = gt[i];
-            tgt[0 * n + i] = (float)((t.x - 2.0 * a.x + b.x) / s1);
-            tgt[1 * n + i] = (float)((t.y - 2.0 * a.y + b.y) / s1);
+            tgt[0 * n + i] = (float)((t.x - a.x - e * (a.x - b.x)) / s1);
+            tgt[1 * n + i] = (float)((t.y - a.y - e * (a.y - b.y)) / s1);
         }
     }
 }
-// g0 = 2 g1 - g2 + s1 * out
+// g0 = g1 + e (g1 - g2) + s1 * out
 __global__ void guess_apply_kernel(const double2* __restrict__ g1, const double2* __restrict__ g2, const float* __restrict__ out,
-                                   long long n, const double* __restrict__ s, double2* __restrict__ g0) {
+                                   long long n, const double* __restrict__ s, double e, double2* __restrict__ g0) {
     const double s1 = s[1];
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const double2 a = g1[i], b = g2[i];
-        g0[i] = make_double2(2.0 * a.x - b.x + s1 * out[0 * n + i], 2.0 * a.y - b.y + s1 * out[1 * n + i]);
+        g0[i] = make_double2(a.x + e * (a.x - b.x) + s1 * out[0 * n + i], a.y + e * (a.y - b.y) + s1 * out[1 * n + i]);
     }
 }
 
@@ -274,6 +276,7 @@ static const int kCout[kLayers] = {32, 32, 32, 2};
 
 struct dd_cnn {
     int H = 0, W = 0;           // image: H = number of traces, W = nodes per trace
+    double e = 1.0;             // base guess: 1 linear extrapolation, 0 the previous vector
     long long HW = 0;
     cudaStream_t s = nullptr;
     long long nparam = 0;
@@ -369,7 +372,7 @@ static int cnn_features(dd_cnn* c, const double* g1, const double* g2, const dou
     count_launches(2);
     guess_norms_kernel<<<1, 512, 0, c->s>>>((const double2*)g1, (const double2*)g2, n, c->sc);
     guess_features_kernel<<<nblk(n, 256), 256, 0, c->s>>>((const double2*)g1, (const double2*)g2, (const double2*)g3,
-                                                         (const double2*)gt, n, c->sc, c->x, c->tgt);
+                                                         (const double2*)gt, n, c->sc, c->e, c->x, c->tgt);
     CCK(cudaGetLastError());
     return DD_NLS_OK;
 }
@@ -424,6 +427,13 @@ extern "C" int dd_cnn_create(int n_traces, int nodes_per_trace, void* stream, dd
 
 extern "C" long long dd_cnn_num_params(const dd_cnn* c) { return c ? c->nparam : 0; }
 
+extern "C" int dd_cnn_set_base(dd_cnn* c, int base) {
+    if (!c || (base != DD_CNN_BASE_PREVIOUS && base != DD_CNN_BASE_EXTRAPOLATE))
+        return DD_NLS_EINVAL;
+    c->e = base == DD_CNN_BASE_EXTRAPOLATE ? 1.0 : 0.0;
+    return DD_NLS_OK;
+}
+
 extern "C" int dd_cnn_set_params(dd_cnn* c, const float* w, int ptr_kind) {
     if (!c || !w) return cfail(c, DD_NLS_EINVAL, "dd_cnn_set_params: NULL argument");
     CCK(cudaMemcpyAsync(c->w, w, sizeof(float) * c->nparam,
@@ -454,7 +464,7 @@ extern "C" int dd_cnn_guess(dd_cnn* c, const double* g1, const double* g2, const
     if (rc) return rc;
     count_launches(1);
     guess_apply_kernel<<<nblk(c->HW, 256), 256, 0, c->s>>>((const double2*)g1, (const double2*)g2, c->pre[kLayers - 1],
-                                                          c->HW, c->sc, (double2*)g0);
+                                                          c->HW, c->sc, c->e, (double2*)g0);
     CCK(cudaGetLastError());
     CCK(cudaStreamSynchronize(c->s));
     return DD_NLS_OK;

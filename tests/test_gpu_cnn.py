@@ -25,20 +25,22 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a, np.complex128)).to("cuda:0")
 
 
-def test_gradients_match_fp64_oracle_elementwise():
+@pytest.mark.parametrize("base", [binding.CNN.BASE_EXTRAPOLATE, binding.CNN.BASE_PREVIOUS])
+def test_gradients_match_fp64_oracle_elementwise(base):
     """Loss, every gradient entry and every predicted value against the oracle with its BF16
     operand rounding switched on (the rounding points of the definition: features, weights, ReLU
     activations, back-propagated output gradients); what remains is FP32 against FP64 accumulation
-    and the rare BF16 rounding it flips."""
+    and the rare BF16 rounding it flips.  Both base guesses (extrapolation, previous vector)."""
     rng = np.random.default_rng(4)
     H, W = 6, 37
-    net = binding.CNN(H, W)
+    e = 1.0 if base == binding.CNN.BASE_EXTRAPOLATE else 0.0
+    net = binding.CNN(H, W, base=base)
     params = binding.CNN.init_params(seed=5, last_scale=0.5)
     params[np.arange(params.size) % 7 == 0] += 0.05          # nonzero biases too
     net.set_params(params)
     g = [rng.standard_normal((H, W)) + 1j * rng.standard_normal((H, W)) for _ in range(4)]
     loss_gpu, grad_gpu = net.loss_grad(*[dev(x) for x in g])
-    x, tgt, _, _ = ocnn.features(g[0], g[1], g[2], g[3])
+    x, tgt, _, _ = ocnn.features(g[0], g[1], g[2], g[3], e=e)
     loss_ref, grad_ref = ocnn.loss_grad(params.astype(np.float64), x, tgt, bf16_ops=True)
     assert abs(loss_gpu - loss_ref) < 1e-4 * loss_ref
     scale = np.max(np.abs(grad_ref))
@@ -46,9 +48,9 @@ def test_gradients_match_fp64_oracle_elementwise():
     # forward: the predicted guess, node by node
     g0 = torch.empty_like(dev(g[0]))
     net.guess(dev(g[0]), dev(g[1]), dev(g[2]), g0)
-    ref = ocnn.guess(params.astype(np.float64), g[0], g[1], g[2], bf16_ops=True)
-    corr_gpu = g0.cpu().numpy() - (2 * g[0] - g[1])
-    corr_ref = ref - (2 * g[0] - g[1])
+    ref = ocnn.guess(params.astype(np.float64), g[0], g[1], g[2], bf16_ops=True, e=e)
+    corr_gpu = g0.cpu().numpy() - (g[0] + e * (g[0] - g[1]))
+    corr_ref = ref - (g[0] + e * (g[0] - g[1]))
     np.testing.assert_allclose(corr_gpu, corr_ref, rtol=2e-2, atol=2e-3 * np.max(np.abs(corr_ref)))
     net.close()
 

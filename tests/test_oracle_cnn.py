@@ -55,6 +55,20 @@ def test_zero_last_layer_is_linear_extrapolation():
     np.testing.assert_allclose(cnn.guess(params, *g), 2 * g[0] - g[1], atol=1e-14)
 
 
+def test_zero_last_layer_with_the_previous_base_is_the_previous_vector():
+    """Base e = 0: an untrained (zero last layer) network reproduces the paper's guess g1, and the
+    training target is the step's change in units of s1."""
+    rng = np.random.default_rng(4)
+    layers = cnn.unpack(pack_random(rng, 0.3))
+    layers[-1] = (np.zeros_like(layers[-1][0]), np.zeros_like(layers[-1][1]))
+    params = cnn.pack(layers)
+    g = [rng.standard_normal((4, 9)) + 1j * rng.standard_normal((4, 9)) for _ in range(4)]
+    np.testing.assert_allclose(cnn.guess(params, *g[:3], e=0.0), g[0], atol=1e-14)
+    _, tgt, _, s1 = cnn.features(*g[:3], gt=g[3], e=0.0)
+    np.testing.assert_allclose(tgt[0] + 1j * tgt[1], (g[3] - g[0]) / np.sqrt(np.mean(np.abs(g[0] - g[1]) ** 2)),
+                               rtol=1e-12)
+
+
 def test_bf16_rounding_is_round_to_nearest_even():
     ulp = 2.0 ** -7                      # BF16 spacing in [1, 2)
     vals = np.array([1.0, 1 + ulp / 2, 1 + 1.5 * ulp, 1 + 0.75 * ulp, -(1 + 0.25 * ulp), 3 + 2 * ulp / 2 + ulp / 4])
