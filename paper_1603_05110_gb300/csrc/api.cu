@@ -771,10 +771,8 @@ static int schwarz(dd_nls* h, dd_nls_stats* st) {
             // g^{k+1} = g^k - P^{-1} (g^k - R(g^k))  (eq. algo_pd)
             ProfScope ps(h, &h->profile.interface_ms);
             if (h->P.psolve == DD_NLS_PSOLVE_MODAL) {
-                CK(launch_sub(h->tmp, g, gn, h->nI, h->s));     // y = g - R(g)
-                CK(launch_modal_apply(G, h->fp32, h->Cf, h->Ci, h->Cf32, h->Ci32, h->fac, h->tmp, h->xs, gn, h->s,
-                                      h->cpart, h->fac32, h->P.psolve_modes));
-                CK(launch_sub(gn, g, h->xs, h->nI, h->s));
+                CK(launch_modal_update(G, h->fp32, h->Cf, h->Ci, h->Cf32, h->Ci32, h->fac, h->fac32, g, gn, gn, h->tmp,
+                                       h->cpart, h->P.psolve_modes, h->s));
             } else {
                 CK(launch_sub(h->tmp, g, gn, h->nI, h->s));
                 CK(launch_copy(gn, h->tmp, h->nI, h->s));          // gn := y

@@ -662,13 +662,10 @@ extern "C" int dd_nls_batch_step(dd_nls_batch* b, int nsteps, dd_nls_stats* stat
                     // g^{k+1} = g^k - P^{-1} (g^k - R(g^k))  (eq. algo_pd), into the half of R(g^k)
                     const Geom& G = b->G[i];
                     dd_nls_batch::Modal& m = b->modal[i];
-                    const long long nIi = 2LL * (G.N - 1) * G.P;
                     double2* gk = b->gbuf + b->goff[i] + (old ? half : 0);
                     double2* gr = b->gbuf + b->goff[i] + (old ? 0 : half);
-                    BCK(launch_sub(m.tmp, gk, gr, nIi, b->s));               // y = g - R(g)
-                    BCK(launch_modal_apply(G, b->fp32, m.Cf, m.Ci, m.Cf32, m.Ci32, m.fac, m.tmp, m.xs, gr, b->s,
-                                           m.cpart, m.fac32, b->P[i].psolve_modes));
-                    BCK(launch_sub(gr, gk, m.xs, nIi, b->s));                // g^{k+1} = g - x
+                    BCK(launch_modal_update(G, b->fp32, m.Cf, m.Ci, m.Cf32, m.Ci32, m.fac, m.fac32, gk, gr, gr, m.tmp,
+                                            m.cpart, b->P[i].psolve_modes, b->s));
                 }
             }
         }

@@ -148,6 +148,12 @@ cudaError_t launch_modal_apply(const AuxGeom& g, bool fp32, const double* Cf, co
                                const float2* fac32 = nullptr,  // FP32 factors for the FP32 forms
                                int kmax = 0);                  // > 0: modes k >= kmax take P = I
 cudaError_t launch_to_float(const double* a, float* b, long long n, cudaStream_t s);
+// g_new = g_k - P^{-1}(g_k - R(g_k)) (eq. algo_pd) with the modal P^-1: five launches (the
+// subtractions fused into the transforms).
+// g_new and tmp may alias rg.
+cudaError_t launch_modal_update(const Geom& g, bool fp32, const double* Cf, const double* Ci, const float* Cf32,
+                                const float* Ci32, const double2* fac, const float2* fac32, const double2* gk,
+                                const double2* rg, double2* gnew, double2* tmp, void* cpart, int kmax, cudaStream_t s);
 
 // ---- rotating frame of the GPE (rotating.cu)
 // Wout = Ws + (w0 trap(t0) + w1 trap(t1)) inv_lap, trap(t) = -(gx2 x^2 + gy2 y^2)/2 at A(t) x~,

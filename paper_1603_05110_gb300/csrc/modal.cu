@@ -206,14 +206,69 @@ __global__ void modal_solve_kernel(Geom g, const T2* __restrict__ fac, double2* 
     }
 }
 
-// part[kz][o][r] = sum over c in slice kz of C[r][c] in[o][c], for the ntr traces of an interface
-// vector (pitch P).  Tiles of 32 rows x 8 traces per block, C and the trace tile staged in shared
-// memory; the column range is split into kCosSlices slices (grid z) so that a 1025-point
-// transform of 30 traces spreads over ~1000 blocks instead of ~130.
+// The same solve with each mode's right side and factors first staged in shared memory: one
+// warp of 32 modes per block, every load of the mode issued before the first step of its sweep
+// (the sweeps are chains of 2(N-1) dependent steps; loading inside them exposes one memory
+// latency per step).  Each thread reads only its own column of the staged arrays.
 constexpr int kCosSlices = 8;
+template <typename T2>
+__global__ void modal_solve_staged_kernel(Geom g, const T2* __restrict__ fac, double2* __restrict__ y, int kmax) {
+    extern __shared__ __align__(16) unsigned char s_modal[];
+    const int n = g.nyn, NI = g.N - 1, P = g.P, lane = threadIdx.x;
+    const int k = blockIdx.x * 32 + lane;
+    const bool on = k < n && !(kmax > 0 && k >= kmax);
+    T2* Fs = (T2*)s_modal;                       // [NI * 9][32]
+    T2* Ys = Fs + (size_t)NI * 9 * 32;           // [2 NI][32]
+    const T2 zero = mk<T2>(0, 0);
+#pragma unroll 8
+    for (int q = 0; q < NI * 9; ++q) Fs[q * 32 + lane] = on ? fac[(long long)q * n + k] : zero;
+#pragma unroll 8
+    for (int q = 0; q < 2 * NI; ++q) {
+        const double2 v = on ? y[(long long)q * P + k] : make_double2(0.0, 0.0);
+        Ys[q * 32 + lane] = mk<T2>(v.x, v.y);
+    }
+    if (!on) return;
+    auto F = [&](int i, int e) { return Fs[(i * 9 + e) * 32 + lane]; };
+    auto Y = [&](int q) -> T2& { return Ys[q * 32 + lane]; };
+    // forward: Yt_i = Y_i - G_i Yt_{i-1}
+    T2 p0 = zero, p1 = zero;
+    for (int i = 0; i < NI; ++i) {
+        T2 a = Y(2 * i), b = Y(2 * i + 1);
+        if (i > 0) {
+            a = csub(a, cadd(cmul(F(i, 4), p0), cmul(F(i, 5), p1)));
+            b = csub(b, cadd(cmul(F(i, 6), p0), cmul(F(i, 7), p1)));
+        }
+        Y(2 * i) = a;
+        Y(2 * i + 1) = b;
+        p0 = a;
+        p1 = b;
+    }
+    // backward: U_i = S_i^{-1} (Yt_i - Up_i U_{i+1})
+    T2 n0 = zero;
+    for (int i = NI - 1; i >= 0; --i) {
+        T2 a = Y(2 * i), b = Y(2 * i + 1);
+        a = csub(a, cmul(F(i, 8), n0));
+        const T2 u0 = cadd(cmul(F(i, 0), a), cmul(F(i, 1), b));
+        const T2 u1 = cadd(cmul(F(i, 2), a), cmul(F(i, 3), b));
+        Y(2 * i) = u0;
+        Y(2 * i + 1) = u1;
+        n0 = u0;
+    }
+#pragma unroll 8
+    for (int q = 0; q < 2 * NI; ++q) {
+        const T2 v = Y(q);
+        y[(long long)q * P + k] = make_double2((double)v.x, (double)v.y);
+    }
+}
+
+// part[kz][o][r] = sum over c in slice kz of C[r][c] in[o][c], for the ntr traces of an interface
+// vector (pitch P); in2 (nullable): the transform of in - in2.  Tiles of 32 rows x 8 traces per
+// block, C and the trace tile staged in shared memory; the column range is split into kCosSlices
+// slices (grid z) so that a 1025-point transform of 30 traces spreads over ~1000 blocks.
 template <typename T>
 __global__ void __launch_bounds__(256) cosine_partial_kernel(int n, int ntr, int P, int klen, const T* __restrict__ C,
                                                              const double2* __restrict__ in,
+                                                             const double2* __restrict__ in2,
                                                              typename C2<T>::t* __restrict__ part) {
     using T2 = typename C2<T>::t;
     __shared__ T Cs[32][33];
@@ -232,7 +287,14 @@ __global__ void __launch_bounds__(256) cosine_partial_kernel(int n, int ntr, int
         {
             const int cc = c0 + tx;
             double2 v = make_double2(0, 0);
-            if (o < ntr && cc < ke) v = in[(long long)o * P + cc];
+            if (o < ntr && cc < ke) {
+                v = in[(long long)o * P + cc];
+                if (in2) {
+                    const double2 w = in2[(long long)o * P + cc];
+                    v.x -= w.x;
+                    v.y -= w.y;
+                }
+            }
             Is[ty][tx] = mk<T2>(v.x, v.y);
         }
         __syncthreads();
@@ -253,9 +315,10 @@ __global__ void __launch_bounds__(256) cosine_partial_kernel(int n, int ntr, int
     }
 }
 
-// out[o][r] = the slices' partial sums, added in slice order
+// out[o][r] = the slices' partial sums, added in slice order; from (nullable): out = from - sum
 template <typename T2>
-__global__ void cosine_reduce_kernel(int n, int ntr, int P, const T2* __restrict__ part, double2* __restrict__ out) {
+__global__ void cosine_reduce_kernel(int n, int ntr, int P, const T2* __restrict__ part, const double2* __restrict__ from,
+                                     double2* __restrict__ out) {
     const long long total = (long long)ntr * n;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
         const int o = (int)(t / n), r = (int)(t - (long long)o * n);
@@ -266,21 +329,66 @@ __global__ void cosine_reduce_kernel(int n, int ntr, int P, const T2* __restrict
             acc.x += v.x;
             acc.y += v.y;
         }
-        out[(long long)o * P + r] = make_double2((double)acc.x, (double)acc.y);
+        double2 v = make_double2((double)acc.x, (double)acc.y);
+        if (from) {
+            const double2 f = from[(long long)o * P + r];
+            v = make_double2(f.x - v.x, f.y - v.y);
+        }
+        out[(long long)o * P + r] = v;
     }
 }
 
+// the partial sums of the transform of in (- in2)
 template <typename T>
-static cudaError_t cosine_apply(int n, int ntr, int P, const T* C, const double2* in, double2* out, void* part,
-                                cudaStream_t s) {
+static cudaError_t cosine_partial(int n, int ntr, int P, const T* C, const double2* in, const double2* in2, void* part,
+                                  cudaStream_t s) {
     using T2 = typename C2<T>::t;
     const int klen = ((n + kCosSlices - 1) / kCosSlices + 31) / 32 * 32;
     dim3 grid((n + 31) / 32, (ntr + 7) / 8, kCosSlices);
-    count_launches(2);
-    cosine_partial_kernel<T><<<grid, 256, 0, s>>>(n, ntr, P, klen, C, in, (T2*)part);
+    count_launches(1);
+    cosine_partial_kernel<T><<<grid, 256, 0, s>>>(n, ntr, P, klen, C, in, in2, (T2*)part);
+    return cudaGetLastError();
+}
+template <typename T>
+static cudaError_t cosine_reduce(int n, int ntr, int P, const void* part, const double2* from, double2* out,
+                                 cudaStream_t s) {
+    using T2 = typename C2<T>::t;
     const long long total = (long long)ntr * n;
     const int nb = (int)std::min<long long>((total + 255) / 256, 152LL * 8);
-    cosine_reduce_kernel<T2><<<nb, 256, 0, s>>>(n, ntr, P, (const T2*)part, out);
+    count_launches(1);
+    cosine_reduce_kernel<T2><<<nb, 256, 0, s>>>(n, ntr, P, (const T2*)part, from, out);
+    return cudaGetLastError();
+}
+template <typename T>
+static cudaError_t cosine_apply(int n, int ntr, int P, const T* C, const double2* in, double2* out, void* part,
+                                cudaStream_t s) {
+    cudaError_t e = cosine_partial<T>(n, ntr, P, C, in, nullptr, part, s);
+    return e != cudaSuccess ? e : cosine_reduce<T>(n, ntr, P, part, nullptr, out, s);
+}
+
+// The per-mode solve on y in place: one warp per block (the per-mode sweeps are chains, spread
+// over as many SMs as possible), staged in shared memory when the mode's data fit.
+static cudaError_t modal_solve(const Geom& g, bool f32, const double2* fac, const float2* fac32, double2* y, int kmax,
+                               cudaStream_t s) {
+    count_launches(1);
+    const int NI = g.N - 1;
+    const size_t smem = (size_t)11 * NI * 32 * (f32 ? sizeof(float2) : sizeof(double2));
+    bool staged = smem <= 220 * 1024;
+    if (staged) {
+        const void* kfn = f32 ? (const void*)modal_solve_staged_kernel<float2> : (const void*)modal_solve_staged_kernel<double2>;
+        if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 1)) != cudaSuccess) {
+            cudaGetLastError();
+            staged = false;
+        }
+    }
+    if (staged) {
+        if (f32) modal_solve_staged_kernel<float2><<<(g.nyn + 31) / 32, 32, smem, s>>>(g, fac32, y, kmax);
+        else modal_solve_staged_kernel<double2><<<(g.nyn + 31) / 32, 32, smem, s>>>(g, fac, y, kmax);
+    } else if (f32) {
+        modal_solve_kernel<float2><<<(g.nyn + 31) / 32, 32, 0, s>>>(g, fac32, y, kmax);
+    } else {
+        modal_solve_kernel<double2><<<(g.nyn + 31) / 32, 32, 0, s>>>(g, fac, y, kmax);
+    }
     return cudaGetLastError();
 }
 
@@ -315,14 +423,32 @@ cudaError_t launch_modal_apply(const Geom& g, bool fp32, const double* Cf, const
     cudaError_t e = fp32 ? cosine_apply<float>(g.nyn, ntr, g.P, Cf32, y, tmp, cpart, s)
                          : cosine_apply<double>(g.nyn, ntr, g.P, Cf, y, tmp, cpart, s);
     if (e != cudaSuccess) return e;
-    // one warp per block: the per-mode sweeps are FP64 chains, spread over as many SMs as possible
-    count_launches(1);
-    if (fp32 && fac32) modal_solve_kernel<float2><<<(g.nyn + 31) / 32, 32, 0, s>>>(g, fac32, tmp, kmax);
-    else modal_solve_kernel<double2><<<(g.nyn + 31) / 32, 32, 0, s>>>(g, fac, tmp, kmax);
+    e = modal_solve(g, fp32 && fac32, fac, fac32, tmp, kmax, s);
+    if (e != cudaSuccess) return e;
     e = fp32 ? cosine_apply<float>(g.nyn, ntr, g.P, Ci32, tmp, x, cpart, s)
              : cosine_apply<double>(g.nyn, ntr, g.P, Ci, tmp, x, cpart, s);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
+}
+
+// g_new = g_k - P^{-1} (g_k - R(g_k))  (eq. algo_pd) in five launches: the forward transform
+// forms y = g_k - R(g_k) as it reads, and the inverse transform's reduction subtracts from g_k.
+// g_new may be rg; tmp (the modal coefficients) may alias rg too.
+cudaError_t launch_modal_update(const Geom& g, bool fp32, const double* Cf, const double* Ci, const float* Cf32,
+                                const float* Ci32, const double2* fac, const float2* fac32, const double2* gk,
+                                const double2* rg, double2* gnew, double2* tmp, void* cpart, int kmax, cudaStream_t s) {
+    const int ntr = 2 * (g.N - 1), n = g.nyn, P = g.P;
+    cudaError_t e = fp32 ? cosine_partial<float>(n, ntr, P, Cf32, gk, rg, cpart, s)
+                         : cosine_partial<double>(n, ntr, P, Cf, gk, rg, cpart, s);
+    if (e == cudaSuccess)
+        e = fp32 ? cosine_reduce<float>(n, ntr, P, cpart, nullptr, tmp, s) : cosine_reduce<double>(n, ntr, P, cpart, nullptr, tmp, s);
+    if (e == cudaSuccess) e = modal_solve(g, fp32 && fac32, fac, fac32, tmp, kmax, s);
+    if (e == cudaSuccess)
+        e = fp32 ? cosine_partial<float>(n, ntr, P, Ci32, tmp, nullptr, cpart, s)
+                 : cosine_partial<double>(n, ntr, P, Ci, tmp, nullptr, cpart, s);
+    if (e == cudaSuccess)
+        e = fp32 ? cosine_reduce<float>(n, ntr, P, cpart, gk, gnew, s) : cosine_reduce<double>(n, ntr, P, cpart, gk, gnew, s);
+    return e;
 }
 
 }  // namespace ddnls

@@ -266,13 +266,21 @@ strip_solve_kernel(StripSolveArgs a) {
     const int Ns = g.nxs * nyn;
     const int m = PADE ? a.pade_m : 0;
     const int Nall = Ns + 2 * m * nyn;       // strip nodes, then phi_{e,s} nodes
-    const int nchunks = (Nall + blockDim.x - 1) / blockDim.x;
     const float inv_nyn = 1.0f / (float)nyn;
     // residual phase work items: runs of RX x-nodes per row, then the phi nodes
     constexpr int RX = 4;
     const int NR = ((g.nxs + RX - 1) / RX) * nyn;
     const int NRall = NR + 2 * m * nyn;
-    const int nchunksR = (NRall + blockDim.x - 1) / blockDim.x;
+    // The nodes (or work items) of this block.  Robin strips: the strip's total split evenly over
+    // its blocks in contiguous ranges (loads stay coalesced; whole blockDim-node chunks dealt
+    // round robin left up to 40% more work on some blocks).  S_pade strips: chunks dealt round
+    // robin, which mixes the costlier edge nodes and the phi rows (stored after the nodes) over
+    // all blocks; contiguous ranges put all of them on a few blocks.
+    auto it_first = [&](int total) {
+        return PADE ? rank * (int)blockDim.x + (int)threadIdx.x : (int)(((long long)total * rank) / bps) + (int)threadIdx.x;
+    };
+    auto it_end = [&](int total) { return PADE ? total : (int)(((long long)total * (rank + 1)) / bps); };
+    const int it_step = PADE ? bps * (int)blockDim.x : (int)blockDim.x;
     const long long sbase = si.off;
 
     // edges of this strip
@@ -566,9 +574,7 @@ strip_solve_kernel(StripSolveArgs a) {
         }
         // the state and b off the edges: this step's already in dw_mode 2
         if (a.dw_mode != 2) {
-            for (int ch = rank; ch < nchunks; ch += bps) {
-                const int n = ch * blockDim.x + threadIdx.x;
-                if (n >= Ns) continue;
+            for (int n = it_first(Ns); n < it_end(Ns); n += it_step) {
                 int ix, iy;
                 split_node(n, nyn, inv_nyn, ix, iy);
                 if (ix == 0 || ix == c) continue;
@@ -612,9 +618,7 @@ strip_solve_kernel(StripSolveArgs a) {
         T rz_re = 0, rz_im = 0;
         float rr_f = 0.f;                        // double-word residual: ||res||^2 partial
         const bool need_b = !DW && nl_it == 0;
-        for (int ch = rank; ch < nchunksR; ch += bps) {
-            const int n = ch * blockDim.x + threadIdx.x;
-            if (n >= NRall) continue;
+        for (int n = it_first(NRall); n < it_end(NRall); n += it_step) {
             if (DW && dwr) {
                 const int seg = n / nyn;
                 const int iy = n - seg * nyn;
@@ -870,9 +874,7 @@ strip_solve_kernel(StripSolveArgs a) {
             if (ctl == 2) { status = s_nli[1]; break; }
         }
         if (DW && dwr && s_nli[0] == 3) {
-            for (int ch = rank; ch < nchunks; ch += bps) {
-                const int n = ch * blockDim.x + threadIdx.x;
-                if (n >= Ns) continue;
+            for (int n = it_first(Ns); n < it_end(Ns); n += it_step) {
                 int ix, iy;
                 split_node(n, nyn, inv_nyn, ix, iy);
                 const long long idx = (long long)ix * P + iy;
@@ -1189,9 +1191,7 @@ strip_solve_kernel(StripSolveArgs a) {
             // w_0 = A z_0, delta_0 = w_0^T z_0
             T d0r = 0, d0i = 0;
             const T2 zeroT = mk<T2>(0.0, 0.0);
-            for (int ch = rank; ch < nchunks; ch += bps) {
-                const int n = ch * blockDim.x + threadIdx.x;
-                if (n >= Ns) continue;
+            for (int n = it_first(Ns); n < it_end(Ns); n += it_step) {
                 int ix, iy;
                 split_node(n, nyn, inv_nyn, ix, iy);
                 const long long idx = (long long)ix * P + iy;
@@ -1256,9 +1256,7 @@ strip_solve_kernel(StripSolveArgs a) {
                 T2* rn_b = rbuf[nxt];
                 T2* wn_b = wbuf[nxt];
                 T g_r = 0, g_i = 0, dlt_r = 0, dlt_i = 0, rr2 = 0;
-                for (int ch = rank; ch < nchunks; ch += bps) {
-                    const int n = ch * blockDim.x + threadIdx.x;
-                    if (n >= Ns) continue;
+                for (int n = it_first(Ns); n < it_end(Ns); n += it_step) {
                     int ix, iy;
                     split_node(n, nyn, inv_nyn, ix, iy);
                     const long long idx = (long long)ix * P + iy;
@@ -1375,9 +1373,7 @@ strip_solve_kernel(StripSolveArgs a) {
             // phase A: q = A z + beta q, p = z + beta p, partial mu = p^T q
             // (per-thread partials in T: the FP64 pipe is ~1/64 of FP32 on this part)
             T am_re = 0, am_im = 0;
-            for (int ch = rank; ch < nchunks; ch += bps) {
-                const int n = ch * blockDim.x + threadIdx.x;
-                if (n >= Nall) continue;
+            for (int n = it_first(Nall); n < it_end(Nall); n += it_step) {
                 if (!PADE || n < Ns) {
                     int ix, iy;
                     split_node(n, nyn, inv_nyn, ix, iy);
@@ -1453,9 +1449,7 @@ strip_solve_kernel(StripSolveArgs a) {
             const T2 malT = T2{-s_sc[0], -s_sc[1]};
             // phase B: x += a p, r -= a q, z = D^-1 r, partials rho' = r^T z, ||r||^2
             T b0s = 0, b1s = 0, b2s = 0;
-            for (int ch = rank; ch < nchunks; ch += bps) {
-                const int n = ch * blockDim.x + threadIdx.x;
-                if (n >= Nall) continue;
+            for (int n = it_first(Nall); n < it_end(Nall); n += it_step) {
                 T2 rn, zn;
                 if (!PADE || n < Ns) {
                     int ix, iy;
@@ -1554,9 +1548,7 @@ strip_solve_kernel(StripSolveArgs a) {
         if (DW && dwr) {
             // double-word zeta and the correction accumulated over the launch
             const dw scd = {s_nlf[2], s_nlf[3]};
-            for (int ch = rank; ch < nchunks; ch += bps) {
-                const int n = ch * blockDim.x + threadIdx.x;
-                if (n >= Ns) continue;
+            for (int n = it_first(Ns); n < it_end(Ns); n += it_step) {
                 int ix, iy;
                 split_node(n, nyn, inv_nyn, ix, iy);
                 const long long idx = (long long)ix * P + iy;
@@ -1566,9 +1558,7 @@ strip_solve_kernel(StripSolveArgs a) {
                 if (a.dw_mode == 0) cdw_st(ddw + idx, cdw_add(cdw_ld(ddw + idx), cc));
             }
         } else
-        for (int ch = rank; ch < nchunks; ch += bps) {
-            const int n = ch * blockDim.x + threadIdx.x;
-            if (n >= Nall) continue;
+        for (int n = it_first(Nall); n < it_end(Nall); n += it_step) {
             if (!PADE || n < Ns) {
                 int ix, iy;
                 split_node(n, nyn, inv_nyn, ix, iy);
@@ -1600,9 +1590,7 @@ strip_solve_kernel(StripSolveArgs a) {
         }
     } else if (DW && dwr) {
         // zeta (FP64) += the launch's accumulated correction, own nodes only
-        for (int ch = rank; ch < nchunks; ch += bps) {
-            const int n = ch * blockDim.x + threadIdx.x;
-            if (n >= Ns) continue;
+        for (int n = it_first(Ns); n < it_end(Ns); n += it_step) {
             int ix, iy;
             split_node(n, nyn, inv_nyn, ix, iy);
             const long long idx = (long long)ix * P + iy;
