@@ -488,7 +488,7 @@ def run_ours(args, rank, world, local_rank):
             dist.destroy_process_group()
         return
 
-    dw_used = args.residual == "dw" and args.tc == "robin"     # S_pade keeps the FP64 residual
+    dw_used = args.residual == "dw"
     peaks, peak_kind = measured_peaks()
     roofline = strip_roofline(prof, stats, w, "fp32", peaks, peak_kind)
     roofline["share_of_step"] = prof["strip_solve_ms"] / total_ms * world
@@ -799,7 +799,8 @@ def run_learned(args, rank, world, local_rank):
     line = {"metric": METRIC, "value": 1e3 / ms["learned"], "unit": "steps/s", "n_gpus": world,
             "steps": len(res["learned"]), "warmup": 0, "ms_per_step": ms["learned"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 inner Krylov + f64 residual (S_pade); CNN bf16 operands / f32 accumulate", "data": "synthetic",
+            "dtype": "f32 inner Krylov + " + ("double-word f32x2" if args.residual == "dw" else "f64")
+                     + " residual, f64 interface; CNN bf16 operands / f32 accumulate", "data": "synthetic",
             "config": {"workload": f"learned_guess: GPE trap, {w.nx}x{w.ny} cells on (-16,16)^2, {w.n_strips} strips, "
                                    f"preconditioned Schwarz, S_pade m=8, Omega_rot 0.4, dt={w.dt}, interface tol {args.tol:g}; "
                                    f"training: {args.learn_traj} trajectories x {per} steps at beta "

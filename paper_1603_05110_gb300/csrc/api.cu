@@ -300,7 +300,7 @@ static int strip_solve_finish(dd_nls* h, const StripSolveArgs& a, int nstrips, i
     // double-word form; once per launch a set-up pass (zeta, rhs0, W in; four double-word
     // fields out) and the FP64 write-back (correction and zeta in, zeta out)
     // (dw_mode 1: set-up only, edge columns written back; dw_mode 2: edge columns only)
-    const bool dw = h->dw && h->pade_m == 0;
+    const bool dw = h->dw;
     const int dm = dw ? a.dw_mode : 0;
     const double bW = sr ? 6 * s2 + s1 : 0.0, bE = !dw ? 32 + s2 : (dm == 0 ? 64 + s2 : 32 + s2);
     const double bL = !dw ? 0.0 : (dm == 0 ? 96 + 48 : (dm == 1 ? 80 : 0.0));
@@ -382,7 +382,7 @@ static StripSolveArgs base_args(dd_nls* h) {
         rre = -sim;
         rim = sre;
     }
-    fill_fp32_constants(a, rre, rim);
+    fill_fp32_constants(a, rre, rim, h->G.hy);
     return a;
 }
 
@@ -718,7 +718,7 @@ static int schwarz(dd_nls* h, dd_nls_stats* st) {
         // double-word fields carry the strip state from launch to launch; a tighter launch
         // first returns the state to zeta (FP64) and finishes in FP64
         a.dw_mode = 0;
-        if (h->dw && h->pade_m == 0) {
+        if (h->dw) {
             if (tol_k >= kDWFinish) {
                 a.dw_mode = h->dw_res ? 2 : 1;
             } else if (h->dw_res) {
@@ -870,7 +870,7 @@ extern "C" int dd_nls_create(const dd_nls_params* p, const double* V, const doub
     if (h->P.gmres_restart < 1) h->P.gmres_restart = 30;
     h->s = (cudaStream_t)stream;
     h->fp32 = p->precision != DD_NLS_FP64;
-    h->dw = p->precision == DD_NLS_FP32_DW && p->tc != DD_NLS_TC_PADE;
+    h->dw = p->precision == DD_NLS_FP32_DW;
     Geom& G = h->G;
     G.N = p->n_strips;
     G.nxs = (int)c + 1;

@@ -230,7 +230,7 @@ static std::vector<std::vector<int>> batch_waves(dd_nls_batch* b, int total) {
 static StripSolveArgs batch_args(dd_nls_batch* b) {
     StripSolveArgs a{};
     a.g = b->G[0];
-    fill_fp32_constants(a, 0.0, a.g.p);   // Robin only; per-instance p comes from geoms
+    fill_fp32_constants(a, 0.0, a.g.p, a.g.hy);   // Robin only; per-instance p comes from geoms
     a.geoms = b->d_geoms;
     a.sinfo = b->d_sinfo;
     a.blk_strip = b->d_blk;

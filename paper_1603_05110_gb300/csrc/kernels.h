@@ -16,8 +16,9 @@ void count_launches(int n);
 constexpr int kMaxPade = 96;   // largest Pade order m of eq. (TCS) the kernels take
 
 struct StripSolveArgs;
-// Fill the FP32 edge coefficient of a strip-solver launch: i (rho_re + i rho_im).
-void fill_fp32_constants(StripSolveArgs& a, double rho_re, double rho_im);
+// Fill the FP32 edge coefficient of a strip-solver launch: rho = rho_re + i rho_im on a mesh of
+// y spacing hy.
+void fill_fp32_constants(StripSolveArgs& a, double rho_re, double rho_im, double hy);
 
 // Batched instances: strip j of the launch belongs to instance `inst` (its own geometry),
 // is strip `jloc` of that instance, and its fields start at element `off` of the field arrays;
@@ -77,8 +78,10 @@ struct StripSolveArgs {
     // blk_strip[c] = strip of cluster c, cluster_smem bytes of dynamic shared memory per CTA
     int cluster;
     unsigned cluster_smem;
-    // the S_pade edge coefficient i sum a_s (re, im) rounded to FP32 on the host
+    // the S_pade edge coefficient i sum a_s (re, im) rounded to FP32 on the host, and rho hy/6 in
+    // double words (re hi, re lo, im hi, im lo) for the double-word residual
     float rho_f[2];
+    float dwrho[4];
     long long* pcyc;         // [gridDim][8] phase cycles (R, A, B, epilogue, waits) or NULL
     // S_pade^m transmission (eq. TCS): auxiliary unknowns phi_{e,s} on both vertical edges
     int pade_m;              // 0: Robin

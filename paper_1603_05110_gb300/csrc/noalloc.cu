@@ -225,7 +225,7 @@ extern "C" int dd_nls_step_noalloc(const dd_nls_params* p, const double* V, doub
     a.err = err;
     a.wait_ns = (unsigned long long)(p->wait_limit_ms > 0.0 ? p->wait_limit_ms * 1e6 : 2e9);
     a.pcyc = nullptr;
-    fill_fp32_constants(a, 0.0, G.p);   // Robin transmission only
+    fill_fp32_constants(a, 0.0, G.p, G.hy);   // Robin transmission only
 
     double2* g = gA;
     double2* gn = gB;

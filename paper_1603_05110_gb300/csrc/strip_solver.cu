@@ -187,9 +187,11 @@ __device__ __forceinline__ T2 edge_mass(const T2* v, int iy, int ny, const Coef1
 // sigma_s = i a_s d_s so that the coupled system is complex symmetric (sigma_s C = B_s^T):
 //   sigma_s [ -(M^G zeta_e) + ((i alpha + d_s) M^G - S^G + diag(c_phi)) phi_s ]
 template <typename T, typename T2>
-__device__ __forceinline__ T2 phi_row(const T2* ze, const T2* ph, int iy, int ny, const Coef1<T>& cy, T2 gam,
-                                      T2 sig, T cphi) {
-    const T2 mz = edge_mass<T, T2>(ze, iy, ny, cy);
+__device__ __forceinline__ T2 phi_row_v(T2 zm, T2 z0, T2 zp, const T2* ph, int iy, int ny, const Coef1<T>& cy,
+                                        T2 gam, T2 sig, T cphi) {
+    T2 mz;
+    mz.x = cy.m[0] * zm.x + cy.m[1] * z0.x + cy.m[2] * zp.x;
+    mz.y = cy.m[0] * zm.y + cy.m[1] * z0.y + cy.m[2] * zp.y;
     const T2 a0 = ph[iy];
     const T2 am = iy > 0 ? ph[iy - 1] : mk<T2>(0.0, 0.0);
     const T2 ap = iy < ny ? ph[iy + 1] : mk<T2>(0.0, 0.0);
@@ -202,6 +204,14 @@ __device__ __forceinline__ T2 phi_row(const T2* ze, const T2* ph, int iy, int ny
     j.x += -tK.x + cphi * a0.x - mz.x;
     j.y += -tK.y + cphi * a0.y - mz.y;
     return cmul(sig, j);
+}
+// the same row with the edge column of zeta read from memory (ze: the column, rows 0..ny)
+template <typename T, typename T2>
+__device__ __forceinline__ T2 phi_row(const T2* ze, const T2* ph, int iy, int ny, const Coef1<T>& cy, T2 gam,
+                                      T2 sig, T cphi) {
+    const T2 zm = iy > 0 ? ze[iy - 1] : mk<T2>(0.0, 0.0);
+    const T2 zp = iy < ny ? ze[iy + 1] : mk<T2>(0.0, 0.0);
+    return phi_row_v<T, T2>(zm, ze[iy], zp, ph, iy, ny, cy, gam, sig, cphi);
 }
 template <typename T, typename T2>
 __device__ __forceinline__ T2 phi_diag_inv(const Coef1<T>& cy, T2 gam, T2 sig, T cphi) {
@@ -331,7 +341,7 @@ strip_solve_kernel(StripSolveArgs a) {
     // double-word residual: the nonlinear residual on the FP32 pipe in ~48-bit arithmetic
     // instead of FP64 (GB300's FP64 rate is ~1/64 of FP32); zeta itself stays FP64 and
     // receives the accumulated correction once, at the end of the launch
-    static_assert(!DW || SR, "the double-word residual is built for the FP32 Robin solver");
+    static_assert(!DW || sizeof(T) == 4, "the double-word residual is built for the FP32 inner solvers");
     float4* zdw = DW ? a.zdw + sbase : nullptr;
     float4* ddw = (DW && a.ddw) ? a.ddw + sbase : nullptr;   // dw_mode 0 only
     float4* bdw = DW ? a.bdw + sbase : nullptr;
@@ -527,7 +537,7 @@ strip_solve_kernel(StripSolveArgs a) {
     // with Tm = [1 dy 1] zeta and Tk = [-1 ey -1] zeta along y, U = [-1 ex -1] Tm,
     // V = [1 dx 1] Tm, Wk = [1 dx 1] Tk along x (exact weights: powers of two), and
     // C1 = hy/(6hx), C2 = alpha hx hy/36, C3 = hx/(6hy), C5 = p hy/6, c = w W + w kappa|zeta|^2.
-    dw nC1{}, nC2{}, C2{}, nC3{}, nC5{}, C5{}, C6{};
+    dw nC1{}, nC2{}, C2{}, nC3{}, nC5{}, C5{}, C5r{}, C6{};
     float C6f = 0.f;
     const float cfacf = a.nl_picard ? 1.f : 2.f;
     if constexpr (DW) {
@@ -536,7 +546,13 @@ strip_solve_kernel(StripSolveArgs a) {
         C2 = {g.dwk[2], g.dwk[3]};
         nC2 = dw_neg(C2);
         nC3 = {g.dwk[4], g.dwk[5]};
-        C5 = {g.dwk[6], g.dwk[7]};
+        // edge coefficient rho hy/6: i p hy/6 (Robin, per instance) or (rho_re + i rho_im) hy/6 (S_pade)
+        if constexpr (PADE) {
+            C5r = {a.dwrho[0], a.dwrho[1]};
+            C5 = {a.dwrho[2], a.dwrho[3]};
+        } else {
+            C5 = {g.dwk[6], g.dwk[7]};
+        }
         nC5 = dw_neg(C5);
         if (a.mode == 0) C6 = {g.dwk[8], g.dwk[9]};
         C6f = C6.h;
@@ -619,7 +635,7 @@ strip_solve_kernel(StripSolveArgs a) {
         float rr_f = 0.f;                        // double-word residual: ||res||^2 partial
         const bool need_b = !DW && nl_it == 0;
         for (int n = it_first(NRall); n < it_end(NRall); n += it_step) {
-            if (DW && dwr) {
+            if (DW && dwr && (!PADE || n < NR)) {
                 const int seg = n / nyn;
                 const int iy = n - seg * nyn;
                 const int x0 = seg * RX, x1 = min(x0 + RX, g.nxs);
@@ -651,11 +667,23 @@ strip_solve_kernel(StripSolveArgs a) {
                     const cdw Wk = cdw_add_s(Kq, cdw_pow2(Tk0, dX));
                     dw ax = dw_add_s(dw_add_s(dw_mul(nC1, U.x), dw_mul(nC2, V.y)), dw_mul(nC3, Wk.x));
                     dw ay = dw_add_s(dw_add_s(dw_mul(nC1, U.y), dw_mul(C2, V.x)), dw_mul(nC3, Wk.y));
+                    const long long idx = (long long)ix * P + iy;
                     if ((ix == 0 && ltc) || (ix == c && rtc)) {
                         ax = dw_add_s(ax, dw_mul(nC5, Tm0.y));
                         ay = dw_add_s(ay, dw_mul(C5, Tm0.x));
+                        if constexpr (PADE) {
+                            ax = dw_add_s(ax, dw_mul(C5r, Tm0.x));
+                            ay = dw_add_s(ay, dw_mul(C5r, Tm0.y));
+                            // B_s phi_s = -i a_s d_s M^G phi_s on the edge rows (FP64; 2(ny+1) nodes)
+                            const int e = ix == 0 ? 0 : 1;
+                            const Coef1<double> cyd = coef1<double>(iy, ny, KYd);
+                            double2 cpl = make_double2(0.0, 0.0);
+                            for (int s2 = 0; s2 < m; ++s2)
+                                cpl = cadd(cpl, cmul(sig_of(s2), edge_mass<double, double2>(phi + ((long long)e * m + s2) * P, iy, ny, cyd)));
+                            ax = dw_sub_s(ax, dw_from(cpl.x));
+                            ay = dw_sub_s(ay, dw_from(cpl.y));
+                        }
                     }
-                    const long long idx = (long long)ix * P + iy;
                     const dw a2 = dw_add_s(dw_mul(z0.x, z0.x), dw_mul(z0.y, z0.y));
                     const float2 wv2 = wdw[idx];
                     const dw cd = dw_add_s(dw{wv2.x, wv2.y}, dw_mul(dw_pow2(C6, qxy), a2));
@@ -676,7 +704,7 @@ strip_solve_kernel(StripSolveArgs a) {
                     const T2 zT = cmul(di, rT);
                     cT[idx] = cop;
                     r[idx] = rT;
-                    dv[idx] = di;
+                    if constexpr (SR) dv[idx] = di;
                     if (!use_sr) {
                         z[idx] = zT;
                         x[idx] = mk<T2>(0.0, 0.0);
@@ -778,19 +806,32 @@ strip_solve_kernel(StripSolveArgs a) {
                 const int ixe = e == 0 ? 0 : c;
                 const long long fi = ((long long)e * m + s2) * P + iy;
                 const Coef1<double> cy = coef1<double>(iy, ny, KYd);
-                const double2 ze = zeta[(long long)ixe * P + iy];
+                // the edge column of the strip state: zeta, or the double-word fields while they are it
+                auto zedge = [&](int yy) -> double2 {
+                    if constexpr (DW) {
+                        if (dwr) {
+                            const cdw q = cdw_ld(zdw + (long long)ixe * P + yy);
+                            return make_double2(dw_to(q.x), dw_to(q.y));
+                        }
+                    }
+                    return zeta[(long long)ixe * P + yy];
+                };
+                const double2 ze = zedge(iy);
+                const double2 zem = iy > 0 ? zedge(iy - 1) : make_double2(0.0, 0.0);
+                const double2 zep = iy < ny ? zedge(iy + 1) : make_double2(0.0, 0.0);
                 const double W = Wn ? Wn[(long long)ixe * P + iy] : 0.0;
                 const double ae2 = ze.x * ze.x + ze.y * ze.y;
                 const double cphi = wq(iy, ny, g.hy) * (W + kap * ae2);
                 const double cphi_op = wq(iy, ny, g.hy) * (W + cfac * kap * ae2);
                 const double2 gam = gam_of(s2), sig = sig_of(s2);
                 const double2 res = make_double2(0.0, 0.0);
-                const double2 J = phi_row<double, double2>(zeta + (long long)ixe * P, phi + ((long long)e * m + s2) * P, iy, ny,
-                                                           cy, gam, sig, cphi);
+                const double2 J = phi_row_v<double, double2>(zem, ze, zep, phi + ((long long)e * m + s2) * P, iy, ny,
+                                                             cy, gam, sig, cphi);
                 const double2 rs = csub(res, J);
-                loc[0] += rs.x * rs.x + rs.y * rs.y;
                 const Coef1<T> cyT = coef1<T>(iy, ny, KYt);
                 const T2 rT = cfrom<T2>(make_double2(rs.x * inv_s, rs.y * inv_s));
+                if (DW && dwr) rr_f += rT.x * rT.x + rT.y * rT.y;   // the double-word pass's scaled sum
+                else loc[0] += rs.x * rs.x + rs.y * rs.y;
                 const T2 di = phi_diag_inv<T, T2>(cyT, cfrom<T2>(gam), cfrom<T2>(sig), (T)cphi_op);
                 const T2 zT = cmul(di, rT);
                 if (s2 == 0) cTf[(long long)e * P + iy] = (T)cphi_op;
@@ -1557,6 +1598,18 @@ strip_solve_kernel(StripSolveArgs a) {
                 cdw_st(zdw + idx, cdw_add(cdw_ld(zdw + idx), cc));
                 if (a.dw_mode == 0) cdw_st(ddw + idx, cdw_add(cdw_ld(ddw + idx), cc));
             }
+            if constexpr (PADE) {
+                // the phi unknowns stay FP64
+                for (int n = it_first(Nall); n < it_end(Nall); n += it_step) {
+                    if (n < Ns) continue;
+                    int e, s2, iy;
+                    split_phi(n, e, s2, iy);
+                    if (!(e == 0 ? ltc : rtc)) continue;
+                    const long long fi = ((long long)e * m + s2) * P + iy;
+                    const double2 dx = cd(xf[fi]);
+                    phi[fi] = make_double2(phi[fi].x + sc * dx.x, phi[fi].y + sc * dx.y);
+                }
+            }
         } else
         for (int n = it_first(Nall); n < it_end(Nall); n += it_step) {
             if (!PADE || n < Ns) {
@@ -1611,9 +1664,14 @@ strip_solve_kernel(StripSolveArgs a) {
     if constexpr (CLU) cluster_sync_all();
 }
 
-void fill_fp32_constants(StripSolveArgs& a, double rho_re, double rho_im) {
+void fill_fp32_constants(StripSolveArgs& a, double rho_re, double rho_im, double hy) {
     a.rho_f[0] = (float)rho_re;
     a.rho_f[1] = (float)rho_im;
+    const double v[2] = {rho_re * hy / 6.0, rho_im * hy / 6.0};
+    for (int i = 0; i < 2; ++i) {
+        a.dwrho[2 * i] = (float)v[i];
+        a.dwrho[2 * i + 1] = (float)(v[i] - (double)a.dwrho[2 * i]);
+    }
 }
 
 unsigned strip_cluster_smem(int nxs, int nyn) {
@@ -1676,6 +1734,8 @@ static cudaError_t launch_strip_solve_t(const StripSolveArgs& args, int nblocks,
     }
     if (a.pade_m > 0) {
         if (a.geoms || a.sinfo) return cudaErrorInvalidValue;   // S_pade strips are never batched
+        if (sizeof(T) == 4 && a.zdw && a.mode == 0)
+            return cudaLaunchCooperativeKernel((const void*)strip_solve_kernel<float, true, 256, true>, grid, dim3(256), params, 0, s);
         return cudaLaunchCooperativeKernel((const void*)strip_solve_kernel<T, true, 256>, grid, dim3(256), params, 0, s);
     }
     if (sizeof(T) == 4 && a.zdw && a.mode == 0)
@@ -1728,6 +1788,8 @@ int strip_solve_max_blocks(bool fp32) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, strip_solve_kernel<float, false, 256>, 256, 0);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, strip_solve_kernel<float, true, 256>, 256, 0);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per3, strip_solve_kernel<float, false, 256, true>, 256, 0);
+        per2 = std::min(per2, per3);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per3, strip_solve_kernel<float, true, 256, true>, 256, 0);
         per2 = std::min(per2, per3);
     } else {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, strip_solve_kernel<double, false, 256>, 256, 0);

@@ -357,20 +357,26 @@ def test_batched_preconditioned_and_classical_instances_match_oracle(precision):
             assert abs(its[step][i] - ref[step][1].iterations) <= 2, (i, step, its, ref[step][1].iterations)
 
 
-@pytest.mark.parametrize("case", ["well", "gpe_far"])
+@pytest.mark.parametrize("case", ["well", "gpe_far", "pade_well"])
 def test_double_word_state_carried_between_launches(case):
     """Strip tolerances of 1e-12 and above: the double-word fields carry the strip state from
     one Schwarz launch to the next (only the edge columns go back to FP64 in between, and the
     whole field at the end of the step).  Interface tolerance 1e-10, so the step agrees with
     the oracle's (solved to 1e-12) to 1e-8."""
+    tc = {}
     if case == "well":
         w, relax = WELL, 1.0
+    elif case == "pade_well":
+        # S_pade: the edge nodes' phi coupling and the phi rows enter the double-word residual
+        w, relax = WELL, 1.0
+        tc = dict(tc="pade", m=4)
     else:
         w = wl.Workload("gpe_far", -18.0, 18.0, -18.0, 18.0, 36, 30, 6, 0.002, 2, lap=0.5, kappa=-500.0, p=45.0,
                         potential="trap", datum="ground_noise", seed=1603)
         relax = 0.6
-    ref = run_oracle(w, 2, algorithm="preconditioned", relax=relax)
-    got = run_gpu(w, 2, tol=1e-10, nl_tol=1e-12, algorithm=binding.PRECONDITIONED, precision=binding.FP32_DW)
+    ref = run_oracle(w, 2, algorithm="preconditioned", relax=relax, **tc)
+    extra = dict(tc=binding.TC_PADE, pade_m=4) if tc else {}
+    got = run_gpu(w, 2, tol=1e-10, nl_tol=1e-12, algorithm=binding.PRECONDITIONED, precision=binding.FP32_DW, **extra)
     for (ug, _), (uo, _) in zip(got, ref):
         assert rel(ug, uo) < 1e-8
 
