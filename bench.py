@@ -82,7 +82,8 @@ def measured_traffic(workload):
 def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: the workload's run length, nls_well 200; gpe_batch 3)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="nls_well")
@@ -92,7 +93,8 @@ def parse(argv=None):
     ap.add_argument("--pade-m", type=int, default=None, help="Pade order (default: the workload's, else 4)")
     ap.add_argument("--algorithm", default="workload", choices=["workload", "classical", "preconditioned"])
     ap.add_argument("--tol", type=float, default=1e-8)
-    ap.add_argument("--fp64-steps", type=int, default=4)
+    ap.add_argument("--fp64-steps", type=int, default=None,
+                    help="plain FP64 steps, from the chosen form's post-warm-up state (default: --steps)")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--residual", default="dw", choices=["fp64", "dw"],
@@ -117,6 +119,8 @@ def parse(argv=None):
     from paper_1603_05110_gb300 import workloads as wl
     w = wl.WORKLOADS.get(args.workload)
     extra = w.extra if w is not None else {}
+    if args.steps is None:
+        args.steps = w.steps if w is not None else 3
     if args.tc is None:
         args.tc = extra.get("tc", "robin")
     if args.pade_m is None:
@@ -153,10 +157,13 @@ def describe(w, args):
 
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """nvidia-smi sampling during the timed region: started before it, waited for until its first
+    sample is out (its start-up must not fall into the timed region), and only the samples
+    written after that are read."""
 
-    def __init__(self, index):
+    def __init__(self, index, ready_timeout=5.0):
         self.proc = None
+        self.skip = 0
         fd, self.path = tempfile.mkstemp(prefix="ddnls_clocks_", suffix=".csv")
         os.close(fd)
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -165,9 +172,22 @@ class Clocks:
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+                                          "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+        if self.proc is not None:
+            t0 = time.perf_counter()
+            while time.perf_counter() - t0 < ready_timeout and self.proc.poll() is None:
+                self.f.flush()
+                try:
+                    with open(self.path) as fh:
+                        n = sum(1 for _ in fh)
+                except OSError:
+                    n = 0
+                if n >= 1:
+                    self.skip = n
+                    break
+                time.sleep(0.02)
 
     def stop(self):
         if self.proc is None:
@@ -180,7 +200,10 @@ class Clocks:
         self.f.close()
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        lines = open(self.path).read().splitlines()
+        if len(lines) > self.skip:
+            lines = lines[self.skip:]        # the samples of the timed region
+        for line in lines:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -421,6 +444,12 @@ def run_ours(args, rank, world, local_rank):
     chosen = binding.Solver(solver_params(w, args, CHOSEN), u0, V, stream=stream)
     for _ in range(args.warmup):
         chosen.step(1)
+    # the state after the warm-up: the timed steps, their profiled repeat and the end-to-end steps
+    # all start from it, so the three cover the same stretch of the trajectory
+    ntr = 2 * (w.n_strips - 1)
+    u_w = torch.empty_like(u0)
+    g_w = torch.empty(ntr, w.ny + 1, dtype=torch.complex128, device=dev) if ntr > 0 else None
+    n_w = chosen.get_state(u_w, g_w)
     barrier()
     clocks = Clocks(local_rank)
     barrier()
@@ -433,6 +462,7 @@ def run_ours(args, rank, world, local_rank):
     # the same number of steps again with the library's profiling on (CUDA events around each
     # phase, each read back at once): the time split, the strip solver's kernel time for the
     # roofline and the launch count come from this repeat
+    chosen.set_state(u_w, g_w, n_w)
     ms_p, stats_p, prof = timed_steps(chosen, args.steps, profile=True)
     chosen.set_profiling(False)
     kry = sum(s["krylov_iterations"] for s in stats_p)
@@ -440,7 +470,9 @@ def run_ours(args, rank, world, local_rank):
     # ---- e2e through the C-ABI with host buffers (pinned): H2D of u_{n-1}, step, D2H of u_n
     uh_in = torch.empty(w.ny + 1, w.nx + 1, dtype=torch.complex128, pin_memory=True)
     uh_out = torch.empty_like(uh_in)
-    step_no = chosen.get_state(uh_in)
+    chosen.set_state(u_w, g_w, n_w)
+    uh_in.copy_(u_w)
+    step_no = n_w
     e2e_ms = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
@@ -456,17 +488,22 @@ def run_ours(args, rank, world, local_rank):
     fp64 = None
     err = None
     if not args.no_fp64 and rank == 0:
+        # the same steps as the chosen form's timed region: from its post-warm-up state
+        k64 = args.fp64_steps if args.fp64_steps else args.steps
         plain = binding.Solver(solver_params(w, args, binding.FP64), u0, V, stream=stream)
-        for _ in range(max(1, args.warmup - 1)):
-            plain.step(1)
-        ms64, st64, _ = timed_steps(plain, args.fp64_steps)
-        _, st64p, prof64 = timed_steps(plain, args.fp64_steps, profile=True)
+        plain.step(1)
+        plain.set_state(u_w, g_w, n_w)
+        ms64, st64, _ = timed_steps(plain, k64)
+        kp = min(k64, 10)
+        plain.set_state(u_w, g_w, n_w)
+        _, st64p, prof64 = timed_steps(plain, kp, profile=True)
         plain.close()
-        fp64 = {"value": args.fp64_steps / (sum(ms64) * 1e-3), "unit": "steps/s",
-                "ms_per_step": sum(ms64) / args.fp64_steps,
+        fp64 = {"value": k64 / (sum(ms64) * 1e-3), "unit": "steps/s", "steps": k64,
+                "ms_per_step": sum(ms64) / k64,
                 "schwarz_iterations_per_step": statistics.mean(s["last_schwarz_iterations"] for s in st64),
                 "strip_solve_gbs": strip_roofline(prof64, st64p, w, "fp64", None, None)["achieved"],
-                "strip_solve_ms_per_step": prof64["strip_solve_ms"] / args.fp64_steps}
+                "strip_solve_ms_per_step": prof64["strip_solve_ms"] / kp,
+                "note": f"from the chosen form's post-warm-up state; strip figures from a profiled repeat of the first {kp} steps"}
         # the paper-literal path: FP64, L_h from unit solves, P x = y by GMRES (Robin only: the
         # library solves S_pade's preconditioned update by the modal solve)
         if args.tc == "robin" and algorithm_of(w, args) == "preconditioned":

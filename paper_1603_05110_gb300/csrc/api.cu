@@ -47,7 +47,7 @@ struct dd_nls {
     int* h_blk = nullptr;   // pinned mirror
     double* bnorm0 = nullptr;   // [N] per-strip ||(2i/dt) M h||
     long long* pcyc = nullptr;  // [maxb][8] phase cycles of the strip solver
-    std::vector<long long> h_pcyc;
+    PinnedVec<long long> h_pcyc;   // pinned: copies into it stay asynchronous
     std::vector<double> wts;    // scheduling weights
     // device state
     double2 *u = nullptr, *zeta = nullptr, *rhs0 = nullptr, *gA = nullptr, *gB = nullptr, *gconv = nullptr;
@@ -96,8 +96,8 @@ struct dd_nls {
     int* tkind = nullptr;
     // host mirrors
     double* hred = nullptr;          // pinned
-    std::vector<int> h_status, h_nl;
-    std::vector<long long> h_kry;
+    PinnedVec<int> h_status, h_nl;  // pinned per-strip results (read after the one wait per launch)
+    PinnedVec<long long> h_kry;
     int step = 0;
     bool have_prev = false;
     std::string error;
@@ -948,9 +948,10 @@ extern "C" int dd_nls_create(const dd_nls_params* p, const double* V, const doub
     CKC(cudaEventCreate(&h->ev1));
     CKC(cudaEventCreate(&h->ev2));
     CKC(cudaEventCreate(&h->ev3));
-    h->h_status.resize(G.N);
-    h->h_nl.resize(G.N);
-    h->h_kry.resize(G.N);
+    if (!h->h_status.resize(G.N) || !h->h_nl.resize(G.N) || !h->h_kry.resize(G.N)) {
+        h->error = "dd_nls_create: pinned host memory for the per-strip results";
+        return bad(DD_NLS_ENOMEM);
+    }
 
     // launch shape of the strip solver: all blocks co-resident, blocks split among strips per launch
     const int maxb = strip_solve_max_blocks(h->fp32);
@@ -992,7 +993,10 @@ extern "C" int dd_nls_create(const dd_nls_params* p, const double* V, const doub
         CKC(dalloc((char**)&h->qf, nf * s2));
         CKC(dalloc((char**)&h->cTf, (size_t)G.N * 2 * G.P * s1));
     }
-    h->h_pcyc.assign((size_t)8 * maxphys, 0);
+    if (!h->h_pcyc.assign((size_t)8 * maxphys, 0)) {
+        h->error = "dd_nls_create: pinned host memory for the phase profile";
+        return bad(DD_NLS_ENOMEM);
+    }
 
     if (upload_nodal(h, u0, ptr_kind, h->u)) return bad(DD_NLS_ECUDA);
     if (V) {

@@ -113,8 +113,8 @@ struct dd_nls_batch {
     int* h_active = nullptr;
     double* h_res = nullptr;
     double* h_bn = nullptr;
-    std::vector<int> h_status, h_nl;
-    std::vector<long long> h_kry;
+    PinnedVec<int> h_status, h_nl;  // pinned: copies into them stay asynchronous
+    PinnedVec<long long> h_kry;
     std::vector<int> cur;           // ping-pong half holding each instance's current g
     std::vector<int> conv_half;     // half holding the converged R(g) of the last step
     std::vector<char> have_prev;
@@ -516,9 +516,10 @@ extern "C" int dd_nls_batch_create(int n, const dd_nls_params* params, const dou
     BCKC(cudaMallocHost((void**)&b->h_bn, sizeof(double) * b->nstrips));
     BCKC(cudaEventCreate(&b->ev0));
     BCKC(cudaEventCreate(&b->ev1));
-    b->h_status.resize(b->nstrips);
-    b->h_nl.resize(b->nstrips);
-    b->h_kry.resize(b->nstrips);
+    if (!b->h_status.resize(b->nstrips) || !b->h_nl.resize(b->nstrips) || !b->h_kry.resize(b->nstrips)) {
+        b->error = "dd_nls_batch_create: pinned host memory for the per-strip results";
+        return bad(DD_NLS_ENOMEM);
+    }
     b->cur.assign(n, 0);
     b->conv_half.assign(n, 0);
     b->have_prev.assign(n, 0);
