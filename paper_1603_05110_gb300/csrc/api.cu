@@ -22,6 +22,7 @@
 #include "../../include/dd_nls.h"
 #include "common.cuh"
 #include "kernels.h"
+#include "host_pinned.h"
 
 using namespace ddnls;
 using cplx = std::complex<double>;

@@ -28,6 +28,7 @@
 #include "../../include/dd_nls.h"
 #include "common.cuh"
 #include "kernels.h"
+#include "host_pinned.h"
 
 using namespace ddnls;
 

@@ -150,42 +150,6 @@ cudaError_t launch_modal_apply(const AuxGeom& g, bool fp32, const double* Cf, co
                                cudaStream_t s, void* cpart,    // cpart: 8 x 2(N-1) x P double2 scratch
                                const float2* fac32 = nullptr,  // FP32 factors for the FP32 forms
                                int kmax = 0);                  // > 0: modes k >= kmax take P = I
-// Page-locked host array (cudaMallocHost): device-to-host copies into it stay asynchronous,
-// where a copy into pageable memory would block the host until the stream reaches it.
-template <typename T> struct PinnedVec {
-    T* p = nullptr;
-    size_t n = 0;
-    PinnedVec() = default;
-    PinnedVec(const PinnedVec&) = delete;
-    PinnedVec& operator=(const PinnedVec&) = delete;
-    ~PinnedVec() { if (p) cudaFreeHost(p); }
-    // false when the allocation fails (the array is then empty)
-    bool resize(size_t m) {
-        if (p) cudaFreeHost(p);
-        p = nullptr;
-        n = 0;
-        if (m == 0) return true;
-        if (cudaMallocHost((void**)&p, m * sizeof(T)) != cudaSuccess) {
-            p = nullptr;
-            cudaGetLastError();
-            return false;
-        }
-        n = m;
-        for (size_t i = 0; i < n; ++i) p[i] = T();
-        return true;
-    }
-    bool assign(size_t m, T v) {
-        if (!resize(m)) return false;
-        for (size_t i = 0; i < n; ++i) p[i] = v;
-        return true;
-    }
-    T* data() { return p; }
-    const T* data() const { return p; }
-    T& operator[](size_t i) { return p[i]; }
-    const T& operator[](size_t i) const { return p[i]; }
-    size_t size() const { return n; }
-};
-
 cudaError_t launch_to_float(const double* a, float* b, long long n, cudaStream_t s);
 // g_new = g_k - P^{-1}(g_k - R(g_k)) (eq. algo_pd) with the modal P^-1: five launches (the
 // subtractions fused into the transforms).
