@@ -98,6 +98,7 @@ struct dd_nls {
     // host mirrors
     double* hred = nullptr;          // pinned
     PinnedVec<int> h_status, h_nl;  // pinned per-strip results (read after the one wait per launch)
+    std::vector<int> cl_order;      // cluster order last copied to d_blk (empty: none)
     PinnedVec<long long> h_kry;
     int step = 0;
     bool have_prev = false;
@@ -241,6 +242,7 @@ static int schedule(dd_nls* h, const std::vector<double>& w, int nstrips, int ca
     }
     st[nstrips] = total;
     cudaMemcpyAsync(h->d_blk, h->h_blk, sizeof(int) * (h->maxb + nstrips + 1), cudaMemcpyHostToDevice, h->s);
+    h->cl_order.clear();                      // the device table no longer holds a cluster order
     a.blk_strip = h->d_blk;
     a.blk_start = h->d_blk + h->maxb;
     return total;
@@ -253,8 +255,13 @@ static int schedule_clusters(dd_nls* h, const std::vector<double>& w, int nstrip
     std::vector<int> order(nstrips);
     for (int j = 0; j < nstrips; ++j) order[j] = j;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return w[x] > w[y]; });
-    for (int j = 0; j < nstrips; ++j) h->h_blk[j] = order[j];
-    cudaMemcpyAsync(h->d_blk, h->h_blk, sizeof(int) * nstrips, cudaMemcpyHostToDevice, h->s);
+    // the copy is skipped when the device already holds this order (the usual case from one
+    // Schwarz iteration to the next)
+    if (order != h->cl_order) {
+        for (int j = 0; j < nstrips; ++j) h->h_blk[j] = order[j];
+        cudaMemcpyAsync(h->d_blk, h->h_blk, sizeof(int) * nstrips, cudaMemcpyHostToDevice, h->s);
+        h->cl_order = order;
+    }
     a.blk_strip = h->d_blk;
     a.blk_start = nullptr;
     a.cluster = 1;

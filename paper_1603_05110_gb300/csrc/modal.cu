@@ -214,19 +214,27 @@ constexpr int kCosSlices = 8;
 template <typename T2>
 __global__ void modal_solve_staged_kernel(Geom g, const T2* __restrict__ fac, double2* __restrict__ y, int kmax) {
     extern __shared__ __align__(16) unsigned char s_modal[];
-    const int n = g.nyn, NI = g.N - 1, P = g.P, lane = threadIdx.x;
-    const int k = blockIdx.x * 32 + lane;
-    const bool on = k < n && !(kmax > 0 && k >= kmax);
+    const int n = g.nyn, NI = g.N - 1, P = g.P, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    const int k0 = blockIdx.x * 32;
     T2* Fs = (T2*)s_modal;                       // [NI * 9][32]
     T2* Ys = Fs + (size_t)NI * 9 * 32;           // [2 NI][32]
     const T2 zero = mk<T2>(0, 0);
-#pragma unroll 8
-    for (int q = 0; q < NI * 9; ++q) Fs[q * 32 + lane] = on ? fac[(long long)q * n + k] : zero;
-#pragma unroll 8
-    for (int q = 0; q < 2 * NI; ++q) {
-        const double2 v = on ? y[(long long)q * P + k] : make_double2(0.0, 0.0);
-        Ys[q * 32 + lane] = mk<T2>(v.x, v.y);
+    // staging by all warps of the block (more loads in flight); warp 0 then runs the sweeps
+    {
+        const int kk = k0 + lane;
+        const bool in = kk < n;
+#pragma unroll 4
+        for (int q = wid; q < NI * 9; q += nw) Fs[q * 32 + lane] = in ? fac[(long long)q * n + kk] : zero;
+#pragma unroll 4
+        for (int q = wid; q < 2 * NI; q += nw) {
+            const double2 v = in ? y[(long long)q * P + kk] : make_double2(0.0, 0.0);
+            Ys[q * 32 + lane] = mk<T2>(v.x, v.y);
+        }
     }
+    __syncthreads();
+    const int k = k0 + lane;
+    const bool on = wid == 0 && k < n && !(kmax > 0 && k >= kmax);
     if (!on) return;
     auto F = [&](int i, int e) { return Fs[(i * 9 + e) * 32 + lane]; };
     auto Y = [&](int q) -> T2& { return Ys[q * 32 + lane]; };
@@ -382,8 +390,8 @@ static cudaError_t modal_solve(const Geom& g, bool f32, const double2* fac, cons
         }
     }
     if (staged) {
-        if (f32) modal_solve_staged_kernel<float2><<<(g.nyn + 31) / 32, 32, smem, s>>>(g, fac32, y, kmax);
-        else modal_solve_staged_kernel<double2><<<(g.nyn + 31) / 32, 32, smem, s>>>(g, fac, y, kmax);
+        if (f32) modal_solve_staged_kernel<float2><<<(g.nyn + 31) / 32, 128, smem, s>>>(g, fac32, y, kmax);
+        else modal_solve_staged_kernel<double2><<<(g.nyn + 31) / 32, 128, smem, s>>>(g, fac, y, kmax);
     } else if (f32) {
         modal_solve_kernel<float2><<<(g.nyn + 31) / 32, 32, 0, s>>>(g, fac32, y, kmax);
     } else {
