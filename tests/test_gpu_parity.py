@@ -423,3 +423,16 @@ def test_cluster_layout_on_strips_wider_than_a_cta_slab():
     got = run_gpu(w, 2, tol=TOL, algorithm=binding.PRECONDITIONED, precision=binding.FP32_DW, solver_layout=2)
     for (ug, _), (uo, _) in zip(got, ref):
         assert rel(ug, uo) < 1e-10
+
+
+def test_strips_too_large_for_a_cluster_fall_back_to_the_cooperative_layout():
+    """A strip of 101 x 481 nodes needs 31 rows x 101 columns = 3131 nodes per CTA of a 16-CTA
+    cluster at most 4608 (fits); one of 201 x 481 nodes (6231 per CTA) does not, so the default
+    layout falls back to the cooperative launch and reproduces solver_layout 1 bit for bit."""
+    w = wl.scaled(wl.NLS_WELL, 400, 480, n_strips=2, xl=-8.0, xr=8.0, yb=-9.0, yu=9.0, dt=0.02, p=3.0)
+    a = run_gpu(w, 1, tol=1e-10, nl_tol=1e-12, algorithm=binding.PRECONDITIONED, precision=binding.FP32_DW,
+                solver_layout=0)
+    b = run_gpu(w, 1, tol=1e-10, nl_tol=1e-12, algorithm=binding.PRECONDITIONED, precision=binding.FP32_DW,
+                solver_layout=1)
+    assert np.array_equal(a[0][0], b[0][0])
+    assert a[0][1]["last_schwarz_iterations"] == b[0][1]["last_schwarz_iterations"]
