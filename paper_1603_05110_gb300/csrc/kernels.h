@@ -145,14 +145,9 @@ cudaError_t launch_modal_setup(const AuxGeom& g, int ntypes, const int* tkind_de
                                double* Cf, double* Ci, float* Cf32, float* Ci32, double2* xm, double2* fac,
                                double2* work, cudaStream_t s, int pade_m = 0, const double2* pa = nullptr,
                                const double2* pd = nullptr);
-cudaError_t launch_modal_apply(const AuxGeom& g, bool fp32, const double* Cf, const double* Ci, const float* Cf32,
-                               const float* Ci32, const double2* fac, const double2* y, double2* x, double2* tmp,
-                               cudaStream_t s, void* cpart,    // cpart: 8 x 2(N-1) x P double2 scratch
-                               const float2* fac32 = nullptr,  // FP32 factors for the FP32 forms
-                               int kmax = 0);                  // > 0: modes k >= kmax take P = I
 cudaError_t launch_to_float(const double* a, float* b, long long n, cudaStream_t s);
 // g_new = g_k - P^{-1}(g_k - R(g_k)) (eq. algo_pd) with the modal P^-1: five launches (the
-// subtractions fused into the transforms).
+// subtractions fused into the transforms).  kmax > 0: modes k >= kmax take P = I.
 // g_new and tmp may alias rg.
 cudaError_t launch_modal_update(const Geom& g, bool fp32, const double* Cf, const double* Ci, const float* Cf32,
                                 const float* Ci32, const double2* fac, const float2* fac32, const double2* gk,

@@ -367,12 +367,6 @@ static cudaError_t cosine_reduce(int n, int ntr, int P, const void* part, const 
     cosine_reduce_kernel<T2><<<nb, 256, 0, s>>>(n, ntr, P, (const T2*)part, from, out);
     return cudaGetLastError();
 }
-template <typename T>
-static cudaError_t cosine_apply(int n, int ntr, int P, const T* C, const double2* in, double2* out, void* part,
-                                cudaStream_t s) {
-    cudaError_t e = cosine_partial<T>(n, ntr, P, C, in, nullptr, part, s);
-    return e != cudaSuccess ? e : cosine_reduce<T>(n, ntr, P, part, nullptr, out, s);
-}
 
 // The per-mode solve on y in place: one warp per block (the per-mode sweeps are chains, spread
 // over as many SMs as possible), staged in shared memory when the mode's data fit.
@@ -424,20 +418,6 @@ cudaError_t launch_modal_setup(const Geom& g, int ntypes, const int* tkind_dev, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_modal_apply(const Geom& g, bool fp32, const double* Cf, const double* Ci, const float* Cf32,
-                               const float* Ci32, const double2* fac, const double2* y, double2* x, double2* tmp,
-                               cudaStream_t s, void* cpart, const float2* fac32, int kmax) {
-    const int ntr = 2 * (g.N - 1);
-    cudaError_t e = fp32 ? cosine_apply<float>(g.nyn, ntr, g.P, Cf32, y, tmp, cpart, s)
-                         : cosine_apply<double>(g.nyn, ntr, g.P, Cf, y, tmp, cpart, s);
-    if (e != cudaSuccess) return e;
-    e = modal_solve(g, fp32 && fac32, fac, fac32, tmp, kmax, s);
-    if (e != cudaSuccess) return e;
-    e = fp32 ? cosine_apply<float>(g.nyn, ntr, g.P, Ci32, tmp, x, cpart, s)
-             : cosine_apply<double>(g.nyn, ntr, g.P, Ci, tmp, x, cpart, s);
-    if (e != cudaSuccess) return e;
-    return cudaGetLastError();
-}
 
 // g_new = g_k - P^{-1} (g_k - R(g_k))  (eq. algo_pd) in five launches: the forward transform
 // forms y = g_k - R(g_k) as it reads, and the inverse transform's reduction subtracts from g_k.
