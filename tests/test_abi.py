@@ -72,3 +72,27 @@ def test_create_rejects_bad_sizes_without_touching_the_gpu(lib):
     with pytest.raises(binding.DDNLSError) as e:
         binding.Solver(p, u0)
     assert e.value.code == 1
+
+
+@pytest.mark.parametrize("case", ["pade", "gmres", "dw_tight_tol", "mixed_precision"])
+def test_batch_create_rejects_unsupported_forms_without_touching_the_gpu(lib, case):
+    """Batched instances take Robin transmission, the classical or the modal-preconditioned
+    algorithm, one precision for the whole batch, and nl_tol >= 1e-12 with the double-word
+    residual; anything else is EINVAL before any device work."""
+    import numpy as np
+    from paper_1603_05110_gb300 import binding
+    base = dict(nx=16, ny=8, n_strips=2, tol=1e-8, nl_tol=1e-11)
+    prms = [dict(base), dict(base)]
+    if case == "pade":
+        prms[1].update(tc=binding.TC_PADE, pade_m=4)
+    elif case == "gmres":
+        prms[1].update(algorithm=binding.PRECONDITIONED, psolve=binding.PSOLVE_GMRES)
+    elif case == "dw_tight_tol":
+        for q in prms:
+            q.update(precision=binding.FP32_DW, nl_tol=1e-13)
+    else:
+        prms[1].update(precision=binding.FP32_INNER)
+    u0 = [np.zeros((9, 17), np.complex128) for _ in prms]
+    with pytest.raises(binding.DDNLSError) as e:
+        binding.Batch(prms, u0)
+    assert e.value.code == 1, str(e.value)
