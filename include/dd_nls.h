@@ -59,9 +59,9 @@ enum { DD_NLS_BC_SAME = 0, DD_NLS_BC_NEUMANN = 1 };        /* physical x-edges *
 enum { DD_NLS_CLASSICAL = 0, DD_NLS_PRECONDITIONED = 1 };  /* eq. algo_d / eq. algo_pd */
 /* Arithmetic of the strip solves: FP64 throughout; FP32 inner Krylov with the FP64 nonlinear
  * residual; or FP32 inner Krylov with the residual in double-word arithmetic (pairs of FP32
- * numbers, about 48 significant bits, on the FP32 pipe; Robin transmission only -- with
- * S_pade it behaves as DD_NLS_FP32_INNER).  Interface vectors, the Schwarz test, u_n and the
- * diagnostics are FP64 in every mode.  In the double-word mode a strip whose tolerance is below
+ * numbers, about 48 significant bits, on the FP32 pipe; with S_pade the auxiliary phi rows
+ * and their coupling to the edge nodes keep the FP64 residual).  Interface vectors, the
+ * Schwarz test, u_n and the diagnostics are FP64 in every mode.  In the double-word mode a strip whose tolerance is below
  * 1e-12 finishes with the FP64 residual; while all strip tolerances of a step are 1e-12 or
  * looser the strip state travels between that step's launches in double-word form and u_n is
  * rebuilt from it (rounded to ~48 bits) at the end of the step. */
