@@ -110,7 +110,7 @@ typedef struct {
                             of the fixed point of eq. localpbrobin, diag(w(W + kappa|zeta|^2)).
                             The residual is exact either way, so the limit is the same. */
     double nl_adapt;     /* 0 (default): strip solves always to nl_tol.  > 0, preconditioned
-                            algorithm only: tol_k = nl_adapt x the last relative interface
+                            algorithm with two or more strips only: tol_k = nl_adapt x the last relative interface
                             residual (at most 1e-6, never below nl_tol), and a step converges
                             only once tol_k <= max(nl_tol, nl_adapt x tol).  Same fixed point,
                             cheaper early Schwarz iterations.  A Schwarz iteration that does not

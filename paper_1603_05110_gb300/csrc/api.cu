@@ -715,7 +715,8 @@ static int schwarz(dd_nls* h, dd_nls_stats* st) {
     // (0.98-0.99 per iteration) to absorb that perturbation.  An iteration that does not cut the
     // interface residual by 4x ends the inexact solves for the rest of the step (strongly
     // nonlinear strips can stall the preconditioned iteration at the inexact solves' level).
-    bool adapt = h->P.algorithm == DD_NLS_PRECONDITIONED && h->P.nl_adapt > 0.0;
+    // A single strip has no interface: its one solve is the step, at nl_tol.
+    bool adapt = G.N > 1 && h->P.algorithm == DD_NLS_PRECONDITIONED && h->P.nl_adapt > 0.0;
     for (int k = 0; k < h->P.max_schwarz; ++k) {
         a.gtr = g;
         const double tol_k = adapt ? std::max(h->P.nl_tol, std::min(1e-6, h->P.nl_adapt * rel_prev)) : h->P.nl_tol;

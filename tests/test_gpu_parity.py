@@ -198,12 +198,17 @@ def test_pade_modal_diagonal_matches_oracle_blocks():
         np.testing.assert_allclose(xm[a], np.diag(Zi @ X[a] @ Z), atol=1e-11)
 
 
-def test_single_strip_is_the_monodomain_solve():
+@pytest.mark.parametrize("form", ["classical", "preconditioned_adapt"])
+def test_single_strip_is_the_monodomain_solve(form):
+    """One strip has no interface: the step is the monodomain solve, also with the
+    preconditioned algorithm and nl_adapt set (the inexact early solves need an interface)."""
     w = wl.scaled(SMALL, 20, 33, n_strips=1)
     prob = oracle_problem(w)
     u1, _, _ = nls.mono_step(prob, w.u0())
-    got = run_gpu(w, 1, tol=TOL)
+    kw = {} if form == "classical" else dict(algorithm=binding.PRECONDITIONED, nl_adapt=0.01)
+    got = run_gpu(w, 1, tol=TOL, **kw)
     assert rel(got[0][0], u1) < 1e-11
+    assert got[0][1]["schwarz_iterations"] == 1
 
 
 @pytest.mark.parametrize("precision", [binding.FP64, binding.FP32_DW])
