@@ -26,13 +26,18 @@
  *    (r_1, l_2, r_2, l_3, ..., r_{N-1}, l_N) of Sec. 2.3, i.e. trace 2i is the right
  *    datum of strip i and trace 2i+1 the left datum of strip i+1 (0-based strips).
  *  - ptr_kind says whether caller pointers are host (DD_NLS_PTR_HOST, any pageable or
- *    pinned memory) or device (DD_NLS_PTR_DEVICE) memory.  Pointers are only used during
- *    the call; the library keeps no reference to caller memory.
+ *    pinned memory) or device (DD_NLS_PTR_DEVICE) memory; any other value is DD_NLS_EINVAL.
+ *    Pointers are only used during the call; the library keeps no reference to caller memory.
  *  - The handle owns all device memory it uses (allocated in dd_nls_create, released in
  *    dd_nls_destroy).  All GPU work is issued on the stream given to dd_nls_create
  *    (NULL: the legacy default stream); calls return after that work has finished.
  *  - Errors are returned as dd_nls_status codes; the GPU is never trapped.  After an
  *    error, dd_nls_last_error() describes it.  A handle is not thread safe.
+ *  - Parameters are checked before any device work (DD_NLS_EINVAL): sizes (nx a multiple of
+ *    n_strips; ny + 1 and nx / n_strips + 1 at most 2^20 nodes, a strip at most 2^30), every
+ *    enum field one of its values, every real field finite, xr > xl, yu > yb, dt > 0,
+ *    lap > 0, Robin p > 0, Pade m in 1..96; tolerances, nl_adapt, trap_gx, trap_gy and
+ *    wait_limit_ms >= 0.
  */
 #ifndef DD_NLS_H
 #define DD_NLS_H
@@ -104,18 +109,19 @@ typedef struct {
     int psolve;          /* DD_NLS_PSOLVE_MODAL (default) or DD_NLS_PSOLVE_GMRES */
     double nl_relax;     /* first relaxation factor of the strip fixed point (1: eq. localpbrobin
                             as printed); a correction that does not cut the residual by 10%
-                            multiplies it by 0.6 (down to 0.25).  Same limit, safer path. */
+                            multiplies it by 0.6 (down to 0.25).  Same limit, safer path.
+                            Values outside (0, 1] act as 1. */
     int nl_picard;       /* operator of each strip correction: 0 (default) the complex-linear part
                             of the Jacobian, diag(w(W + 2 kappa|zeta|^2)); 1 the frozen operator
                             of the fixed point of eq. localpbrobin, diag(w(W + kappa|zeta|^2)).
                             The residual is exact either way, so the limit is the same. */
     double nl_adapt;     /* 0 (default): strip solves always to nl_tol.  > 0, preconditioned
-                            algorithm with two or more strips only: tol_k = nl_adapt x the last relative interface
-                            residual (at most 1e-6, never below nl_tol), and a step converges
-                            only once tol_k <= max(nl_tol, nl_adapt x tol).  Same fixed point,
-                            cheaper early Schwarz iterations.  A Schwarz iteration that does not
-                            cut the relative interface residual by 4x ends the inexact solves
-                            for the rest of the step. */
+                            algorithm with two or more strips only: tol_k = nl_adapt x the last
+                            relative interface residual (at most 1e-6, never below nl_tol), and
+                            a step converges only once tol_k <= max(nl_tol, nl_adapt x tol).
+                            Same fixed point, cheaper early Schwarz iterations.  A Schwarz
+                            iteration that does not cut the relative interface residual by 4x
+                            ends the inexact solves for the rest of the step. */
     /* Rotating frame of the GPE (Sec. 5.2.1, eq. x1Ax, GPE_Trans, u1u).  The solve runs in the
      * coordinates x~ = A(t)^T x, A(t) the rotation by omega_rot t, where the rotation term of
      * eq. (GPE) is absent and the trap becomes time dependent. */
@@ -245,9 +251,13 @@ int dd_nls_step_noalloc(const dd_nls_params* p, const double* V, double* u, cons
 /* Batched instances (many independent problems stepped together).  Every Schwarz
  * iteration solves the strips of all instances that have not yet converged in one
  * persistent launch, then updates every instance's interface vector (eq. fluxlr) in one
- * launch; each instance stops at its own `tol`.  Instances may differ in every field of
- * dd_nls_params except `precision` (DD_NLS_FP64, DD_NLS_FP32_INNER or DD_NLS_FP32_DW; the
- * latter needs nl_tol >= 1e-12).  Each uses Robin transmission and either the classical
+ * launch; each instance stops at its own `tol`.  Instances may differ in the domain, mesh,
+ * strips, dt, lap, kappa, Robin p, bc, algorithm, tol, tol_absolute, nl_tol, max_schwarz,
+ * guess, nl_adapt and psolve_modes.  precision (DD_NLS_FP64, DD_NLS_FP32_INNER or
+ * DD_NLS_FP32_DW; the latter needs nl_tol >= 1e-12), inner_tol, max_nl, max_inner, nl_relax
+ * and nl_picard must agree across instances.  V is static: trap_gx = trap_gy = 0; omega_rot,
+ * solver_layout, wait_limit_ms and the GMRES fields are not used (no per-step diagnostics,
+ * cooperative layout).  Each uses Robin transmission and either the classical
  * algorithm (eq. algo_d) or the preconditioned one (eq. algo_pd) with psolve =
  * DD_NLS_PSOLVE_MODAL (the exact P^-1 on cosine modes, one set of factors per instance, built
  * at create; nl_adapt and psolve_modes apply as in dd_nls_step).  An autotuner picks the

@@ -23,6 +23,7 @@
 #include "common.cuh"
 #include "kernels.h"
 #include "host_pinned.h"
+#include "params_check.h"
 
 using namespace ddnls;
 using cplx = std::complex<double>;
@@ -194,6 +195,7 @@ struct ProfScope {
 };
 
 // ------------------------------------------------------------------------ IO
+static bool known_ptr_kind(int k) { return k == DD_NLS_PTR_HOST || k == DD_NLS_PTR_DEVICE; }
 static int upload_nodal(dd_nls* h, const double* src, int ptr_kind, double2* strips) {
     const size_t bytes = (size_t)(h->G.nx + 1) * h->G.nyn * sizeof(double2);
     CK(cudaMemcpyAsync(h->stage, src, bytes, ptr_kind == DD_NLS_PTR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->s));
@@ -849,29 +851,13 @@ extern "C" int dd_nls_create(const dd_nls_params* p, const double* V, const doub
     }
     if (!p || !u0 || !out) return fail(nullptr, DD_NLS_EINVAL, "dd_nls_create: NULL params, u0 or out");
     *out = nullptr;
-    if (p->nx < 1 || p->ny < 1 || p->n_strips < 1 || p->nx % p->n_strips != 0)
-        return fail(nullptr, DD_NLS_EINVAL, "dd_nls_create: need nx, ny >= 1 and nx a multiple of n_strips");
-    if (!(p->xr > p->xl) || !(p->yu > p->yb) || !(p->dt > 0) || !(p->lap > 0))
-        return fail(nullptr, DD_NLS_EINVAL, "dd_nls_create: need xr > xl, yu > yb, dt > 0, lap > 0");
-    if (p->tc != DD_NLS_TC_ROBIN && p->tc != DD_NLS_TC_PADE)
-        return fail(nullptr, DD_NLS_EINVAL, "dd_nls_create: unknown transmission condition");
-    if (p->tc == DD_NLS_TC_ROBIN && !(p->p > 0.0)) return fail(nullptr, DD_NLS_EINVAL, "dd_nls_create: Robin p must be > 0");
-    if (p->tc == DD_NLS_TC_PADE && (p->pade_m < 1 || p->pade_m > kMaxPade))
-        return fail(nullptr, DD_NLS_EINVAL, "dd_nls_create: Pade order m must be in 1..96");
+    if (const char* why = params_problem(*p)) return fail(nullptr, DD_NLS_EINVAL, std::string("dd_nls_create: ") + why);
     if (p->tc == DD_NLS_TC_PADE && p->algorithm == DD_NLS_PRECONDITIONED && p->psolve == DD_NLS_PSOLVE_GMRES)
         return fail(nullptr, DD_NLS_EINVAL, "dd_nls_create: S_pade with the preconditioned algorithm uses the modal P solve");
-    if (p->precision != DD_NLS_FP64 && p->precision != DD_NLS_FP32_INNER && p->precision != DD_NLS_FP32_DW)
-        return fail(nullptr, DD_NLS_EINVAL, "dd_nls_create: unknown precision");
     if (ptr_kind != DD_NLS_PTR_HOST && ptr_kind != DD_NLS_PTR_DEVICE)
         return fail(nullptr, DD_NLS_EINVAL, "dd_nls_create: unknown ptr_kind");
-    if (!(p->trap_gx >= 0.0) || !(p->trap_gy >= 0.0) || !std::isfinite(p->omega_rot) || p->psolve_modes < 0 ||
-        !(p->wait_limit_ms >= 0.0) || p->solver_layout < 0 || p->solver_layout > 2)
-        return fail(nullptr, DD_NLS_EINVAL, "dd_nls_create: need trap_gx, trap_gy >= 0, finite omega_rot, "
-                                            "psolve_modes >= 0, wait_limit_ms >= 0, solver_layout 0, 1 or 2");
     const long long c = p->nx / p->n_strips;
     const long long nyn = (long long)p->ny + 1;
-    if (nyn > (1 << 20) || c + 1 > (1 << 20) || (c + 1) * nyn > (1LL << 30))
-        return fail(nullptr, DD_NLS_EINVAL, "dd_nls_create: strip too large");
 
     dd_nls* h = new dd_nls();
     h->P = *p;
@@ -1035,6 +1021,7 @@ extern "C" int dd_nls_create(const dd_nls_params* p, const double* V, const doub
 
 extern "C" int dd_nls_step(dd_nls* h, int nsteps, double* u_out, int ptr_kind, dd_nls_stats* st) {
     if (!h) return fail(nullptr, DD_NLS_EINVAL, "dd_nls_step: NULL handle");
+    if (!known_ptr_kind(ptr_kind)) return fail(h, DD_NLS_EINVAL, "dd_nls_step: unknown ptr_kind");
     if (nsteps < 0) return fail(h, DD_NLS_EINVAL, "dd_nls_step: nsteps < 0");
     if (st) { std::memset(st, 0, sizeof(*st)); st->setup_ms = h->setup_ms; }
     for (int n = 0; n < nsteps; ++n) {
@@ -1064,6 +1051,7 @@ extern "C" int dd_nls_step(dd_nls* h, int nsteps, double* u_out, int ptr_kind, d
 
 extern "C" int dd_nls_step_guess(dd_nls* h, const double* g0, double* u_out, int ptr_kind, dd_nls_stats* st) {
     if (!h) return fail(nullptr, DD_NLS_EINVAL, "dd_nls_step_guess: NULL handle");
+    if (!known_ptr_kind(ptr_kind)) return fail(h, DD_NLS_EINVAL, "dd_nls_step_guess: unknown ptr_kind");
     if (!g0) return fail(h, DD_NLS_EINVAL, "dd_nls_step_guess: NULL guess");
     if (st) { std::memset(st, 0, sizeof(*st)); st->setup_ms = h->setup_ms; }
     int rc = load_guess(h, g0, ptr_kind);
@@ -1085,6 +1073,7 @@ extern "C" int dd_nls_step_guess(dd_nls* h, const double* g0, double* u_out, int
 extern "C" int dd_nls_solve_interface(dd_nls* h, const double* g0, double* g_out, double* v_out, int ptr_kind,
                                       dd_nls_stats* st) {
     if (!h) return fail(nullptr, DD_NLS_EINVAL, "dd_nls_solve_interface: NULL handle");
+    if (!known_ptr_kind(ptr_kind)) return fail(h, DD_NLS_EINVAL, "dd_nls_solve_interface: unknown ptr_kind");
     if (st) { std::memset(st, 0, sizeof(*st)); st->setup_ms = h->setup_ms; }
     int rc = load_guess(h, g0, ptr_kind);
     if (rc) return rc;
@@ -1098,6 +1087,7 @@ extern "C" int dd_nls_solve_interface(dd_nls* h, const double* g0, double* g_out
 
 extern "C" int dd_nls_get_state(dd_nls* h, double* u, double* g, int* step, int ptr_kind) {
     if (!h) return fail(nullptr, DD_NLS_EINVAL, "dd_nls_get_state: NULL handle");
+    if (!known_ptr_kind(ptr_kind)) return fail(h, DD_NLS_EINVAL, "dd_nls_get_state: unknown ptr_kind");
     if (u) { int rc = download_nodal(h, h->u, u, ptr_kind); if (rc) return rc; }
     if (g) { int rc = download_g(h, h->gconv, g, ptr_kind); if (rc) return rc; }
     if (step) *step = h->step;
@@ -1107,6 +1097,7 @@ extern "C" int dd_nls_get_state(dd_nls* h, double* u, double* g, int* step, int 
 
 extern "C" int dd_nls_set_state(dd_nls* h, const double* u, const double* g, int step, int ptr_kind) {
     if (!h) return fail(nullptr, DD_NLS_EINVAL, "dd_nls_set_state: NULL handle");
+    if (!known_ptr_kind(ptr_kind)) return fail(h, DD_NLS_EINVAL, "dd_nls_set_state: unknown ptr_kind");
     if (u) { int rc = upload_nodal(h, u, ptr_kind, h->u); if (rc) return rc; }
     if (g) { int rc = upload_g(h, g, ptr_kind, h->gconv); if (rc) return rc; h->have_prev = true; }
     h->step = step;
@@ -1116,6 +1107,7 @@ extern "C" int dd_nls_set_state(dd_nls* h, const double* u, const double* g, int
 
 extern "C" int dd_nls_get_blocks(dd_nls* h, int strip, double* x, int ptr_kind) {
     if (!h) return fail(nullptr, DD_NLS_EINVAL, "dd_nls_get_blocks: NULL handle");
+    if (!known_ptr_kind(ptr_kind)) return fail(h, DD_NLS_EINVAL, "dd_nls_get_blocks: unknown ptr_kind");
     if (!h->X64 || strip < 0 || strip >= h->G.N || !x) return fail(h, DD_NLS_EINVAL, "dd_nls_get_blocks: no L_h or bad strip");
     const long long bs = (long long)h->G.nyn * h->G.nyn;
     CK(cudaMemcpyAsync(x, h->X64 + (long long)h->btype_h[strip] * 4 * bs, 4 * bs * sizeof(double2),
@@ -1126,6 +1118,7 @@ extern "C" int dd_nls_get_blocks(dd_nls* h, int strip, double* x, int ptr_kind) 
 
 extern "C" int dd_nls_get_modal(dd_nls* h, int strip, double* x, int ptr_kind) {
     if (!h) return fail(nullptr, DD_NLS_EINVAL, "dd_nls_get_modal: NULL handle");
+    if (!known_ptr_kind(ptr_kind)) return fail(h, DD_NLS_EINVAL, "dd_nls_get_modal: unknown ptr_kind");
     if (!h->xm || strip < 0 || strip >= h->G.N || !x) return fail(h, DD_NLS_EINVAL, "dd_nls_get_modal: no modal P or bad strip");
     CK(cudaMemcpyAsync(x, h->xm + (long long)h->btype_h[strip] * 4 * h->G.nyn, 4 * h->G.nyn * sizeof(double2),
                        ptr_kind == DD_NLS_PTR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->s));

@@ -29,6 +29,7 @@
 #include "common.cuh"
 #include "kernels.h"
 #include "host_pinned.h"
+#include "params_check.h"
 
 using namespace ddnls;
 
@@ -404,8 +405,9 @@ extern "C" int dd_nls_batch_create(int n, const dd_nls_params* params, const dou
     const int prec = params[0].precision;
     for (int i = 0; i < n; ++i) {
         const dd_nls_params& p = params[i];
-        if (!u0[i] || p.nx < 1 || p.ny < 1 || p.n_strips < 1 || p.nx % p.n_strips)
-            return bfail(nullptr, DD_NLS_EINVAL, "dd_nls_batch_create: instance with bad sizes");
+        if (!u0[i]) return bfail(nullptr, DD_NLS_EINVAL, "dd_nls_batch_create: NULL u0 of an instance");
+        if (const char* why = params_problem(p))
+            return bfail(nullptr, DD_NLS_EINVAL, std::string("dd_nls_batch_create: instance ") + std::to_string(i) + ": " + why);
         if (p.tc != DD_NLS_TC_ROBIN || !(p.p > 0))
             return bfail(nullptr, DD_NLS_EINVAL, "dd_nls_batch_create: batches take Robin transmission with p > 0");
         if (p.algorithm != DD_NLS_CLASSICAL && (p.algorithm != DD_NLS_PRECONDITIONED || p.psolve != DD_NLS_PSOLVE_MODAL))
@@ -415,9 +417,16 @@ extern "C" int dd_nls_batch_create(int n, const dd_nls_params* params, const dou
             return bfail(nullptr, DD_NLS_EINVAL, "dd_nls_batch_create: one precision for the whole batch");
         if (prec == DD_NLS_FP32_DW && !(p.nl_tol >= kDWFinish))
             return bfail(nullptr, DD_NLS_EINVAL, "dd_nls_batch_create: the double-word residual needs nl_tol >= 1e-12");
-        if (!(p.xr > p.xl) || !(p.yu > p.yb) || !(p.dt > 0) || !(p.lap > 0))
-            return bfail(nullptr, DD_NLS_EINVAL, "dd_nls_batch_create: bad domain or time step");
+        if (p.trap_gx > 0.0 || p.trap_gy > 0.0)
+            return bfail(nullptr, DD_NLS_EINVAL, "dd_nls_batch_create: batches take a static V (trap_gx = trap_gy = 0)");
+        const dd_nls_params& q = params[0];       // one strip-solver launch serves every instance
+        if (p.inner_tol != q.inner_tol || p.max_nl != q.max_nl || p.max_inner != q.max_inner ||
+            p.nl_relax != q.nl_relax || p.nl_picard != q.nl_picard)
+            return bfail(nullptr, DD_NLS_EINVAL,
+                         "dd_nls_batch_create: inner_tol, max_nl, max_inner, nl_relax and nl_picard must agree across instances");
     }
+    if (ptr_kind != DD_NLS_PTR_HOST && ptr_kind != DD_NLS_PTR_DEVICE)
+        return bfail(nullptr, DD_NLS_EINVAL, "dd_nls_batch_create: unknown ptr_kind");
     b = new dd_nls_batch();
     auto bad = [&](int code) { std::string m = b->error; batch_release(b); delete b; set_handle_free_error(m.c_str()); return code; };
 #define BCKC(call)                                                                          \
@@ -683,7 +692,8 @@ extern "C" int dd_nls_batch_step(dd_nls_batch* b, int nsteps, dd_nls_stats* stat
 }
 
 extern "C" int dd_nls_batch_get_u(dd_nls_batch* b, int i, double* u, int ptr_kind) {
-    if (!b || i < 0 || i >= b->n || !u) return bfail(b, DD_NLS_EINVAL, "dd_nls_batch_get_u: bad arguments");
+    if (!b || i < 0 || i >= b->n || !u || (ptr_kind != DD_NLS_PTR_HOST && ptr_kind != DD_NLS_PTR_DEVICE))
+        return bfail(b, DD_NLS_EINVAL, "dd_nls_batch_get_u: bad arguments");
     const size_t nodes = (size_t)(b->P[i].nx + 1) * (b->P[i].ny + 1);
     if (ptr_kind == DD_NLS_PTR_DEVICE) {
         BCK(launch_gather_u(b->G[i], b->u + b->foff[i], (double2*)u, b->s));
@@ -696,7 +706,8 @@ extern "C" int dd_nls_batch_get_u(dd_nls_batch* b, int i, double* u, int ptr_kin
 }
 
 extern "C" int dd_nls_batch_set_u(dd_nls_batch* b, int i, const double* u, int ptr_kind) {
-    if (!b || i < 0 || i >= b->n || !u) return bfail(b, DD_NLS_EINVAL, "dd_nls_batch_set_u: bad arguments");
+    if (!b || i < 0 || i >= b->n || !u || (ptr_kind != DD_NLS_PTR_HOST && ptr_kind != DD_NLS_PTR_DEVICE))
+        return bfail(b, DD_NLS_EINVAL, "dd_nls_batch_set_u: bad arguments");
     const size_t nodes = (size_t)(b->P[i].nx + 1) * (b->P[i].ny + 1);
     if (ptr_kind == DD_NLS_PTR_DEVICE) {
         BCK(launch_scatter_u(b->G[i], (const double2*)u, b->u + b->foff[i], b->s));

@@ -436,6 +436,7 @@ extern "C" int dd_cnn_set_base(dd_cnn* c, int base) {
 
 extern "C" int dd_cnn_set_params(dd_cnn* c, const float* w, int ptr_kind) {
     if (!c || !w) return cfail(c, DD_NLS_EINVAL, "dd_cnn_set_params: NULL argument");
+    if (ptr_kind != DD_NLS_PTR_HOST && ptr_kind != DD_NLS_PTR_DEVICE) return cfail(c, DD_NLS_EINVAL, "dd_cnn_set_params: unknown ptr_kind");
     CCK(cudaMemcpyAsync(c->w, w, sizeof(float) * c->nparam,
                         ptr_kind == DD_NLS_PTR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->s));
     CCK(cudaMemsetAsync(c->m, 0, sizeof(float) * c->nparam, c->s));
@@ -450,6 +451,7 @@ extern "C" int dd_cnn_set_params(dd_cnn* c, const float* w, int ptr_kind) {
 
 extern "C" int dd_cnn_get_params(dd_cnn* c, float* w, int ptr_kind) {
     if (!c || !w) return cfail(c, DD_NLS_EINVAL, "dd_cnn_get_params: NULL argument");
+    if (ptr_kind != DD_NLS_PTR_HOST && ptr_kind != DD_NLS_PTR_DEVICE) return cfail(c, DD_NLS_EINVAL, "dd_cnn_get_params: unknown ptr_kind");
     CCK(cudaMemcpyAsync(w, c->w, sizeof(float) * c->nparam,
                         ptr_kind == DD_NLS_PTR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->s));
     CCK(cudaStreamSynchronize(c->s));
@@ -473,6 +475,7 @@ extern "C" int dd_cnn_guess(dd_cnn* c, const double* g1, const double* g2, const
 extern "C" int dd_cnn_loss_grad(dd_cnn* c, const double* g1, const double* g2, const double* g3, const double* gt,
                                 float* grad, double* loss, int ptr_kind) {
     if (!c || !g1 || !g2 || !g3 || !gt) return cfail(c, DD_NLS_EINVAL, "dd_cnn_loss_grad: NULL argument");
+    if (ptr_kind != DD_NLS_PTR_HOST && ptr_kind != DD_NLS_PTR_DEVICE) return cfail(c, DD_NLS_EINVAL, "dd_cnn_loss_grad: unknown ptr_kind");
     int rc = cnn_features(c, g1, g2, g3, gt);
     if (!rc) rc = cnn_forward(c);
     if (!rc) rc = cnn_backward(c, loss);

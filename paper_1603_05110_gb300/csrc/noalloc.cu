@@ -33,6 +33,7 @@
 #include "../../include/dd_nls.h"
 #include "common.cuh"
 #include "kernels.h"
+#include "params_check.h"
 
 namespace ddnls {
 
@@ -81,11 +82,8 @@ extern "C" int dd_nls_step_noalloc(const dd_nls_params* p, const double* V, doub
                                    double* g_out, void* stream, dd_nls_stats* st) {
     set_handle_free_error("");
     if (!p || !u) return noalloc_fail(DD_NLS_EINVAL, "NULL params or u");
-    if (p->nx < 1 || p->ny < 1 || p->n_strips < 1 || p->nx % p->n_strips != 0)
-        return noalloc_fail(DD_NLS_EINVAL, "need nx, ny >= 1 and nx a multiple of n_strips");
+    if (const char* why = params_problem(*p)) return noalloc_fail(DD_NLS_EINVAL, why);
     if (p->n_strips > kMaxStrips) return noalloc_fail(DD_NLS_EINVAL, "more than 64 strips");
-    if (!(p->xr > p->xl) || !(p->yu > p->yb) || !(p->dt > 0) || !(p->lap > 0) || !(p->p > 0))
-        return noalloc_fail(DD_NLS_EINVAL, "need xr > xl, yu > yb, dt > 0, lap > 0, p > 0");
     if (p->tc != DD_NLS_TC_ROBIN || p->algorithm != DD_NLS_CLASSICAL)
         return noalloc_fail(DD_NLS_EINVAL, "only the classical algorithm with Robin transmission");
     if (p->precision != DD_NLS_FP64 && p->precision != DD_NLS_FP32_INNER)

@@ -74,11 +74,56 @@ def test_create_rejects_bad_sizes_without_touching_the_gpu(lib):
     assert e.value.code == 1
 
 
-@pytest.mark.parametrize("case", ["pade", "gmres", "dw_tight_tol", "mixed_precision"])
+BAD_PARAMS = {
+    "nan_dt": dict(dt=float("nan")),
+    "inf_kappa": dict(kappa=float("inf")),
+    "nan_tol": dict(tol=float("nan")),
+    "negative_tol": dict(nl_tol=-1e-12),
+    "unknown_bc": dict(bc=7),
+    "unknown_algorithm": dict(algorithm=5),
+    "unknown_guess": dict(guess=3),
+    "unknown_psolve": dict(psolve=4),
+    "unknown_precision": dict(precision=9),
+    "negative_nl_adapt": dict(nl_adapt=-0.1),
+    "pade_order": dict(tc=1, pade_m=0),
+    "robin_p": dict(p=0.0),
+    "layout": dict(solver_layout=3),
+}
+
+
+@pytest.mark.parametrize("case", sorted(BAD_PARAMS))
+def test_create_rejects_bad_parameters_without_touching_the_gpu(lib, case):
+    """Every enum field one of its values, every real field finite and in range: EINVAL from
+    dd_nls_create, from dd_nls_batch_create (naming the instance) and from the no-allocation
+    step, all before any device work."""
+    import numpy as np
+    from paper_1603_05110_gb300 import binding
+    kw = dict(nx=16, ny=8, n_strips=2, **BAD_PARAMS[case])
+    u0 = np.zeros((9, 17), np.complex128)
+    with pytest.raises(binding.DDNLSError) as e:
+        binding.Solver(binding.default_params(**kw), u0)
+    assert e.value.code == 1, str(e.value)
+    with pytest.raises(binding.DDNLSError) as e:
+        binding.Batch([dict(nx=16, ny=8, n_strips=2), kw], [u0, u0])
+    assert e.value.code == 1 and "instance 1" in str(e.value), str(e.value)
+
+
+def test_create_rejects_a_strip_beyond_32_bit_indexing(lib):
+    import numpy as np
+    from paper_1603_05110_gb300 import binding
+    ny = 1 << 20                                                # ny + 1 nodes per column > 2^20
+    with pytest.raises(binding.DDNLSError) as e:
+        binding.Solver(binding.default_params(nx=1, ny=ny, n_strips=1), np.zeros((ny + 1, 2), np.complex128))
+    assert e.value.code == 1 and "too large" in str(e.value)
+
+
+@pytest.mark.parametrize("case", ["pade", "gmres", "dw_tight_tol", "mixed_precision", "trap", "mixed_inner_tol",
+                                  "mixed_relax"])
 def test_batch_create_rejects_unsupported_forms_without_touching_the_gpu(lib, case):
     """Batched instances take Robin transmission, the classical or the modal-preconditioned
-    algorithm, one precision for the whole batch, and nl_tol >= 1e-12 with the double-word
-    residual; anything else is EINVAL before any device work."""
+    algorithm, one precision and one set of strip-solver settings for the whole batch, a static
+    V, and nl_tol >= 1e-12 with the double-word residual; anything else is EINVAL before any
+    device work."""
     import numpy as np
     from paper_1603_05110_gb300 import binding
     base = dict(nx=16, ny=8, n_strips=2, tol=1e-8, nl_tol=1e-11)
@@ -90,8 +135,14 @@ def test_batch_create_rejects_unsupported_forms_without_touching_the_gpu(lib, ca
     elif case == "dw_tight_tol":
         for q in prms:
             q.update(precision=binding.FP32_DW, nl_tol=1e-13)
-    else:
+    elif case == "mixed_precision":
         prms[1].update(precision=binding.FP32_INNER)
+    elif case == "trap":
+        prms[1].update(trap_gx=1.0, trap_gy=1.2)
+    elif case == "mixed_inner_tol":
+        prms[1].update(inner_tol=1e-3)
+    else:
+        prms[1].update(nl_relax=0.5)
     u0 = [np.zeros((9, 17), np.complex128) for _ in prms]
     with pytest.raises(binding.DDNLSError) as e:
         binding.Batch(prms, u0)

@@ -12,7 +12,10 @@
   beta and the call returns DD_NLS_EBREAKDOWN.
 * A device allocation that fails inside create (test hook DD_NLS_TEST_FAIL_ALLOC): create returns
   DD_NLS_ENOMEM and releases what it had allocated.
+* An unknown ptr_kind: DD_NLS_EINVAL before any copy, and the handle steps on.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -96,3 +99,16 @@ def test_a_failed_device_allocation_in_create_returns_enomem_and_releases(monkey
     assert torch.cuda.mem_get_info()[0] >= free0 - (2 << 20)
     with binding.Solver(gpu_params(w), w.u0(), w.V()) as s:
         assert s.step(1)["steps"] == 1
+
+
+def test_an_unknown_ptr_kind_is_einval_and_the_handle_stays_usable():
+    """Every entry point that takes caller memory checks ptr_kind before it copies."""
+    w = SMALL
+    out = np.zeros((w.ny + 1, w.nx + 1), np.complex128)
+    with binding.Solver(gpu_params(w), w.u0(), w.V()) as s:
+        ptr = ctypes.c_void_p(out.ctypes.data)
+        assert s.lib.dd_nls_step(s.h, 1, ptr, 7, None) == 1
+        assert "ptr_kind" in s.lib.dd_nls_last_error(s.h).decode()
+        assert s.lib.dd_nls_get_state(s.h, ptr, None, None, -1) == 1
+        assert s.step(1, out)["steps"] == 1
+        assert np.isfinite(out).all()
