@@ -289,8 +289,9 @@ void dd_nls_batch_destroy(dd_nls_batch* b);
  * nodes to a correction of a base guess:
  *     g0 = g1 + e (g1 - g2) + s1 * net(g1/s0, (g1-g2)/s1, (g2-g3)/s1),
  * s0 = rms(g1), s1 = rms(g1-g2) (g1 the most recent), e = 1 (linear extrapolation, the default)
- * or e = 0 (the paper's previous-step vector), chosen by dd_cnn_set_base (EINVAL otherwise).  Interface vectors are DEVICE pointers
- * in the ABI layout.  Parameters: one FP32 array of dd_cnn_num_params() values, per layer the
+ * or e = 0 (the paper's previous-step vector), chosen by dd_cnn_set_base (EINVAL otherwise).
+ * n_traces x nodes_per_trace is at most 2^28.  Interface vectors are DEVICE pointers in the
+ * ABI layout.  Parameters: one FP32 array of dd_cnn_num_params() values, per layer the
  * weights [Cout][Cin][3][3] then the biases [Cout]; the caller supplies the initial values.
  * dd_cnn_train_step: one Adam step (lr, betas 0.9/0.999) on the squared error of the
  * correction for the target vector gt; loss (nullable) receives the mean squared error.

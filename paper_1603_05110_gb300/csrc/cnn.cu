@@ -380,6 +380,8 @@ static int cnn_features(dd_cnn* c, const double* g1, const double* g2, const dou
 extern "C" int dd_cnn_create(int n_traces, int nodes_per_trace, void* stream, dd_cnn** out) {
     dd_cnn* c = nullptr;
     if (n_traces < 1 || nodes_per_trace < 1 || !out) return cfail(nullptr, DD_NLS_EINVAL, "dd_cnn_create: bad sizes");
+    if ((long long)n_traces * nodes_per_trace > (1LL << 28))      // the kernels index an image with 32-bit ints
+        return cfail(nullptr, DD_NLS_EINVAL, "dd_cnn_create: n_traces x nodes_per_trace above 2^28");
     *out = nullptr;
     c = new dd_cnn();
     c->H = n_traces;

@@ -147,3 +147,10 @@ def test_batch_create_rejects_unsupported_forms_without_touching_the_gpu(lib, ca
     with pytest.raises(binding.DDNLSError) as e:
         binding.Batch(prms, u0)
     assert e.value.code == 1, str(e.value)
+
+
+def test_cnn_create_rejects_an_image_beyond_32_bit_indexing(lib):
+    out = ctypes.c_void_p()
+    assert lib.dd_cnn_create(1 << 15, 1 << 14, None, ctypes.byref(out)) == 1
+    assert not out.value
+    assert b"2^28" in lib.dd_nls_last_error(None)
