@@ -223,7 +223,7 @@ int dd_nls_get_modal(dd_nls* h, int strip, double* x, int ptr_kind);
  * the current state, on the valid zone (xl/sqrt2, xr/sqrt2) x (yb/sqrt2, yu/sqrt2) of Sec. 5.2.1
  * (inside every rotated copy A(t) Omega of a square domain centred at the origin): out receives
  * (ny_out+1) rows of (nx_out+1) complex values, x fastest, the Q1 interpolant of the computed u~
- * at the rotated points.  Errors: EINVAL for nx_out, ny_out < 1 or a NULL out. */
+ * at the rotated points.  Errors: EINVAL for nx_out or ny_out outside 1 .. 2^30-1 or a NULL out. */
 int dd_nls_lab_frame(dd_nls* h, int nx_out, int ny_out, double* out, int ptr_kind);
 
 int dd_nls_set_profiling(dd_nls* h, int on);

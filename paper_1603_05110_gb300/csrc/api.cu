@@ -1128,8 +1128,8 @@ extern "C" int dd_nls_get_modal(dd_nls* h, int strip, double* x, int ptr_kind) {
 
 extern "C" int dd_nls_lab_frame(dd_nls* h, int nx_out, int ny_out, double* out, int ptr_kind) {
     if (!h) return fail(nullptr, DD_NLS_EINVAL, "dd_nls_lab_frame: NULL handle");
-    if (nx_out < 1 || ny_out < 1 || !out || (ptr_kind != DD_NLS_PTR_HOST && ptr_kind != DD_NLS_PTR_DEVICE))
-        return fail(h, DD_NLS_EINVAL, "dd_nls_lab_frame: need nx_out, ny_out >= 1, an output and a known ptr_kind");
+    if (nx_out < 1 || ny_out < 1 || nx_out >= (1 << 30) || ny_out >= (1 << 30) || !out || !known_ptr_kind(ptr_kind))
+        return fail(h, DD_NLS_EINVAL, "dd_nls_lab_frame: need 1 <= nx_out, ny_out < 2^30, an output and a known ptr_kind");
     const double t = h->step * h->P.dt, r = std::sqrt(2.0);
     const double c = std::cos(h->P.omega_rot * t), s = std::sin(h->P.omega_rot * t);
     const size_t n = (size_t)(nx_out + 1) * (ny_out + 1);
