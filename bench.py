@@ -140,8 +140,9 @@ def algorithm_of(w, args):
 def solver_params(w, args, precision, psolve=None, adapt=0.01):
     from paper_1603_05110_gb300 import binding
     pade = getattr(args, "tc", "robin") == "pade"
-    return dict(psolve=binding.PSOLVE_MODAL if psolve is None else psolve, nl_adapt=adapt,xl=w.xl, xr=w.xr, yb=w.yb, yu=w.yu, nx=w.nx, ny=w.ny, n_strips=w.n_strips, dt=w.dt,
-                lap=w.lap, kappa=w.kappa, p=robin_p(w, args), tol=args.tol, nl_tol=1e-11, inner_tol=1e-4,
+    return dict(psolve=binding.PSOLVE_MODAL if psolve is None else psolve, nl_adapt=adapt,
+                xl=w.xl, xr=w.xr, yb=w.yb, yu=w.yu, nx=w.nx, ny=w.ny, n_strips=w.n_strips, dt=w.dt, lap=w.lap,
+                kappa=w.kappa, p=robin_p(w, args), tol=args.tol, nl_tol=1e-11, inner_tol=1e-4,
                 max_inner=4000, max_schwarz=400, gmres_tol=1e-6, gmres_restart=30, gmres_max=300,
                 algorithm=binding.PRECONDITIONED if algorithm_of(w, args) == "preconditioned" else binding.CLASSICAL,
                 tc=binding.TC_PADE if pade else binding.TC_ROBIN, pade_m=getattr(args, "pade_m", 4),

@@ -7,7 +7,6 @@
 * the partially constructed I - L_h (only the lowest cosine modes solved) reaches the same step;
 * the mass and the energy reported by the library match the oracle's formulas.
 """
-import math
 
 import numpy as np
 import pytest
