@@ -568,6 +568,7 @@ extern "C" int dd_nls_batch_create(int n, const dd_nls_params* params, const dou
 
 extern "C" int dd_nls_batch_step(dd_nls_batch* b, int nsteps, dd_nls_stats* stats) {
     if (!b) return bfail(nullptr, DD_NLS_EINVAL, "dd_nls_batch_step: NULL handle");
+    if (nsteps < 0) return bfail(b, DD_NLS_EINVAL, "dd_nls_batch_step: nsteps < 0");
     if (stats) {
         std::memset(stats, 0, sizeof(dd_nls_stats) * b->n);
     }
