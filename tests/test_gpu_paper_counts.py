@@ -14,11 +14,13 @@ import pytest
 torch = pytest.importorskip("torch")
 
 from paper_1603_05110_gb300 import binding  # noqa: E402
+from tests.helpers import printed_p_table  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-P = [5, 10, 15, 20, 25, 30, 35, 40, 45, 50]
-PRINTED = {2: [57, 35, 32, 36, 41, 46, 53, 59, 66, 73], 32: [57, 35, 33, 36, 41, 47, 53, 60, 66, 73]}
+TABLE = printed_p_table()          # tests/golden: the printed table
+P = TABLE["p"]
+PRINTED = TABLE["cls"]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -59,5 +61,5 @@ def test_preconditioned_counts_are_about_six_at_every_p(N):
         prm, u0 = setup(N, p, binding.PRECONDITIONED)
         with binding.Solver(prm, u0) as s:
             counts.append(s.solve_interface()["last_schwarz_iterations"])
-    print(f"N={N} preconditioned, p=5..50: {counts} (printed 6)")
-    assert all(abs(c - 6) <= 3 for c in counts), counts
+    print(f"N={N} preconditioned, p=5..50: {counts} (printed {TABLE['pd'][N]})")
+    assert all(abs(c - q) <= 3 for c, q in zip(counts, TABLE["pd"][N])), counts

@@ -18,6 +18,7 @@ import numpy as np
 import pytest
 
 from oracle import fem, nls
+from tests.helpers import printed_p_table
 
 
 def cosine_modes(ny):
@@ -177,7 +178,19 @@ def test_strip_pool_gives_the_serial_result():
 
 
 # -------------------------------------------------- the paper's iteration counts (opt-in)
-P9_CLASSICAL_N2 = {5: 57, 10: 35, 15: 32, 20: 36, 25: 41, 30: 46, 35: 53, 40: 59, 45: 66, 50: 73}
+TABLE = printed_p_table()          # tests/golden: the printed table
+P9_CLASSICAL_N2 = dict(zip(TABLE["p"], TABLE["cls"][2]))
+
+
+def test_printed_table_fixture_is_the_printed_table():
+    """The stored copy of Table Influence_p_NL_2_32: p = 5..50, the preconditioned count 6 at
+    every p and N, the classical counts U-shaped with their minimum at p = 15 for both N."""
+    assert TABLE["p"] == list(range(5, 51, 5))
+    for N in (2, 32):
+        assert TABLE["pd"][N] == [6] * 10
+        cls = TABLE["cls"][N]
+        assert int(np.argmin(cls)) == 2 and cls[0] == 57 and cls[-1] == 73
+        assert all(a > b for a, b in zip(cls[:2], cls[1:3])) and all(a < b for a, b in zip(cls[2:], cls[3:]))
 
 
 def p9_problem(p):
